@@ -1,0 +1,136 @@
+/*
+ * ar_loops.h -- the region bodies and their variants, C ABI.
+ *
+ * The paper adapts loop regions by choosing among code variants at run time;
+ * its GPU use case picks the number of threads per team for each region
+ * (Section 3.2.2, Listing 4: variants([64:1024:64]), default 256 threads).
+ * The variants here are hand-written CUDA kernels (sm_103a) for four loops:
+ * daxpy (the paper's vector-update example, Listings 1-5), a 7-point 3D
+ * Jacobi stencil (stand-in for Heat, Table 3), CSR SpMV (stand-in for AMGMk
+ * relax, Table 3) and all-pairs n-body.
+ *
+ * Conventions for every call below:
+ *  - Pointers are DEVICE pointers unless stated; the caller owns them.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = default stream).
+ *    Calls only enqueue work; they do not synchronise.
+ *  - Return AR_OK (0) or a negative ar_status from ar.h: AR_ERR_ARG for a bad
+ *    variant index, size or alignment (nothing is launched), AR_ERR_CUDA if
+ *    the launch failed.  Empty problems (n = 0, N = 0, rows = 0) launch
+ *    nothing and return AR_OK.
+ *  - Variant names are "<loop>_<family>_<shape>", see *_variant_name.
+ */
+#ifndef AR_LOOPS_H
+#define AR_LOOPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "ar.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Loop ids for ar_region_add_builtin. */
+enum { AR_LOOP_DAXPY = 0, AR_LOOP_JACOBI7 = 1, AR_LOOP_SPMV = 2, AR_LOOP_NBODY = 3 };
+
+/* Number of variants of a loop, its default variant (the fixed baseline the
+ * selection is compared with) and a variant's name. */
+int ar_loop_num_variants(int loop);
+int ar_loop_default_variant(int loop);
+int ar_loop_variant_name(int loop, int variant, char *buf, int len);
+
+/* Register all variants of a built-in loop on a region, in index order, with
+ * launchers that read `args` as the loop's ar_*_args block below.  Variant
+ * values are the variant indices. */
+int ar_region_add_builtin(ar_region *r, int loop, int *out_count);
+
+/* ---------------------------------------------------------------- daxpy ---
+ * y[i] <- a*x[i] + y[i] for i in [0, n), float64, one fused multiply-add per
+ * element.  15 variants: threads per block {64,128,256,512,1024} x elements
+ * per thread {1,2,4}; variant = 3*block_index + ept_index.  EPT 2 and 4 use
+ * 128-bit (double2) accesses and need x and y 16-byte aligned (AR_ERR_ARG
+ * otherwise).  Default: 256 threads x 1 element (variant 6), the paper's
+ * 256-thread default (Section 4.2).  x and y must not overlap. */
+typedef struct ar_daxpy_args {
+  int64_t n;
+  double a;
+  const double *x;
+  double *y;
+} ar_daxpy_args;
+int ar_daxpy(int variant, int64_t n, double a, const double *x, double *y, void *stream);
+
+/* -------------------------------------------------------------- Jacobi ---
+ * `sweeps` sweeps of u'(i,j,k) = (u(i-1)+u(i+1)+u(j-1)+u(j+1)+u(k-1)+u(k+1))/6
+ * over N^3 float64 unknowns stored at (k*N + j)*N + i, zero outside the cube.
+ * Reads u0 (unchanged), writes the result to `out`, uses `work` (N^3
+ * doubles) as the ping-pong partner; u0, out and work must be distinct.
+ * Variants: family {naive, smem (2.5D shared-memory z-march), tma
+ * (cp.async.bulk.tensor tiles with mbarrier completion), df (tma staging plus
+ * float-pair arithmetic on the FP32 pipe, ~2^-48 relative; points whose
+ * inputs lie outside [2^-74, 2^118) in magnitude are recomputed in float64)}
+ * x block shape {32x4, 32x8,
+ * 64x4, 128x2}; variant = 4*family + shape.  The tma family needs even N
+ * (16-byte row pitch), N >= BX+4 and 16-byte aligned buffers; otherwise the
+ * tma and df families run the smem kernel of the same shape.  Default: naive 32x8 (variant 1).
+ * `status` (device int, may be NULL) receives AR_ERR_TIMEOUT if a bounded
+ * wait inside a tma kernel gave up; the caller zeroes it. */
+typedef struct ar_jacobi7_args {
+  int N;
+  int sweeps;
+  const double *u0;
+  double *out;
+  double *work;
+  int *status;
+} ar_jacobi7_args;
+int ar_jacobi7(int variant, int N, int sweeps, const double *u0, double *out, double *work,
+               int *status, void *stream);
+
+/* ------------------------------------------------------------ MLP selector ---
+ * The learned selector of the adaptive region: the paper's model kinds are
+ * decision trees and random forests and it names neural networks as a
+ * classifier the design admits (Section 3.1 model_type).  Network:
+ *   x0 = (sign(f) log(1+|f|) - mu) / sd          (F raw features)
+ *   h1 = relu(W1 x0 + b1), h2 = relu(W2 h1 + b2), logits = W3 h2 + b3,
+ *   p = softmax(logits), loss = mean_s -log p_s[label_s]
+ * Parameters theta (float32, ar_mlp_num_params of them) in the order W1 (H x F,
+ * row major), b1 (H), W2 (H x H), b2 (H), W3 (V x H), b3 (V).  Limits:
+ * 1 <= F <= 8, H in {32, 64}, 1 <= V <= 32, minibatch <= 256.  All pointers
+ * are device pointers; features are row-major (rows x F). */
+int ar_mlp_num_params(int F, int H, int V);
+
+/* Inference for B rows: probs (B x V, may be NULL), argmax variant (ties to
+ * the lowest index) and confidence = max probability (either may be NULL). */
+int ar_mlp_forward(const float *theta, const float *mu, const float *sd, int F, int H, int V, int64_t B,
+                   const float *feats, float *probs, int *variant, float *conf, void *stream);
+
+/* Gradient of the mean cross-entropy over one minibatch of B <= 256 rows
+ * (fixed-order sums, deterministic) into grad (ar_mlp_num_params floats) and
+ * the loss into *loss (device float, may be NULL).  Labels outside [0, V) are
+ * clamped into it. */
+int ar_mlp_grad(const float *theta, const float *mu, const float *sd, int F, int H, int V, int B,
+                const float *feats, const int *labels, float *grad, float *loss, void *stream);
+
+/* One Adam step (Kingma & Ba; beta1 0.9, beta2 0.999, eps 1e-8) at step t >= 1
+ * on n parameters: m, v updated in place, theta -= lr m_hat / (sqrt(v_hat)+eps). */
+int ar_mlp_adam(float *theta, const float *grad, float *m, float *v, int64_t n, int t, float lr, void *stream);
+
+/* Whole training run in one single-block launch: for each epoch e and each
+ * minibatch of `batch` consecutive entries of perm[e*n .. e*n+n) (the last one
+ * may be partial): forward, cross-entropy backward and an Adam step.  theta is
+ * updated in place; adam_m and adam_v (n_params floats each) must be zeroed
+ * by the caller; *loss receives the last minibatch's loss. */
+int ar_mlp_train(float *theta, float *adam_m, float *adam_v, const float *mu, const float *sd, int F, int H,
+                 int V, int n, const float *feats, const int *labels, const int *perm, int epochs, int batch,
+                 float lr, float *loss, void *stream);
+
+/* ---------------------------------------------------------------- peaks ---
+ * Issue-rate microbenchmarks (blocking, for roofline denominators): run a
+ * dependent-chain FMA kernel on every SM and return fused multiply-adds per
+ * second for float64 and float32. */
+int ar_measure_fma_rates(double *fp64_fma_per_s, double *fp32_fma_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AR_LOOPS_H */

@@ -1,0 +1,384 @@
+"""ctypes binding of ``libadaptive_region.so`` (argument marshalling only).
+
+Function names match the C ABI (``include/ar.h``, ``include/ar_loops.h``).
+Pointer arguments accept ``torch.Tensor`` (``data_ptr()``), numpy arrays, plain
+integers or ``None``; stream arguments accept ``torch.cuda.Stream``, a raw
+``cudaStream_t`` integer or ``None`` (default stream).  Negative status codes
+raise :class:`ArError`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libadaptive_region.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -m paper_2303_08873_b300.build` "
+        "(there is no non-CUDA fallback)")
+lib = ctypes.CDLL(LIB_PATH)
+
+AR_OK, AR_ERR_ARG, AR_ERR_STATE, AR_ERR_CUDA, AR_ERR_NOMODEL, AR_ERR_IO, AR_ERR_TIMEOUT, AR_ERR_OOM = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+STATUS_NAMES = {0: "AR_OK", -1: "AR_ERR_ARG", -2: "AR_ERR_STATE", -3: "AR_ERR_CUDA", -4: "AR_ERR_NOMODEL",
+                -5: "AR_ERR_IO", -6: "AR_ERR_TIMEOUT", -7: "AR_ERR_OOM"}
+AR_MAX_FEATURES = 8
+AR_MAX_VARIANTS = 64
+AR_LOOP_DAXPY, AR_LOOP_JACOBI7, AR_LOOP_SPMV, AR_LOOP_NBODY = 0, 1, 2, 3
+MODEL_KINDS = {0: "dtree", 1: "mlp", 2: "exhaustive", 3: "fixed"}
+
+
+class ArError(RuntimeError):
+    def __init__(self, code: int, msg: str = ""):
+        self.code = code
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}" if msg else STATUS_NAMES.get(code, str(code)))
+
+
+# ------------------------------------------------------------------ types
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_i64 = ctypes.c_int64
+_d = ctypes.c_double
+_f = ctypes.c_float
+_sz = ctypes.c_size_t
+_cs = ctypes.c_char_p
+_pi = ctypes.POINTER(ctypes.c_int)
+_pi64 = ctypes.POINTER(ctypes.c_int64)
+_pd = ctypes.POINTER(ctypes.c_double)
+_pf = ctypes.POINTER(ctypes.c_float)
+
+LAUNCH_FN = ctypes.CFUNCTYPE(_i, _vp, _i, _d, _vp, _vp)
+FAKE_TIME_FN = ctypes.CFUNCTYPE(_d, _pf, _i, _i, _vp)
+
+
+class ArDaxpyArgs(ctypes.Structure):
+    _fields_ = [("n", _i64), ("a", _d), ("x", _vp), ("y", _vp)]
+
+
+class ArJacobi7Args(ctypes.Structure):
+    _fields_ = [("N", _i), ("sweeps", _i), ("u0", _vp), ("out", _vp), ("work", _vp), ("status", _vp)]
+
+
+_SIGS = {
+    # ar.h
+    "ar_region_create": (_i, [_cs, _i, _cs, _i, ctypes.POINTER(_vp)]),
+    "ar_region_destroy": (None, [_vp]),
+    "ar_variant_register": (_i, [_vp, _cs, _d, LAUNCH_FN, _vp, _pi]),
+    "ar_variant_register_range": (_i, [_vp, _d, _d, _d, LAUNCH_FN, _vp, _pi]),
+    "ar_region_info": (_i, [_vp, _pi, _pi, _pi, _pi, _pi]),
+    "ar_variant_info": (_i, [_vp, _i, _pd, _cs, _i, _pi]),
+    "ar_begin": (_i, [_vp, _vp]),
+    "ar_set_feature": (_i, [_vp, _f]),
+    "ar_get_policy": (_i, [_vp, _pi]),
+    "ar_end": (_i, [_vp, _vp]),
+    "ar_invoke": (_i, [_vp, _pf, _i, _vp, _vp, _pi, _pd]),
+    "ar_select": (_i, [_vp, _pf, _i, _pi, _pf]),
+    "ar_profile": (_i, [_vp, _pf, _i, _vp, _vp, _i, _pf, _pi]),
+    "ar_train": (_i, [_vp]),
+    "ar_flush_records": (_i, [_vp]),
+    "ar_add_record": (_i, [_vp, _pf, _i, _i, _f]),
+    "ar_record_counts": (_i, [_vp, _pi64, _pi64]),
+    "ar_get_records": (_i, [_vp, _i64, _i64, _pf, _pi, _pf]),
+    "ar_tree_export": (_i, [_vp, _i, _pi, _pd, _pi, _pi, _pi, _pi]),
+    "ar_mlp_export": (_i, [_vp, _pf, _pf, _pf, _pi, _pi, _pi]),
+    "ar_region_save": (_i, [_vp, _cs]),
+    "ar_region_load": (_i, [_vp, _cs]),
+    "ar_last_error": (_i, [_vp, _cs, _i]),
+    "ar_set_fake_timer": (_i, [_vp, FAKE_TIME_FN, _vp]),
+    "ar_set_l2_flush": (_i, [_vp, _vp, _sz]),
+    # ar_loops.h
+    "ar_loop_num_variants": (_i, [_i]),
+    "ar_loop_default_variant": (_i, [_i]),
+    "ar_loop_variant_name": (_i, [_i, _i, _cs, _i]),
+    "ar_region_add_builtin": (_i, [_vp, _i, _pi]),
+    "ar_daxpy": (_i, [_i, _i64, _d, _vp, _vp, _vp]),
+    "ar_jacobi7": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp, _vp]),
+    "ar_mlp_num_params": (_i, [_i, _i, _i]),
+    "ar_mlp_forward": (_i, [_vp, _vp, _vp, _i, _i, _i, _i64, _vp, _vp, _vp, _vp, _vp]),
+    "ar_mlp_grad": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp]),
+    "ar_mlp_adam": (_i, [_vp, _vp, _vp, _vp, _i64, _i, _f, _vp]),
+    "ar_mlp_train": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp, _i, _i, _f, _vp, _vp]),
+    "ar_measure_fma_rates": (_i, [_pd, _pd]),
+}
+
+for _name, (_res, _args) in _SIGS.items():
+    _fn = getattr(lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+# ------------------------------------------------------------------ helpers
+def ptr(x):
+    """Device/host address of a tensor, array or int (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def stream_handle(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def check(rc: int, region=None) -> int:
+    if rc is not None and rc < 0:
+        msg = ""
+        if region is not None:
+            buf = ctypes.create_string_buffer(512)
+            lib.ar_last_error(region, buf, 512)
+            msg = buf.value.decode(errors="replace")
+        raise ArError(rc, msg)
+    return rc
+
+
+def _floats(features):
+    f = np.ascontiguousarray(np.asarray(features, dtype=np.float32).ravel())
+    return f, f.ctypes.data_as(_pf), f.size
+
+
+# ------------------------------------------------------------------ loops
+def loop_num_variants(loop: int) -> int:
+    return check(lib.ar_loop_num_variants(loop))
+
+
+def loop_default_variant(loop: int) -> int:
+    return check(lib.ar_loop_default_variant(loop))
+
+
+def loop_variant_name(loop: int, variant: int) -> str:
+    buf = ctypes.create_string_buffer(64)
+    check(lib.ar_loop_variant_name(loop, variant, buf, 64))
+    return buf.value.decode()
+
+
+def ar_daxpy(variant, n, a, x, y, stream=None):
+    return check(lib.ar_daxpy(variant, n, a, ptr(x), ptr(y), stream_handle(stream)))
+
+
+def ar_jacobi7(variant, N, sweeps, u0, out, work, status=None, stream=None):
+    return check(lib.ar_jacobi7(variant, N, sweeps, ptr(u0), ptr(out), ptr(work), ptr(status),
+                                stream_handle(stream)))
+
+
+def ar_mlp_num_params(F, H, V):
+    return check(lib.ar_mlp_num_params(F, H, V))
+
+
+def ar_mlp_forward(theta, mu, sd, F, H, V, B, feats, probs=None, variant=None, conf=None, stream=None):
+    return check(lib.ar_mlp_forward(ptr(theta), ptr(mu), ptr(sd), F, H, V, B, ptr(feats), ptr(probs),
+                                    ptr(variant), ptr(conf), stream_handle(stream)))
+
+
+def ar_mlp_grad(theta, mu, sd, F, H, V, B, feats, labels, grad, loss=None, stream=None):
+    return check(lib.ar_mlp_grad(ptr(theta), ptr(mu), ptr(sd), F, H, V, B, ptr(feats), ptr(labels), ptr(grad),
+                                 ptr(loss), stream_handle(stream)))
+
+
+def ar_mlp_adam(theta, grad, m, v, n, t, lr, stream=None):
+    return check(lib.ar_mlp_adam(ptr(theta), ptr(grad), ptr(m), ptr(v), n, t, lr, stream_handle(stream)))
+
+
+def ar_mlp_train(theta, adam_m, adam_v, mu, sd, F, H, V, n, feats, labels, perm, epochs, batch, lr, loss=None,
+                 stream=None):
+    return check(lib.ar_mlp_train(ptr(theta), ptr(adam_m), ptr(adam_v), ptr(mu), ptr(sd), F, H, V, n, ptr(feats),
+                                  ptr(labels), ptr(perm), epochs, batch, lr, ptr(loss), stream_handle(stream)))
+
+
+def ar_measure_fma_rates():
+    a, b = ctypes.c_double(), ctypes.c_double()
+    check(lib.ar_measure_fma_rates(ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+# ------------------------------------------------------------------ regions
+class Region:
+    """Owning wrapper of an ``ar_region*`` (one call per C function)."""
+
+    def __init__(self, id: str, num_features: int, model_spec: str = "", min_train_data: int = 0):
+        h = _vp()
+        check(lib.ar_region_create(id.encode(), num_features, model_spec.encode(), min_train_data, ctypes.byref(h)))
+        self.h = h
+        self.nf = num_features
+        self._keep = []  # ctypes callbacks and argument blocks that must stay alive
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.ar_region_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def _ck(self, rc):
+        return check(rc, self.h)
+
+    # registration
+    def add_builtin(self, loop: int) -> int:
+        n = ctypes.c_int()
+        self._ck(lib.ar_region_add_builtin(self.h, loop, ctypes.byref(n)))
+        return n.value
+
+    def register(self, name: str, value: float, launcher) -> int:
+        cb = launcher if isinstance(launcher, LAUNCH_FN) else LAUNCH_FN(launcher)
+        self._keep.append(cb)
+        idx = ctypes.c_int()
+        self._ck(lib.ar_variant_register(self.h, name.encode(), value, cb, None, ctypes.byref(idx)))
+        return idx.value
+
+    def register_range(self, begin: float, end: float, step: float, launcher) -> int:
+        cb = launcher if isinstance(launcher, LAUNCH_FN) else LAUNCH_FN(launcher)
+        self._keep.append(cb)
+        n = ctypes.c_int()
+        self._ck(lib.ar_variant_register_range(self.h, begin, end, step, cb, None, ctypes.byref(n)))
+        return n.value
+
+    def info(self) -> dict:
+        v, f, m, t, k = (ctypes.c_int() for _ in range(5))
+        self._ck(lib.ar_region_info(self.h, *(ctypes.byref(x) for x in (v, f, m, t, k))))
+        return {"num_variants": v.value, "num_features": f.value, "min_train_data": m.value,
+                "trained": bool(t.value), "model": MODEL_KINDS.get(k.value, k.value)}
+
+    def variant(self, idx: int) -> dict:
+        val, usable = ctypes.c_double(), ctypes.c_int()
+        name = ctypes.create_string_buffer(128)
+        self._ck(lib.ar_variant_info(self.h, idx, ctypes.byref(val), name, 128, ctypes.byref(usable)))
+        return {"value": val.value, "name": name.value.decode(), "usable": bool(usable.value)}
+
+    # Apollo-shaped calls
+    def begin(self, stream=None):
+        return self._ck(lib.ar_begin(self.h, stream_handle(stream)))
+
+    def set_feature(self, value: float):
+        return self._ck(lib.ar_set_feature(self.h, value))
+
+    def get_policy(self) -> int:
+        v = ctypes.c_int()
+        self._ck(lib.ar_get_policy(self.h, ctypes.byref(v)))
+        return v.value
+
+    def end(self, stream=None):
+        return self._ck(lib.ar_end(self.h, stream_handle(stream)))
+
+    # convenience calls
+    def invoke(self, features, args=None, stream=None):
+        f, fp, n = _floats(features)
+        v, val = ctypes.c_int(), ctypes.c_double()
+        a = ctypes.cast(ctypes.pointer(args), _vp) if args is not None else None
+        self._ck(lib.ar_invoke(self.h, fp, n, a, stream_handle(stream), ctypes.byref(v), ctypes.byref(val)))
+        return v.value, val.value
+
+    def select(self, features):
+        f, fp, n = _floats(features)
+        v, c = ctypes.c_int(), ctypes.c_float()
+        self._ck(lib.ar_select(self.h, fp, n, ctypes.byref(v), ctypes.byref(c)))
+        return v.value, c.value
+
+    def profile(self, features, args=None, stream=None, reps: int = 0):
+        f, fp, n = _floats(features)
+        V = self.info()["num_variants"]
+        ms = (ctypes.c_float * V)()
+        best = ctypes.c_int()
+        a = ctypes.cast(ctypes.pointer(args), _vp) if args is not None else None
+        self._ck(lib.ar_profile(self.h, fp, n, a, stream_handle(stream), reps, ms, ctypes.byref(best)))
+        return list(ms), best.value
+
+    def train(self):
+        return self._ck(lib.ar_train(self.h))
+
+    def flush_records(self):
+        return self._ck(lib.ar_flush_records(self.h))
+
+    def add_record(self, features, variant: int, ms: float):
+        f, fp, n = _floats(features)
+        return self._ck(lib.ar_add_record(self.h, fp, n, variant, ms))
+
+    def counts(self):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        self._ck(lib.ar_record_counts(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def records(self):
+        """Resolved records as a list of (features tuple, variant, ms)."""
+        n, _ = self.counts()
+        if n == 0:
+            return []
+        F = np.zeros((n, AR_MAX_FEATURES), dtype=np.float32)
+        V = np.zeros(n, dtype=np.int32)
+        M = np.zeros(n, dtype=np.float32)
+        self._ck(lib.ar_get_records(self.h, 0, n, F.ctypes.data_as(_pf), V.ctypes.data_as(_pi),
+                                    M.ctypes.data_as(_pf)))
+        return [(tuple(float(x) for x in F[i, :self.nf]), int(V[i]), float(M[i])) for i in range(n)]
+
+    def tree(self):
+        """Decision tree as a list of (feature, threshold, left, right, label)."""
+        cnt = ctypes.c_int()
+        self._ck(lib.ar_tree_export(self.h, 0, None, None, None, None, None, ctypes.byref(cnt)))
+        n = cnt.value
+        fe = (ctypes.c_int * n)()
+        th = (ctypes.c_double * n)()
+        le = (ctypes.c_int * n)()
+        ri = (ctypes.c_int * n)()
+        la = (ctypes.c_int * n)()
+        self._ck(lib.ar_tree_export(self.h, n, fe, th, le, ri, la, ctypes.byref(cnt)))
+        return [(fe[i], th[i] if fe[i] >= 0 else 0.0, le[i], ri[i], la[i]) for i in range(n)]
+
+    def mlp(self):
+        F, H, V = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._ck(lib.ar_mlp_export(self.h, None, None, None, ctypes.byref(F), ctypes.byref(H), ctypes.byref(V)))
+        P = ar_mlp_num_params(F.value, H.value, V.value)
+        th = np.zeros(P, dtype=np.float32)
+        mu = np.zeros(F.value, dtype=np.float32)
+        sd = np.zeros(F.value, dtype=np.float32)
+        self._ck(lib.ar_mlp_export(self.h, th.ctypes.data_as(_pf), mu.ctypes.data_as(_pf), sd.ctypes.data_as(_pf),
+                                   None, None, None))
+        return {"F": F.value, "H": H.value, "V": V.value, "theta": th, "mu": mu, "sd": sd}
+
+    def save(self, path: str):
+        return self._ck(lib.ar_region_save(self.h, str(path).encode()))
+
+    def load(self, path: str):
+        return self._ck(lib.ar_region_load(self.h, str(path).encode()))
+
+    def last_error(self) -> str:
+        buf = ctypes.create_string_buffer(512)
+        lib.ar_last_error(self.h, buf, 512)
+        return buf.value.decode(errors="replace")
+
+    def set_fake_timer(self, fn):
+        """fn(features tuple, variant) -> ms; None restores CUDA-event timing."""
+        if fn is None:
+            return self._ck(lib.ar_set_fake_timer(self.h, FAKE_TIME_FN(), None))
+        nf = self.nf
+
+        def _cb(fp, n, v, user):
+            return float(fn(tuple(fp[i] for i in range(n)), v))
+
+        cb = FAKE_TIME_FN(_cb)
+        self._keep.append(cb)
+        return self._ck(lib.ar_set_fake_timer(self.h, cb, None)) if nf >= 0 else None
+
+    def set_l2_flush(self, buf, nbytes: int):
+        return self._ck(lib.ar_set_l2_flush(self.h, ptr(buf), nbytes))
+
+
+__all__ = ["ArError", "Region", "ArDaxpyArgs", "ArJacobi7Args", "LAUNCH_FN", "FAKE_TIME_FN", "lib", "ptr",
+           "stream_handle", "check", "loop_num_variants", "loop_default_variant", "loop_variant_name", "ar_daxpy",
+           "ar_jacobi7", "ar_mlp_num_params", "ar_mlp_forward", "ar_mlp_grad", "ar_mlp_adam", "ar_mlp_train",
+           "ar_measure_fma_rates", "EXPORTED", "AR_LOOP_DAXPY", "AR_LOOP_JACOBI7", "AR_LOOP_SPMV",
+           "AR_LOOP_NBODY", "AR_OK", "AR_ERR_ARG", "AR_ERR_STATE", "AR_ERR_CUDA", "AR_ERR_NOMODEL", "AR_ERR_IO",
+           "AR_ERR_TIMEOUT", "AR_ERR_OOM", "AR_MAX_FEATURES", "AR_MAX_VARIANTS"]

@@ -1,0 +1,37 @@
+// Shared helpers of the CUDA sources (internal; not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ar.h"
+#include "ar_loops.h"
+
+namespace ar {
+
+constexpr int kNumSMs = 148;  // B300: 2 dies x 74 SMs
+
+inline int launch_status() {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? AR_OK : AR_ERR_CUDA;
+}
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Number of SMs of the current device (cached per process; one GPU).
+int device_sms();
+
+// Per-loop launch hooks used by the builtin launcher table.
+int daxpy_launch(void* args, int variant, double value, void* stream, void* user);
+int jacobi7_launch(void* args, int variant, double value, void* stream, void* user);
+
+int daxpy_num_variants();
+int daxpy_variant_name(int v, char* buf, int len);
+int jacobi7_num_variants();
+int jacobi7_variant_name(int v, char* buf, int len);
+
+}  // namespace ar

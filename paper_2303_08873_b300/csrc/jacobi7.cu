@@ -1,0 +1,402 @@
+// 7-point 3D Jacobi variants (the stencil region; stand-in for the paper's
+// Heat finite-difference benchmark, Table 3, adapted over block shapes as in
+// Section 3.2.2).
+//
+//   out(i,j,k) = (W + E + S + N + D + U) / 6, zero outside [0,N)^3,
+//   unknown (i,j,k) at (k*N + j)*N + i.
+//
+// Ideal traffic is 16 bytes per point per sweep (read once, write once).  On
+// B300 the float64 pipe issues ~0.56e12 DFMA/s against 6.5e12 B/s of HBM, so
+// the 6 float64 operations per point (5 adds, 1 multiply) bound the native
+// families at ~1.5 TB/s.  The df family moves the arithmetic to the FP32 pipe
+// in float-pair form (hi + lo, ~2^-48 relative) and keeps one float64 add per
+// point, so it can run at HBM speed.
+//
+// Families (variant = 4*family + shape; shapes 32x4, 32x8, 64x4, 128x2):
+//   0 naive  one thread per point, 7 global loads through L1/L2
+//   1 smem   2.5D: xy tile + halo in shared memory (double buffered, one
+//            barrier per plane), z neighbours in a 3-register queue
+//   2 tma    cp.async.bulk.tensor loads of (BX+4) x (BY+2) x 8-plane boxes
+//            into a 3-slot ring with mbarrier completion; TMA zero fill
+//            supplies the Dirichlet ghosts (also in z); two boxes in flight
+//   3 df     as tma, plus an in-place conversion of each landed box from
+//            float64 to float pairs; sums by TwoSum on the FP32 pipe
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+#include <mutex>
+
+#include "common.cuh"
+#include "tma.cuh"
+
+namespace ar {
+namespace {
+
+constexpr double kSixth = 1.0 / 6.0;
+constexpr int kDZ = 8;     // planes per TMA box
+constexpr int kRing = 3;   // boxes resident per block
+constexpr int kShapeX[4] = {32, 32, 64, 128};
+constexpr int kShapeY[4] = {4, 8, 4, 2};
+const char* const kFamily[4] = {"naive", "smem", "tma", "df"};
+
+__device__ __forceinline__ double at(const double* __restrict__ u, int N, int i, int j, int k) {
+  if ((unsigned)i >= (unsigned)N || (unsigned)j >= (unsigned)N || (unsigned)k >= (unsigned)N) return 0.0;
+  return u[((int64_t)k * N + j) * N + i];
+}
+
+// ------------------------------------------------------------------ naive
+template <int BX, int BY>
+__global__ void __launch_bounds__(BX* BY) jacobi_naive(int N, const double* __restrict__ in,
+                                                       double* __restrict__ out) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= N || j >= N) return;
+  const int64_t NN = (int64_t)N * N;
+  const int64_t c = k * NN + (int64_t)j * N + i;
+  double s = (i > 0 ? in[c - 1] : 0.0) + (i < N - 1 ? in[c + 1] : 0.0);
+  s += (j > 0 ? in[c - N] : 0.0);
+  s += (j < N - 1 ? in[c + N] : 0.0);
+  s += (k > 0 ? in[c - NN] : 0.0);
+  s += (k < N - 1 ? in[c + NN] : 0.0);
+  out[c] = s * kSixth;
+}
+
+// ------------------------------------------------------------------ 2.5D smem
+template <int BX, int BY>
+__global__ void __launch_bounds__(BX* BY) jacobi_smem(int N, int KC, const double* __restrict__ in,
+                                                      double* __restrict__ out) {
+  __shared__ double tile[2][BY + 2][BX + 2];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.x * BX + tx, j = blockIdx.y * BY + ty;
+  const int kb = blockIdx.z * KC;
+  const int ke = min(N, kb + KC);
+  const bool inside = i < N && j < N;
+  const int64_t NN = (int64_t)N * N;
+  const int64_t col = (int64_t)j * N + i;
+  double below = (inside && kb > 0) ? in[(kb - 1) * NN + col] : 0.0;
+  double cur = inside ? in[kb * NN + col] : 0.0;
+  for (int k = kb; k < ke; ++k) {
+    const int b = (k - kb) & 1;
+    const double above = (inside && k + 1 < N) ? in[(k + 1) * NN + col] : 0.0;
+    tile[b][ty + 1][tx + 1] = cur;
+    if (tx == 0) tile[b][ty + 1][0] = at(in, N, i - 1, j, k);
+    if (tx == BX - 1) tile[b][ty + 1][BX + 1] = at(in, N, i + 1, j, k);
+    if (ty == 0) tile[b][0][tx + 1] = at(in, N, i, j - 1, k);
+    if (ty == BY - 1) tile[b][BY + 1][tx + 1] = at(in, N, i, j + 1, k);
+    __syncthreads();
+    if (inside) {
+      double s = tile[b][ty + 1][tx] + tile[b][ty + 1][tx + 2];
+      s += tile[b][ty][tx + 1];
+      s += tile[b][ty + 2][tx + 1];
+      s += below;
+      s += above;
+      out[k * NN + col] = s * kSixth;
+    }
+    below = cur;
+    cur = above;
+  }
+}
+
+// ------------------------------------------------------------------ float pairs
+// 1/6 as an unevaluated float pair.
+constexpr float kSixthHi = 0.16666667163372039794921875f;           // RN(1/6)
+constexpr float kSixthLo = -4.967053740534411e-09f;  // RN(1/6 - kSixthHi)
+
+// Split x into (hi, lo) with hi = x rounded to 24 significant bits and
+// lo = the remainder, both floats: x = hi + lo to within 2^-48 |x|.  Works on
+// the bit pattern (truncate to 24 bits, round the 29-bit remainder up or
+// down) so no float64 operation is issued.  Values outside the float-pair
+// range (|x| < 2^-74, |x| >= 2^118, inf, NaN) give hi = NaN as a marker; ±0
+// gives (0, 0).
+__device__ __forceinline__ float2 df_split(double x) {
+  const long long b = __double_as_longlong(x);
+  if ((b << 1) == 0) return make_float2(0.f, 0.f);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e < 949 || e > 1140) return make_float2(__int_as_float(0x7fc00001), 0.f);
+  int r = (int)(b & 0x1FFFFFFFLL);
+  float hi = __double2float_rz(x);
+  if (r >= (1 << 28)) {
+    hi = __int_as_float(__float_as_int(hi) + 1);  // one ulp away from zero
+    r -= (1 << 29);
+  }
+  float lo = __int2float_rn(r) * __int_as_float((e - 1075 + 127) << 23);
+  return make_float2(hi, b < 0 ? -lo : lo);
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// (v0 + ... + v5) / 6 in float-pair arithmetic, returned in float64.
+__device__ __forceinline__ double df_avg6(float2 v0, float2 v1, float2 v2, float2 v3, float2 v4, float2 v5) {
+  float s, c, e;
+  two_sum(v0.x, v1.x, s, c);
+  two_sum(s, v2.x, s, e);
+  c += e;
+  two_sum(s, v3.x, s, e);
+  c += e;
+  two_sum(s, v4.x, s, e);
+  c += e;
+  two_sum(s, v5.x, s, e);
+  c += e;
+  c += ((v0.y + v1.y) + (v2.y + v3.y)) + (v4.y + v5.y);
+  const float p = s * kSixthHi;
+  float pe = fmaf(s, kSixthHi, -p);
+  pe = fmaf(s, kSixthLo, pe);
+  pe = fmaf(c, kSixthHi, pe);
+  return (double)p + (double)pe;
+}
+
+// ------------------------------------------------------------------ TMA ring
+template <int BX, int BY>
+struct TmaGeom {
+  static constexpr int PX = BX + 4;              // x: 2 ghost columns each side (16-byte aligned x)
+  static constexpr int PY = BY + 2;
+  static constexpr int PLANE = PX * PY;          // elements per plane
+  static constexpr int GROUP = PLANE * kDZ;      // elements per box
+  static constexpr uint32_t BYTES = GROUP * 8u;
+  static constexpr size_t SMEM = (size_t)kRing * BYTES + 128;
+};
+
+template <int BX, int BY, bool DF>
+__global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUtensorMap tmap, int N, int KC,
+                                                     const double* __restrict__ in, double* __restrict__ out,
+                                                     int* status) {
+  using G = TmaGeom<BX, BY>;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[kRing];
+  double* buf = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+
+  const int tid = threadIdx.x;
+  const int tx = tid % BX, ty = tid / BX;
+  const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
+  const int kb = blockIdx.z * KC;
+  const int kc = min(KC, N - kb);                 // output planes of this block
+  const int ngroups = (kc + 2 + kDZ - 1) / kDZ;   // boxes covering planes kb-1 .. kb+kc
+
+  if (tid == 0) {
+    for (int r = 0; r < kRing; ++r) mbar_init(smem_addr(&bars[r]), 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  auto issue = [&](int g) {
+    const int slot = g % kRing;
+    const uint32_t bar = smem_addr(&bars[slot]);
+    mbar_arrive_expect_tx(bar, G::BYTES);
+    tma_load_3d(smem_addr(buf + (size_t)slot * G::GROUP), &tmap, i0 - 2, j0 - 1, kb - 1 + g * kDZ, bar);
+  };
+  if (tid == 0)
+    for (int g = 0; g < min(ngroups, kRing - 1); ++g) issue(g);
+
+  const int i = i0 + tx, j = j0 + ty;
+  const bool inside = i < N && j < N;
+  const int64_t NN = (int64_t)N * N;
+  const int64_t col = (int64_t)j * N + i;
+  const int c = (ty + 1) * G::PX + tx + 2;
+  int next_p = 1;
+  int g = 0;
+  bool failed = false;
+  for (; g < ngroups; ++g) {
+    const int slot = g % kRing;
+    const bool ok = mbar_wait_bounded(smem_addr(&bars[slot]), (uint32_t)((g / kRing) & 1));
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    if constexpr (DF) {
+      double* box = buf + (size_t)slot * G::GROUP;
+      for (int e = tid; e < G::GROUP; e += BX * BY) {
+        const float2 f = df_split(box[e]);
+        reinterpret_cast<float2*>(box)[e] = f;
+      }
+      __syncthreads();
+    }
+    const int plast = min(kc, (g + 1) * kDZ - 2);
+    for (int p = next_p; p <= plast; ++p) {
+      const double* pm = buf + (size_t)(((p - 1) / kDZ) % kRing) * G::GROUP + ((p - 1) % kDZ) * G::PLANE;
+      const double* pc = buf + (size_t)((p / kDZ) % kRing) * G::GROUP + (p % kDZ) * G::PLANE;
+      const double* pp = buf + (size_t)(((p + 1) / kDZ) % kRing) * G::GROUP + ((p + 1) % kDZ) * G::PLANE;
+      if (inside) {
+        const int k = kb + p - 1;
+        double r;
+        if constexpr (DF) {
+          const float2* qm = reinterpret_cast<const float2*>(pm);
+          const float2* qc = reinterpret_cast<const float2*>(pc);
+          const float2* qp = reinterpret_cast<const float2*>(pp);
+          r = df_avg6(qc[c - 1], qc[c + 1], qc[c - G::PX], qc[c + G::PX], qm[c], qp[c]);
+          if (r != r) {  // a value outside the float-pair range: redo in float64
+            double s = at(in, N, i - 1, j, k) + at(in, N, i + 1, j, k);
+            s += at(in, N, i, j - 1, k);
+            s += at(in, N, i, j + 1, k);
+            s += at(in, N, i, j, k - 1);
+            s += at(in, N, i, j, k + 1);
+            r = s * kSixth;
+          }
+        } else {
+          double s = pc[c - 1] + pc[c + 1];
+          s += pc[c - G::PX];
+          s += pc[c + G::PX];
+          s += pm[c];
+          s += pp[c];
+          r = s * kSixth;
+        }
+        out[(int64_t)k * NN + col] = r;
+      }
+    }
+    if (plast + 1 > next_p) next_p = plast + 1;
+    // every reader of box g-1 is past this barrier: its slot takes box g+2
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0 && g + kRing - 1 < ngroups) issue(g + kRing - 1);
+  }
+  if (failed) {
+    if (tid == 0) {
+      if (status) atomicExch(status, (int)AR_ERR_TIMEOUT);
+      // drain the boxes still in flight (bounded) before the block exits
+      const int issued = min(ngroups, g + kRing - 1);
+      for (int h = g; h < issued; ++h) (void)mbar_wait_bounded(smem_addr(&bars[h % kRing]), (uint32_t)((h / kRing) & 1));
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ host side
+template <int BX, int BY>
+int launch_naive(int N, const double* in, double* out, cudaStream_t s) {
+  dim3 grid((unsigned)ceil_div(N, BX), (unsigned)ceil_div(N, BY), (unsigned)N);
+  jacobi_naive<BX, BY><<<grid, dim3(BX, BY), 0, s>>>(N, in, out);
+  return launch_status();
+}
+
+inline int chunk_planes(int N, int64_t colblocks, int resident_per_sm, int lo, int hi) {
+  const int64_t target = 2LL * device_sms() * resident_per_sm;
+  int64_t kc = ceil_div((int64_t)N * colblocks, target);
+  if (kc < lo) kc = lo;
+  if (kc > hi) kc = hi;
+  if (kc > N) kc = N;
+  return (int)kc;
+}
+
+template <int BX, int BY>
+int launch_smem(int N, const double* in, double* out, cudaStream_t s) {
+  const int64_t cb = ceil_div(N, BX) * ceil_div(N, BY);
+  const int KC = chunk_planes(N, cb, 2048 / (BX * BY), 4, 1 << 30);
+  dim3 grid((unsigned)ceil_div(N, BX), (unsigned)ceil_div(N, BY), (unsigned)ceil_div(N, KC));
+  jacobi_smem<BX, BY><<<grid, dim3(BX, BY), 0, s>>>(N, KC, in, out);
+  return launch_status();
+}
+
+template <int BX, int BY, bool DF>
+int launch_tma(int N, const double* in, double* out, int* status, cudaStream_t s) {
+  using G = TmaGeom<BX, BY>;
+  if ((N & 1) || N < G::PX || N < G::PY || N < kDZ || !aligned16(in)) return launch_smem<BX, BY>(N, in, out, s);
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(jacobi_tma<BX, BY, DF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)G::SMEM);
+  });
+  if (attr_err != cudaSuccess) return AR_ERR_CUDA;
+  CUtensorMap map;
+  if (!encode_tensor_map_3d_f64(&map, in, (uint64_t)N, (uint64_t)N, (uint64_t)N, G::PX, G::PY, kDZ))
+    return AR_ERR_CUDA;
+  const int64_t cb = ceil_div(N, BX) * ceil_div(N, BY);
+  int resident = (int)((227 * 1024) / G::SMEM);
+  if (resident > 2048 / (BX * BY)) resident = 2048 / (BX * BY);
+  if (resident < 1) resident = 1;
+  // KC + 2 a multiple of the box depth wastes no loaded plane
+  int KC = chunk_planes(N, cb, resident, kDZ - 2, 8 * kDZ - 2);
+  KC = (int)(ceil_div(KC + 2, kDZ) * kDZ - 2);
+  dim3 grid((unsigned)ceil_div(N, BX), (unsigned)ceil_div(N, BY), (unsigned)ceil_div(N, KC));
+  jacobi_tma<BX, BY, DF><<<grid, BX * BY, G::SMEM, s>>>(map, N, KC, in, out, status);
+  return launch_status();
+}
+
+template <int BX, int BY>
+int launch_family(int fam, int N, const double* in, double* out, int* status, cudaStream_t s) {
+  switch (fam) {
+    case 0: return launch_naive<BX, BY>(N, in, out, s);
+    case 1: return launch_smem<BX, BY>(N, in, out, s);
+    case 2: return launch_tma<BX, BY, false>(N, in, out, status, s);
+    default: return launch_tma<BX, BY, true>(N, in, out, status, s);
+  }
+}
+
+int sweep(int variant, int N, const double* in, double* out, int* status, cudaStream_t s) {
+  const int fam = variant / 4;
+  switch (variant % 4) {
+    case 0: return launch_family<32, 4>(fam, N, in, out, status, s);
+    case 1: return launch_family<32, 8>(fam, N, in, out, status, s);
+    case 2: return launch_family<64, 4>(fam, N, in, out, status, s);
+    default: return launch_family<128, 2>(fam, N, in, out, status, s);
+  }
+}
+
+}  // namespace
+
+bool encode_tensor_map_3d_f64(CUtensorMap* map, const void* base, uint64_t d0, uint64_t d1, uint64_t d2,
+                              uint32_t b0, uint32_t b1, uint32_t b2) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  if (!encode) return false;
+  cuuint64_t dims[3] = {d0, d1, d2};
+  cuuint64_t strides[2] = {d0 * 8, d0 * d1 * 8};
+  cuuint32_t box[3] = {b0, b1, b2};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<void*>(base), dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int jacobi7_num_variants() { return 16; }
+
+int jacobi7_variant_name(int v, char* buf, int len) {
+  if (v < 0 || v >= 16 || !buf || len <= 0) return AR_ERR_ARG;
+  snprintf(buf, (size_t)len, "jacobi7_%s_%dx%d", kFamily[v / 4], kShapeX[v % 4], kShapeY[v % 4]);
+  return AR_OK;
+}
+
+int jacobi7_launch(void* args, int variant, double, void* stream, void*) {
+  const ar_jacobi7_args* a = static_cast<const ar_jacobi7_args*>(args);
+  if (!a) return AR_ERR_ARG;
+  return ar_jacobi7(variant, a->N, a->sweeps, a->u0, a->out, a->work, a->status, stream);
+}
+
+}  // namespace ar
+
+extern "C" int ar_jacobi7(int variant, int N, int sweeps, const double* u0, double* out, double* work,
+                          int* status, void* stream) {
+  using namespace ar;
+  if (variant < 0 || variant >= 16 || N < 0 || sweeps < 0 || N > 65535) return AR_ERR_ARG;
+  if (N == 0) return AR_OK;
+  if (!u0 || !out || (sweeps > 1 && !work)) return AR_ERR_ARG;
+  if (u0 == out || u0 == work || out == work) return AR_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  const int64_t n3 = (int64_t)N * N * N;
+  if (sweeps == 0) {
+    return cudaMemcpyAsync(out, u0, (size_t)n3 * sizeof(double), cudaMemcpyDeviceToDevice, s) == cudaSuccess
+               ? AR_OK
+               : AR_ERR_CUDA;
+  }
+  const double* src = u0;
+  for (int sw = 0; sw < sweeps; ++sw) {
+    double* dst = ((sweeps - 1 - sw) % 2 == 0) ? out : work;
+    const int rc = sweep(variant, N, src, dst, status, s);
+    if (rc != AR_OK) return rc;
+    src = dst;
+  }
+  return AR_OK;
+}

@@ -1,0 +1,289 @@
+"""Host logic of the region runtime through the C ABI, on CPU.
+
+CUDA-event timing is replaced by a deterministic cost model
+(ar_set_fake_timer) and the variants by host launchers, so these tests need
+no GPU.  The runtime's labels and decision trees are compared with the
+selection oracle on the same records.
+"""
+import ctypes
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2303_08873_b300 as ar
+from oracle import select
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLD = json.load(open(os.path.join(ROOT, "tests", "golden", "variant_ranges.json")))
+
+
+def _declared_functions():
+    names = set()
+    for h in ("ar.h", "ar_loops.h"):
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:int|void)\s+(ar_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_library_exports_every_declared_function():
+    declared = _declared_functions()
+    assert len(declared) >= 30
+    for name in sorted(declared):
+        assert hasattr(ar.lib, name), name
+    assert declared == set(ar.EXPORTED), declared ^ set(ar.EXPORTED)
+
+
+def _noop(args, v, value, stream, user):
+    return 0
+
+
+class Calls:
+    def __init__(self):
+        self.seq = []
+
+    def __call__(self, args, v, value, stream, user):
+        self.seq.append(v)
+        return 0
+
+
+def _region(V=4, nf=1, spec="", mtd=0, cost=None):
+    r = ar.Region("t", nf, spec, mtd)
+    calls = Calls()
+    for v in range(V):
+        r.register(f"v{v}", float(v), calls)
+    r.set_fake_timer(cost or (lambda f, v: 1.0 + v))
+    return r, calls
+
+
+# ------------------------------------------------------------ registration
+def test_categorical_variants_enumerate_in_order():
+    ex = GOLD["apollo_example"]
+    r = ar.Region("vecAdd", ex["num_features"], "DecisionTree,explore=RoundRobin", ex["min_train_data"])
+    for name, idx in ex["policies"].items():
+        assert r.register(name, float(idx), _noop) == idx
+    info = r.info()
+    assert info["num_variants"] == ex["num_policies"] and info["min_train_data"] == 10
+    assert [r.variant(i)["name"] for i in range(2)] == ["cpu", "gpu"]
+
+
+@pytest.mark.parametrize("case", GOLD["ranges"])
+def test_range_registration_matches_oracle(case):
+    r = ar.Region("r", 1)
+    n = r.register_range(case["begin"], case["end"], case["step"], _noop)
+    want = select.expand_range(case["begin"], case["end"], case["step"])
+    assert n == len(want)
+    assert [r.variant(i)["value"] for i in range(n)] == want
+
+
+def test_defaults_min_train_is_variant_count_and_dtree_depth_2():
+    r, _ = _region(V=5)
+    info = r.info()
+    assert info["min_train_data"] == 5 and info["model"] == "dtree"
+
+
+def test_bad_specs_and_arguments():
+    for spec in ("forest", "dtree,0", "mlp,48", "fixed", "dtree,explore=greedy", "reps=0"):
+        with pytest.raises(ar.ArError) as e:
+            ar.Region("x", 1, spec)
+        assert e.value.code == ar.AR_ERR_ARG
+    with pytest.raises(ar.ArError):
+        ar.Region("x", 9)
+    r = ar.Region("x", 1)
+    with pytest.raises(ar.ArError):
+        r.register_range(5, 1, 1, _noop)
+
+
+# ------------------------------------------------------------ exploration
+def test_round_robin_then_model_selects():
+    # variant 0 fastest for small n, variant 2 fastest for large n
+    cost = lambda f, v: (1.0 + v) if f[0] < 100 else (3.0 - v)  # noqa: E731
+    r, calls = _region(V=3, cost=cost, mtd=6)
+    seq = []
+    feats = [10, 1000, 10, 1000, 10, 1000]
+    for k, n in enumerate(feats):
+        v, _ = r.invoke([n])
+        seq.append(v)
+        assert v == select.round_robin(k, 3)
+    assert r.info()["trained"]  # 6 unique (n, v) points reached
+    assert r.invoke([20])[0] == 0
+    assert r.invoke([5000])[0] == 2
+    assert calls.seq == seq + [0, 2]
+
+
+def test_training_fires_once_on_unique_points_only():
+    r, _ = _region(V=2, mtd=3)
+    for _ in range(5):
+        r.invoke([7])  # only (7,0) and (7,1): 2 unique points
+    assert not r.info()["trained"]
+    assert r.counts() == (5, 2)
+    r.invoke([8])
+    assert r.info()["trained"]
+
+
+def test_policy_always_in_range_property():
+    rng = np.random.Generator(np.random.PCG64(0))
+    V = 7
+    r, _ = _region(V=V, nf=2, cost=lambda f, v: float((int(f[0]) * 31 + v * 17) % 11 + 1), mtd=20)
+    for _ in range(200):
+        v, _ = r.invoke([float(rng.integers(0, 50)), float(rng.integers(0, 3))])
+        assert 0 <= v < V
+
+
+def test_labels_and_tree_match_oracle_on_random_costs():
+    for seed in range(8):
+        rng = np.random.Generator(np.random.PCG64(seed))
+        V = int(rng.integers(2, 6))
+        table = rng.uniform(1.0, 2.0, (4, 3, V))
+        cost = lambda f, v: float(table[int(f[0]) % 4, int(f[1]) % 3, v])  # noqa: E731
+        r, _ = _region(V=V, nf=2, cost=cost, mtd=10 ** 6)
+        for _ in range(150):
+            r.invoke([float(rng.integers(0, 4)), float(rng.integers(0, 3))])
+        r.train()
+        recs = r.records()
+        labs = select.labels(recs)
+        X = [list(f) for f, _ in labs]
+        y = [l for _, l in labs]
+        want = select.cart_fit(X, y, max_depth=2)
+        assert r.tree() == want
+        for x in X:
+            assert r.select(x)[0] == select.cart_predict(want, x)
+
+
+# ------------------------------------------------------------ profiling
+def test_profile_exhaustive_argmin_with_ties():
+    cost = lambda f, v: [3.0, 1.004, 1.0, 2.0][v]  # noqa: E731
+    r, calls = _region(V=4, spec="exhaustive,reps=5", cost=cost)
+    ms, best = r.profile([42])
+    assert best == select.exhaustive_argmin(ms) == 1  # 1.004 within 0.5 % of 1.0
+    assert ms == pytest.approx([3.0, 1.004, 1.0, 2.0])
+    assert len(calls.seq) == 4 * 6  # 1 warm-up + 5 timed per variant
+    assert r.counts()[0] == 20
+    assert r.select([42]) == (1, 1.0)
+    with pytest.raises(ar.ArError) as e:
+        r.select([43])
+    assert e.value.code == ar.AR_ERR_NOMODEL
+
+
+def test_fixed_model_always_runs_its_variant():
+    r, calls = _region(V=3, spec="fixed,2")
+    for n in (1, 2, 3):
+        assert r.invoke([n])[0] == 2
+    assert r.select([9])[0] == 2
+
+
+# ------------------------------------------------------------ errors
+def test_state_and_argument_errors():
+    r, _ = _region(V=2)
+    with pytest.raises(ar.ArError) as e:
+        r.select([1])
+    assert e.value.code == ar.AR_ERR_NOMODEL
+    with pytest.raises(ar.ArError) as e:
+        r.invoke([1, 2])
+    assert e.value.code == ar.AR_ERR_STATE
+    with pytest.raises(ar.ArError) as e:
+        r.invoke([float("nan")])
+    assert e.value.code == ar.AR_ERR_ARG
+    r.invoke([1])
+    with pytest.raises(ar.ArError) as e:
+        r.register("late", 9.0, _noop)
+    assert e.value.code == ar.AR_ERR_STATE
+    # Apollo call order
+    with pytest.raises(ar.ArError):
+        r.end()
+    r.begin()
+    with pytest.raises(ar.ArError):
+        r.get_policy()  # feature missing
+    r.set_feature(3.0)
+    with pytest.raises(ar.ArError):
+        r.set_feature(4.0)  # too many
+    v = r.get_policy()
+    assert v == r.get_policy()
+    r.end()
+
+
+def test_failing_launcher_marks_variant_unusable():
+    r = ar.Region("f", 1)
+    r.register("ok", 0.0, _noop)
+    r.register("bad", 1.0, lambda a, v, x, s, u: 7)
+    r.register("ok2", 2.0, _noop)
+    r.set_fake_timer(lambda f, v: 1.0)
+    assert r.invoke([1])[0] == 0
+    with pytest.raises(ar.ArError) as e:
+        r.invoke([1])
+    assert e.value.code == ar.AR_ERR_CUDA
+    assert not r.variant(1)["usable"]
+    seq = [r.invoke([1])[0] for _ in range(4)]
+    assert 1 not in seq
+
+
+# ------------------------------------------------------------ persistence
+def test_save_load_round_trip_and_corruption(tmp_path):
+    cost = lambda f, v: (1.0 + v) if f[0] < 100 else (3.0 - v)  # noqa: E731
+    r, _ = _region(V=3, cost=cost)
+    for n in (10, 1000, 10, 1000, 10, 1000):
+        r.invoke([n])
+    p = tmp_path / "region.bin"
+    r.save(p)
+    q, _ = _region(V=3, cost=cost)
+    q.load(p)
+    assert q.info()["trained"] and q.tree() == r.tree() and q.records() == r.records()
+    assert q.select([5000]) == r.select([5000])
+    data = bytearray(p.read_bytes())
+    data[40] ^= 0xFF
+    bad = tmp_path / "bad.bin"
+    bad.write_bytes(bytes(data))
+    with pytest.raises(ar.ArError) as e:
+        q.load(bad)
+    assert e.value.code == ar.AR_ERR_IO
+    short = tmp_path / "short.bin"
+    short.write_bytes(p.read_bytes()[:20])
+    with pytest.raises(ar.ArError) as e:
+        q.load(short)
+    assert e.value.code == ar.AR_ERR_IO
+    with pytest.raises(ar.ArError) as e:
+        q.load(tmp_path / "missing.bin")
+    assert e.value.code == ar.AR_ERR_IO
+    w, _ = _region(V=4, cost=cost)
+    with pytest.raises(ar.ArError) as e:
+        w.load(p)
+    assert e.value.code == ar.AR_ERR_STATE
+    # the failed loads left q intact
+    assert q.tree() == r.tree()
+
+
+def test_add_record_feeds_training():
+    r, _ = _region(V=2, mtd=100)
+    for n, best in ((1, 0), (2, 0), (50, 1), (60, 1)):
+        r.add_record([n], best, 1.0)
+        r.add_record([n], 1 - best, 2.0)
+    r.train()
+    assert r.select([1.5])[0] == 0 and r.select([55])[0] == 1
+
+
+def test_loop_tables():
+    assert ar.loop_num_variants(ar.AR_LOOP_DAXPY) == 15
+    assert ar.loop_default_variant(ar.AR_LOOP_DAXPY) == 6
+    assert ar.loop_variant_name(ar.AR_LOOP_DAXPY, 6) == "daxpy_b256_e1"
+    assert ar.loop_num_variants(ar.AR_LOOP_JACOBI7) == 16
+    assert ar.loop_variant_name(ar.AR_LOOP_JACOBI7, 1) == "jacobi7_naive_32x8"
+    r = ar.Region("j", 2)
+    assert r.add_builtin(ar.AR_LOOP_JACOBI7) == 16
+    with pytest.raises(ar.ArError):
+        ar.loop_num_variants(17)
+
+
+def test_kernel_entry_points_validate_before_launch():
+    # argument errors are reported without touching the GPU
+    with pytest.raises(ar.ArError) as e:
+        ar.ar_daxpy(15, 10, 1.0, 16, 32)
+    assert e.value.code == ar.AR_ERR_ARG
+    assert ar.lib.ar_daxpy(0, 0, 1.0, None, None, None) == 0  # empty: nothing launched
+    assert ar.lib.ar_daxpy(1, 4, 1.0, 8, 16, None) == ar.AR_ERR_ARG  # misaligned double2
+    assert ar.lib.ar_jacobi7(0, 8, 1, 64, 64, 128, None, None) == ar.AR_ERR_ARG  # aliasing
+    assert ar.lib.ar_mlp_num_params(5, 64, 7) == 5 * 64 + 64 + 64 * 64 + 64 + 7 * 64 + 7
+    assert ar.lib.ar_mlp_num_params(5, 48, 7) == ar.AR_ERR_ARG
