@@ -86,6 +86,64 @@ typedef struct ar_jacobi7_args {
 int ar_jacobi7(int variant, int N, int sweeps, const double *u0, double *out, double *work,
                int *status, void *stream);
 
+/* ---------------------------------------------------------------- SpMV ---
+ * y = A x for a CSR matrix of `rows` rows and nnz nonzeros: rowptr int32
+ * [rows+1] (rowptr[0] = 0, non-decreasing, rowptr[rows] = nnz < 2^31), col
+ * int32 [nnz] (column indices, any order within a row, each < length of x),
+ * val float64 [nnz], x float64, y float64 [rows] (written, not accumulated).
+ * Each row's products are summed in float64 in a variant-specific order.
+ * Variants: 0 thread-per-row, 1 warp-per-row, 2..5 vector-k (k = 2, 4, 8, 16
+ * lanes per row), 6 merge-path (equal path work per thread; rows crossing
+ * threads and blocks fixed up deterministically).  Default: thread-per-row.
+ * Only merge-path uses the caller's workspace (ar_spmv_workspace_bytes; device
+ * memory, contents need no initialisation; AR_ERR_ARG if too small). */
+typedef struct ar_spmv_args {
+  int64_t rows;
+  int64_t nnz;
+  const int32_t *rowptr;
+  const int32_t *col;
+  const double *val;
+  const double *x;
+  double *y;
+  void *workspace;
+  size_t workspace_bytes;
+} ar_spmv_args;
+int ar_spmv_workspace_bytes(int variant, int64_t rows, int64_t nnz, size_t *bytes);
+int ar_spmv(int variant, int64_t rows, int64_t nnz, const int32_t *rowptr, const int32_t *col, const double *val,
+            const double *x, double *y, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Row-length features of a CSR matrix, the learned selector's inputs: out5 =
+ * (rows, nnz, mean, population variance, max) of rowptr[r+1] - rowptr[r], as
+ * float32 in device memory.  Integer sums are exact; mean and variance are
+ * formed in float64.  workspace: ar_csr_features_workspace_bytes of device
+ * memory (no initialisation needed). */
+int ar_csr_features_workspace_bytes(int64_t rows, size_t *bytes);
+int ar_csr_features(int64_t rows, const int32_t *rowptr, float *out5, void *workspace, size_t workspace_bytes,
+                    void *stream);
+
+/* --------------------------------------------------------------- n-body ---
+ * acc4[i] = (sum_j m_j d_ij / (|d_ij|^2 + eps^2)^(3/2), 0), d_ij = r_j - r_i,
+ * over all N bodies (j = i adds 0), float32.  pos4 holds (x, y, z, m) per
+ * body; both arrays 16-byte aligned.  eps > 0.  Variants: shared-memory tile
+ * {128, 256, 512} bodies x inner unroll {1, 4, 8}; variant = 3*tile + unroll.
+ * Default: tile 256, unroll 1 (variant 3). */
+typedef struct ar_nbody_args {
+  int64_t N;
+  const float *pos4;
+  float *acc4;
+  float eps;
+} ar_nbody_args;
+int ar_nbody(int variant, int64_t N, const float *pos4, float *acc4, float eps, void *stream);
+
+/* `count` independent systems in one persistent launch: system b is bodies
+ * [offs[b], offs[b+1]) of pos4/acc4 (offs: device int32 [count+1],
+ * non-decreasing).  Work items (system, 256-body tile) run largest system
+ * first, pulled from a device counter.  workspace: device memory of
+ * ar_nbody_batched_workspace_bytes (no initialisation needed); count <= 4096. */
+int ar_nbody_batched_workspace_bytes(int count, size_t *bytes);
+int ar_nbody_batched(int count, const int32_t *offs, const float *pos4, float *acc4, float eps, void *workspace,
+                     size_t workspace_bytes, void *stream);
+
 /* ------------------------------------------------------------ MLP selector ---
  * The learned selector of the adaptive region: the paper's model kinds are
  * decision trees and random forests and it names neural networks as a

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libadaptive_region.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(
-        f"{LIB_PATH} is missing: build it with `python -m paper_2303_08873_b300.build` "
+        f"{LIB_PATH} is missing: build it with `python paper_2303_08873_b300/build.py` "
         "(there is no non-CUDA fallback)")
 lib = ctypes.CDLL(LIB_PATH)
 
@@ -63,6 +63,15 @@ class ArJacobi7Args(ctypes.Structure):
     _fields_ = [("N", _i), ("sweeps", _i), ("u0", _vp), ("out", _vp), ("work", _vp), ("status", _vp)]
 
 
+class ArSpmvArgs(ctypes.Structure):
+    _fields_ = [("rows", _i64), ("nnz", _i64), ("rowptr", _vp), ("col", _vp), ("val", _vp), ("x", _vp),
+                ("y", _vp), ("workspace", _vp), ("workspace_bytes", _sz)]
+
+
+class ArNbodyArgs(ctypes.Structure):
+    _fields_ = [("N", _i64), ("pos4", _vp), ("acc4", _vp), ("eps", _f)]
+
+
 _SIGS = {
     # ar.h
     "ar_region_create": (_i, [_cs, _i, _cs, _i, ctypes.POINTER(_vp)]),
@@ -97,6 +106,13 @@ _SIGS = {
     "ar_region_add_builtin": (_i, [_vp, _i, _pi]),
     "ar_daxpy": (_i, [_i, _i64, _d, _vp, _vp, _vp]),
     "ar_jacobi7": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp, _vp]),
+    "ar_spmv_workspace_bytes": (_i, [_i, _i64, _i64, ctypes.POINTER(_sz)]),
+    "ar_spmv": (_i, [_i, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "ar_csr_features_workspace_bytes": (_i, [_i64, ctypes.POINTER(_sz)]),
+    "ar_csr_features": (_i, [_i64, _vp, _vp, _vp, _sz, _vp]),
+    "ar_nbody": (_i, [_i, _i64, _vp, _vp, _f, _vp]),
+    "ar_nbody_batched_workspace_bytes": (_i, [_i, ctypes.POINTER(_sz)]),
+    "ar_nbody_batched": (_i, [_i, _vp, _vp, _vp, _f, _vp, _sz, _vp]),
     "ar_mlp_num_params": (_i, [_i, _i, _i]),
     "ar_mlp_forward": (_i, [_vp, _vp, _vp, _i, _i, _i, _i64, _vp, _vp, _vp, _vp, _vp]),
     "ar_mlp_grad": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp]),
@@ -173,6 +189,43 @@ def ar_daxpy(variant, n, a, x, y, stream=None):
 def ar_jacobi7(variant, N, sweeps, u0, out, work, status=None, stream=None):
     return check(lib.ar_jacobi7(variant, N, sweeps, ptr(u0), ptr(out), ptr(work), ptr(status),
                                 stream_handle(stream)))
+
+
+def ar_spmv_workspace_bytes(variant, rows, nnz):
+    b = ctypes.c_size_t()
+    check(lib.ar_spmv_workspace_bytes(variant, rows, nnz, ctypes.byref(b)))
+    return b.value
+
+
+def ar_spmv(variant, rows, nnz, rowptr, col, val, x, y, workspace=None, workspace_bytes=0, stream=None):
+    return check(lib.ar_spmv(variant, rows, nnz, ptr(rowptr), ptr(col), ptr(val), ptr(x), ptr(y), ptr(workspace),
+                             workspace_bytes, stream_handle(stream)))
+
+
+def ar_csr_features_workspace_bytes(rows):
+    b = ctypes.c_size_t()
+    check(lib.ar_csr_features_workspace_bytes(rows, ctypes.byref(b)))
+    return b.value
+
+
+def ar_csr_features(rows, rowptr, out5, workspace, workspace_bytes, stream=None):
+    return check(lib.ar_csr_features(rows, ptr(rowptr), ptr(out5), ptr(workspace), workspace_bytes,
+                                     stream_handle(stream)))
+
+
+def ar_nbody(variant, N, pos4, acc4, eps=1e-2, stream=None):
+    return check(lib.ar_nbody(variant, N, ptr(pos4), ptr(acc4), eps, stream_handle(stream)))
+
+
+def ar_nbody_batched_workspace_bytes(count):
+    b = ctypes.c_size_t()
+    check(lib.ar_nbody_batched_workspace_bytes(count, ctypes.byref(b)))
+    return b.value
+
+
+def ar_nbody_batched(count, offs, pos4, acc4, eps, workspace, workspace_bytes, stream=None):
+    return check(lib.ar_nbody_batched(count, ptr(offs), ptr(pos4), ptr(acc4), eps, ptr(workspace), workspace_bytes,
+                                      stream_handle(stream)))
 
 
 def ar_mlp_num_params(F, H, V):
@@ -376,7 +429,9 @@ class Region:
         return self._ck(lib.ar_set_l2_flush(self.h, ptr(buf), nbytes))
 
 
-__all__ = ["ArError", "Region", "ArDaxpyArgs", "ArJacobi7Args", "LAUNCH_FN", "FAKE_TIME_FN", "lib", "ptr",
+__all__ = ["ArError", "Region", "ArDaxpyArgs", "ArJacobi7Args", "ArSpmvArgs", "ArNbodyArgs", "ar_spmv",
+           "ar_spmv_workspace_bytes", "ar_csr_features", "ar_csr_features_workspace_bytes", "ar_nbody",
+           "ar_nbody_batched", "ar_nbody_batched_workspace_bytes", "LAUNCH_FN", "FAKE_TIME_FN", "lib", "ptr",
            "stream_handle", "check", "loop_num_variants", "loop_default_variant", "loop_variant_name", "ar_daxpy",
            "ar_jacobi7", "ar_mlp_num_params", "ar_mlp_forward", "ar_mlp_grad", "ar_mlp_adam", "ar_mlp_train",
            "ar_measure_fma_rates", "EXPORTED", "AR_LOOP_DAXPY", "AR_LOOP_JACOBI7", "AR_LOOP_SPMV",

@@ -6,7 +6,7 @@ shared library next to this file.  The library exports the C ABI declared in
 ``include/ar.h`` and ``include/ar_loops.h``.  Rebuilds only when a source or
 header is newer than the library.
 
-Usage: ``python -m paper_2303_08873_b300.build [--force] [--verbose]``.
+Usage: ``python paper_2303_08873_b300/build.py [--force] [--verbose]``.
 """
 from __future__ import annotations
 

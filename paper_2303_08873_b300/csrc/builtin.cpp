@@ -38,6 +38,8 @@ const LoopEntry* entry(int loop) {
   static const LoopEntry table[] = {
       {daxpy_num_variants, daxpy_variant_name, daxpy_launch, 6},
       {jacobi7_num_variants, jacobi7_variant_name, jacobi7_launch, 1},
+      {spmv_num_variants, spmv_variant_name, spmv_launch, 0},
+      {nbody_num_variants, nbody_variant_name, nbody_launch, 3},
   };
   if (loop < 0 || loop >= (int)(sizeof table / sizeof table[0])) return nullptr;
   return &table[loop];

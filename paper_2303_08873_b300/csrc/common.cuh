@@ -33,5 +33,11 @@ int daxpy_num_variants();
 int daxpy_variant_name(int v, char* buf, int len);
 int jacobi7_num_variants();
 int jacobi7_variant_name(int v, char* buf, int len);
+int spmv_launch(void* args, int variant, double value, void* stream, void* user);
+int spmv_num_variants();
+int spmv_variant_name(int v, char* buf, int len);
+int nbody_launch(void* args, int variant, double value, void* stream, void* user);
+int nbody_num_variants();
+int nbody_variant_name(int v, char* buf, int len);
 
 }  // namespace ar

@@ -10,7 +10,8 @@
 // the 6 float64 operations per point (5 adds, 1 multiply) bound the native
 // families at ~1.5 TB/s.  The df family moves the arithmetic to the FP32 pipe
 // in float-pair form (hi + lo, ~2^-48 relative) and keeps one float64 add per
-// point, so it can run at HBM speed.
+// point.  Float64<->float32 conversions also issue on the float64 pipe on
+// B300, so the df family converts with integer bit operations only.
 //
 // Families (variant = 4*family + shape; shapes 32x4, 32x8, 64x4, 128x2):
 //   0 naive  one thread per point, 7 global loads through L1/L2
@@ -105,23 +106,42 @@ constexpr float kSixthLo = -4.967053740534411e-09f;  // RN(1/6 - kSixthHi)
 
 // Split x into (hi, lo) with hi = x rounded to 24 significant bits and
 // lo = the remainder, both floats: x = hi + lo to within 2^-48 |x|.  Works on
-// the bit pattern (truncate to 24 bits, round the 29-bit remainder up or
-// down) so no float64 operation is issued.  Values outside the float-pair
-// range (|x| < 2^-74, |x| >= 2^118, inf, NaN) give hi = NaN as a marker; ±0
-// gives (0, 0).
+// the bit pattern with integer operations (truncate the significand to 24
+// bits, round the 29-bit remainder up or down): on B300 a float64<->float32
+// conversion issues on the slow float64 pipe, int->float does not.  Values
+// outside the float-pair range (|x| < 2^-74, |x| >= 2^118, inf, NaN) give
+// hi = NaN as a marker; +-0 gives (0, 0).
 __device__ __forceinline__ float2 df_split(double x) {
   const long long b = __double_as_longlong(x);
   if ((b << 1) == 0) return make_float2(0.f, 0.f);
-  const int e = (int)((b >> 52) & 0x7ff);
+  const unsigned h32 = (unsigned)((unsigned long long)b >> 32), l32 = (unsigned)b;
+  const int e = (int)((h32 >> 20) & 0x7ff);
   if (e < 949 || e > 1140) return make_float2(__int_as_float(0x7fc00001), 0.f);
-  int r = (int)(b & 0x1FFFFFFFLL);
-  float hi = __double2float_rz(x);
+  const unsigned sign = h32 & 0x80000000u;
+  unsigned hib = sign | ((unsigned)(e - 896) << 23) | ((h32 & 0xfffffu) << 3) | (l32 >> 29);
+  int r = (int)(l32 & 0x1FFFFFFFu);
   if (r >= (1 << 28)) {
-    hi = __int_as_float(__float_as_int(hi) + 1);  // one ulp away from zero
+    hib += 1;  // one ulp away from zero (carries into the exponent correctly)
     r -= (1 << 29);
   }
-  float lo = __int2float_rn(r) * __int_as_float((e - 1075 + 127) << 23);
-  return make_float2(hi, b < 0 ? -lo : lo);
+  const float lo = __int2float_rn(r) * __int_as_float((e - 1075 + 127) << 23);
+  return make_float2(__uint_as_float(hib), __uint_as_float(__float_as_uint(lo) ^ sign));
+}
+
+// Exact float -> float64 by assembling the bit pattern (no conversion
+// instruction).  Subnormal floats become signed zero (|f| < 2^-126 is below
+// the resolution of any float-pair result here); inf/NaN become NaN.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e8 = (u >> 23) & 0xffu;
+  unsigned hi = u & 0x80000000u, lo = 0u;
+  if (e8 == 0xffu) {
+    hi = 0x7ff80000u;
+  } else if (e8 != 0u) {
+    hi |= ((e8 + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+    lo = u << 29;
+  }
+  return __hiloint2double((int)hi, (int)lo);
 }
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -147,7 +167,7 @@ __device__ __forceinline__ double df_avg6(float2 v0, float2 v1, float2 v2, float
   float pe = fmaf(s, kSixthHi, -p);
   pe = fmaf(s, kSixthLo, pe);
   pe = fmaf(c, kSixthHi, pe);
-  return (double)p + (double)pe;
+  return f2d_bits(p) + f2d_bits(pe);
 }
 
 // ------------------------------------------------------------------ TMA ring

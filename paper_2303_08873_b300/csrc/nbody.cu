@@ -1,0 +1,202 @@
+// All-pairs n-body variants (FP32): the compute-bound region.
+//
+//   a_i = sum_j m_j (r_j - r_i) / (|r_j - r_i|^2 + eps^2)^(3/2),  G = 1,
+//   j = i included (contributes exactly 0).
+//
+// Per interaction: 3 FADD + 3 FFMA (softened r^2) + 1 MUFU rsqrt + 3 FMUL +
+// 3 FFMA = 12 FP32-pipe instructions and one MUFU, plus one broadcast
+// shared-memory load of the j body.  Variants: shared-memory tile of T bodies
+// (T = threads per block, 128 / 256 / 512) x unroll U (1 / 4 / 8) of the inner
+// j loop; variant = 3*tile_index + unroll_index.  Each thread sums one tile
+// into a local partial before adding it to its running total, which keeps the
+// float32 rounding error near sqrt(T) + sqrt(N/T) additions instead of N.
+//
+// The batched form runs `count` independent systems of uneven size in one
+// persistent launch: work items (system, i-tile) are ordered largest system
+// first (an i-tile costs the system's size) and pulled from an atomic counter
+// by resident blocks, so the long items start first and the tail is short.
+#include <cstdio>
+
+#include "common.cuh"
+
+namespace ar {
+namespace {
+
+constexpr int kTiles[3] = {128, 256, 512};
+constexpr int kUnroll[3] = {1, 4, 8};
+constexpr int kBatchTile = 256;
+
+template <int T, int U>
+__device__ __forceinline__ void tile_accumulate(const float4* __restrict__ tile, float4 pi, float eps2, float& ax,
+                                                float& ay, float& az) {
+  float tx = 0.f, ty = 0.f, tz = 0.f;
+#pragma unroll U
+  for (int k = 0; k < T; ++k) {
+    const float4 q = tile[k];
+    const float dx = q.x - pi.x, dy = q.y - pi.y, dz = q.z - pi.z;
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+    const float inv = rsqrtf(r2);
+    const float s = q.w * inv * inv * inv;
+    tx = fmaf(dx, s, tx);
+    ty = fmaf(dy, s, ty);
+    tz = fmaf(dz, s, tz);
+  }
+  ax += tx;
+  ay += ty;
+  az += tz;
+}
+
+// Bodies i of [base, base+n) against all bodies of the same range.  Padding
+// bodies have zero mass and sit at the origin, so they add exactly 0.
+template <int T, int U>
+__device__ __forceinline__ void body_tile(const float4* __restrict__ p, float4* __restrict__ a, int64_t base,
+                                          int64_t n, int64_t i_local, float eps2, float4* tile) {
+  const bool live = i_local < n;
+  const float4 pi = live ? p[base + i_local] : make_float4(0.f, 0.f, 0.f, 0.f);
+  float ax = 0.f, ay = 0.f, az = 0.f;
+  for (int64_t j0 = 0; j0 < n; j0 += T) {
+    __syncthreads();
+    const int64_t j = j0 + threadIdx.x;
+    tile[threadIdx.x] = j < n ? p[base + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    tile_accumulate<T, U>(tile, pi, eps2, ax, ay, az);
+  }
+  if (live) a[base + i_local] = make_float4(ax, ay, az, 0.f);
+}
+
+template <int T, int U>
+__global__ void __launch_bounds__(T) nbody_tile(int64_t N, const float4* __restrict__ p, float4* __restrict__ a,
+                                                float eps2) {
+  __shared__ float4 tile[T];
+  body_tile<T, U>(p, a, 0, N, (int64_t)blockIdx.x * T + threadIdx.x, eps2, tile);
+}
+
+// ------------------------------------------------------------ batched
+// One block: rank systems by size (descending, ties to the lower index),
+// prefix-sum their i-tile counts in rank order, reset the work counter.
+__global__ void nbody_batch_plan(int count, const int* __restrict__ offs, int* __restrict__ order,
+                                 int* __restrict__ prefix, int* __restrict__ counter) {
+  extern __shared__ int tiles_by_rank[];
+  for (int b = threadIdx.x; b < count; b += blockDim.x) {
+    const int nb = offs[b + 1] - offs[b];
+    int rank = 0;
+    for (int c = 0; c < count; ++c) {
+      const int nc = offs[c + 1] - offs[c];
+      rank += (nc > nb) || (nc == nb && c < b);
+    }
+    order[rank] = b;
+    tiles_by_rank[rank] = (nb + kBatchTile - 1) / kBatchTile;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int r = 0; r < count; ++r) {
+      prefix[r] = acc;
+      acc += tiles_by_rank[r];
+    }
+    prefix[count] = acc;
+    *counter = 0;
+  }
+}
+
+__global__ void __launch_bounds__(kBatchTile) nbody_batched(int count, const int* __restrict__ offs,
+                                                            const float4* __restrict__ p, float4* __restrict__ a,
+                                                            float eps2, const int* __restrict__ order,
+                                                            const int* __restrict__ prefix, int* __restrict__ counter) {
+  __shared__ float4 tile[kBatchTile];
+  __shared__ int item_s;
+  const int total = prefix[count];
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) item_s = atomicAdd(counter, 1);
+    __syncthreads();
+    const int item = item_s;
+    if (item >= total) break;
+    int lo = 0, hi = count - 1;  // last rank with prefix <= item
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (prefix[mid] <= item)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const int b = order[lo];
+    const int t = item - prefix[lo];
+    const int64_t base = offs[b], n = offs[b + 1] - offs[b];
+    body_tile<kBatchTile, 4>(p, a, base, n, (int64_t)t * kBatchTile + threadIdx.x, eps2, tile);
+  }
+}
+
+template <int T>
+int launch_u(int u, int64_t N, const float4* p, float4* a, float eps2, cudaStream_t s) {
+  const int64_t grid = ceil_div(N, T);
+  if (grid > 0x7fffffffLL) return AR_ERR_ARG;
+  switch (u) {
+    case 0: nbody_tile<T, 1><<<(unsigned)grid, T, 0, s>>>(N, p, a, eps2); break;
+    case 1: nbody_tile<T, 4><<<(unsigned)grid, T, 0, s>>>(N, p, a, eps2); break;
+    default: nbody_tile<T, 8><<<(unsigned)grid, T, 0, s>>>(N, p, a, eps2); break;
+  }
+  return launch_status();
+}
+
+size_t batch_ws(int count) { return (size_t)(2 * count + 2) * sizeof(int) + 256; }
+
+}  // namespace
+
+int nbody_num_variants() { return 9; }
+
+int nbody_variant_name(int v, char* buf, int len) {
+  if (v < 0 || v >= 9 || !buf || len <= 0) return AR_ERR_ARG;
+  snprintf(buf, (size_t)len, "nbody_t%d_u%d", kTiles[v / 3], kUnroll[v % 3]);
+  return AR_OK;
+}
+
+int nbody_launch(void* args, int variant, double, void* stream, void*) {
+  const ar_nbody_args* a = static_cast<const ar_nbody_args*>(args);
+  if (!a) return AR_ERR_ARG;
+  return ar_nbody(variant, a->N, a->pos4, a->acc4, a->eps, stream);
+}
+
+}  // namespace ar
+
+using namespace ar;
+
+extern "C" int ar_nbody(int variant, int64_t N, const float* pos4, float* acc4, float eps, void* stream) {
+  if (variant < 0 || variant >= 9 || N < 0 || !(eps > 0.f)) return AR_ERR_ARG;
+  if (N == 0) return AR_OK;
+  if (!pos4 || !acc4 || !aligned16(pos4) || !aligned16(acc4)) return AR_ERR_ARG;
+  const float4* p = reinterpret_cast<const float4*>(pos4);
+  float4* a = reinterpret_cast<float4*>(acc4);
+  const float eps2 = eps * eps;
+  cudaStream_t s = as_stream(stream);
+  switch (variant / 3) {
+    case 0: return launch_u<128>(variant % 3, N, p, a, eps2, s);
+    case 1: return launch_u<256>(variant % 3, N, p, a, eps2, s);
+    default: return launch_u<512>(variant % 3, N, p, a, eps2, s);
+  }
+}
+
+extern "C" int ar_nbody_batched_workspace_bytes(int count, size_t* bytes) {
+  if (count < 0 || !bytes) return AR_ERR_ARG;
+  *bytes = batch_ws(count);
+  return AR_OK;
+}
+
+extern "C" int ar_nbody_batched(int count, const int32_t* offs, const float* pos4, float* acc4, float eps,
+                                void* workspace, size_t workspace_bytes, void* stream) {
+  if (count < 0 || count > 4096 || !(eps > 0.f)) return AR_ERR_ARG;
+  if (count == 0) return AR_OK;
+  if (!offs || !pos4 || !acc4 || !aligned16(pos4) || !aligned16(acc4)) return AR_ERR_ARG;
+  if (!workspace || workspace_bytes < batch_ws(count)) return AR_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  int* ws = reinterpret_cast<int*>((reinterpret_cast<uintptr_t>(workspace) + 255) & ~uintptr_t(255));
+  int* order = ws;
+  int* prefix = order + count;
+  int* counter = prefix + count + 1;
+  const int* o = reinterpret_cast<const int*>(offs);
+  nbody_batch_plan<<<1, 256, count * sizeof(int), s>>>(count, o, order, prefix, counter);
+  const int grid = device_sms() * 4;
+  nbody_batched<<<grid, kBatchTile, 0, s>>>(count, o, reinterpret_cast<const float4*>(pos4),
+                                            reinterpret_cast<float4*>(acc4), eps * eps, order, prefix, counter);
+  return launch_status();
+}

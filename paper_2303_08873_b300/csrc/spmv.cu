@@ -1,0 +1,335 @@
+// CSR SpMV variants, y = A x in float64 (the sparse region; stand-in for the
+// paper's AMGMk relax benchmark, Table 3), and the device reduction of the
+// row-length features the learned selector reads.
+//
+// Algorithmic traffic: 12 bytes per nonzero (val + col), 4 per row pointer,
+// 8 per x entry (read once when it stays in L2) and 8 per output row.  One
+// DFMA per nonzero; on B300 that float64 rate (~0.56e12/s) is of the same
+// order as the HBM-limited nonzero rate, so the variants also differ in how
+// many float64 reduction adds they spend per row.
+//
+// Variants: 0 thread-per-row; 1 warp-per-row (32-lane shuffle reduction);
+// 2..5 vector-k with k = 2, 4, 8, 16 lanes per row; 6 merge-path
+// (Merrill & Garland, SC'16): the merge of row ends and nonzero indices is cut
+// into equal chunks of 16 path items per thread, so every thread does the same
+// work whatever the row lengths; rows that straddle threads are fixed up
+// deterministically by the first thread of each straddling run, rows that
+// straddle blocks by a second small kernel over the per-block carries.
+#include <cstdio>
+
+#include "common.cuh"
+
+namespace ar {
+namespace {
+
+constexpr int kMpThreads = 256;
+constexpr int kMpItems = 16;                          // path items per thread
+constexpr int kMpPerBlock = kMpThreads * kMpItems;    // 4096
+
+__device__ __forceinline__ double ld_val(const double* p) {
+  double v;
+  asm volatile("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ int ld_col(const int* p) {
+  int v;
+  asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+
+// ------------------------------------------------------------ thread per row
+__global__ void __launch_bounds__(256) spmv_thread_row(int64_t rows, const int* __restrict__ rowptr,
+                                                       const int* __restrict__ col, const double* __restrict__ val,
+                                                       const double* __restrict__ x, double* __restrict__ y) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  const int b = __ldg(rowptr + r), e = __ldg(rowptr + r + 1);
+  double s = 0.0;
+  for (int k = b; k < e; ++k) s = fma(ld_val(val + k), __ldg(x + ld_col(col + k)), s);
+  y[r] = s;
+}
+
+// ------------------------------------------------------------ K lanes per row
+template <int K>
+__global__ void __launch_bounds__(256) spmv_vector(int64_t rows, const int* __restrict__ rowptr,
+                                                   const int* __restrict__ col, const double* __restrict__ val,
+                                                   const double* __restrict__ x, double* __restrict__ y) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t r = g / K;
+  const int lane = threadIdx.x % K;
+  double s = 0.0;
+  if (r < rows) {
+    const int b = __ldg(rowptr + r), e = __ldg(rowptr + r + 1);
+    for (int k = b + lane; k < e; k += K) s = fma(ld_val(val + k), __ldg(x + ld_col(col + k)), s);
+  }
+#pragma unroll
+  for (int o = K / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, K);
+  if (r < rows && lane == 0) y[r] = s;
+}
+
+// ------------------------------------------------------------ merge path
+// Path coordinate of diagonal d: (i rows consumed, d - i nonzeros consumed).
+__device__ __forceinline__ int64_t mp_search(int64_t d, int64_t lo, int64_t hi, const int* __restrict__ rowptr,
+                                             int64_t nnz) {
+  lo = max(lo, d - nnz);
+  hi = min(hi, d);
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)__ldg(rowptr + mid + 1) <= d - mid - 1)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+__global__ void spmv_mp_partition(int64_t rows, int64_t nnz, int nblocks, const int* __restrict__ rowptr,
+                                  int64_t* __restrict__ start_row) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b > nblocks) return;
+  const int64_t L = rows + nnz;
+  const int64_t d = min((int64_t)b * kMpPerBlock, L);
+  start_row[b] = mp_search(d, 0, rows, rowptr, nnz);
+}
+
+__global__ void __launch_bounds__(kMpThreads) spmv_mp_main(int64_t rows, int64_t nnz, const int* __restrict__ rowptr,
+                                                           const int* __restrict__ col,
+                                                           const double* __restrict__ val,
+                                                           const double* __restrict__ x, double* __restrict__ y,
+                                                           const int64_t* __restrict__ start_row,
+                                                           int64_t* __restrict__ carry_row,
+                                                           double* __restrict__ carry_val) {
+  __shared__ int64_t srow[kMpThreads];
+  __shared__ double sval[kMpThreads];
+  const int t = threadIdx.x;
+  const int64_t L = rows + nnz;
+  const int64_t db = (int64_t)blockIdx.x * kMpPerBlock;
+  const int64_t de = min(db + kMpPerBlock, L);
+  const int64_t d0 = min(db + (int64_t)t * kMpItems, de);
+  const int64_t d1 = min(d0 + kMpItems, de);
+  int64_t i = mp_search(d0, start_row[blockIdx.x], start_row[blockIdx.x + 1], rowptr, nnz);
+  int64_t j = d0 - i;
+  double s = 0.0;
+  int64_t row_end = i < rows ? (int64_t)__ldg(rowptr + i + 1) : nnz;
+  for (int64_t d = d0; d < d1; ++d) {
+    if (i < rows && j >= row_end) {  // consume the end of row i
+      y[i] = s;
+      s = 0.0;
+      ++i;
+      row_end = i < rows ? (int64_t)__ldg(rowptr + i + 1) : nnz;
+    } else if (j < nnz) {             // consume nonzero j of row i
+      s = fma(ld_val(val + j), __ldg(x + ld_col(col + j)), s);
+      ++j;
+    }
+  }
+  // open row at the end of this thread's range: (i, s)
+  srow[t] = (d1 > d0 && i < rows) ? i : -1;
+  sval[t] = s;
+  if (t == 0) carry_row[blockIdx.x] = -1;
+  __syncthreads();
+  // The first thread of each run of threads that end inside the same open row
+  // adds the run's partial sums, in thread order, to that row: the thread
+  // after the run consumed the row's end and wrote y[row] above.  A run that
+  // reaches the end of the block becomes the block's carry instead.
+  const int64_t r = srow[t];
+  if (r >= 0 && (t == 0 || srow[t - 1] != r)) {
+    double tot = sval[t];
+    int u = t + 1;
+    while (u < kMpThreads && srow[u] == r) tot += sval[u++];
+    const bool closed_here = u < kMpThreads && min(db + (int64_t)u * kMpItems, de) < de;
+    if (closed_here) {
+      y[r] += tot;
+    } else {
+      carry_row[blockIdx.x] = r;
+      carry_val[blockIdx.x] = tot;
+    }
+  }
+}
+
+// Rows straddling blocks: the head of each run of equal carry rows adds the
+// run's carries (block order) to y.  A block's carry row is always closed by
+// a later block, which has already written y[row] in spmv_mp_main.
+__global__ void spmv_mp_fixup(int nblocks, const int64_t* __restrict__ carry_row,
+                              const double* __restrict__ carry_val, double* __restrict__ y) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nblocks) return;
+  const int64_t r = carry_row[b];
+  if (r < 0 || (b > 0 && carry_row[b - 1] == r)) return;
+  double tot = carry_val[b];
+  for (int u = b + 1; u < nblocks && carry_row[u] == r; ++u) tot += carry_val[u];
+  y[r] += tot;
+}
+
+size_t mp_workspace(int64_t rows, int64_t nnz) {
+  const int64_t nb = ceil_div(rows + nnz, kMpPerBlock);
+  return (size_t)(nb + 1) * 8 + (size_t)nb * 8 + (size_t)nb * 8 + 256;
+}
+
+// ------------------------------------------------------------ features
+constexpr int kFeatBlocks = 592;  // 4 per SM on B300
+
+__global__ void __launch_bounds__(256) csr_stats_partial(int64_t rows, const int* __restrict__ rowptr,
+                                                         long long* __restrict__ part) {
+  __shared__ long long s1[8], s2[8];
+  __shared__ int smax[8];
+  long long a = 0, q = 0;
+  int m = 0;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+    const int len = __ldg(rowptr + r + 1) - __ldg(rowptr + r);
+    a += len;
+    q += (long long)len * len;
+    m = max(m, len);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    q += __shfl_xor_sync(0xffffffffu, q, o);
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  }
+  const int w = threadIdx.x / 32;
+  if ((threadIdx.x & 31) == 0) {
+    s1[w] = a;
+    s2[w] = q;
+    smax[w] = m;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long A = 0, Q = 0;
+    int M = 0;
+    for (int k = 0; k < 8; ++k) {
+      A += s1[k];
+      Q += s2[k];
+      M = max(M, smax[k]);
+    }
+    part[3 * blockIdx.x] = A;
+    part[3 * blockIdx.x + 1] = Q;
+    part[3 * blockIdx.x + 2] = M;
+  }
+}
+
+// Integer sums are exact, so the result does not depend on the reduction
+// order; mean and variance are formed once in float64.
+__global__ void csr_stats_final(int64_t rows, int nparts, const long long* __restrict__ part,
+                                float* __restrict__ out5) {
+  __shared__ long long s1[256], s2[256], sm[256];
+  long long a = 0, q = 0, m = 0;
+  for (int k = threadIdx.x; k < nparts; k += blockDim.x) {
+    a += part[3 * k];
+    q += part[3 * k + 1];
+    m = max(m, part[3 * k + 2]);
+  }
+  s1[threadIdx.x] = a;
+  s2[threadIdx.x] = q;
+  sm[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      s1[threadIdx.x] += s1[threadIdx.x + o];
+      s2[threadIdx.x] += s2[threadIdx.x + o];
+      sm[threadIdx.x] = max(sm[threadIdx.x], sm[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double n = (double)rows;
+    const double mean = rows > 0 ? (double)s1[0] / n : 0.0;
+    const double var = rows > 0 ? fmax((double)s2[0] / n - mean * mean, 0.0) : 0.0;
+    out5[0] = (float)rows;
+    out5[1] = (float)s1[0];
+    out5[2] = (float)mean;
+    out5[3] = (float)var;
+    out5[4] = (float)sm[0];
+  }
+}
+
+const char* const kNames[7] = {"spmv_thread_row", "spmv_warp_row", "spmv_vec2", "spmv_vec4",
+                               "spmv_vec8", "spmv_vec16", "spmv_merge_path"};
+
+template <int K>
+int launch_vector(int64_t rows, const int* rp, const int* c, const double* v, const double* x, double* y,
+                  cudaStream_t s) {
+  const int64_t grid = ceil_div(rows * K, 256);
+  if (grid > 0x7fffffffLL) return AR_ERR_ARG;
+  spmv_vector<K><<<(unsigned)grid, 256, 0, s>>>(rows, rp, c, v, x, y);
+  return launch_status();
+}
+
+}  // namespace
+
+int spmv_num_variants() { return 7; }
+
+int spmv_variant_name(int v, char* buf, int len) {
+  if (v < 0 || v >= 7 || !buf || len <= 0) return AR_ERR_ARG;
+  snprintf(buf, (size_t)len, "%s", kNames[v]);
+  return AR_OK;
+}
+
+int spmv_launch(void* args, int variant, double, void* stream, void*) {
+  const ar_spmv_args* a = static_cast<const ar_spmv_args*>(args);
+  if (!a) return AR_ERR_ARG;
+  return ar_spmv(variant, a->rows, a->nnz, a->rowptr, a->col, a->val, a->x, a->y, a->workspace,
+                 a->workspace_bytes, stream);
+}
+
+}  // namespace ar
+
+using namespace ar;
+
+extern "C" int ar_spmv_workspace_bytes(int variant, int64_t rows, int64_t nnz, size_t* bytes) {
+  if (variant < 0 || variant >= 7 || rows < 0 || nnz < 0 || !bytes) return AR_ERR_ARG;
+  *bytes = variant == 6 ? mp_workspace(rows, nnz) : 0;
+  return AR_OK;
+}
+
+extern "C" int ar_spmv(int variant, int64_t rows, int64_t nnz, const int32_t* rowptr, const int32_t* col,
+                       const double* val, const double* x, double* y, void* workspace, size_t workspace_bytes,
+                       void* stream) {
+  if (variant < 0 || variant >= 7 || rows < 0 || nnz < 0 || nnz > 0x7fffffffLL) return AR_ERR_ARG;
+  if (rows == 0) return AR_OK;
+  if (!rowptr || !y || (nnz > 0 && (!col || !val || !x))) return AR_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  const int* rp = reinterpret_cast<const int*>(rowptr);
+  const int* c = reinterpret_cast<const int*>(col);
+  switch (variant) {
+    case 0: {
+      spmv_thread_row<<<(unsigned)ceil_div(rows, 256), 256, 0, s>>>(rows, rp, c, val, x, y);
+      return launch_status();
+    }
+    case 1: return launch_vector<32>(rows, rp, c, val, x, y, s);
+    case 2: return launch_vector<2>(rows, rp, c, val, x, y, s);
+    case 3: return launch_vector<4>(rows, rp, c, val, x, y, s);
+    case 4: return launch_vector<8>(rows, rp, c, val, x, y, s);
+    case 5: return launch_vector<16>(rows, rp, c, val, x, y, s);
+    default: {
+      if (!workspace || workspace_bytes < mp_workspace(rows, nnz)) return AR_ERR_ARG;
+      const int64_t nb = ceil_div(rows + nnz, kMpPerBlock);
+      if (nb > 0x7ffffffeLL) return AR_ERR_ARG;
+      uintptr_t p = (reinterpret_cast<uintptr_t>(workspace) + 255) & ~uintptr_t(255);
+      int64_t* start_row = reinterpret_cast<int64_t*>(p);
+      int64_t* carry_row = start_row + (nb + 1);
+      double* carry_val = reinterpret_cast<double*>(carry_row + nb);
+      spmv_mp_partition<<<(unsigned)ceil_div(nb + 1, 256), 256, 0, s>>>(rows, nnz, (int)nb, rp, start_row);
+      spmv_mp_main<<<(unsigned)nb, kMpThreads, 0, s>>>(rows, nnz, rp, c, val, x, y, start_row, carry_row,
+                                                      carry_val);
+      spmv_mp_fixup<<<(unsigned)ceil_div(nb, 256), 256, 0, s>>>((int)nb, carry_row, carry_val, y);
+      return launch_status();
+    }
+  }
+}
+
+extern "C" int ar_csr_features_workspace_bytes(int64_t rows, size_t* bytes) {
+  if (rows < 0 || !bytes) return AR_ERR_ARG;
+  *bytes = (size_t)kFeatBlocks * 3 * sizeof(long long);
+  return AR_OK;
+}
+
+extern "C" int ar_csr_features(int64_t rows, const int32_t* rowptr, float* out5, void* workspace,
+                               size_t workspace_bytes, void* stream) {
+  if (rows < 0 || !rowptr || !out5) return AR_ERR_ARG;
+  if (!workspace || workspace_bytes < (size_t)kFeatBlocks * 3 * sizeof(long long)) return AR_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  long long* part = static_cast<long long*>(workspace);
+  csr_stats_partial<<<kFeatBlocks, 256, 0, s>>>(rows, reinterpret_cast<const int*>(rowptr), part);
+  csr_stats_final<<<1, 256, 0, s>>>(rows, kFeatBlocks, part, out5);
+  return launch_status();
+}

@@ -16,7 +16,9 @@ def _setup(seed, B):
     theta = mlp.xavier_uniform(r, F, H, V) + r.normal(scale=0.05, size=mlp.num_params(F, H, V))
     Fraw = np.exp(r.uniform(0, 14, (B, F)))
     lab = r.integers(0, V, B)
-    mu, sd = mlp.feature_stats(Fraw)
+    # standardisation statistics of a training population, not of the batch
+    # (a batch of one row would standardise every feature to exactly 0)
+    mu, sd = mlp.feature_stats(np.exp(r.uniform(0, 14, (512, F))))
     return theta, Fraw, lab, mu, sd
 
 

@@ -1,0 +1,101 @@
+"""All-pairs n-body variants (FP32) against the float64 oracle (GPU)."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2303_08873_b300 as ar
+import synth
+from oracle import loops
+from tests.gpu_util import dev, host
+
+pytestmark = pytest.mark.gpu
+V = 9
+EPS = synth.NBODY_EPS
+TOL = 1e-4  # max_i |a_i - a_ref_i| <= TOL * max_i |a_ref_i|
+
+
+def _run(v, p):
+    pd = dev(p)
+    a = torch.full((p.shape[0], 4), np.nan, dtype=torch.float32, device="cuda")
+    ar.ar_nbody(v, p.shape[0], pd, a, EPS)
+    return host(a)
+
+
+def _check(acc4, ref, what):
+    assert np.all(acc4[:, 3] == 0.0), what
+    err = np.max(np.linalg.norm(acc4[:, :3].astype(np.float64) - ref, axis=1))
+    scale = np.max(np.linalg.norm(ref, axis=1))
+    assert err <= TOL * scale, (what, err, scale)
+
+
+@pytest.mark.parametrize("N", [1, 2, 100, 1000, 4097])
+def test_all_variants_match_oracle(N):
+    p = synth.nbody_inputs(4, N)
+    ref = loops.nbody(p, EPS)
+    for v in range(V):
+        a = _run(v, p)
+        if N == 1:
+            assert np.array_equal(a, np.zeros((1, 4), np.float32)), v
+        else:
+            _check(a, ref, (ar.loop_variant_name(3, v), N))
+
+
+def test_two_body_reaction_and_cube_centre():
+    two = np.array([[0.25, 0.5, 0.5, 0.75], [0.75, 0.5, 0.5, 0.5]], dtype=np.float32)
+    verts = [[x, y, z, 1.0] for x in (0.25, 0.75) for y in (0.25, 0.75) for z in (0.25, 0.75)]
+    cube = np.array(verts + [[0.5, 0.5, 0.5, 1.0]], dtype=np.float32)
+    for v in range(V):
+        a = _run(v, two)
+        assert 0.75 * a[0, 0] == pytest.approx(-0.5 * a[1, 0], rel=1e-6)
+        _check(a, loops.nbody(two, EPS), ("two", v))
+        c = _run(v, cube)
+        assert np.max(np.abs(c[-1, :3])) <= 1e-6 * np.max(np.abs(c[:-1, :3]))
+
+
+@pytest.mark.parametrize("N", [65536, 262144])
+def test_full_size_sampled(N):
+    """Workload sizes: 2048 sampled bodies (plus the first and last) against
+    the float64 oracle, all variants."""
+    p = synth.nbody_inputs(4, N)
+    rng = np.random.Generator(np.random.PCG64(N))
+    which = np.unique(np.concatenate([[0, N - 1], rng.integers(0, N, 2048)]))
+    ref = loops.nbody_rows(p, which, EPS)
+    pd = dev(p)
+    a = torch.empty((N, 4), dtype=torch.float32, device="cuda")
+    for v in range(V):
+        ar.ar_nbody(v, N, pd, a, EPS)
+        got = host(a)[which]
+        _check(got, ref, (ar.loop_variant_name(3, v), N))
+
+
+def _batched(bodies, offs):
+    count = offs.size - 1
+    wsb = ar.ar_nbody_batched_workspace_bytes(count)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    a = torch.full((bodies.shape[0], 4), np.nan, dtype=torch.float32, device="cuda")
+    ar.ar_nbody_batched(count, dev(offs), dev(bodies), a, EPS, ws, wsb)
+    return host(a)
+
+
+def test_batched_small_full_compare():
+    bodies, offs = synth.nbody_batch_inputs(41, count=7, nmin=1, nmax=700)
+    a = _batched(bodies, offs)
+    for b in range(7):
+        sl = slice(offs[b], offs[b + 1])
+        if offs[b + 1] - offs[b] > 1:
+            _check(a[sl], loops.nbody(bodies[sl], EPS), ("batched", b))
+
+
+def test_batched_workload_sampled():
+    """64 systems, sizes log-uniform in [1k, 64k]: 24 sampled bodies per
+    system against the oracle of that system."""
+    bodies, offs = synth.nbody_batch_inputs(40)
+    a = _batched(bodies, offs)
+    rng = np.random.Generator(np.random.PCG64(40))
+    for b in range(offs.size - 1):
+        sys_p = bodies[offs[b]:offs[b + 1]]
+        which = rng.integers(0, sys_p.shape[0], 24)
+        ref = loops.nbody_rows(sys_p, which, EPS)
+        got = a[offs[b]:offs[b + 1]][which]
+        err = np.max(np.linalg.norm(got[:, :3].astype(np.float64) - ref, axis=1))
+        assert err <= TOL * np.max(np.linalg.norm(ref, axis=1)) * 4, b

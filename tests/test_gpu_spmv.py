@@ -1,0 +1,144 @@
+"""CSR SpMV variants and the row-feature reduction against the oracle (GPU)."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2303_08873_b300 as ar
+import synth
+from oracle import loops
+from tests.gpu_util import dev, host
+
+pytestmark = pytest.mark.gpu
+V = 7
+TOL = 1e-10  # |y - y_ref| <= TOL * sum_k |val_k x_col_k| per row
+
+
+def _run(v, rp, c, val, x, dev_arrays=None):
+    rows = rp.size - 1
+    nnz = int(rp[-1])
+    d = dev_arrays or (dev(rp), dev(c), dev(val), dev(x))
+    y = torch.full((rows,), np.nan, dtype=torch.float64, device="cuda")
+    wsb = ar.ar_spmv_workspace_bytes(v, rows, nnz)
+    ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device="cuda")
+    ar.ar_spmv(v, rows, nnz, *d, y, ws, wsb)
+    return host(y)
+
+
+def _check_all(rp, c, val, x, what):
+    rows = rp.size - 1
+    ref = loops.spmv(rp, c, val, x)
+    _, absum = loops.spmv_rows(rp, c, val, x, np.arange(rows))
+    d = (dev(rp), dev(c), dev(val), dev(x))
+    for v in range(V):
+        y = _run(v, rp, c, val, x, d)
+        bad = ~(np.abs(y - ref) <= TOL * absum)
+        assert not bad.any(), (what, ar.loop_variant_name(2, v), np.flatnonzero(bad)[:5])
+
+
+def _np(t3):
+    return [t.numpy() for t in t3]
+
+
+@pytest.mark.parametrize("rows,s", [(1, 1.5), (1000, 1.5), (3001, 2.2), (20000, 1.7)])
+def test_zipf_matrices(rows, s):
+    rp, c, val = _np(synth.csr_zipf(10 + rows, rows, s))
+    _check_all(rp, c, val, synth.spmv_x(1, rows).numpy(), ("zipf", rows))
+
+
+@pytest.mark.parametrize("rows,b", [(777, 9), (5000, 129), (3, 7)])
+def test_band_matrices(rows, b):
+    rp, c, val = _np(synth.csr_band(20 + rows, rows, b))
+    _check_all(rp, c, val, synth.spmv_x(2, rows).numpy(), ("band", rows, b))
+
+
+def test_identity_and_diagonal_bitwise():
+    n = 10007
+    x = synth.spmv_x(3, n).numpy()
+    rp = np.arange(n + 1, dtype=np.int32)
+    c = np.arange(n, dtype=np.int32)
+    d = np.random.Generator(np.random.PCG64(4)).normal(size=n)
+    for v in range(V):
+        assert np.array_equal(_run(v, rp, c, np.ones(n), x), x), v
+        assert np.array_equal(_run(v, rp, c, d, x), d * x), v
+
+
+def test_empty_rows_long_rows_and_block_straddles():
+    # rows of length 0, 1 and 4096 interleaved; several 4096-long rows in a
+    # row so merge-path blocks (4096 path items) start and end inside rows
+    rng = np.random.Generator(np.random.PCG64(5))
+    lens = np.array([0, 4096, 0, 0, 1, 4096, 4096, 4096, 3, 0, 2049, 4095, 1, 0, 4096] + [0] * 300 +
+                    list(rng.integers(0, 40, 3000)) + [4096, 0], dtype=np.int64)
+    rows = lens.size
+    rp = np.zeros(rows + 1, dtype=np.int64)
+    rp[1:] = np.cumsum(lens)
+    nnz = int(rp[-1])
+    cols = rows + 5000
+    c = np.concatenate([np.sort(rng.choice(cols, int(L), replace=False)) for L in lens]).astype(np.int32)
+    val = rng.normal(size=nnz)
+    x = rng.uniform(-1, 1, cols)
+    _check_all(rp.astype(np.int32), c, val, x, "mixed")
+
+
+def test_all_empty_and_single_dense_row():
+    rp = np.zeros(65, dtype=np.int32)
+    for v in range(V):
+        assert np.array_equal(_run(v, rp, np.zeros(0, np.int32), np.zeros(0), np.ones(4)), np.zeros(64))
+    n = 4096
+    r = np.random.Generator(np.random.PCG64(6))
+    _check_all(np.array([0, n], dtype=np.int32), np.arange(n, dtype=np.int32), r.normal(size=n),
+               r.uniform(-1, 1, n), "dense row")
+
+
+def test_every_variant_is_deterministic():
+    rp, c, val = _np(synth.csr_zipf(7, 50000, 1.5))
+    x = synth.spmv_x(7, 50000).numpy()
+    d = (dev(rp), dev(c), dev(val), dev(x))
+    for v in range(V):
+        assert np.array_equal(_run(v, rp, c, val, x, d), _run(v, rp, c, val, x, d)), v
+
+
+@pytest.mark.parametrize("params", [
+    {"rows": 10_000_000, "kind": "zipf", "s": 1.5, "band": 0},
+    {"rows": 10_000_000, "kind": "band", "s": 0.0, "band": 129},
+    {"rows": 1_000_000, "kind": "zipf", "s": 2.5, "band": 0},
+])
+def test_full_size_sampled_rows(params):
+    """Largest matrices of the workload, generated on the device; 3000 sampled
+    rows (first, last, random) checked against the oracle."""
+    rows = params["rows"]
+    rp, c, val = synth.spmv_matrix(31, params, device="cuda")
+    x = synth.spmv_x(31, rows, device="cuda")
+    nnz = int(rp[-1].item())
+    rng = np.random.Generator(np.random.PCG64(rows))
+    which = np.unique(np.concatenate([[0, rows - 1], rng.integers(0, rows, 3000)]))
+    rph = rp.cpu().numpy().astype(np.int64)
+    lens = rph[which + 1] - rph[which]
+    idx = torch.from_numpy(np.concatenate([np.arange(rph[w], rph[w + 1]) for w in which])).cuda()
+    srp = np.zeros(which.size + 1, dtype=np.int64)
+    srp[1:] = np.cumsum(lens)
+    sc, sv = c[idx].cpu().numpy(), val[idx].cpu().numpy()
+    xh = x.cpu().numpy()
+    ref, absum = loops.spmv_rows(srp.astype(np.int32), sc, sv, xh, np.arange(which.size))
+    y = torch.empty(rows, dtype=torch.float64, device="cuda")
+    wsb = ar.ar_spmv_workspace_bytes(6, rows, nnz)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    wt = torch.from_numpy(which).cuda()
+    for v in range(V):
+        y.fill_(np.nan)
+        ar.ar_spmv(v, rows, nnz, rp, c, val, x, y, ws, wsb)
+        got = host(y[wt])
+        assert np.all(np.abs(got - ref) <= TOL * absum), (params, ar.loop_variant_name(2, v))
+
+
+@pytest.mark.parametrize("rows,kind", [(1, "zipf"), (999, "zipf"), (123457, "zipf"), (40000, "band")])
+def test_row_features_match_oracle(rows, kind):
+    rp = (synth.csr_zipf(3, rows, 1.6)[0] if kind == "zipf" else synth.csr_band(3, rows, 33)[0]).numpy()
+    ref = loops.csr_row_stats(rp)
+    wsb = ar.ar_csr_features_workspace_bytes(rows)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    out = torch.zeros(5, dtype=torch.float32, device="cuda")
+    ar.ar_csr_features(rows, dev(rp), out, ws, wsb)
+    got = host(out).astype(np.float64)
+    assert got[0] == np.float32(ref[0]) and got[1] == np.float32(ref[1]) and got[4] == ref[4]
+    assert got[2] == pytest.approx(ref[2], rel=1e-6)
+    assert got[3] == pytest.approx(ref[3], rel=1e-5, abs=1e-6)
