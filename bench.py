@@ -230,6 +230,7 @@ def run_ours(args):
     k0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     k1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     big = SIZES[-1]
+    torch.cuda.nvtx.range_push("bench_timed")
     e0.record(stream)
     for t in range(args.steps):
         for n in SIZES:
@@ -239,6 +240,7 @@ def run_ours(args):
             if n == big:
                 k1[t].record(stream)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     stream.synchronize()
     torch.cuda.synchronize()
     clk = clocks.stop()

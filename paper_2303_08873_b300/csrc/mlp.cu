@@ -30,6 +30,8 @@ constexpr int LD = BS + 1;    // padded row length
 constexpr int MAXF = 8;
 constexpr int MAXV = 32;
 constexpr float B1 = 0.9f, B2 = 0.999f, EPS = 1e-8f;
+// 1 - beta as separate constants: 1 - 0.999f rounds to 0.00099998713 in float32
+constexpr float OMB1 = 0.1f, OMB2 = 0.001f;
 
 __host__ __device__ inline int nparams(int F, int H, int V) { return H * F + H + H * H + H + V * H + V; }
 
@@ -293,8 +295,8 @@ __device__ void minibatch_grad(const Smem& m, int F, int V, int Bt, const float*
 }
 
 __device__ __forceinline__ void adam_one(float* th, float g, float* m, float* v, float c1, float c2, float lr) {
-  const float mn = B1 * *m + (1.f - B1) * g;
-  const float vn = B2 * *v + (1.f - B2) * g * g;
+  const float mn = B1 * *m + OMB1 * g;
+  const float vn = B2 * *v + OMB2 * g * g;
   *m = mn;
   *v = vn;
   *th -= lr * (mn / c1) / (sqrtf(vn / c2) + EPS);

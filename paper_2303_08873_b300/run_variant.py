@@ -1,0 +1,73 @@
+"""Run one variant of one region body on a seeded synthetic case.
+
+A small driver for profilers (ncu) and quick timing: builds the inputs with
+``synth``, launches the variant ``--reps`` times through the C ABI and prints
+the mean time per launch (CUDA events) and the algorithmic bandwidth or flop
+rate.
+
+  python -m paper_2303_08873_b300.run_variant jacobi7 13 --size 320 --sweeps 1
+  python -m paper_2303_08873_b300.run_variant spmv 6 --size 2000000
+  python -m paper_2303_08873_b300.run_variant nbody 4 --size 65536
+  python -m paper_2303_08873_b300.run_variant daxpy 8 --size 33554432
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import torch
+
+import paper_2303_08873_b300 as ar
+import synth
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("loop", choices=["daxpy", "jacobi7", "spmv", "nbody"])
+    p.add_argument("variant", type=int)
+    p.add_argument("--size", type=int, required=True, help="n (daxpy), N (jacobi7, nbody) or rows (spmv)")
+    p.add_argument("--sweeps", type=int, default=1)
+    p.add_argument("--reps", type=int, default=3)
+    p.add_argument("--zipf", type=float, default=1.5, help="Zipf exponent of the spmv row lengths")
+    a = p.parse_args()
+    dev = torch.device("cuda", 0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if a.loop == "daxpy":
+        al, x, y = synth.daxpy_inputs(1, a.size)
+        x, y = torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev)
+        run = lambda: ar.ar_daxpy(a.variant, a.size, al, x, y)  # noqa: E731
+        work, unit = 24.0 * a.size, "GB/s"
+    elif a.loop == "jacobi7":
+        u0 = torch.from_numpy(synth.grid_inputs(1000 + a.size, a.size)).to(dev)
+        out, wk = torch.empty_like(u0), torch.empty_like(u0)
+        run = lambda: ar.ar_jacobi7(a.variant, a.size, a.sweeps, u0, out, wk)  # noqa: E731
+        work, unit = 16.0 * a.size ** 3 * a.sweeps, "GB/s"
+    elif a.loop == "spmv":
+        rp, c, v = synth.csr_zipf(31, a.size, a.zipf, device="cuda")
+        x = synth.spmv_x(31, a.size, device="cuda")
+        y = torch.empty(a.size, dtype=torch.float64, device=dev)
+        nnz = int(rp[-1].item())
+        wsb = ar.ar_spmv_workspace_bytes(a.variant, a.size, nnz)
+        ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=dev)
+        run = lambda: ar.ar_spmv(a.variant, a.size, nnz, rp, c, v, x, y, ws, wsb)  # noqa: E731
+        work, unit = 12.0 * nnz + 4.0 * (a.size + 1) + 16.0 * a.size, "GB/s"
+    else:
+        pos = torch.from_numpy(synth.nbody_inputs(4, a.size)).to(dev)
+        acc = torch.empty_like(pos)
+        run = lambda: ar.ar_nbody(a.variant, a.size, pos, acc, synth.NBODY_EPS)  # noqa: E731
+        work, unit = 20.0 * a.size ** 2, "GFLOP/s"
+    run()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(a.reps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.reps
+    print(json.dumps({"loop": a.loop, "variant": a.variant, "name": ar.loop_variant_name(
+        ["daxpy", "jacobi7", "spmv", "nbody"].index(a.loop), a.variant), "size": a.size, "ms": ms,
+        "rate": work / (ms * 1e-3) / 1e9, "unit": unit}))
+
+
+if __name__ == "__main__":
+    main()
