@@ -112,6 +112,31 @@ int ar_spmv_workspace_bytes(int variant, int64_t rows, int64_t nnz, size_t *byte
 int ar_spmv(int variant, int64_t rows, int64_t nnz, const int32_t *rowptr, const int32_t *col, const double *val,
             const double *x, double *y, void *workspace, size_t workspace_bytes, void *stream);
 
+/* Merge-path SpMV (variant 6 above) for callers that cannot allocate device
+ * memory: its scratch is a fixed array of AR_SPMV_NOALLOC_SCRATCH_BYTES
+ * compiled into this library, so the caller passes only inputs and outputs.
+ * This entry point has no counterpart in the paper; it exists for callers
+ * such as plug-ins handed a device whose memory another allocator already
+ * owns, or latency-critical loops that must not pay the device-wide
+ * synchronisation cudaMalloc/cudaFree imply.
+ *  - Capacity: rows + nnz <= AR_SPMV_NOALLOC_MAX_PATH (about 1.43e9, enough
+ *    for every matrix of the workload); larger problems return AR_ERR_ARG
+ *    with a message on stderr and launch nothing.
+ *  - Memory: every GPU that loads the library holds the 8 MiB array until the
+ *    process exits.  The first call on a device looks up the array's device
+ *    address (cudaGetSymbolAddress, once per device, with that device
+ *    current); make that first call before any stream capture.
+ *  - No allocation: calls no cudaMalloc, cudaFree or allocating routine.
+ *  - Sharing: all calls on a device use the same array; the kernels write
+ *    every scratch word before reading it, so nothing needs clearing, but two
+ *    calls that overlap on the GPU (different streams, no ordering) race on
+ *    the scratch and give wrong results.  Order them on one stream.
+ * Returns AR_OK, AR_ERR_ARG (bad arguments or over capacity) or AR_ERR_CUDA. */
+#define AR_SPMV_NOALLOC_SCRATCH_BYTES (8u << 20)
+#define AR_SPMV_NOALLOC_MAX_PATH ((long long)(((AR_SPMV_NOALLOC_SCRATCH_BYTES - 8u) / 24u) * 4096u))
+int ar_spmv_merge_path_noalloc(int64_t rows, int64_t nnz, const int32_t *rowptr, const int32_t *col,
+                               const double *val, const double *x, double *y, void *stream);
+
 /* Row-length features of a CSR matrix, the learned selector's inputs: out5 =
  * (rows, nnz, mean, population variance, max) of rowptr[r+1] - rowptr[r], as
  * float32 in device memory.  Integer sums are exact; mean and variance are

@@ -108,6 +108,7 @@ _SIGS = {
     "ar_jacobi7": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp, _vp]),
     "ar_spmv_workspace_bytes": (_i, [_i, _i64, _i64, ctypes.POINTER(_sz)]),
     "ar_spmv": (_i, [_i, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "ar_spmv_merge_path_noalloc": (_i, [_i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "ar_csr_features_workspace_bytes": (_i, [_i64, ctypes.POINTER(_sz)]),
     "ar_csr_features": (_i, [_i64, _vp, _vp, _vp, _sz, _vp]),
     "ar_nbody": (_i, [_i, _i64, _vp, _vp, _f, _vp]),
@@ -200,6 +201,11 @@ def ar_spmv_workspace_bytes(variant, rows, nnz):
 def ar_spmv(variant, rows, nnz, rowptr, col, val, x, y, workspace=None, workspace_bytes=0, stream=None):
     return check(lib.ar_spmv(variant, rows, nnz, ptr(rowptr), ptr(col), ptr(val), ptr(x), ptr(y), ptr(workspace),
                              workspace_bytes, stream_handle(stream)))
+
+
+def ar_spmv_merge_path_noalloc(rows, nnz, rowptr, col, val, x, y, stream=None):
+    return check(lib.ar_spmv_merge_path_noalloc(rows, nnz, ptr(rowptr), ptr(col), ptr(val), ptr(x), ptr(y),
+                                                stream_handle(stream)))
 
 
 def ar_csr_features_workspace_bytes(rows):
@@ -430,7 +436,7 @@ class Region:
 
 
 __all__ = ["ArError", "Region", "ArDaxpyArgs", "ArJacobi7Args", "ArSpmvArgs", "ArNbodyArgs", "ar_spmv",
-           "ar_spmv_workspace_bytes", "ar_csr_features", "ar_csr_features_workspace_bytes", "ar_nbody",
+           "ar_spmv_workspace_bytes", "ar_spmv_merge_path_noalloc", "ar_csr_features", "ar_csr_features_workspace_bytes", "ar_nbody",
            "ar_nbody_batched", "ar_nbody_batched_workspace_bytes", "LAUNCH_FN", "FAKE_TIME_FN", "lib", "ptr",
            "stream_handle", "check", "loop_num_variants", "loop_default_variant", "loop_variant_name", "ar_daxpy",
            "ar_jacobi7", "ar_mlp_num_params", "ar_mlp_forward", "ar_mlp_grad", "ar_mlp_adam", "ar_mlp_train",

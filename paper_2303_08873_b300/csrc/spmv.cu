@@ -16,6 +16,7 @@
 // deterministically by the first thread of each straddling run, rows that
 // straddle blocks by a second small kernel over the per-block carries.
 #include <cstdio>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -331,5 +332,65 @@ extern "C" int ar_csr_features(int64_t rows, const int32_t* rowptr, float* out5,
   long long* part = static_cast<long long*>(workspace);
   csr_stats_partial<<<kFeatBlocks, 256, 0, s>>>(rows, reinterpret_cast<const int*>(rowptr), part);
   csr_stats_final<<<1, 256, 0, s>>>(rows, kFeatBlocks, part, out5);
+  return launch_status();
+}
+
+// ------------------------------------------------------------ no-allocation entry point
+// Merge-path SpMV whose scratch (partition rows and per-block carries) lives
+// in a fixed device array compiled into this library, for callers that must
+// not allocate device memory.  The array exists on every GPU that loads the
+// library and is held until the process exits.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)AR_SPMV_NOALLOC_SCRATCH_BYTES;
+static __device__ __align__(256) unsigned char g_spmv_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_spmv_scratch on the current device, looked up once per
+// device (in host code the symbol names a host-side stand-in, not device
+// memory).  Returns nullptr if the lookup fails.
+void* scratch_on_current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_spmv_scratch) != cudaSuccess) return nullptr;
+    g_scratch_ptr[dev] = p;
+  }
+  return g_scratch_ptr[dev];
+}
+
+}  // namespace
+
+extern "C" int ar_spmv_merge_path_noalloc(int64_t rows, int64_t nnz, const int32_t* rowptr, const int32_t* col,
+                                          const double* val, const double* x, double* y, void* stream) {
+  if (rows < 0 || nnz < 0 || nnz > 0x7fffffffLL) return AR_ERR_ARG;
+  if (rows == 0) return AR_OK;
+  if (!rowptr || !y || (nnz > 0 && (!col || !val || !x))) return AR_ERR_ARG;
+  if (rows + nnz > (int64_t)AR_SPMV_NOALLOC_MAX_PATH) {
+    fprintf(stderr,
+            "ar_spmv_merge_path_noalloc: rows + nnz = %lld exceeds the fixed scratch limit %lld; "
+            "use ar_spmv with a caller-provided workspace\n",
+            (long long)(rows + nnz), (long long)AR_SPMV_NOALLOC_MAX_PATH);
+    return AR_ERR_ARG;
+  }
+  void* base = scratch_on_current_device();
+  if (!base) return AR_ERR_CUDA;
+  const int64_t nb = ceil_div(rows + nnz, kMpPerBlock);
+  // every scratch word the kernels read is written earlier in the same call:
+  // no clearing is needed between calls
+  int64_t* start_row = static_cast<int64_t*>(base);
+  int64_t* carry_row = start_row + (nb + 1);
+  double* carry_val = reinterpret_cast<double*>(carry_row + nb);
+  cudaStream_t s = as_stream(stream);
+  const int* rp = reinterpret_cast<const int*>(rowptr);
+  const int* c = reinterpret_cast<const int*>(col);
+  spmv_mp_partition<<<(unsigned)ceil_div(nb + 1, 256), 256, 0, s>>>(rows, nnz, (int)nb, rp, start_row);
+  spmv_mp_main<<<(unsigned)nb, kMpThreads, 0, s>>>(rows, nnz, rp, c, val, x, y, start_row, carry_row, carry_val);
+  spmv_mp_fixup<<<(unsigned)ceil_div(nb, 256), 256, 0, s>>>((int)nb, carry_row, carry_val, y);
   return launch_status();
 }
