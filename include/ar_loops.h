@@ -73,8 +73,13 @@ int ar_daxpy(int variant, int64_t n, double a, const double *x, double *y, void 
  * 64x4, 128x2}; variant = 4*family + shape.  The tma family needs even N
  * (16-byte row pitch), N >= BX+4 and 16-byte aligned buffers; otherwise the
  * tma and df families run the smem kernel of the same shape.  Default: naive 32x8 (variant 1).
- * `status` (device int, may be NULL) receives AR_ERR_TIMEOUT if a bounded
- * wait inside a tma kernel gave up; the caller zeroes it. */
+ * `status` (device int[2], may be NULL): status[0] receives AR_ERR_TIMEOUT if
+ * a bounded wait inside a tma/df kernel gave up (the caller zeroes it);
+ * status[1] is scratch for the df family, which with a status array and 3+
+ * sweeps keeps float pairs (8 bytes per unknown) in out/work between sweeps
+ * and falls back to float64 storage for the whole call when a value after
+ * the first sweep lies outside the float-pair range.  Without a status array
+ * every df sweep converts from and to float64. */
 typedef struct ar_jacobi7_args {
   int N;
   int sweeps;

@@ -150,8 +150,11 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
-// (v0 + ... + v5) / 6 in float-pair arithmetic, returned in float64.
-__device__ __forceinline__ double df_avg6(float2 v0, float2 v1, float2 v2, float2 v3, float2 v4, float2 v5) {
+// (v0 + ... + v5) / 6 in float-pair arithmetic: returns the unevaluated
+// pair (p, pe) with p + pe = the average to ~2^-46 relative.  The hi parts
+// are summed exactly by a TwoSum chain, the lo parts and the chain's errors
+// in plain float, then the sum is multiplied by 1/6 as a float pair.
+__device__ __forceinline__ float2 df_avg6(float2 v0, float2 v1, float2 v2, float2 v3, float2 v4, float2 v5) {
   float s, c, e;
   two_sum(v0.x, v1.x, s, c);
   two_sum(s, v2.x, s, e);
@@ -167,7 +170,23 @@ __device__ __forceinline__ double df_avg6(float2 v0, float2 v1, float2 v2, float
   float pe = fmaf(s, kSixthHi, -p);
   pe = fmaf(s, kSixthLo, pe);
   pe = fmaf(c, kSixthHi, pe);
-  return f2d_bits(p) + f2d_bits(pe);
+  return make_float2(p, pe);
+}
+
+__device__ __forceinline__ double pair_to_double(float2 v) { return f2d_bits(v.x) + f2d_bits(v.y); }
+
+__device__ __forceinline__ float2 pair_normalize(float2 v) {
+  float hi, lo;
+  two_sum(v.x, v.y, hi, lo);
+  return make_float2(hi, lo);
+}
+
+// A float64 value the float-pair path cannot carry to later sweeps.
+__device__ __forceinline__ bool outside_pair_range(double v) {
+  const long long b = __double_as_longlong(v);
+  if ((b << 1) == 0) return false;
+  const int e = (int)((b >> 52) & 0x7ff);
+  return e < 949 || e > 1140;
 }
 
 // ------------------------------------------------------------------ TMA ring
@@ -177,14 +196,26 @@ struct TmaGeom {
   static constexpr int PY = BY + 2;
   static constexpr int PLANE = PX * PY;          // elements per plane
   static constexpr int GROUP = PLANE * kDZ;      // elements per box
+  static constexpr int RING = kRing * kDZ;       // planes resident
   static constexpr uint32_t BYTES = GROUP * 8u;
   static constexpr size_t SMEM = (size_t)kRing * BYTES + 128;
 };
 
-template <int BX, int BY, bool DF>
+// Sweep modes of the TMA kernel.  Buffers between the sweeps of one df call
+// may hold float pairs (8 bytes per unknown, like a float64):
+//   M_NATIVE  float64 in, float64 out, float64 arithmetic
+//   M_DD      float64 in, float64 out, float-pair arithmetic; points whose
+//             inputs are outside the float-pair range are redone in float64;
+//             if `flag` is given, any output outside that range sets *flag
+//   M_DP      float64 in, float pairs out      } when *flag is set (by the
+//   M_PP      float pairs in, float pairs out  } first sweep) these run as
+//   M_PD      float pairs in, float64 out      } M_NATIVE on float64 buffers
+enum Mode { M_NATIVE = 0, M_DD = 1, M_DP = 2, M_PP = 3, M_PD = 4 };
+
+template <int BX, int BY, int MODE>
 __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUtensorMap tmap, int N, int KC,
-                                                     const double* __restrict__ in, double* __restrict__ out,
-                                                     int* status) {
+                                                     const double* __restrict__ in, void* __restrict__ outv,
+                                                     int* status, int* flag) {
   using G = TmaGeom<BX, BY>;
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[kRing];
@@ -196,6 +227,10 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
   const int kb = blockIdx.z * KC;
   const int kc = min(KC, N - kb);                 // output planes of this block
   const int ngroups = (kc + 2 + kDZ - 1) / kDZ;   // boxes covering planes kb-1 .. kb+kc
+  // block-uniform: the flag was settled by an earlier launch on this stream
+  const bool native = (MODE == M_NATIVE) || (MODE >= M_DP && flag != nullptr && *flag != 0);
+  const bool split_boxes = !native && (MODE == M_DD || MODE == M_DP);
+  const bool pair_out = !native && (MODE == M_DP || MODE == M_PP);
 
   if (tid == 0) {
     for (int r = 0; r < kRing; ++r) mbar_init(smem_addr(&bars[r]), 1);
@@ -217,6 +252,12 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
   const int64_t NN = (int64_t)N * N;
   const int64_t col = (int64_t)j * N + i;
   const int c = (ty + 1) * G::PX + tx + 2;
+  double* outd = static_cast<double*>(outv);
+  float2* outp = static_cast<float2*>(outv);
+  // z queue: centres of planes p-1 and p (ring index qm = (p-1) mod RING)
+  double dm = 0.0, d0 = 0.0;
+  float2 fm = make_float2(0.f, 0.f), f0 = make_float2(0.f, 0.f);
+  int qm = 0;
   int next_p = 1;
   int g = 0;
   bool failed = false;
@@ -227,45 +268,61 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
       failed = true;
       break;
     }
-    if constexpr (DF) {
+    if (split_boxes) {
       double* box = buf + (size_t)slot * G::GROUP;
-      for (int e = tid; e < G::GROUP; e += BX * BY) {
-        const float2 f = df_split(box[e]);
-        reinterpret_cast<float2*>(box)[e] = f;
-      }
+      for (int e = tid; e < G::GROUP; e += BX * BY) reinterpret_cast<float2*>(box)[e] = df_split(box[e]);
       __syncthreads();
+    }
+    if (g == 0) {  // centres of planes 0 and 1 (relative) start the queue
+      if (native) {
+        dm = buf[c];
+        d0 = buf[G::PLANE + c];
+      } else {
+        fm = reinterpret_cast<const float2*>(buf)[c];
+        f0 = reinterpret_cast<const float2*>(buf)[G::PLANE + c];
+      }
     }
     const int plast = min(kc, (g + 1) * kDZ - 2);
     for (int p = next_p; p <= plast; ++p) {
-      const double* pm = buf + (size_t)(((p - 1) / kDZ) % kRing) * G::GROUP + ((p - 1) % kDZ) * G::PLANE;
-      const double* pc = buf + (size_t)((p / kDZ) % kRing) * G::GROUP + (p % kDZ) * G::PLANE;
-      const double* pp = buf + (size_t)(((p + 1) / kDZ) % kRing) * G::GROUP + ((p + 1) % kDZ) * G::PLANE;
-      if (inside) {
-        const int k = kb + p - 1;
-        double r;
-        if constexpr (DF) {
-          const float2* qm = reinterpret_cast<const float2*>(pm);
-          const float2* qc = reinterpret_cast<const float2*>(pc);
-          const float2* qp = reinterpret_cast<const float2*>(pp);
-          r = df_avg6(qc[c - 1], qc[c + 1], qc[c - G::PX], qc[c + G::PX], qm[c], qp[c]);
-          if (r != r) {  // a value outside the float-pair range: redo in float64
-            double s = at(in, N, i - 1, j, k) + at(in, N, i + 1, j, k);
-            s += at(in, N, i, j - 1, k);
-            s += at(in, N, i, j + 1, k);
-            s += at(in, N, i, j, k - 1);
-            s += at(in, N, i, j, k + 1);
-            r = s * kSixth;
+      const int q0 = (qm + 1 == G::RING) ? 0 : qm + 1;
+      const int qp = (q0 + 1 == G::RING) ? 0 : q0 + 1;
+      const int k = kb + p - 1;
+      if (native) {
+        const double* pc = buf + (size_t)q0 * G::PLANE;
+        const double up = buf[(size_t)qp * G::PLANE + c];
+        double s = pc[c - 1] + pc[c + 1];
+        s += pc[c - G::PX];
+        s += pc[c + G::PX];
+        s += dm;
+        s += up;
+        if (inside) outd[(int64_t)k * NN + col] = s * kSixth;
+        dm = d0;
+        d0 = up;
+      } else {
+        const float2* pc = reinterpret_cast<const float2*>(buf) + (size_t)q0 * G::PLANE;
+        const float2 up = reinterpret_cast<const float2*>(buf)[(size_t)qp * G::PLANE + c];
+        const float2 r = df_avg6(pc[c - 1], pc[c + 1], pc[c - G::PX], pc[c + G::PX], fm, up);
+        if (inside) {
+          if (pair_out) {
+            outp[(int64_t)k * NN + col] = pair_normalize(r);
+          } else {
+            double v = pair_to_double(r);
+            if (MODE == M_DD && v != v) {  // an input outside the float-pair range: redo in float64
+              double sd = at(in, N, i - 1, j, k) + at(in, N, i + 1, j, k);
+              sd += at(in, N, i, j - 1, k);
+              sd += at(in, N, i, j + 1, k);
+              sd += at(in, N, i, j, k - 1);
+              sd += at(in, N, i, j, k + 1);
+              v = sd * kSixth;
+            }
+            if (MODE == M_DD && flag != nullptr && outside_pair_range(v)) atomicOr(flag, 1);
+            outd[(int64_t)k * NN + col] = v;
           }
-        } else {
-          double s = pc[c - 1] + pc[c + 1];
-          s += pc[c - G::PX];
-          s += pc[c + G::PX];
-          s += pm[c];
-          s += pp[c];
-          r = s * kSixth;
         }
-        out[(int64_t)k * NN + col] = r;
+        fm = f0;
+        f0 = up;
       }
+      qm = q0;
     }
     if (plast + 1 > next_p) next_p = plast + 1;
     // every reader of box g-1 is past this barrier: its slot takes box g+2
@@ -310,14 +367,21 @@ int launch_smem(int N, const double* in, double* out, cudaStream_t s) {
   return launch_status();
 }
 
-template <int BX, int BY, bool DF>
-int launch_tma(int N, const double* in, double* out, int* status, cudaStream_t s) {
+// TMA staging needs a 16-byte row pitch (even N), a grid at least one box wide
+// and 16-byte aligned buffers; decided once per call so that every sweep of a
+// call uses the same buffer format.
+bool tma_usable(int shape, int N, const void* a, const void* b, const void* c) {
+  const int PX = kShapeX[shape] + 4, PY = kShapeY[shape] + 2;
+  return !(N & 1) && N >= PX && N >= PY && N >= kDZ && aligned16(a) && (!b || aligned16(b)) && (!c || aligned16(c));
+}
+
+template <int BX, int BY, int MODE>
+int launch_tma(int N, const double* in, void* out, int* status, int* flag, cudaStream_t s) {
   using G = TmaGeom<BX, BY>;
-  if ((N & 1) || N < G::PX || N < G::PY || N < kDZ || !aligned16(in)) return launch_smem<BX, BY>(N, in, out, s);
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(jacobi_tma<BX, BY, DF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr_err = cudaFuncSetAttribute(jacobi_tma<BX, BY, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)G::SMEM);
   });
   if (attr_err != cudaSuccess) return AR_ERR_CUDA;
@@ -332,27 +396,32 @@ int launch_tma(int N, const double* in, double* out, int* status, cudaStream_t s
   int KC = chunk_planes(N, cb, resident, kDZ - 2, 8 * kDZ - 2);
   KC = (int)(ceil_div(KC + 2, kDZ) * kDZ - 2);
   dim3 grid((unsigned)ceil_div(N, BX), (unsigned)ceil_div(N, BY), (unsigned)ceil_div(N, KC));
-  jacobi_tma<BX, BY, DF><<<grid, BX * BY, G::SMEM, s>>>(map, N, KC, in, out, status);
+  jacobi_tma<BX, BY, MODE><<<grid, BX * BY, G::SMEM, s>>>(map, N, KC, in, out, status, flag);
   return launch_status();
 }
 
 template <int BX, int BY>
-int launch_family(int fam, int N, const double* in, double* out, int* status, cudaStream_t s) {
-  switch (fam) {
-    case 0: return launch_naive<BX, BY>(N, in, out, s);
-    case 1: return launch_smem<BX, BY>(N, in, out, s);
-    case 2: return launch_tma<BX, BY, false>(N, in, out, status, s);
-    default: return launch_tma<BX, BY, true>(N, in, out, status, s);
+int launch_family(int fam, int mode, bool tma, int N, const double* in, double* out, int* status, int* flag,
+                  cudaStream_t s) {
+  if (fam == 0) return launch_naive<BX, BY>(N, in, out, s);
+  if (fam == 1 || !tma) return launch_smem<BX, BY>(N, in, out, s);
+  switch (mode) {
+    case M_NATIVE: return launch_tma<BX, BY, M_NATIVE>(N, in, out, status, nullptr, s);
+    case M_DD: return launch_tma<BX, BY, M_DD>(N, in, out, status, flag, s);
+    case M_DP: return launch_tma<BX, BY, M_DP>(N, in, out, status, flag, s);
+    case M_PP: return launch_tma<BX, BY, M_PP>(N, in, out, status, flag, s);
+    default: return launch_tma<BX, BY, M_PD>(N, in, out, status, flag, s);
   }
 }
 
-int sweep(int variant, int N, const double* in, double* out, int* status, cudaStream_t s) {
+int sweep(int variant, int mode, bool tma, int N, const double* in, double* out, int* status, int* flag,
+          cudaStream_t s) {
   const int fam = variant / 4;
   switch (variant % 4) {
-    case 0: return launch_family<32, 4>(fam, N, in, out, status, s);
-    case 1: return launch_family<32, 8>(fam, N, in, out, status, s);
-    case 2: return launch_family<64, 4>(fam, N, in, out, status, s);
-    default: return launch_family<128, 2>(fam, N, in, out, status, s);
+    case 0: return launch_family<32, 4>(fam, mode, tma, N, in, out, status, flag, s);
+    case 1: return launch_family<32, 8>(fam, mode, tma, N, in, out, status, flag, s);
+    case 2: return launch_family<64, 4>(fam, mode, tma, N, in, out, status, flag, s);
+    default: return launch_family<128, 2>(fam, mode, tma, N, in, out, status, flag, s);
   }
 }
 
@@ -411,10 +480,27 @@ extern "C" int ar_jacobi7(int variant, int N, int sweeps, const double* u0, doub
                ? AR_OK
                : AR_ERR_CUDA;
   }
+  const int fam = variant / 4;
+  const bool tma = fam >= 2 && tma_usable(variant % 4, N, u0, out, sweeps > 1 ? work : nullptr);
+  // df calls of 3+ sweeps keep float pairs between sweeps; status[1] carries
+  // the first sweep's verdict on whether every value fits the pair range
+  int* flag = (fam == 3 && tma && sweeps >= 3 && status) ? status + 1 : nullptr;
+  if (flag && cudaMemsetAsync(flag, 0, sizeof(int), s) != cudaSuccess) return AR_ERR_CUDA;
   const double* src = u0;
   for (int sw = 0; sw < sweeps; ++sw) {
     double* dst = ((sweeps - 1 - sw) % 2 == 0) ? out : work;
-    const int rc = sweep(variant, N, src, dst, status, s);
+    int mode = M_NATIVE;
+    if (fam == 3) {
+      if (!flag || sw == 0)
+        mode = M_DD;
+      else if (sw == sweeps - 1)
+        mode = M_PD;
+      else if (sw == 1)
+        mode = M_DP;
+      else
+        mode = M_PP;
+    }
+    const int rc = sweep(variant, mode, tma, N, src, dst, status, flag, s);
     if (rc != AR_OK) return rc;
     src = dst;
   }

@@ -40,7 +40,8 @@ def main():
     elif a.loop == "jacobi7":
         u0 = torch.from_numpy(synth.grid_inputs(1000 + a.size, a.size)).to(dev)
         out, wk = torch.empty_like(u0), torch.empty_like(u0)
-        run = lambda: ar.ar_jacobi7(a.variant, a.size, a.sweeps, u0, out, wk)  # noqa: E731
+        st = torch.zeros(2, dtype=torch.int32, device=dev)
+        run = lambda: ar.ar_jacobi7(a.variant, a.size, a.sweeps, u0, out, wk, st)  # noqa: E731
         work, unit = 16.0 * a.size ** 3 * a.sweeps, "GB/s"
     elif a.loop == "spmv":
         rp, c, v = synth.csr_zipf(31, a.size, a.zipf, device="cuda")

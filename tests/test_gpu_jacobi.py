@@ -13,12 +13,17 @@ V = 16
 TOL = 1e-13  # max |gpu - ref| <= TOL * max |ref|
 
 
-def _run(v, u0, sweeps, status=None):
+def _run(v, u0, sweeps, status="new"):
+    """status "new": a fresh int[2] status array (lets the df family keep
+    float pairs between sweeps); None: no status array."""
     N = u0.shape[0]
     ud = dev(u0)
     out = torch.empty_like(ud)
     work = torch.empty_like(ud)
-    ar.ar_jacobi7(v, N, sweeps, ud, out, work, status)
+    st = torch.zeros(2, dtype=torch.int32, device="cuda") if isinstance(status, str) else status
+    ar.ar_jacobi7(v, N, sweeps, ud, out, work, st)
+    if st is not None:
+        assert int(st[0].item()) == 0
     return host(out)
 
 
@@ -34,10 +39,12 @@ def _check(out, ref, what):
 def test_all_variants_match_oracle(N, sweeps):
     u0 = synth.grid_inputs(2, N)
     ref = loops.jacobi7(u0, sweeps)
-    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    status = torch.zeros(2, dtype=torch.int32, device="cuda")
     for v in range(V):
         _check(_run(v, u0, sweeps, status), ref, (ar.loop_variant_name(1, v), N, sweeps))
-    assert int(status.item()) == 0
+        assert int(status[0].item()) == 0
+    for v in range(12, 16):  # df family without a status array: float64 between sweeps
+        _check(_run(v, u0, sweeps, None), ref, (ar.loop_variant_name(1, v), N, sweeps, "no status"))
 
 
 def test_zero_sweeps_copies():
@@ -69,13 +76,21 @@ def test_df_range_guard_falls_back_to_float64():
     ref = loops.jacobi7(u0, 3)
     big = np.abs(ref) > 1e3
     for v in range(12, 16):
-        out = _run(v, u0, 3)
-        _check(out[~big], ref[~big], ("df mixed", v))
-        assert np.all(np.abs(out[big] - ref[big]) <= 1e-15 * np.abs(ref[big]) * 8)
+        for st in ("new", None):
+            out = _run(v, u0, 3, st)
+            _check(out[~big], ref[~big], ("df mixed", v, st))
+            assert np.all(np.abs(out[big] - ref[big]) <= 1e-15 * np.abs(ref[big]) * 8)
     tiny = synth.grid_inputs(5, 36) * 1e-80
-    reft = loops.jacobi7(tiny, 2)
+    reft = loops.jacobi7(tiny, 4)
     for v in range(12, 16):
-        _check(_run(v, tiny, 2), reft, ("df tiny", v))
+        _check(_run(v, tiny, 4), reft, ("df tiny", v))
+    # the first sweep's verdict: float64 storage between sweeps when a value
+    # leaves the float-pair range, float pairs otherwise
+    st = torch.zeros(2, dtype=torch.int32, device="cuda")
+    _run(13, u0, 3, st)
+    assert int(st[1].item()) == 1
+    _run(13, synth.grid_inputs(4, N), 3, st)
+    assert int(st[1].item()) == 0
     u1 = synth.grid_inputs(6, 36)
     u1[3, 3, 3] = np.inf
     u1[20, 3, 3] = np.nan
@@ -111,8 +126,9 @@ def test_bench_sizes_sampled(N):
     ud = dev(u0)
     out = torch.empty_like(ud)
     work = torch.empty_like(ud)
+    status = torch.zeros(2, dtype=torch.int32, device="cuda")
     idx = torch.tensor([(p[0] * N + p[1]) * N + p[2] for p in pts], device="cuda")
     for v in range(V):
-        ar.ar_jacobi7(v, N, s, ud, out, work)
+        ar.ar_jacobi7(v, N, s, ud, out, work, status)
         got = host(out.view(-1)[idx])
         assert np.max(np.abs(got - refs)) <= TOL * scale, (ar.loop_variant_name(1, v), N)
