@@ -48,6 +48,12 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--workload", default="jacobi7", choices=["jacobi7", "spmv"],
+                   help="jacobi7: the headline line; spmv: the learned-selector study (one JSON line)")
+    p.add_argument("--train", type=int, default=2000, help="spmv: profiled training matrices")
+    p.add_argument("--test", type=int, default=500, help="spmv: held-out test matrices")
+    p.add_argument("--rows-max", type=float, default=1e7, help="spmv: largest row count")
+    p.add_argument("--epochs", type=int, default=200, help="spmv: MLP epochs")
     return p.parse_args()
 
 
@@ -332,10 +338,118 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+
+# ---------------------------------------------------------------- SpMV selector study
+SPMV_FEATURES = ("rows", "nnz", "mean", "var", "max")
+
+
+def spmv_bytes(rows, nnz):
+    """Algorithmic bytes of one y = A x: val + col per nonzero, row pointers,
+    x read once, y written once."""
+    return 12.0 * nnz + 4.0 * (rows + 1) + 8.0 * rows + 8.0 * rows
+
+
+def run_spmv(args):
+    """Config 3: profile `train` seeded matrices (7 variants, 5 reps after a
+    warm-up, L2 flushed), train the MLP selector on the device and the depth-2
+    tree on the same records, then compare their choices with the exhaustive
+    argmin and the fixed default (thread per row) on `test` held-out matrices."""
+    import torch
+
+    import paper_2303_08873_b300 as ar
+    import synth
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    ws = torch.empty(16 << 20, dtype=torch.uint8, device=dev)
+    fwsb = ar.ar_csr_features_workspace_bytes(0)
+    fws = torch.empty(fwsb, dtype=torch.uint8, device=dev)
+    f5 = torch.zeros(5, dtype=torch.float32, device=dev)
+
+    def case(seed):
+        prm = synth.spmv_matrix_params(seed, rows_max=args.rows_max)
+        rp, c, v = synth.spmv_matrix(seed, prm, device="cuda")
+        rows = prm["rows"]
+        nnz = int(rp[-1].item())
+        x = synth.spmv_x(seed, rows, device="cuda")
+        y = torch.empty(rows, dtype=torch.float64, device=dev)
+        ar.ar_csr_features(rows, rp, f5, fws, fwsb, stream=stream)
+        stream.synchronize()
+        feats = f5.cpu().tolist()
+        a = ar.ArSpmvArgs(rows, nnz, rp.data_ptr(), c.data_ptr(), v.data_ptr(), x.data_ptr(), y.data_ptr(),
+                          ws.data_ptr(), ws.numel())
+        return feats, a, (rp, c, v, x, y), rows, nnz
+
+    mlp = ar.Region("spmv-mlp", 5, f"mlp,64,epochs={args.epochs},seed=7", 10 ** 9)
+    tree = ar.Region("spmv-dtree", 5, "dtree,2", 10 ** 9)
+    exh = ar.Region("spmv-exhaustive", 5, "exhaustive,reps=5")
+    V = mlp.add_builtin(ar.AR_LOOP_SPMV)
+    tree.add_builtin(ar.AR_LOOP_SPMV)
+    exh.add_builtin(ar.AR_LOOP_SPMV)
+    for r in (mlp, exh):
+        r.set_l2_flush(flush, flush.numel())
+    default = ar.loop_default_variant(ar.AR_LOOP_SPMV)
+    names = [ar.loop_variant_name(ar.AR_LOOP_SPMV, v) for v in range(V)]
+
+    t0 = time.perf_counter()
+    prof_ms = 0.0
+    for k in range(args.train):
+        feats, a, keep, rows, nnz = case(1000 + k)
+        ms, _ = mlp.profile(feats, a, stream=stream)
+        prof_ms += 6 * sum(ms)  # warm-up + 5 timed runs of every variant
+        del keep
+    for f, v, ms in mlp.records():
+        tree.add_record(list(f), v, ms)
+    t_prof = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    mlp.train()
+    t_mlp = time.perf_counter() - t1
+    tree.train()
+
+    per = []
+    for k in range(args.test):
+        feats, a, keep, rows, nnz = case(3000 + k)
+        ms, best = exh.profile(feats, a, stream=stream)
+        vm, conf = mlp.select(feats)
+        vt, _ = tree.select(feats)
+        per.append({"rows": rows, "nnz": nnz, "bytes": spmv_bytes(rows, nnz), "ms": ms, "best": best,
+                    "mlp": vm, "conf": conf, "dtree": vt})
+        del keep
+
+    def agg(key):
+        tsel = [p["ms"][p[key] if key != "default" else default] for p in per]
+        reg = [t / p["ms"][p["best"]] - 1.0 for t, p in zip(tsel, per)]
+        gbs = sum(p["bytes"] for p in per) / (sum(tsel) * 1e-3) / 1e9
+        return {"gbs": gbs, "mean_regret_pct": 100 * statistics.mean(reg),
+                "p90_regret_pct": 100 * float(np.percentile(reg, 90)),
+                "exact_pct": 100 * statistics.mean(1.0 if (p[key] if key != "default" else default) == p["best"]
+                                                   else 0.0 for p in per)}
+
+    best_gbs = sum(p["bytes"] for p in per) / (sum(p["ms"][p["best"]] for p in per) * 1e-3) / 1e9
+    res = {"mlp": agg("mlp"), "dtree": agg("dtree"), "default": agg("default")}
+    low_conf = sum(1 for p in per if p["conf"] < 0.5)
+    line = {
+        "metric": METRIC, "value": res["mlp"]["gbs"], "unit": "GB/s", "n_gpus": 1, "dtype": "f64",
+        "data": "synthetic", "higher_is_better": True, "vs_baseline": None,
+        "config": {"workload": f"spmv float64 CSR, {args.train} training + {args.test} test matrices, rows "
+                               f"log-uniform [1e4, {args.rows_max:.0e}], 50% Zipf(s in [1.5,2.5]) / 50% band(7..129)",
+                   "features": list(SPMV_FEATURES), "variants": names, "default": names[default]},
+        "selection": {"exhaustive_best_gbs": best_gbs, **{k + "_" + m: v for k, d in res.items() for m, v in d.items()},
+                      "mlp_low_confidence_calls": low_conf,
+                      "best_variant_histogram": {names[v]: sum(1 for p in per if p["best"] == v) for v in range(V)}},
+        "cost": {"profiling_wall_s": t_prof, "profiling_gpu_ms": prof_ms, "train_mlp_s": t_mlp,
+                 "train_records": len(mlp.records())},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "spmv":
+        run_spmv(args)
     else:
         run_ours(args)
 

@@ -174,6 +174,57 @@ int ar_nbody_batched_workspace_bytes(int count, size_t *bytes);
 int ar_nbody_batched(int count, const int32_t *offs, const float *pos4, float *acc4, float eps, void *workspace,
                      size_t workspace_bytes, void *stream);
 
+/* ------------------------------------------------------------ mixed stream ---
+ * Persistent execution of a batch of region invocations of the four loops
+ * (up to AR_EXEC_MAX_CALLS per batch) in three launches on `stream`:
+ *   1. features: per call, the selector's features (daxpy: n; Jacobi: N,
+ *      sweeps; SpMV: rows, nnz, mean, variance, max of the row lengths,
+ *      reduced from rowptr on the device; n-body: N);
+ *   2. plan (one block): per call, the variant -- force_variant[c] if given,
+ *      else the argmax of the loop's MLP (models->theta[loop]; the loop's
+ *      default variant if that is NULL) with its confidence -- and the
+ *      phase-major table of work items (one phase per Jacobi sweep; two for
+ *      merge-path SpMV, main pass and carry fix-up; one otherwise);
+ *   3. run: a persistent kernel whose blocks pull work items from an atomic
+ *      counter and run the chosen variant's tile of that call.  An item of
+ *      phase p waits (bounded) until every item of phase p-1 of its call is
+ *      done; items are handed out phase-major, so every awaited item was
+ *      handed out earlier.
+ * The tiles compute exactly what the stand-alone variants compute (same
+ * data, same tolerances); the tma family runs the smem tile inside the
+ * executor.  EPT 2/4 daxpy variants on buffers that are not 16-byte aligned
+ * run with one element per thread.
+ * All arrays are device memory.  Per call c: variant[c], conf[c] (1 when
+ * forced or defaulted), features[8c..8c+7], t_start[c] / t_end[c] (%globaltimer
+ * ns of the first tile's start and the last tile's end), status[c] (AR_OK,
+ * AR_ERR_ARG for a bad loop/variant, AR_ERR_TIMEOUT if a dependency wait gave
+ * up).  The call table and models must stay valid until the work completes.
+ * workspace: ar_exec_workspace_bytes(max_calls) bytes, no initialisation
+ * needed.  The launches contain no host synchronisation and can be captured
+ * in a CUDA graph together with the copy that refreshes `calls`. */
+#define AR_EXEC_MAX_CALLS 256
+#define AR_EXEC_MAX_PHASES 64
+typedef struct ar_exec_call {
+  int32_t loop;   /* AR_LOOP_* */
+  int32_t sweeps; /* Jacobi sweeps, 1 .. AR_EXEC_MAX_PHASES */
+  int64_t n;      /* daxpy n | Jacobi N | SpMV rows | n-body N */
+  int64_t nnz;    /* SpMV nonzeros */
+  double a;       /* daxpy a */
+  float eps;      /* n-body softening */
+  int32_t reserved;
+  const void *in0, *in1, *in2, *in3; /* daxpy x | Jacobi u0 | SpMV rowptr, col, val, x | n-body pos4 */
+  void *out0, *out1;                 /* daxpy y | Jacobi out, work | SpMV y, merge-path workspace | n-body acc4 */
+  uint64_t out1_bytes;               /* SpMV: merge-path workspace bytes (16 per 4096 rows+nnz) */
+} ar_exec_call;
+typedef struct ar_exec_models {
+  int32_t F[4], V[4], H; /* per loop: features, variants (must match the loop); hidden width 32/64 */
+  const float *theta[4], *mu[4], *sd[4];
+} ar_exec_models;
+int ar_exec_workspace_bytes(int max_calls, size_t *bytes);
+int ar_exec_batch(const ar_exec_call *calls, int ncalls, const ar_exec_models *models, const int32_t *force_variant,
+                  int32_t *variant, float *conf, float *features, uint64_t *t_start, uint64_t *t_end,
+                  int32_t *status, void *workspace, size_t workspace_bytes, void *stream);
+
 /* ------------------------------------------------------------ MLP selector ---
  * The learned selector of the adaptive region: the paper's model kinds are
  * decision trees and random forests and it names neural networks as a

@@ -72,6 +72,21 @@ class ArNbodyArgs(ctypes.Structure):
     _fields_ = [("N", _i64), ("pos4", _vp), ("acc4", _vp), ("eps", _f)]
 
 
+class ArExecCall(ctypes.Structure):
+    _fields_ = [("loop", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("n", _i64), ("nnz", _i64), ("a", _d),
+                ("eps", _f), ("reserved", ctypes.c_int32), ("in0", _vp), ("in1", _vp), ("in2", _vp), ("in3", _vp),
+                ("out0", _vp), ("out1", _vp), ("out1_bytes", ctypes.c_uint64)]
+
+
+class ArExecModels(ctypes.Structure):
+    _fields_ = [("F", ctypes.c_int32 * 4), ("V", ctypes.c_int32 * 4), ("H", ctypes.c_int32),
+                ("theta", _vp * 4), ("mu", _vp * 4), ("sd", _vp * 4)]
+
+
+AR_EXEC_MAX_CALLS = 256
+AR_EXEC_MAX_PHASES = 64
+
+
 _SIGS = {
     # ar.h
     "ar_region_create": (_i, [_cs, _i, _cs, _i, ctypes.POINTER(_vp)]),
@@ -114,6 +129,8 @@ _SIGS = {
     "ar_nbody": (_i, [_i, _i64, _vp, _vp, _f, _vp]),
     "ar_nbody_batched_workspace_bytes": (_i, [_i, ctypes.POINTER(_sz)]),
     "ar_nbody_batched": (_i, [_i, _vp, _vp, _vp, _f, _vp, _sz, _vp]),
+    "ar_exec_workspace_bytes": (_i, [_i, ctypes.POINTER(_sz)]),
+    "ar_exec_batch": (_i, [_vp, _i, ctypes.POINTER(ArExecModels), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "ar_mlp_num_params": (_i, [_i, _i, _i]),
     "ar_mlp_forward": (_i, [_vp, _vp, _vp, _i, _i, _i, _i64, _vp, _vp, _vp, _vp, _vp]),
     "ar_mlp_grad": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp]),
@@ -232,6 +249,28 @@ def ar_nbody_batched_workspace_bytes(count):
 def ar_nbody_batched(count, offs, pos4, acc4, eps, workspace, workspace_bytes, stream=None):
     return check(lib.ar_nbody_batched(count, ptr(offs), ptr(pos4), ptr(acc4), eps, ptr(workspace), workspace_bytes,
                                       stream_handle(stream)))
+
+
+def ar_exec_workspace_bytes(max_calls):
+    b = ctypes.c_size_t()
+    check(lib.ar_exec_workspace_bytes(max_calls, ctypes.byref(b)))
+    return b.value
+
+
+def ar_exec_batch(calls, ncalls, models, force_variant, variant, conf, features, t_start, t_end, status, workspace,
+                  workspace_bytes, stream=None):
+    """calls: device buffer holding `ncalls` ArExecCall records; models: an
+    ArExecModels (host) or None."""
+    mp = ctypes.byref(models) if models is not None else None
+    return check(lib.ar_exec_batch(ptr(calls), ncalls, mp, ptr(force_variant), ptr(variant), ptr(conf), ptr(features),
+                                   ptr(t_start), ptr(t_end), ptr(status), ptr(workspace), workspace_bytes,
+                                   stream_handle(stream)))
+
+
+def exec_table_bytes(calls) -> bytes:
+    """Pack a list of ArExecCall into the byte image of the device call table."""
+    arr = (ArExecCall * len(calls))(*calls)
+    return bytes(arr)
 
 
 def ar_mlp_num_params(F, H, V):
@@ -435,7 +474,8 @@ class Region:
         return self._ck(lib.ar_set_l2_flush(self.h, ptr(buf), nbytes))
 
 
-__all__ = ["ArError", "Region", "ArDaxpyArgs", "ArJacobi7Args", "ArSpmvArgs", "ArNbodyArgs", "ar_spmv",
+__all__ = ["ArExecCall", "ArExecModels", "ar_exec_workspace_bytes", "ar_exec_batch", "exec_table_bytes",
+           "AR_EXEC_MAX_CALLS", "AR_EXEC_MAX_PHASES", "ArError", "Region", "ArDaxpyArgs", "ArJacobi7Args", "ArSpmvArgs", "ArNbodyArgs", "ar_spmv",
            "ar_spmv_workspace_bytes", "ar_spmv_merge_path_noalloc", "ar_csr_features", "ar_csr_features_workspace_bytes", "ar_nbody",
            "ar_nbody_batched", "ar_nbody_batched_workspace_bytes", "LAUNCH_FN", "FAKE_TIME_FN", "lib", "ptr",
            "stream_handle", "check", "loop_num_variants", "loop_default_variant", "loop_variant_name", "ar_daxpy",

@@ -1,0 +1,691 @@
+// Persistent mixed-stream executor: a batch of region invocations of the
+// four loops runs as features -> plan (device MLP selection) -> one
+// persistent launch that pulls (phase, call, tile) work items from an atomic
+// counter and dispatches each to the chosen variant's tile function.
+//
+// Ordering and waits: items are numbered phase-major (all calls' phase 0,
+// then phase 1, ...), so an item of phase p, which waits for the phase p-1
+// items of its own call, only ever waits for items handed out before it to
+// blocks that are already running; the wait is bounded and reports
+// AR_ERR_TIMEOUT per call.  Data written inside this launch (Jacobi sweeps,
+// merge-path carries) are read with L1-bypassing loads (ld.global.cg).
+#include <cstdio>
+
+#include "common.cuh"
+#include "pairs.cuh"
+
+namespace ar {
+namespace {
+
+constexpr int T = 256;                   // threads per executor block
+constexpr int PM = AR_EXEC_MAX_PHASES;   // phases per call
+constexpr int kJKC = 16;                 // Jacobi planes per tile
+constexpr uint32_t kDepSpin = 1u << 24;  // dependency polls (with backoff) before giving up
+constexpr int kMpItems = 16, kMpPerTile = T * kMpItems;
+
+__constant__ int c_nvar[4] = {15, 16, 7, 9};
+__constant__ int c_default[4] = {6, 1, 0, 3};
+__constant__ int c_nfeat[4] = {1, 2, 5, 1};
+__constant__ int c_dx_block[5] = {64, 128, 256, 512, 1024};
+__constant__ int c_dx_ept[3] = {1, 2, 4};
+__constant__ int c_j_bx[4] = {32, 32, 64, 128};
+__constant__ int c_j_by[4] = {4, 8, 4, 2};
+__constant__ int c_sp_k[5] = {32, 2, 4, 8, 16};
+__constant__ int c_nb_tile[3] = {128, 256, 512};
+
+struct ModelsDev {
+  int F[4], V[4], H;
+  const float *theta[4], *mu[4], *sd[4];
+};
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+__device__ __forceinline__ int phases_of(const ar_exec_call& c, int v) {
+  if (c.loop == AR_LOOP_JACOBI7) return c.sweeps;
+  if (c.loop == AR_LOOP_SPMV && v == 6) return 2;
+  return 1;
+}
+
+__device__ int64_t tiles_of(const ar_exec_call& c, int v, int p) {
+  switch (c.loop) {
+    case AR_LOOP_DAXPY: return cdiv(c.n, (int64_t)c_dx_block[v / 3] * c_dx_ept[v % 3]);
+    case AR_LOOP_JACOBI7: {
+      const int64_t N = c.n;
+      return cdiv(N, c_j_bx[v % 4]) * cdiv(N, c_j_by[v % 4]) * cdiv(N, kJKC);
+    }
+    case AR_LOOP_SPMV: {
+      if (v == 0) return cdiv(c.n, T);
+      if (v < 6) return cdiv(c.n, T / c_sp_k[v - 1]);
+      const int64_t nb = cdiv(c.n + c.nnz, kMpPerTile);
+      return p == 0 ? nb : cdiv(nb, T);
+    }
+    default: return cdiv(c.n, c_nb_tile[v / 3]);
+  }
+}
+
+// ------------------------------------------------------------------ features
+__global__ void __launch_bounds__(T) exec_features(const ar_exec_call* __restrict__ calls, float* __restrict__ feats,
+                                                   unsigned long long* __restrict__ part) {
+  __shared__ unsigned long long s1[T / 32], s2[T / 32];
+  __shared__ int sm[T / 32];
+  const int c = blockIdx.y;
+  const ar_exec_call k = calls[c];
+  if (k.loop == AR_LOOP_SPMV) {
+    const int* rp = static_cast<const int*>(k.in0);
+    unsigned long long a = 0, q = 0;
+    int m = 0;
+    for (int64_t r = (int64_t)blockIdx.x * T + threadIdx.x; r < k.n; r += (int64_t)gridDim.x * T) {
+      const int len = __ldg(rp + r + 1) - __ldg(rp + r);
+      a += (unsigned long long)len;
+      q += (unsigned long long)len * (unsigned long long)len;
+      m = max(m, len);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      q += __shfl_xor_sync(0xffffffffu, q, o);
+      m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      s1[threadIdx.x / 32] = a;
+      s2[threadIdx.x / 32] = q;
+      sm[threadIdx.x / 32] = m;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long A = 0, Q = 0;
+      int M = 0;
+      for (int w = 0; w < T / 32; ++w) {
+        A += s1[w];
+        Q += s2[w];
+        M = max(M, sm[w]);
+      }
+      // integer sums: the result does not depend on the order of the atomics
+      atomicAdd(part + 3 * c, A);
+      atomicAdd(part + 3 * c + 1, Q);
+      atomicMax(part + 3 * c + 2, (unsigned long long)M);
+    }
+  } else if (blockIdx.x == 0 && threadIdx.x < 8) {
+    float v = 0.f;
+    if (threadIdx.x == 0) v = (float)k.n;
+    if (threadIdx.x == 1 && k.loop == AR_LOOP_JACOBI7) v = (float)k.sweeps;
+    feats[8 * c + threadIdx.x] = v;
+  }
+}
+
+// ------------------------------------------------------------------ plan
+template <int H>
+__device__ int mlp_choose(const ModelsDev& m, int L, const float* f, float* conf) {
+  const int F = m.F[L], V = m.V[L];
+  const float* th = m.theta[L];
+  const float* W1 = th;
+  const float* b1 = W1 + H * F;
+  const float* W2 = b1 + H;
+  const float* b2 = W2 + H * H;
+  const float* W3 = b2 + H;
+  const float* b3 = W3 + V * H;
+  float x0[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    x0[i] = i < F ? (copysignf(log1pf(fabsf(f[i])), f[i]) - __ldg(m.mu[L] + i)) / __ldg(m.sd[L] + i) : 0.f;
+  float h1[H];
+#pragma unroll
+  for (int o = 0; o < H; ++o) {
+    float a = __ldg(b1 + o);
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (i < F) a = fmaf(__ldg(W1 + o * F + i), x0[i], a);
+    h1[o] = fmaxf(a, 0.f);
+  }
+  float lg[32];
+#pragma unroll
+  for (int v = 0; v < 32; ++v) lg[v] = v < V ? __ldg(b3 + v) : -INFINITY;
+  for (int o = 0; o < H; ++o) {
+    float a = __ldg(b2 + o);
+#pragma unroll
+    for (int i = 0; i < H; ++i) a = fmaf(__ldg(W2 + o * H + i), h1[i], a);
+    a = fmaxf(a, 0.f);
+#pragma unroll
+    for (int v = 0; v < 32; ++v)
+      if (v < V) lg[v] = fmaf(__ldg(W3 + v * H + o), a, lg[v]);
+  }
+  int best = 0;
+  float mx = lg[0];
+#pragma unroll
+  for (int v = 1; v < 32; ++v)
+    if (lg[v] > mx) {
+      mx = lg[v];
+      best = v;
+    }
+  float z = 0.f;
+#pragma unroll
+  for (int v = 0; v < 32; ++v)
+    if (v < V) z += expf(lg[v] - mx);
+  *conf = 1.f / z;
+  return best;
+}
+
+__global__ void __launch_bounds__(T) exec_plan(const ar_exec_call* __restrict__ calls, int ncalls, ModelsDev m,
+                                               bool have_models, const int* __restrict__ force,
+                                               int* __restrict__ variant, float* __restrict__ conf,
+                                               float* __restrict__ feats, const unsigned long long* __restrict__ part,
+                                               int* __restrict__ tiles, long long* __restrict__ prefix,
+                                               int* __restrict__ done, unsigned long long* __restrict__ counter,
+                                               uint64_t* __restrict__ t0, uint64_t* __restrict__ t1,
+                                               int* __restrict__ status, int* __restrict__ vint) {
+  __shared__ long long scan[T];
+  const int c = threadIdx.x;
+  if (c < ncalls) {
+    const ar_exec_call k = calls[c];
+    int st = AR_OK, v = -1;
+    float cf = 1.f;
+    const bool loop_ok = k.loop >= 0 && k.loop < 4;
+    if (loop_ok && k.loop == AR_LOOP_SPMV) {
+      const double rows = (double)k.n, A = (double)part[3 * c], Q = (double)part[3 * c + 1];
+      const double mean = k.n > 0 ? A / rows : 0.0;
+      const double var = k.n > 0 ? fmax(Q / rows - mean * mean, 0.0) : 0.0;
+      float* f = feats + 8 * c;
+      f[0] = (float)k.n;
+      f[1] = (float)A;
+      f[2] = (float)mean;
+      f[3] = (float)var;
+      f[4] = (float)part[3 * c + 2];
+      f[5] = f[6] = f[7] = 0.f;
+    }
+    if (!loop_ok || (k.loop == AR_LOOP_JACOBI7 && (k.sweeps < 1 || k.sweeps > PM)) || k.n < 0) {
+      st = AR_ERR_ARG;
+    } else if (force) {
+      v = force[c];
+    } else if (have_models && m.theta[k.loop]) {
+      float f[8];
+      for (int i = 0; i < 8; ++i) f[i] = feats[8 * c + i];
+      v = m.H == 64 ? mlp_choose<64>(m, k.loop, f, &cf) : mlp_choose<32>(m, k.loop, f, &cf);
+    } else {
+      v = c_default[k.loop];
+    }
+    if (st == AR_OK && (v < 0 || v >= c_nvar[k.loop])) st = AR_ERR_ARG;
+    if (st == AR_OK && k.loop == AR_LOOP_SPMV && v == 6 &&
+        (!k.out1 || k.out1_bytes < 16ull * (unsigned long long)cdiv(k.n + k.nnz, kMpPerTile)))
+      st = AR_ERR_ARG;  // merge-path needs its carry workspace
+    if (st == AR_OK && k.loop == AR_LOOP_DAXPY && v % 3 != 0 &&
+        (((uintptr_t)k.in0 | (uintptr_t)k.out0) & 15u) != 0)
+      v -= v % 3;  // double2 variants need 16-byte alignment: one element per thread
+    const int ph = st == AR_OK ? phases_of(k, v) : 0;
+    for (int p = 0; p < PM; ++p) {
+      tiles[c * PM + p] = p < ph ? (int)tiles_of(k, v, p) : 0;
+      done[c * PM + p] = 0;
+    }
+    t0[c] = ~0ull;
+    t1[c] = 0ull;
+    status[c] = st;
+    variant[c] = st == AR_OK ? v : -1;
+    vint[c] = v;
+    conf[c] = cf;
+  }
+  __syncthreads();
+  // phase-major exclusive prefix over (p, c): thread t owns a run of entries
+  const int total = PM * ncalls;
+  const int per = (total + T - 1) / T;
+  const int lo = threadIdx.x * per, hi = min(total, lo + per);
+  long long s = 0;
+  for (int e = lo; e < hi; ++e) s += tiles[(e % ncalls) * PM + e / ncalls];
+  scan[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long acc = 0;
+    for (int t = 0; t < T; ++t) {
+      const long long x = scan[t];
+      scan[t] = acc;
+      acc += x;
+    }
+    prefix[total] = acc;
+    *counter = 0ull;
+  }
+  __syncthreads();
+  long long acc = scan[threadIdx.x];
+  for (int e = lo; e < hi; ++e) {
+    prefix[e] = acc;
+    acc += tiles[(e % ncalls) * PM + e / ncalls];
+  }
+}
+
+// ------------------------------------------------------------------ tiles
+__device__ void daxpy_tile(const ar_exec_call& k, int v, int64_t t) {
+  const int BS = c_dx_block[v / 3], EPT = c_dx_ept[v % 3];
+  const int64_t n = k.n, base = t * (int64_t)BS * EPT;
+  const double a = k.a;
+  const double* x = static_cast<const double*>(k.in0);
+  double* y = static_cast<double*>(k.out0);
+  if (EPT == 1) {
+    for (int e = threadIdx.x; e < BS; e += T) {
+      const int64_t i = base + e;
+      if (i < n) y[i] = fma(a, __ldg(x + i), y[i]);
+    }
+  } else {
+    const double2* x2 = reinterpret_cast<const double2*>(x);
+    double2* y2 = reinterpret_cast<double2*>(y);
+    const int64_t n2 = n >> 1, wb = base >> 1;
+    const int W = BS * EPT / 2;
+    for (int e = threadIdx.x; e < W; e += T) {
+      const int64_t w = wb + e;
+      if (w < n2) {
+        const double2 xv = __ldg(x2 + w);
+        double2 yv = y2[w];
+        yv.x = fma(a, xv.x, yv.x);
+        yv.y = fma(a, xv.y, yv.y);
+        y2[w] = yv;
+      }
+    }
+    if ((n & 1) && threadIdx.x == 0 && n - 1 >= base && n - 1 < base + (int64_t)BS * EPT)
+      y[n - 1] = fma(a, x[n - 1], y[n - 1]);
+  }
+}
+
+__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+
+__device__ __forceinline__ double atcg(const double* __restrict__ u, int N, int i, int j, int k) {
+  if ((unsigned)i >= (unsigned)N || (unsigned)j >= (unsigned)N || (unsigned)k >= (unsigned)N) return 0.0;
+  return __ldcg(u + ((int64_t)k * N + j) * N + i);
+}
+
+__device__ void jacobi_tile(const ar_exec_call& k, int v, int p, int64_t t, unsigned char* smraw) {
+  const int N = (int)k.n, S = k.sweeps;
+  const int fam = v / 4, BX = c_j_bx[v % 4], BY = c_j_by[v % 4];
+  const double* u0 = static_cast<const double*>(k.in0);
+  double* out = static_cast<double*>(k.out0);
+  double* work = static_cast<double*>(k.out1);
+  double* dst = ((S - 1 - p) % 2 == 0) ? out : work;
+  const double* src = p == 0 ? u0 : (((S - p) % 2 == 0) ? out : work);
+  const int64_t gx = (N + BX - 1) / BX, gy = (N + BY - 1) / BY;
+  const int bx = (int)(t % gx), by = (int)((t / gx) % gy), bz = (int)(t / (gx * gy));
+  const int kb = bz * kJKC, ke = min(N, kb + kJKC);
+  const bool active = threadIdx.x < BX * BY;
+  const int lx = threadIdx.x % BX, ly = threadIdx.x / BX;
+  const int i = bx * BX + lx, j = by * BY + ly;
+  const bool inside = active && i < N && j < N;
+  const int64_t NN = (int64_t)N * N, col = (int64_t)j * N + i;
+  if (fam == 0) {  // naive: 6 loads per point
+    if (!inside) return;
+    for (int kk = kb; kk < ke; ++kk) {
+      double s = atcg(src, N, i - 1, j, kk) + atcg(src, N, i + 1, j, kk);
+      s += atcg(src, N, i, j - 1, kk);
+      s += atcg(src, N, i, j + 1, kk);
+      s += atcg(src, N, i, j, kk - 1);
+      s += atcg(src, N, i, j, kk + 1);
+      dst[kk * NN + col] = s * kSixth;
+    }
+    return;
+  }
+  // 2.5D: double-buffered xy tile with halo, z neighbours in registers
+  const int PXs = BX + 2, PL = PXs * (BY + 2);
+  const int cidx = (ly + 1) * PXs + lx + 1;
+  if (fam < 3) {
+    double* tile = reinterpret_cast<double*>(smraw);
+    double below = inside ? atcg(src, N, i, j, kb - 1) : 0.0;
+    double cur = inside ? atcg(src, N, i, j, kb) : 0.0;
+    for (int kk = kb; kk < ke; ++kk) {
+      double* tb = tile + ((kk - kb) & 1) * PL;
+      const double above = inside ? atcg(src, N, i, j, kk + 1) : 0.0;
+      if (active) {
+        tb[cidx] = cur;
+        if (lx == 0) tb[cidx - 1] = atcg(src, N, i - 1, j, kk);
+        if (lx == BX - 1) tb[cidx + 1] = atcg(src, N, i + 1, j, kk);
+        if (ly == 0) tb[cidx - PXs] = atcg(src, N, i, j - 1, kk);
+        if (ly == BY - 1) tb[cidx + PXs] = atcg(src, N, i, j + 1, kk);
+      }
+      __syncthreads();
+      if (inside) {
+        double s = tb[cidx - 1] + tb[cidx + 1];
+        s += tb[cidx - PXs];
+        s += tb[cidx + PXs];
+        s += below;
+        s += above;
+        dst[kk * NN + col] = s * kSixth;
+      }
+      below = cur;
+      cur = above;
+    }
+    return;
+  }
+  // df: the same tile in float pairs; points with an input outside the pair
+  // range are redone in float64
+  float2* tile = reinterpret_cast<float2*>(smraw);
+  float2 below = df_split(inside ? atcg(src, N, i, j, kb - 1) : 0.0);
+  float2 cur = df_split(inside ? atcg(src, N, i, j, kb) : 0.0);
+  for (int kk = kb; kk < ke; ++kk) {
+    float2* tb = tile + ((kk - kb) & 1) * PL;
+    const float2 above = df_split(inside ? atcg(src, N, i, j, kk + 1) : 0.0);
+    if (active) {
+      tb[cidx] = cur;
+      if (lx == 0) tb[cidx - 1] = df_split(atcg(src, N, i - 1, j, kk));
+      if (lx == BX - 1) tb[cidx + 1] = df_split(atcg(src, N, i + 1, j, kk));
+      if (ly == 0) tb[cidx - PXs] = df_split(atcg(src, N, i, j - 1, kk));
+      if (ly == BY - 1) tb[cidx + PXs] = df_split(atcg(src, N, i, j + 1, kk));
+    }
+    __syncthreads();
+    if (inside) {
+      double r = pair_to_double(df_avg6(tb[cidx - 1], tb[cidx + 1], tb[cidx - PXs], tb[cidx + PXs], below, above));
+      if (r != r) {
+        double s = atcg(src, N, i - 1, j, kk) + atcg(src, N, i + 1, j, kk);
+        s += atcg(src, N, i, j - 1, kk);
+        s += atcg(src, N, i, j + 1, kk);
+        s += atcg(src, N, i, j, kk - 1);
+        s += atcg(src, N, i, j, kk + 1);
+        r = s * kSixth;
+      }
+      dst[kk * NN + col] = r;
+    }
+    below = cur;
+    cur = above;
+  }
+}
+
+__device__ __forceinline__ int64_t mp_find(int64_t d, int64_t lo, int64_t hi, const int* __restrict__ rp,
+                                           int64_t nnz) {
+  lo = max(lo, d - nnz);
+  hi = min(hi, d);
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)__ldg(rp + mid + 1) <= d - mid - 1)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+__device__ void spmv_tile(const ar_exec_call& k, int v, int p, int64_t t, unsigned char* smraw) {
+  const int* rp = static_cast<const int*>(k.in0);
+  const int* col = static_cast<const int*>(k.in1);
+  const double* val = static_cast<const double*>(k.in2);
+  const double* x = static_cast<const double*>(k.in3);
+  double* y = static_cast<double*>(k.out0);
+  const int64_t rows = k.n, nnz = k.nnz;
+  if (v == 0) {
+    const int64_t r = t * T + threadIdx.x;
+    if (r < rows) {
+      double s = 0.0;
+      for (int e = __ldg(rp + r); e < __ldg(rp + r + 1); ++e) s = fma(__ldg(val + e), __ldg(x + __ldg(col + e)), s);
+      y[r] = s;
+    }
+    return;
+  }
+  if (v < 6) {
+    const int K = c_sp_k[v - 1];
+    const int64_t r = t * (T / K) + threadIdx.x / K;
+    const int lane = threadIdx.x % K;
+    double s = 0.0;
+    if (r < rows)
+      for (int e = __ldg(rp + r) + lane; e < __ldg(rp + r + 1); e += K) s = fma(__ldg(val + e), __ldg(x + __ldg(col + e)), s);
+    for (int o = K / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, K);
+    if (r < rows && lane == 0) y[r] = s;
+    return;
+  }
+  const int64_t nb = cdiv(rows + nnz, kMpPerTile);
+  int64_t* carry_row = static_cast<int64_t*>(k.out1);
+  double* carry_val = reinterpret_cast<double*>(carry_row + nb);
+  if (p == 1) {  // carry fix-up over path blocks t*T ..
+    const int64_t b = t * T + threadIdx.x;
+    if (b >= nb) return;
+    const int64_t r = __ldcg((const long long*)carry_row + b);
+    if (r < 0 || (b > 0 && __ldcg((const long long*)carry_row + b - 1) == r)) return;
+    double tot = __ldcg(carry_val + b);
+    for (int64_t u = b + 1; u < nb && __ldcg((const long long*)carry_row + u) == r; ++u) tot += __ldcg(carry_val + u);
+    y[r] = __ldcg(y + r) + tot;
+    return;
+  }
+  // main pass of path block t
+  int64_t* srow = reinterpret_cast<int64_t*>(smraw);
+  double* sval = reinterpret_cast<double*>(smraw + T * sizeof(int64_t));
+  int64_t* sbounds = reinterpret_cast<int64_t*>(smraw + T * (sizeof(int64_t) + sizeof(double)));
+  const int64_t L = rows + nnz;
+  const int64_t db = t * kMpPerTile, de = min(db + kMpPerTile, L);
+  if (threadIdx.x == 0) {
+    sbounds[0] = mp_find(db, 0, rows, rp, nnz);
+    sbounds[1] = mp_find(de, 0, rows, rp, nnz);
+  }
+  __syncthreads();
+  const int64_t d0 = min(db + (int64_t)threadIdx.x * kMpItems, de), d1 = min(d0 + kMpItems, de);
+  int64_t i = mp_find(d0, sbounds[0], sbounds[1], rp, nnz), j = d0 - i;
+  double s = 0.0;
+  int64_t row_end = i < rows ? (int64_t)__ldg(rp + i + 1) : nnz;
+  for (int64_t d = d0; d < d1; ++d) {
+    if (i < rows && j >= row_end) {
+      y[i] = s;
+      s = 0.0;
+      ++i;
+      row_end = i < rows ? (int64_t)__ldg(rp + i + 1) : nnz;
+    } else if (j < nnz) {
+      s = fma(__ldg(val + j), __ldg(x + __ldg(col + j)), s);
+      ++j;
+    }
+  }
+  srow[threadIdx.x] = (d1 > d0 && i < rows) ? i : -1;
+  sval[threadIdx.x] = s;
+  if (threadIdx.x == 0) carry_row[t] = -1;
+  __syncthreads();
+  const int64_t r = srow[threadIdx.x];
+  if (r >= 0 && (threadIdx.x == 0 || srow[threadIdx.x - 1] != r)) {
+    double tot = sval[threadIdx.x];
+    int u = threadIdx.x + 1;
+    while (u < T && srow[u] == r) tot += sval[u++];
+    if (u < T && min(db + (int64_t)u * kMpItems, de) < de) {
+      y[r] += tot;
+    } else {
+      carry_row[t] = r;
+      carry_val[t] = tot;
+    }
+  }
+}
+
+template <int U>
+__device__ __forceinline__ void nbody_accum(const float4* __restrict__ tile, int cnt, float4 pi, float eps2, float& ax,
+                                            float& ay, float& az) {
+  float tx = 0.f, ty = 0.f, tz = 0.f;
+#pragma unroll U
+  for (int q = 0; q < cnt; ++q) {
+    const float4 o = tile[q];
+    const float dx = o.x - pi.x, dy = o.y - pi.y, dz = o.z - pi.z;
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+    const float inv = rsqrtf(r2);
+    const float s = o.w * inv * inv * inv;
+    tx = fmaf(dx, s, tx);
+    ty = fmaf(dy, s, ty);
+    tz = fmaf(dz, s, tz);
+  }
+  ax += tx;
+  ay += ty;
+  az += tz;
+}
+
+__device__ void nbody_tile(const ar_exec_call& k, int v, int64_t t, unsigned char* smraw) {
+  const int Tt = c_nb_tile[v / 3], uidx = v % 3;
+  const float4* pos = static_cast<const float4*>(k.in0);
+  float4* acc = static_cast<float4*>(k.out0);
+  const int64_t N = k.n;
+  const float eps2 = k.eps * k.eps;
+  float4* tile = reinterpret_cast<float4*>(smraw);
+  const int nown = Tt > T ? 2 : 1;  // bodies per thread
+  float4 pi[2];
+  int64_t ii[2];
+  float ax[2] = {0.f, 0.f}, ay[2] = {0.f, 0.f}, az[2] = {0.f, 0.f};
+  for (int o = 0; o < nown; ++o) {
+    ii[o] = t * Tt + threadIdx.x + (int64_t)o * T;
+    const bool own = threadIdx.x + o * T < Tt && ii[o] < N;
+    pi[o] = own ? pos[ii[o]] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  for (int64_t j0 = 0; j0 < N; j0 += Tt) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < Tt; q += T) {
+      const int64_t jj = j0 + q;
+      tile[q] = jj < N ? pos[jj] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    for (int o = 0; o < nown; ++o) {
+      if (threadIdx.x + o * T >= Tt) continue;
+      if (uidx == 0)
+        nbody_accum<1>(tile, Tt, pi[o], eps2, ax[o], ay[o], az[o]);
+      else if (uidx == 1)
+        nbody_accum<4>(tile, Tt, pi[o], eps2, ax[o], ay[o], az[o]);
+      else
+        nbody_accum<8>(tile, Tt, pi[o], eps2, ax[o], ay[o], az[o]);
+    }
+  }
+  for (int o = 0; o < nown; ++o)
+    if (threadIdx.x + o * T < Tt && ii[o] < N) acc[ii[o]] = make_float4(ax[o], ay[o], az[o], 0.f);
+}
+
+// ------------------------------------------------------------------ run
+constexpr int kSmemBytes = 8448;  // largest tile: 2 x 4 x 130 doubles (Jacobi 128x2) / 512 float4
+
+__global__ void __launch_bounds__(T, 2) exec_run(const ar_exec_call* __restrict__ calls, int ncalls,
+                                                 const int* __restrict__ vint, const int* __restrict__ tiles,
+                                                 const long long* __restrict__ prefix, int* done,
+                                                 unsigned long long* counter, uint64_t* t0, uint64_t* t1,
+                                                 int* status) {
+  __shared__ __align__(16) unsigned char smraw[kSmemBytes];
+  __shared__ long long s_item, s_t;
+  __shared__ int s_c, s_p, s_ok;
+  const int E = PM * ncalls;
+  const long long total = prefix[E];
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long long it = (long long)atomicAdd(counter, 1ull);
+      s_item = it;
+      if (it < total) {
+        int lo = 0, hi = E - 1;  // last entry whose range starts at or before it
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (prefix[mid] <= it)
+            lo = mid;
+          else
+            hi = mid - 1;
+        }
+        const int p = lo / ncalls, c = lo % ncalls;
+        int ok = 1;
+        if (p > 0) {
+          const volatile int* d = done + c * PM + p - 1;
+          const int need = tiles[c * PM + p - 1];
+          uint32_t spins = 0;
+          while (*d < need) {
+            if (++spins > kDepSpin) {
+              ok = 0;
+              atomicExch(status + c, (int)AR_ERR_TIMEOUT);
+              break;
+            }
+            __nanosleep(100);
+          }
+          __threadfence();
+        }
+        if (ok) atomicMin((unsigned long long*)t0 + c, (unsigned long long)gtimer());
+        s_c = c;
+        s_p = p;
+        s_t = it - prefix[lo];
+        s_ok = ok;
+      }
+    }
+    __syncthreads();
+    if (s_item >= total) break;
+    const int c = s_c, p = s_p;
+    const long long t = s_t;
+    if (s_ok) {
+      const ar_exec_call k = calls[c];
+      const int v = vint[c];
+      switch (k.loop) {
+        case AR_LOOP_DAXPY: daxpy_tile(k, v, t); break;
+        case AR_LOOP_JACOBI7: jacobi_tile(k, v, p, t, smraw); break;
+        case AR_LOOP_SPMV: spmv_tile(k, v, p, t, smraw); break;
+        default: nbody_tile(k, v, t, smraw); break;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(done + c * PM + p, 1);
+      atomicMax((unsigned long long*)t1 + c, (unsigned long long)gtimer());
+    }
+  }
+}
+
+struct WsLayout {
+  size_t part, tiles, prefix, done, counter, vint, total;
+};
+
+WsLayout layout(int max_calls) {
+  auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+  WsLayout w;
+  size_t o = 0;
+  w.part = o;
+  o = up(o + (size_t)max_calls * 3 * 8);
+  w.tiles = o;
+  o = up(o + (size_t)max_calls * PM * 4);
+  w.prefix = o;
+  o = up(o + ((size_t)max_calls * PM + 1) * 8);
+  w.done = o;
+  o = up(o + (size_t)max_calls * PM * 4);
+  w.counter = o;
+  o = up(o + 8);
+  w.vint = o;
+  o = up(o + (size_t)max_calls * 4);
+  w.total = o + 256;
+  return w;
+}
+
+}  // namespace
+}  // namespace ar
+
+using namespace ar;
+
+extern "C" int ar_exec_workspace_bytes(int max_calls, size_t* bytes) {
+  if (max_calls < 1 || max_calls > AR_EXEC_MAX_CALLS || !bytes) return AR_ERR_ARG;
+  *bytes = layout(max_calls).total;
+  return AR_OK;
+}
+
+extern "C" int ar_exec_batch(const ar_exec_call* calls, int ncalls, const ar_exec_models* models,
+                             const int32_t* force_variant, int32_t* variant, float* conf, float* features,
+                             uint64_t* t_start, uint64_t* t_end, int32_t* status, void* workspace,
+                             size_t workspace_bytes, void* stream) {
+  if (ncalls < 0 || ncalls > AR_EXEC_MAX_CALLS) return AR_ERR_ARG;
+  if (ncalls == 0) return AR_OK;
+  if (!calls || !variant || !conf || !features || !t_start || !t_end || !status || !workspace) return AR_ERR_ARG;
+  const WsLayout w = layout(ncalls);
+  if (workspace_bytes < w.total) return AR_ERR_ARG;
+  ModelsDev m{};
+  bool have = false;
+  if (models) {
+    if (models->H != 32 && models->H != 64) return AR_ERR_ARG;
+    const int nfeat[4] = {1, 2, 5, 1}, nvar[4] = {15, 16, 7, 9};
+    for (int L = 0; L < 4; ++L) {
+      m.F[L] = models->F[L];
+      m.V[L] = models->V[L];
+      m.theta[L] = models->theta[L];
+      m.mu[L] = models->mu[L];
+      m.sd[L] = models->sd[L];
+      if (m.theta[L] && (m.F[L] != nfeat[L] || m.V[L] != nvar[L] || !m.mu[L] || !m.sd[L])) return AR_ERR_ARG;
+    }
+    m.H = models->H;
+    have = true;
+  }
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(workspace) + 255) &
+                                                         ~uintptr_t(255));
+  unsigned long long* part = reinterpret_cast<unsigned long long*>(base + w.part);
+  int* tiles = reinterpret_cast<int*>(base + w.tiles);
+  long long* prefix = reinterpret_cast<long long*>(base + w.prefix);
+  int* done = reinterpret_cast<int*>(base + w.done);
+  unsigned long long* counter = reinterpret_cast<unsigned long long*>(base + w.counter);
+  int* vint = reinterpret_cast<int*>(base + w.vint);
+  cudaStream_t s = as_stream(stream);
+  if (cudaMemsetAsync(part, 0, (size_t)ncalls * 3 * 8, s) != cudaSuccess) return AR_ERR_CUDA;
+  exec_features<<<dim3(64, (unsigned)ncalls), T, 0, s>>>(calls, features, part);
+  exec_plan<<<1, T, 0, s>>>(calls, ncalls, m, have, force_variant, variant, conf, features, part, tiles, prefix,
+                            done, counter, t_start, t_end, status, vint);
+  exec_run<<<device_sms() * 2, T, 0, s>>>(calls, ncalls, vint, tiles, prefix, done, counter, t_start, t_end, status);
+  return launch_status();
+}

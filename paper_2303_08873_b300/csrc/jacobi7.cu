@@ -28,22 +28,17 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "pairs.cuh"
 #include "tma.cuh"
 
 namespace ar {
 namespace {
 
-constexpr double kSixth = 1.0 / 6.0;
 constexpr int kDZ = 8;     // planes per TMA box
 constexpr int kRing = 3;   // boxes resident per block
 constexpr int kShapeX[4] = {32, 32, 64, 128};
 constexpr int kShapeY[4] = {4, 8, 4, 2};
 const char* const kFamily[4] = {"naive", "smem", "tma", "df"};
-
-__device__ __forceinline__ double at(const double* __restrict__ u, int N, int i, int j, int k) {
-  if ((unsigned)i >= (unsigned)N || (unsigned)j >= (unsigned)N || (unsigned)k >= (unsigned)N) return 0.0;
-  return u[((int64_t)k * N + j) * N + i];
-}
 
 // ------------------------------------------------------------------ naive
 template <int BX, int BY>
@@ -97,96 +92,6 @@ __global__ void __launch_bounds__(BX* BY) jacobi_smem(int N, int KC, const doubl
     below = cur;
     cur = above;
   }
-}
-
-// ------------------------------------------------------------------ float pairs
-// 1/6 as an unevaluated float pair.
-constexpr float kSixthHi = 0.16666667163372039794921875f;           // RN(1/6)
-constexpr float kSixthLo = -4.967053740534411e-09f;  // RN(1/6 - kSixthHi)
-
-// Split x into (hi, lo) with hi = x rounded to 24 significant bits and
-// lo = the remainder, both floats: x = hi + lo to within 2^-48 |x|.  Works on
-// the bit pattern with integer operations (truncate the significand to 24
-// bits, round the 29-bit remainder up or down): on B300 a float64<->float32
-// conversion issues on the slow float64 pipe, int->float does not.  Values
-// outside the float-pair range (|x| < 2^-74, |x| >= 2^118, inf, NaN) give
-// hi = NaN as a marker; +-0 gives (0, 0).
-__device__ __forceinline__ float2 df_split(double x) {
-  const long long b = __double_as_longlong(x);
-  if ((b << 1) == 0) return make_float2(0.f, 0.f);
-  const unsigned h32 = (unsigned)((unsigned long long)b >> 32), l32 = (unsigned)b;
-  const int e = (int)((h32 >> 20) & 0x7ff);
-  if (e < 949 || e > 1140) return make_float2(__int_as_float(0x7fc00001), 0.f);
-  const unsigned sign = h32 & 0x80000000u;
-  unsigned hib = sign | ((unsigned)(e - 896) << 23) | ((h32 & 0xfffffu) << 3) | (l32 >> 29);
-  int r = (int)(l32 & 0x1FFFFFFFu);
-  if (r >= (1 << 28)) {
-    hib += 1;  // one ulp away from zero (carries into the exponent correctly)
-    r -= (1 << 29);
-  }
-  const float lo = __int2float_rn(r) * __int_as_float((e - 1075 + 127) << 23);
-  return make_float2(__uint_as_float(hib), __uint_as_float(__float_as_uint(lo) ^ sign));
-}
-
-// Exact float -> float64 by assembling the bit pattern (no conversion
-// instruction).  Subnormal floats become signed zero (|f| < 2^-126 is below
-// the resolution of any float-pair result here); inf/NaN become NaN.
-__device__ __forceinline__ double f2d_bits(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned e8 = (u >> 23) & 0xffu;
-  unsigned hi = u & 0x80000000u, lo = 0u;
-  if (e8 == 0xffu) {
-    hi = 0x7ff80000u;
-  } else if (e8 != 0u) {
-    hi |= ((e8 + 896u) << 20) | ((u & 0x7fffffu) >> 3);
-    lo = u << 29;
-  }
-  return __hiloint2double((int)hi, (int)lo);
-}
-
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
-// (v0 + ... + v5) / 6 in float-pair arithmetic: returns the unevaluated
-// pair (p, pe) with p + pe = the average to ~2^-46 relative.  The hi parts
-// are summed exactly by a TwoSum chain, the lo parts and the chain's errors
-// in plain float, then the sum is multiplied by 1/6 as a float pair.
-__device__ __forceinline__ float2 df_avg6(float2 v0, float2 v1, float2 v2, float2 v3, float2 v4, float2 v5) {
-  float s, c, e;
-  two_sum(v0.x, v1.x, s, c);
-  two_sum(s, v2.x, s, e);
-  c += e;
-  two_sum(s, v3.x, s, e);
-  c += e;
-  two_sum(s, v4.x, s, e);
-  c += e;
-  two_sum(s, v5.x, s, e);
-  c += e;
-  c += ((v0.y + v1.y) + (v2.y + v3.y)) + (v4.y + v5.y);
-  const float p = s * kSixthHi;
-  float pe = fmaf(s, kSixthHi, -p);
-  pe = fmaf(s, kSixthLo, pe);
-  pe = fmaf(c, kSixthHi, pe);
-  return make_float2(p, pe);
-}
-
-__device__ __forceinline__ double pair_to_double(float2 v) { return f2d_bits(v.x) + f2d_bits(v.y); }
-
-__device__ __forceinline__ float2 pair_normalize(float2 v) {
-  float hi, lo;
-  two_sum(v.x, v.y, hi, lo);
-  return make_float2(hi, lo);
-}
-
-// A float64 value the float-pair path cannot carry to later sweeps.
-__device__ __forceinline__ bool outside_pair_range(double v) {
-  const long long b = __double_as_longlong(v);
-  if ((b << 1) == 0) return false;
-  const int e = (int)((b >> 52) & 0x7ff);
-  return e < 949 || e > 1140;
 }
 
 // ------------------------------------------------------------------ TMA ring

@@ -1,0 +1,221 @@
+"""Persistent mixed-stream executor against the oracle (GPU).
+
+One batch mixes every variant of the four loops (forced variants), so the
+phase-major scheduling, the Jacobi sweep dependencies and the merge-path
+fix-up phase all run in the same persistent launch.  A second batch lets the
+device MLPs choose; a third is replayed from a captured CUDA graph.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2303_08873_b300 as ar
+import synth
+from oracle import loops
+from tests.gpu_util import dev, host
+
+pytestmark = pytest.mark.gpu
+EPS = synth.NBODY_EPS
+
+
+class Batch:
+    """Calls with their own device buffers, plus the expected outputs."""
+
+    def __init__(self):
+        self.calls, self.keep, self.check = [], [], []
+
+    def daxpy(self, n, seed):
+        a, x, y = synth.daxpy_inputs(seed, n)
+        xd, yd = dev(x), dev(y)
+        self.keep += [xd, yd]
+        self.calls.append(ar.ArExecCall(loop=0, n=n, a=a, in0=xd.data_ptr(), out0=yd.data_ptr()))
+        ref = loops.daxpy(a, x, y)
+        scale = np.abs(a * x) + np.abs(y)
+        self.check.append(lambda yd=yd, ref=ref, scale=scale: np.all(np.abs(host(yd) - ref) <= 1e-13 * scale))
+
+    def jacobi(self, N, sweeps, seed):
+        u0 = synth.grid_inputs(seed, N)
+        ud = dev(u0)
+        out, work = torch.empty_like(ud), torch.empty_like(ud)
+        self.keep += [ud, out, work]
+        self.calls.append(ar.ArExecCall(loop=1, sweeps=sweeps, n=N, in0=ud.data_ptr(), out0=out.data_ptr(),
+                                        out1=work.data_ptr()))
+        ref = loops.jacobi7(u0, sweeps)
+        self.check.append(lambda out=out, ref=ref: np.max(np.abs(host(out) - ref)) <= 1e-13 * np.max(np.abs(ref)))
+
+    def spmv(self, mat, seed):
+        rp, c, v = mat
+        rows = rp.numel() - 1
+        nnz = int(rp[-1])
+        x = synth.spmv_x(seed, rows).numpy()
+        d = [t.cuda() for t in (rp, c, v)] + [dev(x)]
+        y = torch.full((rows,), np.nan, dtype=torch.float64, device="cuda")
+        nb = -(-(rows + nnz) // 4096)
+        ws = torch.empty(16 * nb + 16, dtype=torch.uint8, device="cuda")
+        self.keep += d + [y, ws]
+        self.calls.append(ar.ArExecCall(loop=2, n=rows, nnz=nnz, in0=d[0].data_ptr(), in1=d[1].data_ptr(),
+                                        in2=d[2].data_ptr(), in3=d[3].data_ptr(), out0=y.data_ptr(),
+                                        out1=ws.data_ptr(), out1_bytes=ws.numel()))
+        rph, ch, vh = rp.numpy(), c.numpy(), v.numpy()
+        ref, absum = loops.spmv_rows(rph, ch, vh, x, np.arange(rows))
+        self.check.append(lambda y=y, ref=ref, absum=absum: np.all(np.abs(host(y) - ref) <= 1e-10 * absum))
+        return loops.csr_row_stats(rph)
+
+    def nbody(self, N, seed):
+        p = synth.nbody_inputs(seed, N)
+        pd = dev(p)
+        acc = torch.full((N, 4), np.nan, dtype=torch.float32, device="cuda")
+        self.keep += [pd, acc]
+        self.calls.append(ar.ArExecCall(loop=3, n=N, eps=EPS, in0=pd.data_ptr(), out0=acc.data_ptr()))
+        ref = loops.nbody(p, EPS)
+        scale = np.max(np.linalg.norm(ref, axis=1))
+
+        def ok(acc=acc, ref=ref, scale=scale):
+            a = host(acc)
+            return np.max(np.linalg.norm(a[:, :3] - ref, axis=1)) <= 1e-4 * scale and np.all(a[:, 3] == 0)
+        self.check.append(ok)
+
+    def run(self, force=None, models=None, stream=None):
+        n = len(self.calls)
+        table = torch.frombuffer(bytearray(ar.exec_table_bytes(self.calls)), dtype=torch.uint8).cuda()
+        self.keep.append(table)
+        out = {"variant": torch.full((n,), -9, dtype=torch.int32, device="cuda"),
+               "conf": torch.zeros(n, dtype=torch.float32, device="cuda"),
+               "features": torch.zeros((n, 8), dtype=torch.float32, device="cuda"),
+               "t0": torch.zeros(n, dtype=torch.int64, device="cuda"),
+               "t1": torch.zeros(n, dtype=torch.int64, device="cuda"),
+               "status": torch.full((n,), 99, dtype=torch.int32, device="cuda")}
+        wsb = ar.ar_exec_workspace_bytes(n)
+        ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+        fv = dev(np.asarray(force, dtype=np.int32)) if force is not None else None
+        ar.ar_exec_batch(table, n, models, fv, out["variant"], out["conf"], out["features"], out["t0"], out["t1"],
+                         out["status"], ws, wsb, stream=stream)
+        torch.cuda.synchronize()
+        return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def test_every_variant_of_every_loop_in_one_batch():
+    b = Batch()
+    force = []
+    for v in range(15):
+        b.daxpy(100003 + v, 10 + v)
+        force.append(v)
+    for v in range(16):
+        b.jacobi(37 if v % 2 else 50, 3, 30 + v)
+        force.append(v)
+    zipf = synth.csr_zipf(5, 20000, 1.6)
+    band = synth.csr_band(6, 9000, 129)
+    stats = []
+    for v in range(7):
+        stats.append(b.spmv(zipf if v % 2 == 0 else band, 50 + v))
+        force.append(v)
+    for v in range(9):
+        b.nbody(1000 + 37 * v, 70 + v)
+        force.append(v)
+    r = b.run(force=force)
+    assert np.all(r["status"] == 0)
+    assert np.array_equal(r["variant"], np.array(force))
+    for k, ok in enumerate(b.check):
+        assert ok(), (k, b.calls[k].loop, force[k])
+    assert np.all(r["t1"] >= r["t0"]) and np.all(r["t0"] > 0)
+    # features of the SpMV calls (reduced on the device)
+    for k, st in zip(range(31, 38), stats):
+        f = r["features"][k]
+        assert f[0] == np.float32(st[0]) and f[1] == np.float32(st[1]) and f[4] == st[4]
+        assert f[2] == pytest.approx(st[2], rel=1e-6) and f[3] == pytest.approx(st[3], rel=1e-5)
+    assert r["features"][0][0] == 100003 and tuple(r["features"][15][:2]) == (50.0, 3.0)
+
+
+def test_bad_variant_and_loop_are_reported_per_call():
+    b = Batch()
+    b.daxpy(1000, 1)
+    b.daxpy(1000, 2)
+    b.calls.append(ar.ArExecCall(loop=7, n=10))
+    b.check.append(lambda: True)
+    r = b.run(force=[3, 15, 0])
+    assert r["status"][0] == 0 and r["status"][1] == ar.AR_ERR_ARG and r["status"][2] == ar.AR_ERR_ARG
+    assert b.check[0]()
+
+
+def _trained_models():
+    """One MLP per loop, trained on the device from a deterministic cost model
+    of the features (no timing involved)."""
+    specs = [(1, 15, lambda f: int(np.log2(f[0])) % 15), (2, 16, lambda f: (int(f[0]) // 40) % 16),
+             (5, 7, lambda f: 6 if f[2] > 20 else (1 if f[4] > 1000 else 3)), (1, 9, lambda f: int(f[0] > 2000) * 4)]
+    models = ar.ArExecModels()
+    models.H = 64
+    keep, regions = [], []
+    rng = np.random.Generator(np.random.PCG64(9))
+    samples = {0: [[float(2 ** rng.uniform(10, 24))] for _ in range(300)],
+               1: [[float(rng.integers(8, 600)), 3.0] for _ in range(300)],
+               2: [[float(rng.integers(1e3, 1e6)), 1e6, float(rng.uniform(1, 60)), 5.0, float(rng.integers(1, 4096))]
+                   for _ in range(300)],
+               3: [[float(rng.integers(500, 5000))] for _ in range(300)]}
+    for L, (F, V, best) in enumerate(specs):
+        r = ar.Region(f"exec{L}", F, "mlp,64,epochs=400,seed=1", 10 ** 9)
+        for v in range(V):
+            r.register(f"v{v}", float(v), lambda a, v, x, s, u: 0)
+        r.set_fake_timer(lambda f, v, best=best: 1.0 if v == best(f) else 2.0)
+        for f in samples[L]:
+            r.profile(f, reps=1)
+        r.train()
+        m = r.mlp()
+        th, mu, sd = dev(m["theta"]), dev(m["mu"]), dev(m["sd"])
+        keep += [th, mu, sd]
+        models.F[L], models.V[L] = F, V
+        models.theta[L], models.mu[L], models.sd[L] = th.data_ptr(), mu.data_ptr(), sd.data_ptr()
+        regions.append(r)
+    return models, keep, regions
+
+
+def test_device_mlp_selection_matches_host_models():
+    models, keep, regions = _trained_models()
+    b = Batch()
+    b.daxpy(70000, 1)
+    b.daxpy(3000000, 2)
+    b.jacobi(45, 2, 3)
+    b.jacobi(130, 1, 4)
+    b.spmv(synth.csr_zipf(7, 30000, 1.5), 5)
+    b.nbody(1500, 6)
+    b.nbody(3000, 7)
+    r = b.run(models=models)
+    assert np.all(r["status"] == 0)
+    for k, call in enumerate(b.calls):
+        f = r["features"][k][:regions[call.loop].nf]
+        want, conf = regions[call.loop].select(list(f))
+        assert r["variant"][k] == want, (k, call.loop)
+        assert r["conf"][k] == pytest.approx(conf, abs=1e-4)
+        assert b.check[k](), k
+
+
+def test_graph_capture_and_replay_with_new_table():
+    b1, b2 = Batch(), Batch()
+    for b, s in ((b1, 0), (b2, 100)):
+        b.daxpy(50001, 1 + s)
+        b.jacobi(40, 4, 2 + s)
+        b.spmv(synth.csr_zipf(3 + s, 5000, 2.0), 4 + s)
+        b.nbody(700, 5 + s)
+    n = 4
+    force = dev(np.array([8, 13, 6, 4], dtype=np.int32))
+    table = torch.zeros(96 * n, dtype=torch.uint8, device="cuda")
+    host_table = torch.zeros(96 * n, dtype=torch.uint8).pin_memory()
+    outs = [torch.zeros(n, dtype=torch.int32, device="cuda"), torch.zeros(n, dtype=torch.float32, device="cuda"),
+            torch.zeros((n, 8), dtype=torch.float32, device="cuda"), torch.zeros(n, dtype=torch.int64, device="cuda"),
+            torch.zeros(n, dtype=torch.int64, device="cuda"), torch.zeros(n, dtype=torch.int32, device="cuda")]
+    wsb = ar.ar_exec_workspace_bytes(n)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    host_table.copy_(torch.frombuffer(bytearray(ar.exec_table_bytes(b1.calls)), dtype=torch.uint8))
+    with torch.cuda.graph(g, stream=s):
+        table.copy_(host_table, non_blocking=True)
+        ar.ar_exec_batch(table, n, None, force, *outs, ws, wsb, stream=s)
+    for b in (b1, b2):
+        host_table.copy_(torch.frombuffer(bytearray(ar.exec_table_bytes(b.calls)), dtype=torch.uint8))
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.all(outs[5].cpu().numpy() == 0)
+        for k, ok in enumerate(b.check):
+            assert ok(), k
