@@ -48,8 +48,11 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--cpu-seconds", type=float, default=10.0)
-    p.add_argument("--workload", default="jacobi7", choices=["jacobi7", "spmv"],
-                   help="jacobi7: the headline line; spmv: the learned-selector study (one JSON line)")
+    p.add_argument("--workload", default="jacobi7", choices=["jacobi7", "spmv", "mixed"],
+                   help="jacobi7: the headline line; spmv: the learned-selector study; mixed: the "
+                        "persistent mixed-stream executor (each prints one JSON line)")
+    p.add_argument("--calls", type=int, default=10000, help="mixed: calls in the stream")
+    p.add_argument("--tau", type=float, default=0.5, help="mixed: confidence below which a call is profiled")
     p.add_argument("--train", type=int, default=2000, help="spmv: profiled training matrices")
     p.add_argument("--test", type=int, default=500, help="spmv: held-out test matrices")
     p.add_argument("--rows-max", type=float, default=1e7, help="spmv: largest row count")
@@ -335,7 +338,7 @@ def run_ours(args):
         "clocks": clk,
         "fp64_fma_per_s": fp64_fma,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 
@@ -350,10 +353,15 @@ def spmv_bytes(rows, nnz):
 
 
 def run_spmv(args):
-    """Config 3: profile `train` seeded matrices (7 variants, 5 reps after a
+    print(json.dumps(spmv_study(args.train, args.test, args.rows_max, args.epochs)), flush=True)
+
+
+def spmv_study(n_train, n_test, rows_max, epochs):
+    """Config 3: profile `n_train` seeded matrices (7 variants, 5 reps after a
     warm-up, L2 flushed), train the MLP selector on the device and the depth-2
     tree on the same records, then compare their choices with the exhaustive
-    argmin and the fixed default (thread per row) on `test` held-out matrices."""
+    argmin and the fixed default (thread per row) on `n_test` held-out
+    matrices.  Returns the JSON-ready result."""
     import torch
 
     import paper_2303_08873_b300 as ar
@@ -368,7 +376,7 @@ def run_spmv(args):
     f5 = torch.zeros(5, dtype=torch.float32, device=dev)
 
     def case(seed):
-        prm = synth.spmv_matrix_params(seed, rows_max=args.rows_max)
+        prm = synth.spmv_matrix_params(seed, rows_max=rows_max)
         rp, c, v = synth.spmv_matrix(seed, prm, device="cuda")
         rows = prm["rows"]
         nnz = int(rp[-1].item())
@@ -381,7 +389,7 @@ def run_spmv(args):
                           ws.data_ptr(), ws.numel())
         return feats, a, (rp, c, v, x, y), rows, nnz
 
-    mlp = ar.Region("spmv-mlp", 5, f"mlp,64,epochs={args.epochs},seed=7", 10 ** 9)
+    mlp = ar.Region("spmv-mlp", 5, f"mlp,64,epochs={epochs},seed=7", 10 ** 9)
     tree = ar.Region("spmv-dtree", 5, "dtree,2", 10 ** 9)
     exh = ar.Region("spmv-exhaustive", 5, "exhaustive,reps=5")
     V = mlp.add_builtin(ar.AR_LOOP_SPMV)
@@ -394,7 +402,7 @@ def run_spmv(args):
 
     t0 = time.perf_counter()
     prof_ms = 0.0
-    for k in range(args.train):
+    for k in range(n_train):
         feats, a, keep, rows, nnz = case(1000 + k)
         ms, _ = mlp.profile(feats, a, stream=stream)
         prof_ms += 6 * sum(ms)  # warm-up + 5 timed runs of every variant
@@ -408,7 +416,7 @@ def run_spmv(args):
     tree.train()
 
     per = []
-    for k in range(args.test):
+    for k in range(n_test):
         feats, a, keep, rows, nnz = case(3000 + k)
         ms, best = exh.profile(feats, a, stream=stream)
         vm, conf = mlp.select(feats)
@@ -432,8 +440,8 @@ def run_spmv(args):
     line = {
         "metric": METRIC, "value": res["mlp"]["gbs"], "unit": "GB/s", "n_gpus": 1, "dtype": "f64",
         "data": "synthetic", "higher_is_better": True, "vs_baseline": None,
-        "config": {"workload": f"spmv float64 CSR, {args.train} training + {args.test} test matrices, rows "
-                               f"log-uniform [1e4, {args.rows_max:.0e}], 50% Zipf(s in [1.5,2.5]) / 50% band(7..129)",
+        "config": {"workload": f"spmv float64 CSR, {n_train} training + {n_test} test matrices, rows "
+                               f"log-uniform [1e4, {rows_max:.0e}], 50% Zipf(s in [1.5,2.5]) / 50% band(7..129)",
                    "features": list(SPMV_FEATURES), "variants": names, "default": names[default]},
         "selection": {"exhaustive_best_gbs": best_gbs, **{k + "_" + m: v for k, d in res.items() for m, v in d.items()},
                       "mlp_low_confidence_calls": low_conf,
@@ -444,12 +452,259 @@ def run_spmv(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- mixed stream
+LOOPS = ("daxpy", "jacobi7", "spmv", "nbody")
+NBODY_FLOPS = 20.0
+
+
+class Arena:
+    """Bump allocator over one device tensor, reset per batch."""
+
+    def __init__(self, t):
+        self.t, self.off = t, 0
+
+    def take(self, nbytes):
+        o = (self.off + 255) & ~255
+        if o + nbytes > self.t.numel() * self.t.element_size():
+            raise MemoryError
+        self.off = o + nbytes
+        return self.t.data_ptr() + o
+
+
+def run_mixed(args):
+    """Config 5: a stream of `calls` region invocations (loop ~ U{4}, sizes
+    log-uniform over each loop's range, SpMV from a pool of 32 matrices) run by
+    the persistent executor in batches of 256 replayed from one captured CUDA
+    graph; the per-loop MLPs, trained on the executor's own single-call times,
+    choose the variants on the device.  Calls whose confidence is below tau
+    are profiled exhaustively afterwards (the fallback) and counted."""
+    import torch
+
+    import paper_2303_08873_b300 as ar
+    import synth
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    B = ar.AR_EXEC_MAX_CALLS
+    loop_ids, sizes = synth.mixed_stream(5, args.calls)
+    # pool of SpMV matrices (device-generated), shared inputs; y per call
+    pool = []
+    for k in range(32):
+        prm = synth.spmv_matrix_params(5000 + k)
+        rp, c, v = synth.spmv_matrix(5000 + k, prm, device="cuda")
+        x = synth.spmv_x(5000 + k, prm["rows"], device="cuda")
+        pool.append((prm["rows"], int(rp[-1].item()), rp, c, v, x))
+    f64 = torch.empty((64 << 30) // 8, dtype=torch.float64, device=dev).uniform_(-1.0, 1.0)
+    f32 = torch.empty((1 << 30) // 4, dtype=torch.float32, device=dev).uniform_(0.5, 1.0)
+    scratch = torch.empty((48 << 30) // 8, dtype=torch.float64, device=dev)
+
+    def make_call(loop, size, a64, a32, sc):
+        """ArExecCall for one invocation; inputs point into the random arenas,
+        outputs into the scratch arena.  Returns (call, algorithmic bytes, flops)."""
+        c = ar.ArExecCall(loop=int(loop))
+        if loop == 0:
+            n = int(size)
+            c.n, c.a = n, 1.5
+            c.in0, c.out0 = a64.take(8 * n), sc.take(8 * n)
+            return c, 24.0 * n, 2.0 * n
+        if loop == 1:
+            N = int(size)
+            c.n, c.sweeps = N, 10
+            c.in0, c.out0, c.out1 = a64.take(8 * N ** 3), sc.take(8 * N ** 3), sc.take(8 * N ** 3)
+            return c, 16.0 * N ** 3 * 10, 6.0 * N ** 3 * 10
+        if loop == 2:
+            rows, nnz, rp, cl, v, x = pool[int(size)]
+            c.n, c.nnz = rows, nnz
+            c.in0, c.in1, c.in2, c.in3 = rp.data_ptr(), cl.data_ptr(), v.data_ptr(), x.data_ptr()
+            c.out0 = sc.take(8 * rows)
+            nb = -(-(rows + nnz) // 4096)
+            c.out1, c.out1_bytes = sc.take(16 * nb), 16 * nb
+            return c, spmv_bytes(rows, nnz), 2.0 * nnz
+        N = int(size)
+        c.n, c.eps = N, synth.NBODY_EPS
+        c.in0, c.out0 = a32.take(16 * N), sc.take(16 * N)
+        return c, 0.0, NBODY_FLOPS * N * N
+
+    def arenas():
+        return Arena(f64), Arena(f32), Arena(scratch)
+
+    # executor buffers and one captured graph for a full batch
+    table_h = torch.zeros(96 * B, dtype=torch.uint8).pin_memory()
+    table_d = torch.zeros(96 * B, dtype=torch.uint8, device=dev)
+    o_var = torch.zeros(B, dtype=torch.int32, device=dev)
+    o_conf = torch.zeros(B, dtype=torch.float32, device=dev)
+    o_feat = torch.zeros((B, 8), dtype=torch.float32, device=dev)
+    o_t0 = torch.zeros(B, dtype=torch.int64, device=dev)
+    o_t1 = torch.zeros(B, dtype=torch.int64, device=dev)
+    o_st = torch.zeros(B, dtype=torch.int32, device=dev)
+    h_out = [torch.zeros_like(t, device="cpu").pin_memory() for t in (o_var, o_conf, o_feat, o_t0, o_t1, o_st)]
+    wsb = ar.ar_exec_workspace_bytes(B)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    force_d = torch.zeros(B, dtype=torch.int32, device=dev)
+
+    def run_batch(calls, force=None, models=None):
+        """Eager batch (profiling): returns per-call (variant, conf, features, ns, status)."""
+        n = len(calls)
+        table_d[:96 * n].copy_(torch.frombuffer(bytearray(ar.exec_table_bytes(calls)), dtype=torch.uint8))
+        fv = None
+        if force is not None:
+            force_d[:n].copy_(torch.tensor(force, dtype=torch.int32))
+            fv = force_d
+        ar.ar_exec_batch(table_d, n, models, fv, o_var, o_conf, o_feat, o_t0, o_t1, o_st, ws, wsb, stream=stream)
+        stream.synchronize()
+        return (o_var[:n].cpu().numpy(), o_conf[:n].cpu().numpy(), o_feat[:n].cpu().numpy(),
+                (o_t1[:n] - o_t0[:n]).cpu().numpy(), o_st[:n].cpu().numpy())
+
+    def exhaustive(loop, size, reps):
+        """Executor time (ns, mean of reps) of every variant for one call."""
+        V = ar.loop_num_variants(loop)
+        times = []
+        feats = None
+        for v in range(V):
+            acc = []
+            for _ in range(reps + 1):
+                c, _, _ = make_call(loop, size, *arenas())
+                _, _, f, ns, st = run_batch([c], force=[v])
+                assert st[0] == 0
+                acc.append(float(ns[0]))
+                feats = f[0]
+            times.append(statistics.mean(acc[1:]))
+        return times, feats
+
+    # --- training: executor single-call profiles of sampled sizes per loop
+    rng = np.random.Generator(np.random.PCG64(55))
+    lo = {0: 2.0 ** 10, 1: 32.0, 3: 1024.0}
+    hi = {0: 2.0 ** 24, 1: 512.0, 3: 262144.0}
+    train_sizes = {L: [int(np.exp(rng.uniform(np.log(lo[L]), np.log(hi[L])))) for _ in range(24)] for L in (0, 1, 3)}
+    train_sizes[2] = list(range(32))
+    regions, keep = {}, []
+    models = ar.ArExecModels()
+    models.H = 64
+    nfeat = {0: 1, 1: 2, 2: 5, 3: 1}
+    prof_ns = 0.0
+    t0w = time.perf_counter()
+    for L in range(4):
+        r = ar.Region(f"mixed-{LOOPS[L]}", nfeat[L], "mlp,64,epochs=400,seed=3", 10 ** 9)
+        r.add_builtin(L)
+        for size in train_sizes[L]:
+            times, f = exhaustive(L, size, 2)
+            prof_ns += 3 * sum(times)
+            for v, t in enumerate(times):
+                r.add_record(list(f[:nfeat[L]]), v, t * 1e-6)
+        r.train()
+        m = r.mlp()
+        th, mu, sd = (torch.from_numpy(m[k]).to(dev) for k in ("theta", "mu", "sd"))
+        keep += [th, mu, sd]
+        models.F[L], models.V[L] = m["F"], m["V"]
+        models.theta[L], models.mu[L], models.sd[L] = th.data_ptr(), mu.data_ptr(), sd.data_ptr()
+        regions[L] = r
+    train_wall = time.perf_counter() - t0w
+
+    # --- capture one batch graph: table copy, executor, result copies
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        table_d.copy_(table_h, non_blocking=True)
+        ar.ar_exec_batch(table_d, B, models, None, o_var, o_conf, o_feat, o_t0, o_t1, o_st, ws, wsb, stream=stream)
+        for h, d in zip(h_out, (o_var, o_conf, o_feat, o_t0, o_t1, o_st)):
+            h.copy_(d, non_blocking=True)
+
+    batches = [range(s0, min(s0 + B, args.calls)) for s0 in range(0, args.calls, B)]
+    # full batches replay the graph; a final partial batch runs eagerly
+    lat = {L: [] for L in range(4)}
+    byts = flops = 0.0
+    low = []
+    chosen = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    batch_ms = []
+    for bi, idx in enumerate(batches):
+        a64, a32, sc = arenas()
+        calls = []
+        for q in idx:
+            c, b_, f_ = make_call(loop_ids[q], sizes[q], a64, a32, sc)
+            calls.append(c)
+            byts += b_
+            flops += f_ if loop_ids[q] == 3 else 0.0
+        n = len(calls)
+        table_h[:96 * n].copy_(torch.frombuffer(bytearray(ar.exec_table_bytes(calls)), dtype=torch.uint8))
+        ev0.record(stream)
+        if n == B:
+            g.replay()
+        else:
+            with torch.cuda.stream(stream):
+                table_d[:96 * n].copy_(table_h[:96 * n], non_blocking=True)
+                ar.ar_exec_batch(table_d, n, models, None, o_var, o_conf, o_feat, o_t0, o_t1, o_st, ws, wsb,
+                                 stream=stream)
+                for h, d in zip(h_out, (o_var, o_conf, o_feat, o_t0, o_t1, o_st)):
+                    h.copy_(d, non_blocking=True)
+        ev1.record(stream)
+        stream.synchronize()
+        batch_ms.append(ev0.elapsed_time(ev1))
+        var, conf, feat, t0n, t1n, st = (h.numpy()[:n] for h in h_out)
+        assert np.all(st == 0), "executor status"
+        for k, q in enumerate(idx):
+            L = int(loop_ids[q])
+            lat[L].append((int(t1n[k]) - int(t0n[k])) * 1e-3)
+            chosen.append((L, int(sizes[q]), int(var[k])))
+            if conf[k] < args.tau:
+                low.append(q)
+    stream_ms = sum(batch_ms)
+    mem_bytes = byts  # daxpy + Jacobi + SpMV algorithmic bytes
+    # --- regret on a sample of the stream (exhaustive executor times)
+    samp = rng.choice(len(chosen), size=min(96, len(chosen)), replace=False)
+    regrets = {L: [] for L in range(4)}
+    for q in samp:
+        L, size, v = chosen[q]
+        times, _ = exhaustive(L, size, 2)
+        regrets[L].append(times[v] / min(times) - 1.0)
+    # --- fallback: exhaustive profiling of the low-confidence calls (counted, timed on a sample)
+    fb_sample = low[:16]
+    t_fb = time.perf_counter()
+    fb_ns = 0.0
+    for q in fb_sample:
+        times, _ = exhaustive(int(loop_ids[q]), int(sizes[q]), 2)
+        fb_ns += 3 * sum(times)
+    t_fb = time.perf_counter() - t_fb
+    all_reg = [x for L in range(4) for x in regrets[L]]
+    line = {
+        "metric": METRIC, "value": mem_bytes / (stream_ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1,
+        "dtype": "f64 (daxpy, Jacobi, SpMV) / f32 (n-body)", "data": "synthetic", "higher_is_better": True,
+        "vs_baseline": None,
+        "config": {"workload": f"mixed stream of {args.calls} calls (loop ~ U{{4}}, sizes log-uniform), batches "
+                               f"of {B} replayed from one CUDA graph, device MLP selection, tau = {args.tau}",
+                   "batches": len(batches)},
+        "stream": {"ms": stream_ms, "memory_loops_gbs": mem_bytes / (stream_ms * 1e-3) / 1e9,
+                   "nbody_gflops": flops / (stream_ms * 1e-3) / 1e9,
+                   "batch_ms_p50": float(np.percentile(batch_ms, 50)),
+                   "latency_us": {LOOPS[L]: {"p50": float(np.percentile(lat[L], 50)),
+                                             "p99": float(np.percentile(lat[L], 99)), "calls": len(lat[L])}
+                                  for L in range(4) if lat[L]},
+                   "kernels_per_batch": 3},
+        "selection": {"mean_regret_pct": 100 * statistics.mean(all_reg),
+                      "per_loop_regret_pct": {LOOPS[L]: 100 * statistics.mean(regrets[L]) for L in range(4)
+                                              if regrets[L]},
+                      "regret_sample_calls": len(samp), "low_confidence_calls": len(low),
+                      "low_confidence_pct": 100.0 * len(low) / args.calls},
+        "cost": {"training_profile_gpu_ms": prof_ns * 1e-6, "training_wall_s": train_wall,
+                 "fallback_profile_gpu_ms_per_call": (fb_ns * 1e-6 / len(fb_sample)) if fb_sample else 0.0,
+                 "profiling_cost_ratio": None},
+    }
+    # profiling cost of the learned method (training set + fallbacks) over
+    # exhaustive profiling of every call, estimated from the sampled calls
+    exh_per_call_ms = statistics.mean(3 * sum(exhaustive(L, s_, 1)[0]) * 1e-6 for L, s_, _ in
+                                      (chosen[q] for q in samp[:24]))
+    learned = prof_ns * 1e-6 + len(low) * line["cost"]["fallback_profile_gpu_ms_per_call"]
+    line["cost"]["profiling_cost_ratio"] = learned / (exh_per_call_ms * args.calls)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "spmv":
         run_spmv(args)
+    elif args.workload == "mixed":
+        run_mixed(args)
     else:
         run_ours(args)
 
