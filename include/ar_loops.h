@@ -200,8 +200,12 @@ int ar_nbody_batched(int count, const int32_t *offs, const float *pos4, float *a
  * AR_ERR_ARG for a bad loop/variant, AR_ERR_TIMEOUT if a dependency wait gave
  * up).  The call table and models must stay valid until the work completes.
  * workspace: ar_exec_workspace_bytes(max_calls) bytes, no initialisation
- * needed.  The launches contain no host synchronisation and can be captured
- * in a CUDA graph together with the copy that refreshes `calls`. */
+ * needed.  Two batches that share a workspace (or a call table) must not
+ * overlap on the GPU: order them on one stream.  The launches contain no host
+ * synchronisation and can be captured in a CUDA graph together with the copy
+ * that refreshes `calls` (a captured graph replays on the stream it is
+ * launched on, which must be the one other batches using the workspace run
+ * on). */
 #define AR_EXEC_MAX_CALLS 256
 #define AR_EXEC_MAX_PHASES 64
 typedef struct ar_exec_call {

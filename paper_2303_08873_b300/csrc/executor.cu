@@ -594,9 +594,11 @@ __global__ void __launch_bounds__(T, 2) exec_run(const ar_exec_call* __restrict_
     if (s_item >= total) break;
     const int c = s_c, p = s_p;
     const long long t = s_t;
-    if (s_ok) {
-      const ar_exec_call k = calls[c];
-      const int v = vint[c];
+    const ar_exec_call k = calls[c];
+    const int v = vint[c];
+    // the plan validated (loop, variant); re-checked so that a call table
+    // changed under a running batch cannot index outside the variant tables
+    if (s_ok && k.loop >= 0 && k.loop < 4 && v >= 0 && v < c_nvar[k.loop]) {
       switch (k.loop) {
         case AR_LOOP_DAXPY: daxpy_tile(k, v, t); break;
         case AR_LOOP_JACOBI7: jacobi_tile(k, v, p, t, smraw); break;

@@ -5,7 +5,6 @@ phase-major scheduling, the Jacobi sweep dependencies and the merge-path
 fix-up phase all run in the same persistent launch.  A second batch lets the
 device MLPs choose; a third is replayed from a captured CUDA graph.
 """
-import ctypes
 
 import numpy as np
 import pytest
@@ -214,8 +213,9 @@ def test_graph_capture_and_replay_with_new_table():
         ar.ar_exec_batch(table, n, None, force, *outs, ws, wsb, stream=s)
     for b in (b1, b2):
         host_table.copy_(torch.frombuffer(bytearray(ar.exec_table_bytes(b.calls)), dtype=torch.uint8))
-        g.replay()
-        torch.cuda.synchronize()
+        with torch.cuda.stream(s):  # replay() runs on the current stream
+            g.replay()
+        s.synchronize()
         assert np.all(outs[5].cpu().numpy() == 0)
         for k, ok in enumerate(b.check):
             assert ok(), k
