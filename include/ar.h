@@ -69,6 +69,9 @@ typedef double (*ar_fake_time_fn)(const float *features, int nf, int variant, vo
  *   model_spec      NULL/"" for the default, else comma-separated:
  *                     "dtree[,<depth>]"  decision tree, default depth 2
  *                                        (Section 3.1 model_type)
+ *                     "rfc[,<ntrees>,<depth>]"  random forest: both
+ *                                        numbers or neither (Section 3.1);
+ *                                        default 10 trees of depth 2
  *                     "mlp[,<hidden>]"   3-layer MLP selector, hidden 64
  *                     "exhaustive"       per-feature-vector table of the
  *                                        fastest profiled variant
@@ -105,7 +108,7 @@ int ar_variant_register_range(ar_region *r, double begin, double end, double ste
 
 /* Region facts: variant count, feature count, effective min_train_data,
  * whether a model is trained (1) and the model kind (0 dtree, 1 mlp,
- * 2 exhaustive, 3 fixed).  Any out pointer may be NULL. */
+ * 2 exhaustive, 3 fixed, 4 rfc).  Any out pointer may be NULL. */
 int ar_region_info(const ar_region *r, int *num_variants, int *num_features, int *min_train_data,
                    int *trained, int *model_kind);
 
@@ -191,6 +194,18 @@ int ar_get_records(const ar_region *r, int64_t first, int64_t count, float *feat
  * AR_ERR_NOMODEL if the region has no trained tree. */
 int ar_tree_export(const ar_region *r, int max_nodes, int *feat, double *thr, int *left, int *right,
                    int *label, int *out_nodes);
+
+/* Random forest: number of trees, and one tree in the layout of
+ * ar_tree_export.  Each tree is CART grown on a bootstrap sample of the
+ * training set with max(1, floor(sqrt(num_features))) candidate features per
+ * split; all draws come from one SplitMix64 stream (the spec's seed, default
+ * 0x5eed) consumed tree by tree: the n bootstrap indices (next() mod n), then
+ * per split attempt in depth-first preorder a partial Fisher-Yates shuffle
+ * (a + next() mod (F - a)).  Prediction: majority vote, ties to the lowest
+ * variant; confidence = vote share.  AR_ERR_NOMODEL without a trained forest. */
+int ar_forest_size(const ar_region *r, int *ntrees);
+int ar_forest_tree_export(const ar_region *r, int tree, int max_nodes, int *feat, double *thr, int *left,
+                          int *right, int *label, int *out_nodes);
 
 /* Export the trained MLP: theta (ar_mlp_num_params floats, layout of
  * ar_loops.h), mu and sd (F floats each).  Any pointer may be NULL to query

@@ -109,7 +109,7 @@ def _majority(ys) -> int:
     return min(y for y, c in cnt.items() if c == top)
 
 
-def cart_fit(X, y, max_depth: int = 2):
+def cart_fit(X, y, max_depth: int = 2, samples=None, feature_draw=None):
     """Greedy CART classifier (Gini).
 
     Readings: candidate thresholds are midpoints (in float64) of consecutive
@@ -119,6 +119,10 @@ def cart_fit(X, y, max_depth: int = 2):
     is pure, or when no feature varies; a leaf predicts the majority label,
     ties to the lowest label.  Returns a list of nodes
     (feature, threshold, left, right, label); feature -1 marks a leaf.
+
+    ``samples`` (default: every row once) is the multiset of row indices the
+    tree is grown on; ``feature_draw()``, if given, is called once per split
+    attempt and returns the candidate features for that node (random forest).
     """
     nodes = []
 
@@ -126,12 +130,12 @@ def cart_fit(X, y, max_depth: int = 2):
         me = len(nodes)
         nodes.append(None)
         ys = [y[i] for i in idx]
-        if depth >= max_depth or len(set(ys)) <= 1:
+        if depth >= max_depth or len(set(ys)) <= 1 or len(idx) < 2:
             nodes[me] = (-1, 0.0, -1, -1, _majority(ys))
             return me
         best = None
         F = len(X[0])
-        for f in range(F):
+        for f in (sorted(feature_draw()) if feature_draw else range(F)):
             vals = sorted({float(X[i][f]) for i in idx})
             for a in range(len(vals) - 1):
                 thr = (vals[a] + vals[a + 1]) / 2.0
@@ -157,8 +161,65 @@ def cart_fit(X, y, max_depth: int = 2):
         nodes[me] = (f, thr, left, right, _majority(ys))
         return me
 
-    grow(list(range(len(y))), 0)
+    grow(list(range(len(y))) if samples is None else list(samples), 0)
     return nodes
+
+
+# ------------------------------------------------------------ random forest
+MASK64 = (1 << 64) - 1
+
+
+class SplitMix64:
+    """SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): a 64-bit state advanced
+    by the golden-ratio increment, output through two xor-shift-multiply
+    rounds and a final xor-shift."""
+
+    def __init__(self, seed: int):
+        self.s = seed & MASK64
+
+    def next(self) -> int:
+        self.s = (self.s + 0x9E3779B97F4A7C15) & MASK64
+        z = self.s
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+        return z ^ (z >> 31)
+
+
+def rfc_fit(X, y, ntrees: int, max_depth: int, seed: int):
+    """Random forest (Section 3.1, model_type rfc with a tree count and a
+    depth).  Reading: tree t is CART grown on a bootstrap sample (n indices
+    next() mod n) and, at every split attempt in depth-first preorder, on
+    mtry = max(1, floor(sqrt(F))) features drawn by a partial Fisher-Yates
+    shuffle (position a swaps with a + next() mod (F - a)); one SplitMix64
+    stream serves all trees in order."""
+    rng = SplitMix64(seed)
+    n, F = len(y), len(X[0])
+    mtry = max(1, int(math.floor(math.sqrt(F))))
+
+    def draw():
+        feats = list(range(F))
+        for a in range(mtry):
+            b = a + rng.next() % (F - a)
+            feats[a], feats[b] = feats[b], feats[a]
+        return feats[:mtry]
+
+    forest = []
+    for _ in range(ntrees):
+        samples = [rng.next() % n for _ in range(n)]
+        forest.append(cart_fit(X, y, max_depth, samples=samples, feature_draw=draw))
+    return forest
+
+
+def rfc_predict(forest, x):
+    """Majority vote of the trees, ties to the lowest label; returns (label,
+    vote share)."""
+    votes: dict = {}
+    for t in forest:
+        v = cart_predict(t, x)
+        votes[v] = votes.get(v, 0) + 1
+    top = max(votes.values())
+    lab = min(v for v, c in votes.items() if c == top)
+    return lab, top / len(forest)
 
 
 def cart_predict(nodes, x) -> int:

@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "AR_OK", -1: "AR_ERR_ARG", -2: "AR_ERR_STATE", -3: "AR_ERR_CU
 AR_MAX_FEATURES = 8
 AR_MAX_VARIANTS = 64
 AR_LOOP_DAXPY, AR_LOOP_JACOBI7, AR_LOOP_SPMV, AR_LOOP_NBODY = 0, 1, 2, 3
-MODEL_KINDS = {0: "dtree", 1: "mlp", 2: "exhaustive", 3: "fixed"}
+MODEL_KINDS = {0: "dtree", 1: "mlp", 2: "exhaustive", 3: "fixed", 4: "rfc"}
 
 
 class ArError(RuntimeError):
@@ -108,6 +108,8 @@ _SIGS = {
     "ar_record_counts": (_i, [_vp, _pi64, _pi64]),
     "ar_get_records": (_i, [_vp, _i64, _i64, _pf, _pi, _pf]),
     "ar_tree_export": (_i, [_vp, _i, _pi, _pd, _pi, _pi, _pi, _pi]),
+    "ar_forest_size": (_i, [_vp, _pi]),
+    "ar_forest_tree_export": (_i, [_vp, _i, _i, _pi, _pd, _pi, _pi, _pi, _pi]),
     "ar_mlp_export": (_i, [_vp, _pf, _pf, _pf, _pi, _pi, _pi]),
     "ar_region_save": (_i, [_vp, _cs]),
     "ar_region_load": (_i, [_vp, _cs]),
@@ -434,6 +436,21 @@ class Region:
         la = (ctypes.c_int * n)()
         self._ck(lib.ar_tree_export(self.h, n, fe, th, le, ri, la, ctypes.byref(cnt)))
         return [(fe[i], th[i] if fe[i] >= 0 else 0.0, le[i], ri[i], la[i]) for i in range(n)]
+
+    def forest(self):
+        """Random forest as a list of trees in the layout of tree()."""
+        nt = ctypes.c_int()
+        self._ck(lib.ar_forest_size(self.h, ctypes.byref(nt)))
+        out = []
+        for t in range(nt.value):
+            cnt = ctypes.c_int()
+            self._ck(lib.ar_forest_tree_export(self.h, t, 0, None, None, None, None, None, ctypes.byref(cnt)))
+            n = cnt.value
+            fe, th = (ctypes.c_int * n)(), (ctypes.c_double * n)()
+            le, ri, la = (ctypes.c_int * n)(), (ctypes.c_int * n)(), (ctypes.c_int * n)()
+            self._ck(lib.ar_forest_tree_export(self.h, t, n, fe, th, le, ri, la, ctypes.byref(cnt)))
+            out.append([(fe[i], th[i] if fe[i] >= 0 else 0.0, le[i], ri[i], la[i]) for i in range(n)])
+        return out
 
     def mlp(self):
         F, H, V = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

@@ -71,6 +71,8 @@ struct Fit {
   const std::vector<int>& y;
   int nf, max_depth, nlab;
   std::vector<TreeNode> nodes;
+  SplitMix64* rng = nullptr;  // random forest: per-node feature subsets
+  int mtry = 0;
 
   void majority(const std::vector<int>& idx, int* label, float* conf) const {
     std::vector<int> cnt((size_t)nlab, 0);
@@ -110,7 +112,21 @@ struct Fit {
     int bf = -1;
     double bthr = 0.0;
     std::vector<std::pair<double, int>> vals;
-    for (int f = 0; f < nf; ++f) {
+    // candidate features: all, or (forest) mtry distinct ones drawn by a
+    // partial Fisher-Yates shuffle, visited in ascending order
+    int feats[AR_MAX_FEATURES];
+    int nfe = nf;
+    for (int f = 0; f < nf; ++f) feats[f] = f;
+    if (rng) {
+      for (int a = 0; a < mtry; ++a) {
+        const int b = a + (int)(rng->next() % (uint64_t)(nf - a));
+        std::swap(feats[a], feats[b]);
+      }
+      nfe = mtry;
+      std::sort(feats, feats + nfe);
+    }
+    for (int fi = 0; fi < nfe; ++fi) {
+      const int f = feats[fi];
       vals.clear();
       for (int i : idx) vals.push_back({(double)X[i][f], y[i]});
       std::sort(vals.begin(), vals.end());
@@ -162,6 +178,44 @@ std::vector<TreeNode> tree_fit(const std::vector<std::array<float, AR_MAX_FEATUR
   for (size_t i = 0; i < y.size(); ++i) idx[i] = (int)i;
   if (!idx.empty()) fit.grow(idx, 0);
   return fit.nodes;
+}
+
+std::vector<std::vector<TreeNode>> forest_fit(const std::vector<std::array<float, AR_MAX_FEATURES>>& X,
+                                              const std::vector<int>& y, int nf, int ntrees, int max_depth,
+                                              uint64_t seed) {
+  int nlab = 1;
+  for (int v : y) nlab = std::max(nlab, v + 1);
+  SplitMix64 rng{seed};
+  const int n = (int)y.size();
+  int mtry = (int)std::floor(std::sqrt((double)nf));
+  if (mtry < 1) mtry = 1;
+  std::vector<std::vector<TreeNode>> forest;
+  for (int t = 0; t < ntrees; ++t) {
+    std::vector<int> idx((size_t)n);
+    for (int i = 0; i < n; ++i) idx[i] = (int)(rng.next() % (uint64_t)n);  // bootstrap sample
+    Fit fit{X, y, nf, max_depth, nlab, {}};
+    fit.rng = &rng;
+    fit.mtry = mtry;
+    if (n > 0) fit.grow(idx, 0);
+    forest.push_back(std::move(fit.nodes));
+  }
+  return forest;
+}
+
+int forest_predict(const std::vector<std::vector<TreeNode>>& forest, const float* f, float* conf) {
+  if (forest.empty()) return -1;
+  std::vector<int> votes;
+  for (const auto& t : forest) {
+    const int v = tree_predict(t, f, nullptr);
+    if (v < 0) continue;
+    if ((int)votes.size() <= v) votes.resize((size_t)v + 1, 0);
+    votes[v]++;
+  }
+  int best = 0;
+  for (int v = 1; v < (int)votes.size(); ++v)
+    if (votes[v] > votes[best]) best = v;
+  if (conf) *conf = (float)votes[best] / (float)forest.size();
+  return best;
 }
 
 int tree_predict(const std::vector<TreeNode>& t, const float* f, float* conf) {

@@ -49,6 +49,19 @@ std::vector<TreeNode> tree_fit(const std::vector<std::array<float, AR_MAX_FEATUR
                                const std::vector<int>& y, int nf, int max_depth);
 int tree_predict(const std::vector<TreeNode>& t, const float* f, float* conf);
 
+// Random forest (Section 3.1 model_type rfc, ntrees, depth): tree t is the
+// CART above grown on a bootstrap sample of the training set (n draws with
+// replacement) and, at every node it tries to split, on mtry =
+// max(1, floor(sqrt(nf))) features drawn without replacement.  All draws come
+// from one SplitMix64 stream seeded with `seed`, consumed tree by tree:
+// n bootstrap indices (next() mod n), then per split attempt in depth-first
+// preorder a partial Fisher-Yates shuffle (a + next() mod (nf - a)).
+// Prediction: majority vote, ties to the lowest label; confidence = vote share.
+std::vector<std::vector<TreeNode>> forest_fit(const std::vector<std::array<float, AR_MAX_FEATURES>>& X,
+                                              const std::vector<int>& y, int nf, int ntrees, int max_depth,
+                                              uint64_t seed);
+int forest_predict(const std::vector<std::vector<TreeNode>>& forest, const float* f, float* conf);
+
 // MLP selector (layout of ar_mlp_num_params): features -> signed log1p ->
 // z-score -> Linear(F,H) ReLU Linear(H,H) ReLU Linear(H,V) -> softmax.
 struct MlpModel {

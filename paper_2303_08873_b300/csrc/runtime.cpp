@@ -29,7 +29,7 @@ namespace {
 
 using ar::FKey;
 
-enum Kind { K_DTREE = 0, K_MLP = 1, K_EXHAUSTIVE = 2, K_FIXED = 3 };
+enum Kind { K_DTREE = 0, K_MLP = 1, K_EXHAUSTIVE = 2, K_FIXED = 3, K_RFC = 4 };
 
 struct Variant {
   std::string name;
@@ -52,6 +52,7 @@ struct ar_region {
   int nf = 0;
   Kind kind = K_DTREE;
   int depth = 2;
+  int ntrees = 10;
   int hidden = 64;
   int fixed = 0;
   int reps = 5;
@@ -80,6 +81,7 @@ struct ar_region {
   bool auto_trained = false;
 
   std::vector<ar::TreeNode> tree;
+  std::vector<std::vector<ar::TreeNode>> forest;
   ar::MlpModel mlp;
   std::map<FKey, int> table;
 
@@ -142,6 +144,19 @@ int parse_spec(ar_region* r, const char* spec) {
         if (v < 1 || v > 16) return fail(r, AR_ERR_ARG, "dtree depth %ld out of [1, 16]", v);
         r->depth = (int)v;
         ++i;
+      }
+    } else if (k == "rfc") {
+      // Section 3.1: the number of trees and the depth are given together or not at all
+      r->kind = K_RFC;
+      long d = 0;
+      const bool a1 = tok.size() > 1 && parse_int(tok[1], &v);
+      const bool a2 = a1 && tok.size() > 2 && parse_int(tok[2], &d);
+      if (a1 && !a2) return fail(r, AR_ERR_ARG, "rfc takes both ntrees and depth, or neither");
+      if (a2) {
+        if (v < 1 || v > 256 || d < 1 || d > 16) return fail(r, AR_ERR_ARG, "rfc ntrees in [1,256], depth in [1,16]");
+        r->ntrees = (int)v;
+        r->depth = (int)d;
+        i += 2;
       }
     } else if (k == "mlp") {
       r->kind = K_MLP;
@@ -265,6 +280,9 @@ int predict(const ar_region* r, const float* f, float* conf) {
       break;
     case K_DTREE:
       if (!r->tree.empty()) v = ar::tree_predict(r->tree, f, &c);
+      break;
+    case K_RFC:
+      if (!r->forest.empty()) v = ar::forest_predict(r->forest, f, &c);
       break;
     case K_MLP:
       if (r->mlp.V > 0) v = ar::mlp_predict_host(r->mlp, f, &c);
@@ -633,6 +651,12 @@ int ar_train(ar_region* r) {
       r->tree = ar::tree_fit(X, labels, r->nf, r->depth);
       break;
     }
+    case K_RFC: {
+      std::vector<std::array<float, AR_MAX_FEATURES>> X(keys.size());
+      for (size_t i = 0; i < keys.size(); ++i) X[i] = ar::key_values(keys[i]);
+      r->forest = ar::forest_fit(X, labels, r->nf, r->ntrees, r->depth, r->seed);
+      break;
+    }
     case K_EXHAUSTIVE:
       r->table.clear();
       for (size_t i = 0; i < keys.size(); ++i) r->table[keys[i]] = labels[i];
@@ -702,6 +726,31 @@ int ar_tree_export(const ar_region* r, int max_nodes, int* feat, double* thr, in
   return AR_OK;
 }
 
+int ar_forest_size(const ar_region* r, int* ntrees) {
+  if (!r || !ntrees) return AR_ERR_ARG;
+  if (r->kind != K_RFC || r->forest.empty()) return AR_ERR_NOMODEL;
+  *ntrees = (int)r->forest.size();
+  return AR_OK;
+}
+
+int ar_forest_tree_export(const ar_region* r, int tree, int max_nodes, int* feat, double* thr, int* left, int* right,
+                          int* label, int* out_nodes) {
+  if (!r) return AR_ERR_ARG;
+  if (r->kind != K_RFC || r->forest.empty()) return AR_ERR_NOMODEL;
+  if (tree < 0 || tree >= (int)r->forest.size()) return AR_ERR_ARG;
+  const auto& t = r->forest[tree];
+  const int n = (int)t.size();
+  if (out_nodes) *out_nodes = n;
+  for (int i = 0; i < n && i < max_nodes; ++i) {
+    if (feat) feat[i] = t[i].feat;
+    if (thr) thr[i] = t[i].thr;
+    if (left) left[i] = t[i].left;
+    if (right) right[i] = t[i].right;
+    if (label) label[i] = t[i].label;
+  }
+  return AR_OK;
+}
+
 int ar_mlp_export(const ar_region* r, float* theta, float* mu, float* sd, int* F, int* H, int* V) {
   if (!r) return AR_ERR_ARG;
   if (r->kind != K_MLP || r->mlp.V == 0) return AR_ERR_NOMODEL;
@@ -743,7 +792,7 @@ int ar_region_save(const ar_region* r, const char* path) {
   if (rc != AR_OK) return rc;
   ar::Blob b;
   b.put_bytes("ARREGION", 8);
-  b.put_u32(1);
+  b.put_u32(2);
   b.put_u32((uint32_t)r->nf);
   b.put_u32((uint32_t)r->variants.size());
   b.put_u32((uint32_t)r->kind);
@@ -762,6 +811,18 @@ int ar_region_save(const ar_region* r, const char* path) {
     b.put_u32((uint32_t)t.right);
     b.put_u32((uint32_t)t.label);
     b.put_f32(t.conf);
+  }
+  b.put_u32((uint32_t)r->forest.size());
+  for (const auto& t : r->forest) {
+    b.put_u32((uint32_t)t.size());
+    for (const auto& nd : t) {
+      b.put_u32((uint32_t)nd.feat);
+      b.put_f64(nd.thr);
+      b.put_u32((uint32_t)nd.left);
+      b.put_u32((uint32_t)nd.right);
+      b.put_u32((uint32_t)nd.label);
+      b.put_f32(nd.conf);
+    }
   }
   b.put_u32((uint32_t)r->mlp.F);
   b.put_u32((uint32_t)r->mlp.H);
@@ -804,7 +865,7 @@ int ar_region_load(ar_region* r, const char* path) {
   if (!in.ok || memcmp(magic, "ARREGION", 8) != 0) return fail(r, AR_ERR_IO, "%s: not a region file", path);
   const uint32_t version = in.get_u32();
   const uint32_t nf = in.get_u32(), V = in.get_u32(), kind = in.get_u32();
-  if (!in.ok || version != 1) return fail(r, AR_ERR_IO, "%s: unsupported version", path);
+  if (!in.ok || version != 2) return fail(r, AR_ERR_IO, "%s: unsupported version", path);
   if ((int)nf != r->nf || (int)V != (int)r->variants.size())
     return fail(r, AR_ERR_STATE, "%s: region has %d features and %d variants, file %u and %u", path, r->nf,
                 (int)r->variants.size(), nf, V);
@@ -832,6 +893,28 @@ int ar_region_load(ar_region* r, const char* path) {
     t.conf = in.get_f32();
     if (t.feat >= (int)nf || t.label < 0 || t.label >= (int)V) in.ok = false;
     if (t.feat >= 0 && (t.left <= 0 || t.right <= 0 || t.left >= (int)ntree || t.right >= (int)ntree)) in.ok = false;
+  }
+  auto read_nodes = [&](std::vector<ar::TreeNode>& nodes, uint32_t count) {
+    nodes.resize(count);
+    for (auto& t : nodes) {
+      t.feat = (int)in.get_u32();
+      t.thr = in.get_f64();
+      t.left = (int)in.get_u32();
+      t.right = (int)in.get_u32();
+      t.label = (int)in.get_u32();
+      t.conf = in.get_f32();
+      if (t.feat >= (int)nf || t.label < 0 || t.label >= (int)V) in.ok = false;
+      if (t.feat >= 0 && (t.left <= 0 || t.right <= 0 || t.left >= (int)count || t.right >= (int)count))
+        in.ok = false;
+    }
+  };
+  const uint32_t nforest = in.get_u32();
+  if (!in.ok || nforest > 256) return fail(r, AR_ERR_IO, "%s: corrupt forest", path);
+  std::vector<std::vector<ar::TreeNode>> forest(nforest);
+  for (auto& t : forest) {
+    const uint32_t cnt = in.get_u32();
+    if (!in.ok || cnt > 1u << 20) return fail(r, AR_ERR_IO, "%s: corrupt forest", path);
+    read_nodes(t, cnt);
   }
   ar::MlpModel m;
   m.F = (int)in.get_u32();
@@ -863,6 +946,7 @@ int ar_region_load(ar_region* r, const char* path) {
   r->unique.clear();
   for (const auto& rec : r->records) r->unique.insert({ar::record_key(rec), rec.variant});
   r->tree.swap(tree);
+  r->forest.swap(forest);
   r->mlp = std::move(m);
   r->table.swap(table);
   r->trained = trained != 0;

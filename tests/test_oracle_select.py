@@ -143,3 +143,36 @@ def test_cart_depth_two_solves_two_thresholds():
 def test_cart_constant_features_give_majority_leaf():
     tree = select.cart_fit([[1.0, 2.0]] * 5, [2, 1, 1, 2, 0], max_depth=2)
     assert tree == [(-1, 0.0, -1, -1, 1)]
+
+
+# ------------------------------------------------------------- random forest
+def test_splitmix64_known_outputs():
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "splitmix64.json")))
+    r = select.SplitMix64(g["seed"])
+    assert [r.next() for _ in g["outputs"]] == [int(h, 16) for h in g["outputs"]]
+
+
+def test_rfc_trees_respect_depth_and_vote():
+    rng = np.random.Generator(np.random.PCG64(7))
+    X = rng.integers(0, 6, (30, 3)).astype(np.float32).tolist()
+    y = [int(a > 2) + 2 * int(b > 3) for a, b, _ in X]
+    forest = select.rfc_fit(X, y, ntrees=25, max_depth=3, seed=11)
+    assert len(forest) == 25 and all(select.cart_depth(t) <= 3 for t in forest)
+    labs = set(y)
+    for x in X:
+        lab, share = select.rfc_predict(forest, x)
+        assert lab in labs and 0 < share <= 1
+    acc = np.mean([select.rfc_predict(forest, x)[0] == t for x, t in zip(X, y)])
+    assert acc >= 0.8
+
+
+def test_rfc_single_feature_bootstrap_of_all_identical_rows():
+    # one distinct row: every bootstrap sample is that row, every tree a leaf
+    forest = select.rfc_fit([[2.0, 5.0]] * 4, [3, 3, 3, 3], ntrees=3, max_depth=2, seed=1)
+    assert forest == [[(-1, 0.0, -1, -1, 3)]] * 3
+    assert select.rfc_predict(forest, [0.0, 0.0]) == (3, 1.0)
+
+
+def test_rfc_vote_ties_go_to_lowest_label():
+    forest = [[(-1, 0.0, -1, -1, 4)], [(-1, 0.0, -1, -1, 1)]]
+    assert select.rfc_predict(forest, [0.0]) == (1, 0.5)

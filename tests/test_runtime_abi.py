@@ -287,3 +287,42 @@ def test_kernel_entry_points_validate_before_launch():
     assert ar.lib.ar_jacobi7(0, 8, 1, 64, 64, 128, None, None) == ar.AR_ERR_ARG  # aliasing
     assert ar.lib.ar_mlp_num_params(5, 64, 7) == 5 * 64 + 64 + 64 * 64 + 64 + 7 * 64 + 7
     assert ar.lib.ar_mlp_num_params(5, 48, 7) == ar.AR_ERR_ARG
+
+
+def test_random_forest_matches_oracle_and_needs_both_parameters():
+    for bad in ("rfc,5", "rfc,0,2", "rfc,5,0"):
+        with pytest.raises(ar.ArError) as e:
+            ar.Region("x", 2, bad)
+        assert e.value.code == ar.AR_ERR_ARG
+    for seed, (nt, depth) in enumerate([(7, 2), (4, 3), (10, 1)]):
+        rng = np.random.Generator(np.random.PCG64(40 + seed))
+        V = 4
+        table = rng.uniform(1.0, 2.0, (5, 4, V))
+        cost = lambda f, v: float(table[int(f[0]) % 5, int(f[1]) % 4, v])  # noqa: E731
+        r = ar.Region("rf", 2, f"rfc,{nt},{depth},seed={seed + 3}", 10 ** 6)
+        for v in range(V):
+            r.register(f"v{v}", float(v), _noop)
+        r.set_fake_timer(cost)
+        for _ in range(120):
+            r.invoke([float(rng.integers(0, 5)), float(rng.integers(0, 4))])
+        r.train()
+        assert r.info()["model"] == "rfc"
+        labs = select.labels(r.records())
+        X = [list(f) for f, _ in labs]
+        y = [lab for _, lab in labs]
+        want = select.rfc_fit(X, y, nt, depth, seed + 3)
+        assert r.forest() == want
+        for x in X:
+            v, conf = r.select(x)
+            assert (v, conf) == pytest.approx(select.rfc_predict(want, x))
+
+
+def test_random_forest_save_load(tmp_path):
+    r, _ = _region(V=3, spec="rfc,5,2", mtd=6, cost=lambda f, v: (1.0 + v) if f[0] < 100 else (3.0 - v))
+    for n in (10, 1000, 10, 1000, 10, 1000, 40, 4000):
+        r.invoke([n])
+    p = tmp_path / "rf.bin"
+    r.save(p)
+    q, _ = _region(V=3, spec="rfc,5,2")
+    q.load(p)
+    assert q.forest() == r.forest() and q.select([5000]) == r.select([5000])
