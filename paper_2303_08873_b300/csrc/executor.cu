@@ -371,7 +371,7 @@ __device__ void jacobi_tile(const ar_exec_call& k, int v, int p, int64_t t, unsi
     __syncthreads();
     if (inside) {
       double r = pair_to_double(df_avg6(tb[cidx - 1], tb[cidx + 1], tb[cidx - PXs], tb[cidx + PXs], below, above));
-      if (r != r) {
+      if ((__double_as_longlong(r) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) {  // NaN: redo in float64
         double s = atcg(src, N, i - 1, j, kk) + atcg(src, N, i + 1, j, kk);
         s += atcg(src, N, i, j - 1, kk);
         s += atcg(src, N, i, j + 1, kk);
@@ -493,7 +493,8 @@ __device__ __forceinline__ void nbody_accum(const float4* __restrict__ tile, int
     const float4 o = tile[q];
     const float dx = o.x - pi.x, dy = o.y - pi.y, dz = o.z - pi.z;
     const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-    const float inv = rsqrtf(r2);
+    float inv;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(r2));  // r2 >= eps^2: never subnormal
     const float s = o.w * inv * inv * inv;
     tx = fmaf(dx, s, tx);
     ty = fmaf(dy, s, ty);

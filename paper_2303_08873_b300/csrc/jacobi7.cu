@@ -212,7 +212,9 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
             outp[(int64_t)k * NN + col] = pair_normalize(r);
           } else {
             double v = pair_to_double(r);
-            if (MODE == M_DD && v != v) {  // an input outside the float-pair range: redo in float64
+            // NaN test on the bit pattern (a float64 compare would use the float64 pipe)
+            if (MODE == M_DD && (__double_as_longlong(v) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) {
+              // an input outside the float-pair range: redo in float64
               double sd = at(in, N, i - 1, j, k) + at(in, N, i + 1, j, k);
               sd += at(in, N, i, j - 1, k);
               sd += at(in, N, i, j + 1, k);

@@ -5,9 +5,11 @@
 //
 // Per interaction: 3 FADD + 3 FFMA (softened r^2) + 1 MUFU rsqrt + 3 FMUL +
 // 3 FFMA = 12 FP32-pipe instructions and one MUFU, plus one broadcast
-// shared-memory load of the j body.  Variants: shared-memory tile of T bodies
-// (T = threads per block, 128 / 256 / 512) x unroll U (1 / 4 / 8) of the inner
-// j loop; variant = 3*tile_index + unroll_index.  Each thread sums one tile
+// shared-memory load of the j body shared by the thread's bodies.  Variants:
+// shared-memory tile of T bodies (T = threads per block, 128 / 256 / 512) x
+// unroll U (1 / 4 / 8) of the inner j loop; variant = 3*tile_index +
+// unroll_index.  Each thread integrates two bodies (i and i + T) when that
+// still leaves at least two blocks per SM, else one.  Each thread sums one tile
 // into a local partial before adding it to its running total, which keeps the
 // float32 rounding error near sqrt(T) + sqrt(N/T) additions instead of N.
 //
@@ -26,49 +28,77 @@ constexpr int kTiles[3] = {128, 256, 512};
 constexpr int kUnroll[3] = {1, 4, 8};
 constexpr int kBatchTile = 256;
 
-template <int T, int U>
-__device__ __forceinline__ void tile_accumulate(const float4* __restrict__ tile, float4 pi, float eps2, float& ax,
-                                                float& ay, float& az) {
-  float tx = 0.f, ty = 0.f, tz = 0.f;
+// 1/sqrt(x) by the hardware approximation (one MUFU instruction, relative
+// error about 2^-23); x = r^2 + eps^2 >= eps^2 is never subnormal, so the
+// flush-to-zero form loses nothing.
+__device__ __forceinline__ float rsqrt_hw(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// R bodies per thread share every shared-memory load of a j body.
+template <int T, int U, int R>
+__device__ __forceinline__ void tile_accumulate(const float4* __restrict__ tile, const float4 (&pi)[R], float eps2,
+                                                float (&ax)[R], float (&ay)[R], float (&az)[R]) {
+  float tx[R], ty[R], tz[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) tx[r] = ty[r] = tz[r] = 0.f;
 #pragma unroll U
   for (int k = 0; k < T; ++k) {
     const float4 q = tile[k];
-    const float dx = q.x - pi.x, dy = q.y - pi.y, dz = q.z - pi.z;
-    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-    const float inv = rsqrtf(r2);
-    const float s = q.w * inv * inv * inv;
-    tx = fmaf(dx, s, tx);
-    ty = fmaf(dy, s, ty);
-    tz = fmaf(dz, s, tz);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float dx = q.x - pi[r].x, dy = q.y - pi[r].y, dz = q.z - pi[r].z;
+      const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+      const float inv = rsqrt_hw(r2);
+      const float s = q.w * inv * inv * inv;
+      tx[r] = fmaf(dx, s, tx[r]);
+      ty[r] = fmaf(dy, s, ty[r]);
+      tz[r] = fmaf(dz, s, tz[r]);
+    }
   }
-  ax += tx;
-  ay += ty;
-  az += tz;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    ax[r] += tx[r];
+    ay[r] += ty[r];
+    az[r] += tz[r];
+  }
 }
 
-// Bodies i of [base, base+n) against all bodies of the same range.  Padding
-// bodies have zero mass and sit at the origin, so they add exactly 0.
-template <int T, int U>
+// Bodies base + i_first + r*T (r < R) of [base, base+n) against all bodies of
+// the same range.  Padding bodies have zero mass and sit at the origin, so
+// they add exactly 0.
+template <int T, int U, int R>
 __device__ __forceinline__ void body_tile(const float4* __restrict__ p, float4* __restrict__ a, int64_t base,
-                                          int64_t n, int64_t i_local, float eps2, float4* tile) {
-  const bool live = i_local < n;
-  const float4 pi = live ? p[base + i_local] : make_float4(0.f, 0.f, 0.f, 0.f);
-  float ax = 0.f, ay = 0.f, az = 0.f;
+                                          int64_t n, int64_t i_first, float eps2, float4* tile) {
+  float4 pi[R];
+  float ax[R], ay[R], az[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int64_t i = i_first + (int64_t)r * T;
+    pi[r] = i < n ? p[base + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    ax[r] = ay[r] = az[r] = 0.f;
+  }
   for (int64_t j0 = 0; j0 < n; j0 += T) {
     __syncthreads();
     const int64_t j = j0 + threadIdx.x;
     tile[threadIdx.x] = j < n ? p[base + j] : make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
-    tile_accumulate<T, U>(tile, pi, eps2, ax, ay, az);
+    tile_accumulate<T, U, R>(tile, pi, eps2, ax, ay, az);
   }
-  if (live) a[base + i_local] = make_float4(ax, ay, az, 0.f);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int64_t i = i_first + (int64_t)r * T;
+    if (i < n) a[base + i] = make_float4(ax[r], ay[r], az[r], 0.f);
+  }
 }
 
-template <int T, int U>
+template <int T, int U, int R>
 __global__ void __launch_bounds__(T) nbody_tile(int64_t N, const float4* __restrict__ p, float4* __restrict__ a,
                                                 float eps2) {
   __shared__ float4 tile[T];
-  body_tile<T, U>(p, a, 0, N, (int64_t)blockIdx.x * T + threadIdx.x, eps2, tile);
+  body_tile<T, U, R>(p, a, 0, N, (int64_t)blockIdx.x * (T * R) + threadIdx.x, eps2, tile);
 }
 
 // ------------------------------------------------------------ batched
@@ -123,20 +153,31 @@ __global__ void __launch_bounds__(kBatchTile) nbody_batched(int count, const int
     const int b = order[lo];
     const int t = item - prefix[lo];
     const int64_t base = offs[b], n = offs[b + 1] - offs[b];
-    body_tile<kBatchTile, 4>(p, a, base, n, (int64_t)t * kBatchTile + threadIdx.x, eps2, tile);
+    body_tile<kBatchTile, 4, 1>(p, a, base, n, (int64_t)t * kBatchTile + threadIdx.x, eps2, tile);
   }
+}
+
+// Two bodies per thread when the grid still fills the GPU twice over,
+// otherwise one (small N keeps all its blocks).
+template <int T, int U>
+int launch_r(int64_t N, const float4* p, float4* a, float eps2, cudaStream_t s) {
+  const bool two = ceil_div(N, 2 * T) >= 2LL * device_sms();
+  const int64_t grid = ceil_div(N, two ? 2 * T : T);
+  if (grid > 0x7fffffffLL) return AR_ERR_ARG;
+  if (two)
+    nbody_tile<T, U, 2><<<(unsigned)grid, T, 0, s>>>(N, p, a, eps2);
+  else
+    nbody_tile<T, U, 1><<<(unsigned)grid, T, 0, s>>>(N, p, a, eps2);
+  return launch_status();
 }
 
 template <int T>
 int launch_u(int u, int64_t N, const float4* p, float4* a, float eps2, cudaStream_t s) {
-  const int64_t grid = ceil_div(N, T);
-  if (grid > 0x7fffffffLL) return AR_ERR_ARG;
   switch (u) {
-    case 0: nbody_tile<T, 1><<<(unsigned)grid, T, 0, s>>>(N, p, a, eps2); break;
-    case 1: nbody_tile<T, 4><<<(unsigned)grid, T, 0, s>>>(N, p, a, eps2); break;
-    default: nbody_tile<T, 8><<<(unsigned)grid, T, 0, s>>>(N, p, a, eps2); break;
+    case 0: return launch_r<T, 1>(N, p, a, eps2, s);
+    case 1: return launch_r<T, 4>(N, p, a, eps2, s);
+    default: return launch_r<T, 8>(N, p, a, eps2, s);
   }
-  return launch_status();
 }
 
 size_t batch_ws(int count) { return (size_t)(2 * count + 2) * sizeof(int) + 256; }

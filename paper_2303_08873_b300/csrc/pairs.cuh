@@ -31,19 +31,17 @@ constexpr float kSixthLo = -4.967053740534411e-09f;  // RN(1/6 - kSixthHi)
 // hi = NaN as a marker; +-0 gives (0, 0).
 __device__ __forceinline__ float2 df_split(double x) {
   const long long b = __double_as_longlong(x);
-  if ((b << 1) == 0) return make_float2(0.f, 0.f);
   const unsigned h32 = (unsigned)((unsigned long long)b >> 32), l32 = (unsigned)b;
   const int e = (int)((h32 >> 20) & 0x7ff);
-  if (e < 949 || e > 1140) return make_float2(__int_as_float(0x7fc00001), 0.f);
   const unsigned sign = h32 & 0x80000000u;
-  unsigned hib = sign | ((unsigned)(e - 896) << 23) | ((h32 & 0xfffffu) << 3) | (l32 >> 29);
-  int r = (int)(l32 & 0x1FFFFFFFu);
-  if (r >= (1 << 28)) {
-    hib += 1;  // one ulp away from zero (carries into the exponent correctly)
-    r -= (1 << 29);
-  }
-  const float lo = __int2float_rn(r) * __int_as_float((e - 1075 + 127) << 23);
-  return make_float2(__uint_as_float(hib), __uint_as_float(__float_as_uint(lo) ^ sign));
+  const int rraw = (int)(l32 & 0x1FFFFFFFu);
+  const int up = rraw >= (1 << 28);  // round the remainder: hi one ulp away from zero
+  const unsigned hib = (sign | ((unsigned)(e - 896) << 23) | ((h32 & 0xfffffu) << 3) | (l32 >> 29)) + (unsigned)up;
+  const float lo = __int2float_rn(rraw - (up << 29)) * __int_as_float((e - 948) << 23);  // r * 2^(e-1075)
+  float2 out = make_float2(__uint_as_float(hib), __uint_as_float(__float_as_uint(lo) ^ sign));
+  // branch-free selects: +-0 -> (0, 0); outside [2^-74, 2^118) or inf/NaN -> marker
+  if ((unsigned)(e - 949) > 191u) out = ((b << 1) == 0) ? make_float2(0.f, 0.f) : make_float2(__int_as_float(0x7fc00001), 0.f);
+  return out;
 }
 
 // Exact float -> float64 by assembling the bit pattern (no conversion
