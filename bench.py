@@ -57,6 +57,9 @@ def parse():
     p.add_argument("--test", type=int, default=500, help="spmv: held-out test matrices")
     p.add_argument("--rows-max", type=float, default=1e7, help="spmv: largest row count")
     p.add_argument("--epochs", type=int, default=200, help="spmv: MLP epochs")
+    p.add_argument("--kfold", action="store_true",
+                   help="spmv: also run the paper's K-fold protocol (K=4, f = 25/50/75 %%, 10 shuffles) and "
+                        "Adaptive-100 on all profiled matrices")
     return p.parse_args()
 
 
@@ -353,10 +356,72 @@ def spmv_bytes(rows, nnz):
 
 
 def run_spmv(args):
-    print(json.dumps(spmv_study(args.train, args.test, args.rows_max, args.epochs)), flush=True)
+    print(json.dumps(spmv_study(args.train, args.test, args.rows_max, args.epochs, kfold=args.kfold)), flush=True)
 
 
-def spmv_study(n_train, n_test, rows_max, epochs):
+def kfold_protocol(table, V, F, epochs, shuffles=10, K=4, seed=77):
+    """The paper's evaluation protocol (Section 4.1): inputs split into K equal
+    groups; a fraction f of the groups trains the model and the others test
+    it (Adaptive-25/50/75; every group trains and tests across the K
+    rotations); repeated over `shuffles` permutations.  Adaptive-100 trains
+    and tests on everything; Static,Best is the single variant fastest in
+    total over the training groups.  `table` holds (features, per-variant
+    mean ms).  Returns mean regret (%) per model and fraction."""
+    import paper_2303_08873_b300 as ar
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = len(table)
+
+    def fit(kind, idx):
+        spec = {"mlp": f"mlp,64,epochs={epochs},seed=7", "dtree": "dtree,2", "rfc": "rfc,10,4"}[kind]
+        r = ar.Region("kfold", F, spec, 10 ** 9)
+        for v in range(V):
+            r.register(f"v{v}", float(v), lambda a, v_, x, s_, u: 0)
+        for i in idx:
+            f, ms = table[i]
+            for v in range(V):
+                r.add_record(f, v, ms[v])
+        r.train()
+        return r
+
+    def regret(model, idx):
+        out = []
+        for i in idx:
+            f, ms = table[i]
+            v = model(f)
+            out.append(ms[v] / min(ms) - 1.0)
+        return 100.0 * statistics.mean(out)
+
+    res = {}
+    for kind in ("mlp", "dtree", "rfc", "static_best"):
+        res[kind] = {}
+        for frac in (1, 2, 3):
+            vals = []
+            for _ in range(shuffles):
+                perm = rng.permutation(n)
+                groups = np.array_split(perm, K)
+                for rot in range(K):
+                    tr = np.concatenate([groups[(rot + g) % K] for g in range(frac)])
+                    te = np.concatenate([groups[(rot + g) % K] for g in range(frac, K)])
+                    if kind == "static_best":
+                        tot = [sum(table[i][1][v] for i in tr) for v in range(V)]
+                        vb = int(np.argmin(tot))
+                        vals.append(regret(lambda f, vb=vb: vb, te))
+                    else:
+                        r = fit(kind, tr)
+                        vals.append(regret(lambda f, r=r: r.select(f)[0], te))
+            res[kind][f"adaptive_{25 * frac}"] = statistics.mean(vals)
+        if kind == "static_best":
+            tot = [sum(t[1][v] for t in table) for v in range(V)]
+            vb = int(np.argmin(tot))
+            res[kind]["adaptive_100"] = regret(lambda f: vb, range(n))
+        else:
+            r = fit(kind, range(n))
+            res[kind]["adaptive_100"] = regret(lambda f, r=r: r.select(f)[0], range(n))
+    return res
+
+
+def spmv_study(n_train, n_test, rows_max, epochs, kfold=False):
     """Config 3: profile `n_train` seeded matrices (7 variants, 5 reps after a
     warm-up, L2 flushed), train the MLP selector on the device and the depth-2
     tree on the same records, then compare their choices with the exhaustive
@@ -402,10 +467,12 @@ def spmv_study(n_train, n_test, rows_max, epochs):
 
     t0 = time.perf_counter()
     prof_ms = 0.0
+    table = []
     for k in range(n_train):
         feats, a, keep, rows, nnz = case(1000 + k)
         ms, _ = mlp.profile(feats, a, stream=stream)
         prof_ms += 6 * sum(ms)  # warm-up + 5 timed runs of every variant
+        table.append((feats, ms))
         del keep
     for f, v, ms in mlp.records():
         tree.add_record(list(f), v, ms)
@@ -423,6 +490,7 @@ def spmv_study(n_train, n_test, rows_max, epochs):
         vt, _ = tree.select(feats)
         per.append({"rows": rows, "nnz": nnz, "bytes": spmv_bytes(rows, nnz), "ms": ms, "best": best,
                     "mlp": vm, "conf": conf, "dtree": vt})
+        table.append((feats, ms))
         del keep
 
     def agg(key):
@@ -449,6 +517,10 @@ def spmv_study(n_train, n_test, rows_max, epochs):
         "cost": {"profiling_wall_s": t_prof, "profiling_gpu_ms": prof_ms, "train_mlp_s": t_mlp,
                  "train_records": len(mlp.records())},
     }
+    if kfold:
+        t2 = time.perf_counter()
+        line["kfold_mean_regret_pct"] = kfold_protocol(table, V, 5, epochs)
+        line["kfold_wall_s"] = time.perf_counter() - t2
     return line
 
 
