@@ -75,11 +75,12 @@ int ar_daxpy(int variant, int64_t n, double a, const double *x, double *y, void 
  * tma and df families run the smem kernel of the same shape.  Default: naive 32x8 (variant 1).
  * `status` (device int[2], may be NULL): status[0] receives AR_ERR_TIMEOUT if
  * a bounded wait inside a tma/df kernel gave up (the caller zeroes it);
- * status[1] is scratch for the df family, which with a status array and 3+
+ * status[1] is scratch for the df family, which with a status array and 2+
  * sweeps keeps float pairs (8 bytes per unknown) in out/work between sweeps
- * and falls back to float64 storage for the whole call when a value after
- * the first sweep lies outside the float-pair range.  Without a status array
- * every df sweep converts from and to float64. */
+ * and, when an input lies outside the float-pair range, recomputes the whole
+ * call in float64 (one extra launch at the end, which otherwise exits at
+ * once).  Without a status array every df sweep converts from and to
+ * float64 and redoes out-of-range points in float64. */
 typedef struct ar_jacobi7_args {
   int N;
   int sweeps;

@@ -110,17 +110,21 @@ struct TmaGeom {
 // may hold float pairs (8 bytes per unknown, like a float64):
 //   M_NATIVE  float64 in, float64 out, float64 arithmetic
 //   M_DD      float64 in, float64 out, float-pair arithmetic; points whose
-//             inputs are outside the float-pair range are redone in float64;
-//             if `flag` is given, any output outside that range sets *flag
-//   M_DP      float64 in, float pairs out      } when *flag is set (by the
-//   M_PP      float pairs in, float pairs out  } first sweep) these run as
-//   M_PD      float pairs in, float64 out      } M_NATIVE on float64 buffers
+//             inputs are outside the float-pair range are redone in float64
+//   M_DP      first sweep of a pair chain: float64 in, float pairs out; any
+//             input outside the float-pair range sets *flag
+//   M_PP      float pairs in, float pairs out  } when *flag is set these run
+//   M_PD      float pairs in, float64 out      } the previous sweep in
+//             float64 instead, from the alternate source (tmap_alt) to
+//             out_alt, so the flagged chain ends one launch late (see the
+//             catch-up kernel)
 enum Mode { M_NATIVE = 0, M_DD = 1, M_DP = 2, M_PP = 3, M_PD = 4 };
 
 template <int BX, int BY, int MODE>
-__global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUtensorMap tmap, int N, int KC,
+__global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUtensorMap tmap,
+                                                     const __grid_constant__ CUtensorMap tmap_alt, int N, int KC,
                                                      const double* __restrict__ in, void* __restrict__ outv,
-                                                     int* status, int* flag) {
+                                                     double* __restrict__ out_alt, int* status, int* flag) {
   using G = TmaGeom<BX, BY>;
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[kRing];
@@ -133,9 +137,11 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
   const int kc = min(KC, N - kb);                 // output planes of this block
   const int ngroups = (kc + 2 + kDZ - 1) / kDZ;   // boxes covering planes kb-1 .. kb+kc
   // block-uniform: the flag was settled by an earlier launch on this stream
-  const bool native = (MODE == M_NATIVE) || (MODE >= M_DP && flag != nullptr && *flag != 0);
+  const bool flagged = (MODE == M_PP || MODE == M_PD) && flag != nullptr && *flag != 0;
+  const bool native = (MODE == M_NATIVE) || flagged;
   const bool split_boxes = !native && (MODE == M_DD || MODE == M_DP);
   const bool pair_out = !native && (MODE == M_DP || MODE == M_PP);
+  const CUtensorMap* src_map = flagged ? &tmap_alt : &tmap;
 
   if (tid == 0) {
     for (int r = 0; r < kRing; ++r) mbar_init(smem_addr(&bars[r]), 1);
@@ -147,7 +153,7 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
     const int slot = g % kRing;
     const uint32_t bar = smem_addr(&bars[slot]);
     mbar_arrive_expect_tx(bar, G::BYTES);
-    tma_load_3d(smem_addr(buf + (size_t)slot * G::GROUP), &tmap, i0 - 2, j0 - 1, kb - 1 + g * kDZ, bar);
+    tma_load_3d(smem_addr(buf + (size_t)slot * G::GROUP), src_map, i0 - 2, j0 - 1, kb - 1 + g * kDZ, bar);
   };
   if (tid == 0)
     for (int g = 0; g < min(ngroups, kRing - 1); ++g) issue(g);
@@ -157,7 +163,7 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
   const int64_t NN = (int64_t)N * N;
   const int64_t col = (int64_t)j * N + i;
   const int c = (ty + 1) * G::PX + tx + 2;
-  double* outd = static_cast<double*>(outv);
+  double* outd = flagged ? out_alt : static_cast<double*>(outv);
   float2* outp = static_cast<float2*>(outv);
   // z queue: centres of planes p-1 and p (ring index qm = (p-1) mod RING)
   double dm = 0.0, d0 = 0.0;
@@ -175,8 +181,13 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
     }
     if (split_boxes) {
       double* box = buf + (size_t)slot * G::GROUP;
-      for (int e = tid; e < G::GROUP; e += BX * BY) reinterpret_cast<float2*>(box)[e] = df_split(box[e]);
-      __syncthreads();
+      bool marker = false;
+      for (int e = tid; e < G::GROUP; e += BX * BY) {
+        const float2 f = df_split(box[e]);
+        marker |= (f.x != f.x);
+        reinterpret_cast<float2*>(box)[e] = f;
+      }
+      if (__syncthreads_or(marker) && MODE == M_DP && tid == 0 && flag) atomicOr(flag, 1);
     }
     if (g == 0) {  // centres of planes 0 and 1 (relative) start the queue
       if (native) {
@@ -222,7 +233,6 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
               sd += at(in, N, i, j, k + 1);
               v = sd * kSixth;
             }
-            if (MODE == M_DD && flag != nullptr && outside_pair_range(v)) atomicOr(flag, 1);
             outd[(int64_t)k * NN + col] = v;
           }
         }
@@ -282,8 +292,26 @@ bool tma_usable(int shape, int N, const void* a, const void* b, const void* c) {
   return !(N & 1) && N >= PX && N >= PY && N >= kDZ && aligned16(a) && (!b || aligned16(b)) && (!c || aligned16(c));
 }
 
+// Float64 sweep of the flagged pair chain's last step: does nothing unless
+// the first sweep flagged an input outside the float-pair range.
+__global__ void __launch_bounds__(256) jacobi_catchup(int N, const int* __restrict__ flag,
+                                                      const double* __restrict__ in, double* __restrict__ out) {
+  if (*flag == 0) return;
+  const int64_t n3 = (int64_t)N * N * N, NN = (int64_t)N * N;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n3; c += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % N), j = (int)((c / N) % N), k = (int)(c / NN);
+    double s = at(in, N, i - 1, j, k) + at(in, N, i + 1, j, k);
+    s += at(in, N, i, j - 1, k);
+    s += at(in, N, i, j + 1, k);
+    s += at(in, N, i, j, k - 1);
+    s += at(in, N, i, j, k + 1);
+    out[c] = s * kSixth;
+  }
+}
+
 template <int BX, int BY, int MODE>
-int launch_tma(int N, const double* in, void* out, int* status, int* flag, cudaStream_t s) {
+int launch_tma(int N, const double* in, void* out, const double* in_alt, double* out_alt, int* status, int* flag,
+               cudaStream_t s) {
   using G = TmaGeom<BX, BY>;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
@@ -292,8 +320,10 @@ int launch_tma(int N, const double* in, void* out, int* status, int* flag, cudaS
                                     (int)G::SMEM);
   });
   if (attr_err != cudaSuccess) return AR_ERR_CUDA;
-  CUtensorMap map;
-  if (!encode_tensor_map_3d_f64(&map, in, (uint64_t)N, (uint64_t)N, (uint64_t)N, G::PX, G::PY, kDZ))
+  CUtensorMap map, map_alt;
+  if (!encode_tensor_map_3d_f64(&map, in, (uint64_t)N, (uint64_t)N, (uint64_t)N, G::PX, G::PY, kDZ) ||
+      !encode_tensor_map_3d_f64(&map_alt, in_alt ? in_alt : in, (uint64_t)N, (uint64_t)N, (uint64_t)N, G::PX, G::PY,
+                                kDZ))
     return AR_ERR_CUDA;
   const int64_t cb = ceil_div(N, BX) * ceil_div(N, BY);
   int resident = (int)((227 * 1024) / G::SMEM);
@@ -303,32 +333,32 @@ int launch_tma(int N, const double* in, void* out, int* status, int* flag, cudaS
   int KC = chunk_planes(N, cb, resident, kDZ - 2, 8 * kDZ - 2);
   KC = (int)(ceil_div(KC + 2, kDZ) * kDZ - 2);
   dim3 grid((unsigned)ceil_div(N, BX), (unsigned)ceil_div(N, BY), (unsigned)ceil_div(N, KC));
-  jacobi_tma<BX, BY, MODE><<<grid, BX * BY, G::SMEM, s>>>(map, N, KC, in, out, status, flag);
+  jacobi_tma<BX, BY, MODE><<<grid, BX * BY, G::SMEM, s>>>(map, map_alt, N, KC, in, out, out_alt, status, flag);
   return launch_status();
 }
 
 template <int BX, int BY>
-int launch_family(int fam, int mode, bool tma, int N, const double* in, double* out, int* status, int* flag,
-                  cudaStream_t s) {
+int launch_family(int fam, int mode, bool tma, int N, const double* in, double* out, const double* in_alt,
+                  double* out_alt, int* status, int* flag, cudaStream_t s) {
   if (fam == 0) return launch_naive<BX, BY>(N, in, out, s);
   if (fam == 1 || !tma) return launch_smem<BX, BY>(N, in, out, s);
   switch (mode) {
-    case M_NATIVE: return launch_tma<BX, BY, M_NATIVE>(N, in, out, status, nullptr, s);
-    case M_DD: return launch_tma<BX, BY, M_DD>(N, in, out, status, flag, s);
-    case M_DP: return launch_tma<BX, BY, M_DP>(N, in, out, status, flag, s);
-    case M_PP: return launch_tma<BX, BY, M_PP>(N, in, out, status, flag, s);
-    default: return launch_tma<BX, BY, M_PD>(N, in, out, status, flag, s);
+    case M_NATIVE: return launch_tma<BX, BY, M_NATIVE>(N, in, out, nullptr, nullptr, status, nullptr, s);
+    case M_DD: return launch_tma<BX, BY, M_DD>(N, in, out, nullptr, nullptr, status, nullptr, s);
+    case M_DP: return launch_tma<BX, BY, M_DP>(N, in, out, nullptr, nullptr, status, flag, s);
+    case M_PP: return launch_tma<BX, BY, M_PP>(N, in, out, in_alt, out_alt, status, flag, s);
+    default: return launch_tma<BX, BY, M_PD>(N, in, out, in_alt, out_alt, status, flag, s);
   }
 }
 
-int sweep(int variant, int mode, bool tma, int N, const double* in, double* out, int* status, int* flag,
-          cudaStream_t s) {
+int sweep(int variant, int mode, bool tma, int N, const double* in, double* out, const double* in_alt,
+          double* out_alt, int* status, int* flag, cudaStream_t s) {
   const int fam = variant / 4;
   switch (variant % 4) {
-    case 0: return launch_family<32, 4>(fam, mode, tma, N, in, out, status, flag, s);
-    case 1: return launch_family<32, 8>(fam, mode, tma, N, in, out, status, flag, s);
-    case 2: return launch_family<64, 4>(fam, mode, tma, N, in, out, status, flag, s);
-    default: return launch_family<128, 2>(fam, mode, tma, N, in, out, status, flag, s);
+    case 0: return launch_family<32, 4>(fam, mode, tma, N, in, out, in_alt, out_alt, status, flag, s);
+    case 1: return launch_family<32, 8>(fam, mode, tma, N, in, out, in_alt, out_alt, status, flag, s);
+    case 2: return launch_family<64, 4>(fam, mode, tma, N, in, out, in_alt, out_alt, status, flag, s);
+    default: return launch_family<128, 2>(fam, mode, tma, N, in, out, in_alt, out_alt, status, flag, s);
   }
 }
 
@@ -389,27 +419,37 @@ extern "C" int ar_jacobi7(int variant, int N, int sweeps, const double* u0, doub
   }
   const int fam = variant / 4;
   const bool tma = fam >= 2 && tma_usable(variant % 4, N, u0, out, sweeps > 1 ? work : nullptr);
-  // df calls of 3+ sweeps keep float pairs between sweeps; status[1] carries
-  // the first sweep's verdict on whether every value fits the pair range
-  int* flag = (fam == 3 && tma && sweeps >= 3 && status) ? status + 1 : nullptr;
+  auto dst_of = [&](int j) -> double* { return ((sweeps - 1 - j) % 2 == 0) ? out : work; };
+  // df calls of 2+ sweeps keep float pairs between sweeps; status[1] records
+  // whether the first sweep met an input outside the float-pair range, in
+  // which case every later launch computes the previous sweep in float64 from
+  // the float64 data and a final catch-up launch computes the last one
+  int* flag = (fam == 3 && tma && sweeps >= 2 && status) ? status + 1 : nullptr;
   if (flag && cudaMemsetAsync(flag, 0, sizeof(int), s) != cudaSuccess) return AR_ERR_CUDA;
-  const double* src = u0;
   for (int sw = 0; sw < sweeps; ++sw) {
-    double* dst = ((sweeps - 1 - sw) % 2 == 0) ? out : work;
+    const double* src = sw == 0 ? u0 : dst_of(sw - 1);
+    double* dst = dst_of(sw);
     int mode = M_NATIVE;
+    const double* alt_src = nullptr;
+    double* alt_dst = nullptr;
     if (fam == 3) {
-      if (!flag || sw == 0)
+      if (!flag) {
         mode = M_DD;
-      else if (sw == sweeps - 1)
-        mode = M_PD;
-      else if (sw == 1)
+      } else if (sw == 0) {
         mode = M_DP;
-      else
-        mode = M_PP;
+      } else {
+        mode = (sw == sweeps - 1) ? M_PD : M_PP;
+        alt_src = sw == 1 ? u0 : dst_of(sw - 2);
+        alt_dst = dst_of(sw - 1);
+      }
     }
-    const int rc = sweep(variant, mode, tma, N, src, dst, status, flag, s);
+    const int rc = sweep(variant, mode, tma, N, src, dst, alt_src, alt_dst, status, flag, s);
     if (rc != AR_OK) return rc;
-    src = dst;
+  }
+  if (flag) {
+    const double* src = sweeps >= 2 ? dst_of(sweeps - 2) : u0;
+    jacobi_catchup<<<device_sms() * 4, 256, 0, s>>>(N, flag, src, dst_of(sweeps - 1));
+    return launch_status();
   }
   return AR_OK;
 }
