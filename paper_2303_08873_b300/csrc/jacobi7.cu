@@ -220,7 +220,9 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
         const float2 r = df_avg6(pc[c - 1], pc[c + 1], pc[c - G::PX], pc[c + G::PX], fm, up);
         if (inside) {
           if (pair_out) {
-            outp[(int64_t)k * NN + col] = pair_normalize(r);
+            // stored unnormalised: the next sweep sums the hi parts exactly and
+            // the lo parts in float, so |lo| of a few ulps of hi costs ~2^-46
+            outp[(int64_t)k * NN + col] = r;
           } else {
             double v = pair_to_double(r);
             // NaN test on the bit pattern (a float64 compare would use the float64 pipe)

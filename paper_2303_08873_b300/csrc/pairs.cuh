@@ -91,12 +91,6 @@ __device__ __forceinline__ float2 df_avg6(float2 v0, float2 v1, float2 v2, float
 
 __device__ __forceinline__ double pair_to_double(float2 v) { return f2d_bits(v.x) + f2d_bits(v.y); }
 
-__device__ __forceinline__ float2 pair_normalize(float2 v) {
-  float hi, lo;
-  two_sum(v.x, v.y, hi, lo);
-  return make_float2(hi, lo);
-}
-
 // A float64 value the float-pair path cannot carry to later sweeps.
 __device__ __forceinline__ bool outside_pair_range(double v) {
   const long long b = __double_as_longlong(v);
