@@ -39,6 +39,11 @@ BYTES_PER_POINT = 16.0          # one float64 read + one write per point per swe
 FP64_OPS_PER_POINT = 6          # 5 adds + 1 multiply in the native families
 METRIC = "selected-variant GB/s (or GFLOP/s) vs exhaustive-best & fixed default; regret %"
 FALLBACK_HBM_GBS = 6400.0
+# DRAM bytes (read + write) of one pairs -> pairs sweep of jacobi7_df_32x8 at
+# N = 320 (ncu dram__bytes_read.sum + dram__bytes_write.sum, see
+# profiles/jacobi7_df_pp_N320.md), scaled to N = 512 by the unknowns; writes
+# still dirty in L2 when the kernel ends are not counted by ncu.
+DF_PP_TRAFFIC_N320 = 262299136.0 + 215584256.0
 
 
 def parse():
@@ -76,6 +81,15 @@ def peaks():
         d = json.load(open(path))
         return float(d["hbm_gbs"]), "measured"
     return FALLBACK_HBM_GBS, "fallback"
+
+
+def jacobi_launches(name, N, sweeps):
+    """Kernel launches of one ar_jacobi7 call: one per sweep, plus the
+    catch-up launch of a df call that keeps float pairs between sweeps (TMA
+    staging usable: even N at least one box wide)."""
+    bx = int(name.split("_")[-1].split("x")[0])
+    df_chain = name.startswith("jacobi7_df") and N % 2 == 0 and N >= bx + 4 and N >= 10 and sweeps >= 2
+    return sweeps + (1 if df_chain else 0)
 
 
 def workload_bytes(sizes, sweeps):
@@ -270,9 +284,12 @@ def run_ours(args):
     achieved = BYTES_PER_POINT * big ** 3 / (big_ms * 1e-3) / 1e9
     vbig = chosen[big]
     if names[vbig].startswith("jacobi7_df"):
+        traffic = DF_PP_TRAFFIC_N320 * (big / 320.0) ** 3 if names[vbig] == "jacobi7_df_32x8" else None
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
-                "kernel": names[vbig]}
+                "frac": achieved / hbm_peak, "traffic": traffic, "peak_source": peak_src,
+                "kernel": names[vbig],
+                "note": "achieved: the N=512 invocation's time per sweep (10 sweep launches + 1 catch-up); "
+                        "traffic: DRAM bytes of one pairs->pairs sweep launch, measured at N=320 and scaled"}
     else:
         alu_gbs = fp64_fma / FP64_OPS_PER_POINT * BYTES_PER_POINT / 1e9
         roof = {"bound": "alu", "achieved": achieved, "peak": alu_gbs, "unit": "GB/s",
@@ -337,7 +354,7 @@ def run_ours(args):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": args.steps * len(SIZES) * SWEEPS,
+        "gpu_launches": args.steps * sum(jacobi_launches(names[chosen[n]], n, SWEEPS) for n in SIZES),
         "clocks": clk,
         "fp64_fma_per_s": fp64_fma,
     }
