@@ -312,6 +312,27 @@ def run_ours(args):
                     "default_gbs": BYTES_PER_POINT * n ** 3 * SWEEPS / ms_n[default] / 1e6})
     regret = statistics.mean(p["regret_pct"] for p in per)
 
+    # --- the paper's Online mode (Section 4.2): one fresh region per N, default
+    # min_train_data (= number of variants), RoundRobin exploration over real
+    # invocations, automatic training, then the tree's choice; regret from the
+    # exhaustive table above
+    online = []
+    for n in SIZES:
+        ro = ar.Region(f"jacobi7-online-{n}", 2, "dtree,2")
+        ro.add_builtin(ar.AR_LOOP_JACOBI7)
+        explore_ms = 0.0
+        calls = 0
+        while not ro.info()["trained"]:
+            ro.invoke([n, SWEEPS], argblocks[n], stream=stream)
+            calls += 1
+        stream.synchronize()
+        explore_ms = sum(ms_ for _, _, ms_ in ro.records())
+        v_on, _ = ro.select([n, SWEEPS])
+        ms_n, best = table[(n, SWEEPS)]
+        online.append({"N": n, "explore_calls": calls, "selected": names[v_on],
+                       "regret_pct": 100 * (ms_n[v_on] / ms_n[best] - 1),
+                       "explore_overhead_pct": 100 * (explore_ms / (calls * ms_n[best]) - 1)})
+
     # --- end to end through host buffers (pinned), copies inside the timed region
     host_in = {n: bufs[n][0].cpu().pin_memory() for n in SIZES}
     host_out = {n: torch.empty_like(host_in[n]).pin_memory() for n in SIZES}
@@ -350,6 +371,8 @@ def run_ours(args):
         "selection": {"exhaustive_best_gbs": step_bytes / t_best / 1e6, "default_gbs": step_bytes / t_def / 1e6,
                       "selected_table_gbs": step_bytes / t_sel / 1e6, "regret_pct": regret,
                       "default_variant": names[default], "per_N": per, "tree": tree,
+                      "online": {"mean_regret_pct": statistics.mean(o["regret_pct"] for o in online),
+                                 "per_N": online},
                       "profiling_s": t_prof, "profiled_points": len(table), "variants": V},
         "roofline": roof,
         "cpu_baseline": cpu,
