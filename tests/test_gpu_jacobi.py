@@ -132,3 +132,19 @@ def test_bench_sizes_sampled(N):
         ar.ar_jacobi7(v, N, s, ud, out, work, status)
         got = host(out.view(-1)[idx])
         assert np.max(np.abs(got - refs)) <= TOL * scale, (ar.loop_variant_name(1, v), N)
+
+
+def test_every_variant_is_deterministic():
+    u0 = synth.grid_inputs(9, 66)
+    for v in range(V):
+        assert np.array_equal(_run(v, u0, 4), _run(v, u0, 4)), v
+
+
+def test_two_sweep_pair_chain_with_flagged_input():
+    # 2 sweeps: float64 -> pairs, pairs -> float64, and the catch-up launch
+    u0 = synth.grid_inputs(10, 40)
+    u0[7, 8, 9] = 1e-200
+    ref = loops.jacobi7(u0, 2)
+    st = torch.zeros(2, dtype=torch.int32, device="cuda")
+    for v in range(12, 16):
+        _check(_run(v, u0, 2, st), ref, ("flagged 2 sweeps", v))

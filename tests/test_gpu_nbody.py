@@ -99,3 +99,9 @@ def test_batched_workload_sampled():
         got = a[offs[b]:offs[b + 1]][which]
         err = np.max(np.linalg.norm(got[:, :3].astype(np.float64) - ref, axis=1))
         assert err <= TOL * np.max(np.linalg.norm(ref, axis=1)) * 4, b
+
+
+def test_every_variant_is_deterministic():
+    p = synth.nbody_inputs(12, 70000)
+    for v in range(V):
+        assert np.array_equal(_run(v, p), _run(v, p)), v
