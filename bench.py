@@ -83,6 +83,24 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def max_over_ranks(ms: float, device) -> float:
+    """Slowest rank's time: the timed region ends when every replica is done."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(step_bytes: float, steps: int, world: int, ms: float) -> float:
+    """Whole-job GB/s: the bytes every replica processed over the slowest
+    replica's time (weak scaling: each rank runs the full workload)."""
+    return step_bytes * steps * world / (ms * 1e-3) / 1e9
+
+
 def jacobi_launches(name, N, sweeps):
     """Kernel launches of one ar_jacobi7 call: one per sweep, plus the
     catch-up launch of a df call that keeps float pairs between sweeps (TMA
@@ -270,13 +288,9 @@ def run_ours(args):
     stream.synchronize()
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dev)
     step_bytes = workload_bytes(SIZES, SWEEPS)
-    value = step_bytes * args.steps * ws / (ms * 1e-3) / 1e9
+    value = job_rate(step_bytes, args.steps, ws, ms)
     assert int(status[0].item()) == 0, "a bounded wait inside a TMA kernel timed out"
 
     # --- dominant kernel roofline: the N=512 invocation's sweeps
