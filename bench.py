@@ -40,10 +40,10 @@ FP64_OPS_PER_POINT = 6          # 5 adds + 1 multiply in the native families
 METRIC = "selected-variant GB/s (or GFLOP/s) vs exhaustive-best & fixed default; regret %"
 FALLBACK_HBM_GBS = 6400.0
 # DRAM bytes (read + write) of one pairs -> pairs sweep of jacobi7_df_32x8 at
-# N = 320 (ncu dram__bytes_read.sum + dram__bytes_write.sum, see
-# profiles/jacobi7_df_pp_N320.md), scaled to N = 512 by the unknowns; writes
+# N = 320 (ncu dram__bytes_read.sum + dram__bytes_write.sum, median of the 8
+# middle sweeps of a 10-sweep call), scaled to N = 512 by the unknowns; writes
 # still dirty in L2 when the kernel ends are not counted by ncu.
-DF_PP_TRAFFIC_N320 = 262299136.0 + 215584256.0
+DF_PP_TRAFFIC_N320 = 262360704.0 + 217589120.0
 
 
 def parse():

@@ -97,12 +97,18 @@ int ar_jacobi7(int variant, int N, int sweeps, const double *u0, double *out, do
  * [rows+1] (rowptr[0] = 0, non-decreasing, rowptr[rows] = nnz < 2^31), col
  * int32 [nnz] (column indices, any order within a row, each < length of x),
  * val float64 [nnz], x float64, y float64 [rows] (written, not accumulated).
- * Each row's products are summed in float64 in a variant-specific order.
- * Variants: 0 thread-per-row, 1 warp-per-row, 2..5 vector-k (k = 2, 4, 8, 16
- * lanes per row), 6 merge-path (equal path work per thread; rows crossing
- * threads and blocks fixed up deterministically).  Default: thread-per-row.
- * Only merge-path uses the caller's workspace (ar_spmv_workspace_bytes; device
- * memory, contents need no initialisation; AR_ERR_ARG if too small). */
+ * Each row's products are summed in float64 in a variant-specific order,
+ * except variant 7.  Variants: 0 thread-per-row, 1 warp-per-row, 2..5
+ * vector-k (k = 2, 4, 8, 16 lanes per row), 6 merge-path (equal path work
+ * per thread, products staged in shared memory; rows crossing threads and
+ * blocks summed in a fixed order), 7 merge-path in float-pair arithmetic
+ * (operands split into float pairs, products and row sums carried to
+ * ~2^-46 relative of the sum of |val x|; the rows of a path block holding a
+ * nonzero operand of magnitude outside [2^-62, 2^62), or a sum that
+ * overflows a float, are redone in float64).
+ * Default: thread-per-row.  Only merge-path (6, 7) uses the caller's
+ * workspace (ar_spmv_workspace_bytes; device memory, contents need no
+ * initialisation; AR_ERR_ARG if too small).  Results are deterministic. */
 typedef struct ar_spmv_args {
   int64_t rows;
   int64_t nnz;

@@ -12,6 +12,7 @@
 #include <cstdio>
 
 #include "common.cuh"
+#include "merge_path.cuh"
 #include "pairs.cuh"
 
 namespace ar {
@@ -20,10 +21,12 @@ namespace {
 constexpr int T = 256;                   // threads per executor block
 constexpr int PM = AR_EXEC_MAX_PHASES;   // phases per call
 constexpr int kJKC = 16;                 // Jacobi planes per tile
+constexpr int kCatchTiles = 512;         // tiles of a df call's catch-up phase
 constexpr uint32_t kDepSpin = 1u << 24;  // dependency polls (with backoff) before giving up
-constexpr int kMpItems = 16, kMpPerTile = T * kMpItems;
+constexpr int kMpPerTile = mp::kPerBlock;
+static_assert(mp::kThreads == T, "merge-path tiles use the executor's block size");
 
-__constant__ int c_nvar[4] = {15, 16, 7, 9};
+__constant__ int c_nvar[4] = {15, 16, 8, 9};
 __constant__ int c_default[4] = {6, 1, 0, 3};
 __constant__ int c_nfeat[4] = {1, 2, 5, 1};
 __constant__ int c_dx_block[5] = {64, 128, 256, 512, 1024};
@@ -46,9 +49,16 @@ __device__ __forceinline__ uint64_t gtimer() {
 
 __device__ __forceinline__ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// A df Jacobi call of 2+ sweeps keeps float pairs in out/work between sweeps
+// and ends with a catch-up phase (a float64 sweep that only runs when the
+// first sweep met an input outside the float-pair range).
+__device__ __forceinline__ bool jacobi_pair_chain(const ar_exec_call& c, int v) {
+  return c.loop == AR_LOOP_JACOBI7 && v / 4 == 3 && c.sweeps >= 2 && c.sweeps + 1 <= PM;
+}
+
 __device__ __forceinline__ int phases_of(const ar_exec_call& c, int v) {
-  if (c.loop == AR_LOOP_JACOBI7) return c.sweeps;
-  if (c.loop == AR_LOOP_SPMV && v == 6) return 2;
+  if (c.loop == AR_LOOP_JACOBI7) return c.sweeps + (jacobi_pair_chain(c, v) ? 1 : 0);
+  if (c.loop == AR_LOOP_SPMV && v >= 6) return 2;  // merge path: blocks, then the carry fix-up
   return 1;
 }
 
@@ -57,6 +67,7 @@ __device__ int64_t tiles_of(const ar_exec_call& c, int v, int p) {
     case AR_LOOP_DAXPY: return cdiv(c.n, (int64_t)c_dx_block[v / 3] * c_dx_ept[v % 3]);
     case AR_LOOP_JACOBI7: {
       const int64_t N = c.n;
+      if (jacobi_pair_chain(c, v) && p == c.sweeps) return kCatchTiles;
       return cdiv(N, c_j_bx[v % 4]) * cdiv(N, c_j_by[v % 4]) * cdiv(N, kJKC);
     }
     case AR_LOOP_SPMV: {
@@ -210,7 +221,7 @@ __global__ void __launch_bounds__(T) exec_plan(const ar_exec_call* __restrict__ 
       v = c_default[k.loop];
     }
     if (st == AR_OK && (v < 0 || v >= c_nvar[k.loop])) st = AR_ERR_ARG;
-    if (st == AR_OK && k.loop == AR_LOOP_SPMV && v == 6 &&
+    if (st == AR_OK && k.loop == AR_LOOP_SPMV && v >= 6 &&
         (!k.out1 || k.out1_bytes < 16ull * (unsigned long long)cdiv(k.n + k.nnz, kMpPerTile)))
       st = AR_ERR_ARG;  // merge-path needs its carry workspace
     if (st == AR_OK && k.loop == AR_LOOP_DAXPY && v % 3 != 0 &&
@@ -294,14 +305,16 @@ __device__ __forceinline__ double atcg(const double* __restrict__ u, int N, int 
   return __ldcg(u + ((int64_t)k * N + j) * N + i);
 }
 
-__device__ void jacobi_tile(const ar_exec_call& k, int v, int p, int64_t t, unsigned char* smraw) {
-  const int N = (int)k.n, S = k.sweeps;
+// One BX x BY x 16-plane tile of one sweep, 2.5D: an xy tile with halo in
+// shared memory (double buffered), z neighbours in registers.  Values are
+// float64 or float pairs in memory (src_pairs / dst_pairs); `pair_math`
+// selects float-pair arithmetic.  With float64 input and float-pair
+// arithmetic, inputs outside the pair range mark the point: it is redone in
+// float64 (dst float64) or, when dst holds pairs, reported through *flag.
+__device__ void jacobi_sweep_tile(const ar_exec_call& k, int v, int64_t t, const double* src, double* dst,
+                                  bool pair_math, bool src_pairs, bool dst_pairs, int* flag, unsigned char* smraw) {
+  const int N = (int)k.n;
   const int fam = v / 4, BX = c_j_bx[v % 4], BY = c_j_by[v % 4];
-  const double* u0 = static_cast<const double*>(k.in0);
-  double* out = static_cast<double*>(k.out0);
-  double* work = static_cast<double*>(k.out1);
-  double* dst = ((S - 1 - p) % 2 == 0) ? out : work;
-  const double* src = p == 0 ? u0 : (((S - p) % 2 == 0) ? out : work);
   const int64_t gx = (N + BX - 1) / BX, gy = (N + BY - 1) / BY;
   const int bx = (int)(t % gx), by = (int)((t / gx) % gy), bz = (int)(t / (gx * gy));
   const int kb = bz * kJKC, ke = min(N, kb + kJKC);
@@ -322,10 +335,9 @@ __device__ void jacobi_tile(const ar_exec_call& k, int v, int p, int64_t t, unsi
     }
     return;
   }
-  // 2.5D: double-buffered xy tile with halo, z neighbours in registers
   const int PXs = BX + 2, PL = PXs * (BY + 2);
   const int cidx = (ly + 1) * PXs + lx + 1;
-  if (fam < 3) {
+  if (!pair_math) {
     double* tile = reinterpret_cast<double*>(smraw);
     double below = inside ? atcg(src, N, i, j, kb - 1) : 0.0;
     double cur = inside ? atcg(src, N, i, j, kb) : 0.0;
@@ -353,51 +365,97 @@ __device__ void jacobi_tile(const ar_exec_call& k, int v, int p, int64_t t, unsi
     }
     return;
   }
-  // df: the same tile in float pairs; points with an input outside the pair
-  // range are redone in float64
+  // float-pair arithmetic; loads give pairs directly or split float64 values
+  const float2* srcp = reinterpret_cast<const float2*>(src);
+  bool marker = false;
+  auto ldp = [&](int ii, int jj, int kk) -> float2 {
+    if ((unsigned)ii >= (unsigned)N || (unsigned)jj >= (unsigned)N || (unsigned)kk >= (unsigned)N)
+      return make_float2(0.f, 0.f);
+    const int64_t o = ((int64_t)kk * N + jj) * N + ii;
+    if (src_pairs) return __ldcg(srcp + o);
+    const float2 f = df_split(__ldcg(src + o));
+    marker |= (f.x != f.x);
+    return f;
+  };
   float2* tile = reinterpret_cast<float2*>(smraw);
-  float2 below = df_split(inside ? atcg(src, N, i, j, kb - 1) : 0.0);
-  float2 cur = df_split(inside ? atcg(src, N, i, j, kb) : 0.0);
+  float2 below = inside ? ldp(i, j, kb - 1) : make_float2(0.f, 0.f);
+  float2 cur = inside ? ldp(i, j, kb) : make_float2(0.f, 0.f);
   for (int kk = kb; kk < ke; ++kk) {
     float2* tb = tile + ((kk - kb) & 1) * PL;
-    const float2 above = df_split(inside ? atcg(src, N, i, j, kk + 1) : 0.0);
+    const float2 above = inside ? ldp(i, j, kk + 1) : make_float2(0.f, 0.f);
     if (active) {
       tb[cidx] = cur;
-      if (lx == 0) tb[cidx - 1] = df_split(atcg(src, N, i - 1, j, kk));
-      if (lx == BX - 1) tb[cidx + 1] = df_split(atcg(src, N, i + 1, j, kk));
-      if (ly == 0) tb[cidx - PXs] = df_split(atcg(src, N, i, j - 1, kk));
-      if (ly == BY - 1) tb[cidx + PXs] = df_split(atcg(src, N, i, j + 1, kk));
+      if (lx == 0) tb[cidx - 1] = ldp(i - 1, j, kk);
+      if (lx == BX - 1) tb[cidx + 1] = ldp(i + 1, j, kk);
+      if (ly == 0) tb[cidx - PXs] = ldp(i, j - 1, kk);
+      if (ly == BY - 1) tb[cidx + PXs] = ldp(i, j + 1, kk);
     }
     __syncthreads();
     if (inside) {
-      double r = pair_to_double(df_avg6(tb[cidx - 1], tb[cidx + 1], tb[cidx - PXs], tb[cidx + PXs], below, above));
-      if ((__double_as_longlong(r) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) {  // NaN: redo in float64
-        double s = atcg(src, N, i - 1, j, kk) + atcg(src, N, i + 1, j, kk);
-        s += atcg(src, N, i, j - 1, kk);
-        s += atcg(src, N, i, j + 1, kk);
-        s += atcg(src, N, i, j, kk - 1);
-        s += atcg(src, N, i, j, kk + 1);
-        r = s * kSixth;
+      const float2 r = df_avg6(tb[cidx - 1], tb[cidx + 1], tb[cidx - PXs], tb[cidx + PXs], below, above);
+      if (dst_pairs) {
+        reinterpret_cast<float2*>(dst)[kk * NN + col] = r;
+      } else {
+        double d = pair_to_double(r);
+        if (!src_pairs && (__double_as_longlong(d) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) {
+          // an input outside the float-pair range: redo this point in float64
+          double s = atcg(src, N, i - 1, j, kk) + atcg(src, N, i + 1, j, kk);
+          s += atcg(src, N, i, j - 1, kk);
+          s += atcg(src, N, i, j + 1, kk);
+          s += atcg(src, N, i, j, kk - 1);
+          s += atcg(src, N, i, j, kk + 1);
+          d = s * kSixth;
+        }
+        dst[kk * NN + col] = d;
       }
-      dst[kk * NN + col] = r;
     }
     below = cur;
     cur = above;
   }
+  if (dst_pairs && marker && flag) atomicOr(flag, 1);
 }
 
-__device__ __forceinline__ int64_t mp_find(int64_t d, int64_t lo, int64_t hi, const int* __restrict__ rp,
-                                           int64_t nnz) {
-  lo = max(lo, d - nnz);
-  hi = min(hi, d);
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if ((int64_t)__ldg(rp + mid + 1) <= d - mid - 1)
-      lo = mid + 1;
-    else
-      hi = mid;
+// Phase p of a Jacobi call.  Buffers ping-pong so that the last sweep lands in
+// `out`.  A df call with a pair chain: phase 0 float64 -> pairs, phases
+// 1..S-2 pairs -> pairs, phase S-1 pairs -> float64, phase S the catch-up;
+// once the call's flag is set, phase p >= 1 computes sweep p-1 in float64
+// from float64 data and the catch-up computes sweep S-1.
+__device__ void jacobi_tile(const ar_exec_call& k, int v, int p, int64_t t, int* flag, unsigned char* smraw) {
+  const int S = k.sweeps, N = (int)k.n;
+  const double* u0 = static_cast<const double*>(k.in0);
+  double* out = static_cast<double*>(k.out0);
+  double* work = static_cast<double*>(k.out1);
+  auto dst_of = [&](int sw) -> double* { return ((S - 1 - sw) % 2 == 0) ? out : work; };
+  auto src_of = [&](int sw) -> const double* { return sw == 0 ? u0 : dst_of(sw - 1); };
+  const int fam = v / 4;
+  if (!jacobi_pair_chain(k, v)) {
+    jacobi_sweep_tile(k, v, t, src_of(p), dst_of(p), fam == 3, false, false, nullptr, smraw);
+    return;
   }
-  return lo;
+  // block-uniform: the tile bodies below hold barriers
+  const bool flagged = __syncthreads_or(p >= 1 && __ldcg(flag) != 0);
+  if (p == S) {  // catch-up: float64 sweep S-1 over a contiguous chunk of unknowns
+    if (!flagged) return;
+    const double* src = src_of(S - 1);
+    double* dst = dst_of(S - 1);
+    const int64_t n3 = (int64_t)N * N * N, NN = (int64_t)N * N;
+    const int64_t chunk = cdiv(n3, kCatchTiles);
+    for (int64_t c = t * chunk + threadIdx.x; c < min(n3, (t + 1) * chunk); c += T) {
+      const int i = (int)(c % N), j = (int)((c / N) % N), kk = (int)(c / NN);
+      double s = atcg(src, N, i - 1, j, kk) + atcg(src, N, i + 1, j, kk);
+      s += atcg(src, N, i, j - 1, kk);
+      s += atcg(src, N, i, j + 1, kk);
+      s += atcg(src, N, i, j, kk - 1);
+      s += atcg(src, N, i, j, kk + 1);
+      dst[c] = s * kSixth;
+    }
+    return;
+  }
+  if (flagged) {  // one sweep late, in float64
+    jacobi_sweep_tile(k, v, t, src_of(p - 1), dst_of(p - 1), false, false, false, nullptr, smraw);
+    return;
+  }
+  jacobi_sweep_tile(k, v, t, src_of(p), dst_of(p), true, p > 0, p < S - 1, flag, smraw);
 }
 
 __device__ void spmv_tile(const ar_exec_call& k, int v, int p, int64_t t, unsigned char* smraw) {
@@ -440,48 +498,19 @@ __device__ void spmv_tile(const ar_exec_call& k, int v, int p, int64_t t, unsign
     y[r] = __ldcg(y + r) + tot;
     return;
   }
-  // main pass of path block t
-  int64_t* srow = reinterpret_cast<int64_t*>(smraw);
-  double* sval = reinterpret_cast<double*>(smraw + T * sizeof(int64_t));
-  int64_t* sbounds = reinterpret_cast<int64_t*>(smraw + T * (sizeof(int64_t) + sizeof(double)));
-  const int64_t L = rows + nnz;
-  const int64_t db = t * kMpPerTile, de = min(db + kMpPerTile, L);
+  // main pass of path block t (v 6: float64, v 7: float pairs)
+  int64_t* sbounds = reinterpret_cast<int64_t*>(smraw + mp::kSmemBytes);
+  const int64_t db = t * kMpPerTile, de = min(db + kMpPerTile, rows + nnz);
   if (threadIdx.x == 0) {
-    sbounds[0] = mp_find(db, 0, rows, rp, nnz);
-    sbounds[1] = mp_find(de, 0, rows, rp, nnz);
+    sbounds[0] = mp::search(db, 0, rows, rp, nnz);
+    sbounds[1] = mp::search(de, 0, rows, rp, nnz);
   }
   __syncthreads();
-  const int64_t d0 = min(db + (int64_t)threadIdx.x * kMpItems, de), d1 = min(d0 + kMpItems, de);
-  int64_t i = mp_find(d0, sbounds[0], sbounds[1], rp, nnz), j = d0 - i;
-  double s = 0.0;
-  int64_t row_end = i < rows ? (int64_t)__ldg(rp + i + 1) : nnz;
-  for (int64_t d = d0; d < d1; ++d) {
-    if (i < rows && j >= row_end) {
-      y[i] = s;
-      s = 0.0;
-      ++i;
-      row_end = i < rows ? (int64_t)__ldg(rp + i + 1) : nnz;
-    } else if (j < nnz) {
-      s = fma(__ldg(val + j), __ldg(x + __ldg(col + j)), s);
-      ++j;
-    }
-  }
-  srow[threadIdx.x] = (d1 > d0 && i < rows) ? i : -1;
-  sval[threadIdx.x] = s;
-  if (threadIdx.x == 0) carry_row[t] = -1;
-  __syncthreads();
-  const int64_t r = srow[threadIdx.x];
-  if (r >= 0 && (threadIdx.x == 0 || srow[threadIdx.x - 1] != r)) {
-    double tot = sval[threadIdx.x];
-    int u = threadIdx.x + 1;
-    while (u < T && srow[u] == r) tot += sval[u++];
-    if (u < T && min(db + (int64_t)u * kMpItems, de) < de) {
-      y[r] += tot;
-    } else {
-      carry_row[t] = r;
-      carry_val[t] = tot;
-    }
-  }
+  const int64_t i0 = sbounds[0], i1 = sbounds[1];
+  if (v == 6)
+    mp::block<false>(rows, nnz, rp, col, val, x, y, db, i0, i1, carry_row + t, carry_val + t, smraw);
+  else
+    mp::block<true>(rows, nnz, rp, col, val, x, y, db, i0, i1, carry_row + t, carry_val + t, smraw);
 }
 
 template <int U>
@@ -543,13 +572,16 @@ __device__ void nbody_tile(const ar_exec_call& k, int v, int64_t t, unsigned cha
 }
 
 // ------------------------------------------------------------------ run
-constexpr int kSmemBytes = 8448;  // largest tile: 2 x 4 x 130 doubles (Jacobi 128x2) / 512 float4
+// largest tile: a merge-path block (staged products and row ends, open rows,
+// partial sums) plus its two path bounds; Jacobi needs 2 x 4 x 130 doubles
+constexpr int kSmemBytes = mp::kSmemBytes + 16;
+static_assert(kSmemBytes >= 8448, "shared memory of the Jacobi and n-body tiles");
 
 __global__ void __launch_bounds__(T, 2) exec_run(const ar_exec_call* __restrict__ calls, int ncalls,
                                                  const int* __restrict__ vint, const int* __restrict__ tiles,
                                                  const long long* __restrict__ prefix, int* done,
                                                  unsigned long long* counter, uint64_t* t0, uint64_t* t1,
-                                                 int* status) {
+                                                 int* status, int* flags) {
   __shared__ __align__(16) unsigned char smraw[kSmemBytes];
   __shared__ long long s_item, s_t;
   __shared__ int s_c, s_p, s_ok;
@@ -602,7 +634,7 @@ __global__ void __launch_bounds__(T, 2) exec_run(const ar_exec_call* __restrict_
     if (s_ok && k.loop >= 0 && k.loop < 4 && v >= 0 && v < c_nvar[k.loop]) {
       switch (k.loop) {
         case AR_LOOP_DAXPY: daxpy_tile(k, v, t); break;
-        case AR_LOOP_JACOBI7: jacobi_tile(k, v, p, t, smraw); break;
+        case AR_LOOP_JACOBI7: jacobi_tile(k, v, p, t, flags + c, smraw); break;
         case AR_LOOP_SPMV: spmv_tile(k, v, p, t, smraw); break;
         default: nbody_tile(k, v, t, smraw); break;
       }
@@ -617,7 +649,7 @@ __global__ void __launch_bounds__(T, 2) exec_run(const ar_exec_call* __restrict_
 }
 
 struct WsLayout {
-  size_t part, tiles, prefix, done, counter, vint, total;
+  size_t part, tiles, prefix, done, counter, vint, flags, total;
 };
 
 WsLayout layout(int max_calls) {
@@ -635,6 +667,8 @@ WsLayout layout(int max_calls) {
   w.counter = o;
   o = up(o + 8);
   w.vint = o;
+  o = up(o + (size_t)max_calls * 4);
+  w.flags = o;
   o = up(o + (size_t)max_calls * 4);
   w.total = o + 256;
   return w;
@@ -684,11 +718,14 @@ extern "C" int ar_exec_batch(const ar_exec_call* calls, int ncalls, const ar_exe
   int* done = reinterpret_cast<int*>(base + w.done);
   unsigned long long* counter = reinterpret_cast<unsigned long long*>(base + w.counter);
   int* vint = reinterpret_cast<int*>(base + w.vint);
+  int* flags = reinterpret_cast<int*>(base + w.flags);
   cudaStream_t s = as_stream(stream);
   if (cudaMemsetAsync(part, 0, (size_t)ncalls * 3 * 8, s) != cudaSuccess) return AR_ERR_CUDA;
+  if (cudaMemsetAsync(flags, 0, (size_t)ncalls * 4, s) != cudaSuccess) return AR_ERR_CUDA;
   exec_features<<<dim3(64, (unsigned)ncalls), T, 0, s>>>(calls, features, part);
   exec_plan<<<1, T, 0, s>>>(calls, ncalls, m, have, force_variant, variant, conf, features, part, tiles, prefix,
                             done, counter, t_start, t_end, status, vint);
-  exec_run<<<device_sms() * 2, T, 0, s>>>(calls, ncalls, vint, tiles, prefix, done, counter, t_start, t_end, status);
+  exec_run<<<device_sms() * 2, T, 0, s>>>(calls, ncalls, vint, tiles, prefix, done, counter, t_start, t_end, status,
+                                          flags);
   return launch_status();
 }

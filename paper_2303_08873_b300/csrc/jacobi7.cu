@@ -26,6 +26,7 @@
 
 #include <cstdio>
 #include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 #include "pairs.cuh"
@@ -34,7 +35,7 @@
 namespace ar {
 namespace {
 
-constexpr int kDZ = 8;     // planes per TMA box
+constexpr int kDZ = 4;     // planes per TMA box
 constexpr int kRing = 3;   // boxes resident per block
 constexpr int kShapeX[4] = {32, 32, 64, 128};
 constexpr int kShapeY[4] = {4, 8, 4, 2};
@@ -128,7 +129,9 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
   using G = TmaGeom<BX, BY>;
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[kRing];
-  double* buf = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  // 128-byte aligned box ring; offsetting smem_raw itself (no integer round
+  // trip) keeps the pointer in the shared window, so loads compile to LDS
+  double* buf = reinterpret_cast<double*>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
 
   const int tid = threadIdx.x;
   const int tx = tid % BX, ty = tid / BX;
@@ -140,7 +143,6 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
   const bool flagged = (MODE == M_PP || MODE == M_PD) && flag != nullptr && *flag != 0;
   const bool native = (MODE == M_NATIVE) || flagged;
   const bool split_boxes = !native && (MODE == M_DD || MODE == M_DP);
-  const bool pair_out = !native && (MODE == M_DP || MODE == M_PP);
   const CUtensorMap* src_map = flagged ? &tmap_alt : &tmap;
 
   if (tid == 0) {
@@ -165,22 +167,23 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
   const int c = (ty + 1) * G::PX + tx + 2;
   double* outd = flagged ? out_alt : static_cast<double*>(outv);
   float2* outp = static_cast<float2*>(outv);
-  // z queue: centres of planes p-1 and p (ring index qm = (p-1) mod RING)
+  // z queue: the values of planes p-1 and p at this thread's column
   double dm = 0.0, d0 = 0.0;
   float2 fm = make_float2(0.f, 0.f), f0 = make_float2(0.f, 0.f);
-  int qm = 0;
-  int next_p = 1;
+  int64_t off = (int64_t)kb * NN + col;  // output offset of the next plane
   int g = 0;
   bool failed = false;
   for (; g < ngroups; ++g) {
     const int slot = g % kRing;
+    const int pslot = slot == 0 ? kRing - 1 : slot - 1;
     const bool ok = mbar_wait_bounded(smem_addr(&bars[slot]), (uint32_t)((g / kRing) & 1));
     if (__syncthreads_or(!ok)) {
       failed = true;
       break;
     }
+    double* box = buf + (size_t)slot * G::GROUP;
+    const double* prev = buf + (size_t)pslot * G::GROUP;
     if (split_boxes) {
-      double* box = buf + (size_t)slot * G::GROUP;
       bool marker = false;
       for (int e = tid; e < G::GROUP; e += BX * BY) {
         const float2 f = df_split(box[e]);
@@ -189,61 +192,81 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
       }
       if (__syncthreads_or(marker) && MODE == M_DP && tid == 0 && flag) atomicOr(flag, 1);
     }
-    if (g == 0) {  // centres of planes 0 and 1 (relative) start the queue
-      if (native) {
-        dm = buf[c];
-        d0 = buf[G::PLANE + c];
-      } else {
-        fm = reinterpret_cast<const float2*>(buf)[c];
-        f0 = reinterpret_cast<const float2*>(buf)[G::PLANE + c];
-      }
-    }
-    const int plast = min(kc, (g + 1) * kDZ - 2);
-    for (int p = next_p; p <= plast; ++p) {
-      const int q0 = (qm + 1 == G::RING) ? 0 : qm + 1;
-      const int qp = (q0 + 1 == G::RING) ? 0 : q0 + 1;
-      const int k = kb + p - 1;
-      if (native) {
-        const double* pc = buf + (size_t)q0 * G::PLANE;
-        const double up = buf[(size_t)qp * G::PLANE + c];
-        double s = pc[c - 1] + pc[c + 1];
-        s += pc[c - G::PX];
-        s += pc[c + G::PX];
-        s += dm;
-        s += up;
-        if (inside) outd[(int64_t)k * NN + col] = s * kSixth;
-        dm = d0;
-        d0 = up;
-      } else {
-        const float2* pc = reinterpret_cast<const float2*>(buf) + (size_t)q0 * G::PLANE;
-        const float2 up = reinterpret_cast<const float2*>(buf)[(size_t)qp * G::PLANE + c];
-        const float2 r = df_avg6(pc[c - 1], pc[c + 1], pc[c - G::PX], pc[c + G::PX], fm, up);
-        if (inside) {
-          if (pair_out) {
-            // stored unnormalised: the next sweep sums the hi parts exactly and
-            // the lo parts in float, so |lo| of a few ulps of hi costs ~2^-46
-            outp[(int64_t)k * NN + col] = r;
-          } else {
-            double v = pair_to_double(r);
-            // NaN test on the bit pattern (a float64 compare would use the float64 pipe)
-            if (MODE == M_DD && (__double_as_longlong(v) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) {
-              // an input outside the float-pair range: redo in float64
-              double sd = at(in, N, i - 1, j, k) + at(in, N, i + 1, j, k);
-              sd += at(in, N, i, j - 1, k);
-              sd += at(in, N, i, j + 1, k);
-              sd += at(in, N, i, j, k - 1);
-              sd += at(in, N, i, j, k + 1);
-              v = sd * kSixth;
-            }
-            outd[(int64_t)k * NN + col] = v;
+    // Box g holds relative planes D*g .. D*g+D-1 (D = kDZ planes per box,
+    // relative plane 0 = kb - 1), so it completes output planes
+    // p = D*g-1 .. D*g+D-2; the centre plane of p is plane r-1 of this box, or
+    // the last plane of the previous box for r = 0.  Unrolled, every
+    // shared-memory offset below is a constant; the arithmetic kind and the
+    // edge guards are hoisted out of the plane loop.
+    auto planes = [&](auto native_c, auto guard_c) {
+      constexpr bool NAT = decltype(native_c)::value;
+      constexpr bool GUARD = decltype(guard_c)::value;
+#pragma unroll
+      for (int r = 0; r < kDZ; ++r) {
+        const int p = g * kDZ - 1 + r;
+        const bool live = !GUARD || (p >= 1 && p <= kc);  // block-uniform
+        const int cp = (r == 0 ? (kDZ - 1) * G::PLANE : (r - 1) * G::PLANE) + c;
+        if constexpr (NAT) {
+          const double* pc = (r == 0 ? prev : box) + cp;
+          const double up = box[r * G::PLANE + c];
+          if (live) {
+            double s = pc[-1] + pc[1];
+            s += pc[-G::PX];
+            s += pc[G::PX];
+            s += dm;
+            s += up;
+            if (inside) outd[off] = s * kSixth;
+            off += NN;
           }
+          dm = d0;
+          d0 = up;
+        } else {
+          const float2* pc = reinterpret_cast<const float2*>(r == 0 ? prev : box) + cp;
+          const float2 up = reinterpret_cast<const float2*>(box)[r * G::PLANE + c];
+          if (live) {
+            const float2 res = df_avg6(pc[-1], pc[1], pc[-G::PX], pc[G::PX], fm, up);
+            if (inside) {
+              if constexpr (MODE == M_DP || MODE == M_PP) {  // pairs out (the native case is above)
+                // stored unnormalised: the next sweep sums the hi parts exactly and
+                // the lo parts in float, so |lo| of a few ulps of hi costs ~2^-46
+                outp[off] = res;
+              } else {
+                double v = pair_to_double(res);
+                // NaN test on the bit pattern (a float64 compare would use the float64 pipe)
+                if (MODE == M_DD && (__double_as_longlong(v) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) {
+                  // an input outside the float-pair range: redo in float64
+                  const int k = kb + p - 1;
+                  double sd = at(in, N, i - 1, j, k) + at(in, N, i + 1, j, k);
+                  sd += at(in, N, i, j - 1, k);
+                  sd += at(in, N, i, j + 1, k);
+                  sd += at(in, N, i, j, k - 1);
+                  sd += at(in, N, i, j, k + 1);
+                  v = sd * kSixth;
+                }
+                outd[off] = v;
+              }
+            }
+            off += NN;
+          }
+          fm = f0;
+          f0 = up;
         }
-        fm = f0;
-        f0 = up;
       }
-      qm = q0;
+    };
+    using T_ = std::true_type;
+    using F_ = std::false_type;
+    const bool guard = g == 0 || g * kDZ + kDZ - 2 > kc;
+    if (native) {
+      if (guard)
+        planes(T_{}, T_{});
+      else
+        planes(T_{}, F_{});
+    } else {
+      if (guard)
+        planes(F_{}, T_{});
+      else
+        planes(F_{}, F_{});
     }
-    if (plast + 1 > next_p) next_p = plast + 1;
     // every reader of box g-1 is past this barrier: its slot takes box g+2
     fence_proxy_async_smem();
     __syncthreads();

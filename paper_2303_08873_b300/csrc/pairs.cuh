@@ -91,6 +91,41 @@ __device__ __forceinline__ float2 df_avg6(float2 v0, float2 v1, float2 v2, float
 
 __device__ __forceinline__ double pair_to_double(float2 v) { return f2d_bits(v.x) + f2d_bits(v.y); }
 
+// Split a product operand x into floats hi + lo (hi = x truncated to 24
+// significant bits, 0 <= lo/x < 2^-23, x - hi - lo below 2^-46 |x|) with
+// integer operations and one float add.  The
+// range is [2^-62, 2^62) in magnitude, so that products of two operands and
+// their low parts stay normal floats; +-0 gives (0, 0).  Returns false (and
+// (0, 0)) for any other value: the caller redoes that work in float64.
+__device__ __forceinline__ bool prod_split(double x, float& hi, float& lo) {
+  const long long b = __double_as_longlong(x);
+  const unsigned h32 = (unsigned)((unsigned long long)b >> 32), l32 = (unsigned)b;
+  const unsigned e = (h32 >> 20) & 0x7ffu;
+  const unsigned sign = h32 & 0x80000000u;
+  // float exponent e - 896 lands in bits 31..23 as (e mod 512) + 128 mod 512,
+  // which is e - 896 < 256 for every e in range: sign bit left clear
+  const unsigned hib = (__funnelshift_l(l32, h32, 3) + 0x40000000u) | sign;
+  // lo from the top 23 of the 29 remainder bits (the dropped 6 bits are below
+  // 2^-46 |x|): 2^23 + q is a float read straight from its bits, so no
+  // int->float conversion instruction is needed
+  const float q = __uint_as_float(0x4b000000u | ((l32 >> 6) & 0x7fffffu)) - 8388608.0f;
+  const float scale = __uint_as_float(((e - 942u) << 23) | sign);  // +-2^(e-1069)
+  const bool ok = e - 961u < 124u;
+  hi = ok ? __uint_as_float(hib) : 0.f;
+  lo = ok ? q * scale : 0.f;
+  return ok || ((h32 & 0x7fffffffu) | l32) == 0u;
+}
+
+// (S, C) += (p, pe) for unevaluated float pairs ("sloppy" pair addition):
+// the absolute error is below ~2^-46 (|S| + |p|) whatever the signs.
+__device__ __forceinline__ void pair_add(float& S, float& C, float p, float pe) {
+  float s, e;
+  two_sum(S, p, s, e);
+  e += C + pe;
+  S = s + e;
+  C = e - (S - s);
+}
+
 // A float64 value the float-pair path cannot carry to later sweeps.
 __device__ __forceinline__ bool outside_pair_range(double v) {
   const long long b = __double_as_longlong(v);

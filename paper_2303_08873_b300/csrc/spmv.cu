@@ -5,38 +5,33 @@
 // Algorithmic traffic: 12 bytes per nonzero (val + col), 4 per row pointer,
 // 8 per x entry (read once when it stays in L2) and 8 per output row.  One
 // DFMA per nonzero; on B300 that float64 rate (~0.56e12/s) is of the same
-// order as the HBM-limited nonzero rate, so the variants also differ in how
-// many float64 reduction adds they spend per row.
+// order as the HBM-limited nonzero rate, and a float64 instruction occupies
+// the float64 pipe for its whole warp however many lanes are active, so the
+// variants also differ in how many (partly masked) float64 instructions they
+// spend per row.
 //
 // Variants: 0 thread-per-row; 1 warp-per-row (32-lane shuffle reduction);
 // 2..5 vector-k with k = 2, 4, 8, 16 lanes per row; 6 merge-path
-// (Merrill & Garland, SC'16): the merge of row ends and nonzero indices is cut
-// into equal chunks of 16 path items per thread, so every thread does the same
-// work whatever the row lengths; rows that straddle threads are fixed up
-// deterministically by the first thread of each straddling run, rows that
-// straddle blocks by a second small kernel over the per-block carries.
+// (Merrill & Garland, SC'16) with the block's products staged in shared
+// memory; 7 the same merge path in float-pair arithmetic (merge_path.cuh).
+// Merge path cuts the merge of row ends and nonzero indices into equal chunks
+// of 16 path items per thread, so every thread does the same work whatever
+// the row lengths; rows that straddle threads are summed by a segmented scan
+// inside the block, rows that straddle blocks by a second small kernel over
+// the per-block carries.
 #include <cstdio>
 #include <mutex>
 
 #include "common.cuh"
+#include "merge_path.cuh"
 
 namespace ar {
 namespace {
 
-constexpr int kMpThreads = 256;
-constexpr int kMpItems = 16;                          // path items per thread
-constexpr int kMpPerBlock = kMpThreads * kMpItems;    // 4096
-
-__device__ __forceinline__ double ld_val(const double* p) {
-  double v;
-  asm volatile("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
-  return v;
-}
-__device__ __forceinline__ int ld_col(const int* p) {
-  int v;
-  asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
-  return v;
-}
+using mp::ld_col;
+using mp::ld_val;
+constexpr int kMpThreads = mp::kThreads;
+constexpr int kMpPerBlock = mp::kPerBlock;
 
 // ------------------------------------------------------------ thread per row
 __global__ void __launch_bounds__(256) spmv_thread_row(int64_t rows, const int* __restrict__ rowptr,
@@ -69,30 +64,18 @@ __global__ void __launch_bounds__(256) spmv_vector(int64_t rows, const int* __re
 }
 
 // ------------------------------------------------------------ merge path
-// Path coordinate of diagonal d: (i rows consumed, d - i nonzeros consumed).
-__device__ __forceinline__ int64_t mp_search(int64_t d, int64_t lo, int64_t hi, const int* __restrict__ rowptr,
-                                             int64_t nnz) {
-  lo = max(lo, d - nnz);
-  hi = min(hi, d);
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if ((int64_t)__ldg(rowptr + mid + 1) <= d - mid - 1)
-      lo = mid + 1;
-    else
-      hi = mid;
-  }
-  return lo;
-}
-
 __global__ void spmv_mp_partition(int64_t rows, int64_t nnz, int nblocks, const int* __restrict__ rowptr,
                                   int64_t* __restrict__ start_row) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b > nblocks) return;
   const int64_t L = rows + nnz;
   const int64_t d = min((int64_t)b * kMpPerBlock, L);
-  start_row[b] = mp_search(d, 0, rows, rowptr, nnz);
+  start_row[b] = mp::search(d, 0, rows, rowptr, nnz);
 }
 
+// One path block per CTA (see merge_path.cuh); DF selects float-pair
+// arithmetic.
+template <bool DF>
 __global__ void __launch_bounds__(kMpThreads) spmv_mp_main(int64_t rows, int64_t nnz, const int* __restrict__ rowptr,
                                                            const int* __restrict__ col,
                                                            const double* __restrict__ val,
@@ -100,51 +83,10 @@ __global__ void __launch_bounds__(kMpThreads) spmv_mp_main(int64_t rows, int64_t
                                                            const int64_t* __restrict__ start_row,
                                                            int64_t* __restrict__ carry_row,
                                                            double* __restrict__ carry_val) {
-  __shared__ int64_t srow[kMpThreads];
-  __shared__ double sval[kMpThreads];
-  const int t = threadIdx.x;
-  const int64_t L = rows + nnz;
-  const int64_t db = (int64_t)blockIdx.x * kMpPerBlock;
-  const int64_t de = min(db + kMpPerBlock, L);
-  const int64_t d0 = min(db + (int64_t)t * kMpItems, de);
-  const int64_t d1 = min(d0 + kMpItems, de);
-  int64_t i = mp_search(d0, start_row[blockIdx.x], start_row[blockIdx.x + 1], rowptr, nnz);
-  int64_t j = d0 - i;
-  double s = 0.0;
-  int64_t row_end = i < rows ? (int64_t)__ldg(rowptr + i + 1) : nnz;
-  for (int64_t d = d0; d < d1; ++d) {
-    if (i < rows && j >= row_end) {  // consume the end of row i
-      y[i] = s;
-      s = 0.0;
-      ++i;
-      row_end = i < rows ? (int64_t)__ldg(rowptr + i + 1) : nnz;
-    } else if (j < nnz) {             // consume nonzero j of row i
-      s = fma(ld_val(val + j), __ldg(x + ld_col(col + j)), s);
-      ++j;
-    }
-  }
-  // open row at the end of this thread's range: (i, s)
-  srow[t] = (d1 > d0 && i < rows) ? i : -1;
-  sval[t] = s;
-  if (t == 0) carry_row[blockIdx.x] = -1;
-  __syncthreads();
-  // The first thread of each run of threads that end inside the same open row
-  // adds the run's partial sums, in thread order, to that row: the thread
-  // after the run consumed the row's end and wrote y[row] above.  A run that
-  // reaches the end of the block becomes the block's carry instead.
-  const int64_t r = srow[t];
-  if (r >= 0 && (t == 0 || srow[t - 1] != r)) {
-    double tot = sval[t];
-    int u = t + 1;
-    while (u < kMpThreads && srow[u] == r) tot += sval[u++];
-    const bool closed_here = u < kMpThreads && min(db + (int64_t)u * kMpItems, de) < de;
-    if (closed_here) {
-      y[r] += tot;
-    } else {
-      carry_row[blockIdx.x] = r;
-      carry_val[blockIdx.x] = tot;
-    }
-  }
+  __shared__ __align__(16) unsigned char smem[mp::kSmemBytes];
+  const int b = blockIdx.x;
+  mp::block<DF>(rows, nnz, rowptr, col, val, x, y, (int64_t)b * kMpPerBlock, start_row[b], start_row[b + 1],
+                carry_row + b, carry_val + b, smem);
 }
 
 // Rows straddling blocks: the head of each run of equal carry rows adds the
@@ -243,8 +185,9 @@ __global__ void csr_stats_final(int64_t rows, int nparts, const long long* __res
   }
 }
 
-const char* const kNames[7] = {"spmv_thread_row", "spmv_warp_row", "spmv_vec2", "spmv_vec4",
-                               "spmv_vec8", "spmv_vec16", "spmv_merge_path"};
+constexpr int kNumVariants = 8;
+const char* const kNames[kNumVariants] = {"spmv_thread_row", "spmv_warp_row", "spmv_vec2",       "spmv_vec4",
+                                          "spmv_vec8",       "spmv_vec16",    "spmv_merge_path", "spmv_df_merge_path"};
 
 template <int K>
 int launch_vector(int64_t rows, const int* rp, const int* c, const double* v, const double* x, double* y,
@@ -257,10 +200,10 @@ int launch_vector(int64_t rows, const int* rp, const int* c, const double* v, co
 
 }  // namespace
 
-int spmv_num_variants() { return 7; }
+int spmv_num_variants() { return kNumVariants; }
 
 int spmv_variant_name(int v, char* buf, int len) {
-  if (v < 0 || v >= 7 || !buf || len <= 0) return AR_ERR_ARG;
+  if (v < 0 || v >= kNumVariants || !buf || len <= 0) return AR_ERR_ARG;
   snprintf(buf, (size_t)len, "%s", kNames[v]);
   return AR_OK;
 }
@@ -277,15 +220,15 @@ int spmv_launch(void* args, int variant, double, void* stream, void*) {
 using namespace ar;
 
 extern "C" int ar_spmv_workspace_bytes(int variant, int64_t rows, int64_t nnz, size_t* bytes) {
-  if (variant < 0 || variant >= 7 || rows < 0 || nnz < 0 || !bytes) return AR_ERR_ARG;
-  *bytes = variant == 6 ? mp_workspace(rows, nnz) : 0;
+  if (variant < 0 || variant >= kNumVariants || rows < 0 || nnz < 0 || !bytes) return AR_ERR_ARG;
+  *bytes = variant >= 6 ? mp_workspace(rows, nnz) : 0;
   return AR_OK;
 }
 
 extern "C" int ar_spmv(int variant, int64_t rows, int64_t nnz, const int32_t* rowptr, const int32_t* col,
                        const double* val, const double* x, double* y, void* workspace, size_t workspace_bytes,
                        void* stream) {
-  if (variant < 0 || variant >= 7 || rows < 0 || nnz < 0 || nnz > 0x7fffffffLL) return AR_ERR_ARG;
+  if (variant < 0 || variant >= kNumVariants || rows < 0 || nnz < 0 || nnz > 0x7fffffffLL) return AR_ERR_ARG;
   if (rows == 0) return AR_OK;
   if (!rowptr || !y || (nnz > 0 && (!col || !val || !x))) return AR_ERR_ARG;
   cudaStream_t s = as_stream(stream);
@@ -310,8 +253,12 @@ extern "C" int ar_spmv(int variant, int64_t rows, int64_t nnz, const int32_t* ro
       int64_t* carry_row = start_row + (nb + 1);
       double* carry_val = reinterpret_cast<double*>(carry_row + nb);
       spmv_mp_partition<<<(unsigned)ceil_div(nb + 1, 256), 256, 0, s>>>(rows, nnz, (int)nb, rp, start_row);
-      spmv_mp_main<<<(unsigned)nb, kMpThreads, 0, s>>>(rows, nnz, rp, c, val, x, y, start_row, carry_row,
-                                                      carry_val);
+      if (variant == 6)
+        spmv_mp_main<false><<<(unsigned)nb, kMpThreads, 0, s>>>(rows, nnz, rp, c, val, x, y, start_row, carry_row,
+                                                                carry_val);
+      else
+        spmv_mp_main<true><<<(unsigned)nb, kMpThreads, 0, s>>>(rows, nnz, rp, c, val, x, y, start_row, carry_row,
+                                                               carry_val);
       spmv_mp_fixup<<<(unsigned)ceil_div(nb, 256), 256, 0, s>>>((int)nb, carry_row, carry_val, y);
       return launch_status();
     }
@@ -390,7 +337,8 @@ extern "C" int ar_spmv_merge_path_noalloc(int64_t rows, int64_t nnz, const int32
   const int* rp = reinterpret_cast<const int*>(rowptr);
   const int* c = reinterpret_cast<const int*>(col);
   spmv_mp_partition<<<(unsigned)ceil_div(nb + 1, 256), 256, 0, s>>>(rows, nnz, (int)nb, rp, start_row);
-  spmv_mp_main<<<(unsigned)nb, kMpThreads, 0, s>>>(rows, nnz, rp, c, val, x, y, start_row, carry_row, carry_val);
+  spmv_mp_main<false><<<(unsigned)nb, kMpThreads, 0, s>>>(rows, nnz, rp, c, val, x, y, start_row, carry_row,
+                                                          carry_val);
   spmv_mp_fixup<<<(unsigned)ceil_div(nb, 256), 256, 0, s>>>((int)nb, carry_row, carry_val, y);
   return launch_status();
 }

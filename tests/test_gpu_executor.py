@@ -34,8 +34,10 @@ class Batch:
         scale = np.abs(a * x) + np.abs(y)
         self.check.append(lambda yd=yd, ref=ref, scale=scale: np.all(np.abs(host(yd) - ref) <= 1e-13 * scale))
 
-    def jacobi(self, N, sweeps, seed):
+    def jacobi(self, N, sweeps, seed, plant=None):
         u0 = synth.grid_inputs(seed, N)
+        if plant is not None:
+            u0[N // 2, N // 3, N // 4] = plant
         ud = dev(u0)
         out, work = torch.empty_like(ud), torch.empty_like(ud)
         self.keep += [ud, out, work]
@@ -107,7 +109,7 @@ def test_every_variant_of_every_loop_in_one_batch():
     zipf = synth.csr_zipf(5, 20000, 1.6)
     band = synth.csr_band(6, 9000, 129)
     stats = []
-    for v in range(7):
+    for v in range(8):
         stats.append(b.spmv(zipf if v % 2 == 0 else band, 50 + v))
         force.append(v)
     for v in range(9):
@@ -120,11 +122,29 @@ def test_every_variant_of_every_loop_in_one_batch():
         assert ok(), (k, b.calls[k].loop, force[k])
     assert np.all(r["t1"] >= r["t0"]) and np.all(r["t0"] > 0)
     # features of the SpMV calls (reduced on the device)
-    for k, st in zip(range(31, 38), stats):
+    for k, st in zip(range(31, 39), stats):
         f = r["features"][k]
         assert f[0] == np.float32(st[0]) and f[1] == np.float32(st[1]) and f[4] == st[4]
         assert f[2] == pytest.approx(st[2], rel=1e-6) and f[3] == pytest.approx(st[3], rel=1e-5)
     assert r["features"][0][0] == 100003 and tuple(r["features"][15][:2]) == (50.0, 3.0)
+
+
+def test_float_pair_chain_with_and_without_range_flag():
+    """The float-pair Jacobi variants keep pairs between sweeps (float64 in,
+    float64 out) and redo the call in float64 from the second phase on when an
+    input lies outside the pair range; calls with and without such an input
+    share one batch, so the range flag is per call."""
+    b = Batch()
+    force = []
+    for k, (N, sweeps, plant) in enumerate([(40, 1, None), (40, 2, None), (33, 3, None), (50, 6, None),
+                                            (40, 1, 1e40), (40, 2, 1e40), (33, 3, 1e-30), (50, 6, -3e39),
+                                            (29, 5, 0.0), (64, 4, 2.0 ** -80)]):
+        b.jacobi(N, sweeps, 90 + k, plant)
+        force.append(12 + k % 4)
+    r = b.run(force=force)
+    assert np.all(r["status"] == 0)
+    for k, ok in enumerate(b.check):
+        assert ok(), (k, force[k])
 
 
 def test_bad_variant_and_loop_are_reported_per_call():

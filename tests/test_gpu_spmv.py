@@ -9,7 +9,8 @@ from oracle import loops
 from tests.gpu_util import dev, host
 
 pytestmark = pytest.mark.gpu
-V = 7
+V = ar.loop_num_variants(2)
+DF = [v for v in range(V) if "_df_" in ar.loop_variant_name(2, v)]  # float-pair arithmetic
 TOL = 1e-10  # |y - y_ref| <= TOL * sum_k |val_k x_col_k| per row
 
 
@@ -58,8 +59,12 @@ def test_identity_and_diagonal_bitwise():
     c = np.arange(n, dtype=np.int32)
     d = np.random.Generator(np.random.PCG64(4)).normal(size=n)
     for v in range(V):
-        assert np.array_equal(_run(v, rp, c, np.ones(n), x), x), v
-        assert np.array_equal(_run(v, rp, c, d, x), d * x), v
+        if v in DF:  # each operand is carried to 2^-46 by its float pair, a product to ~3 * 2^-46
+            assert np.all(np.abs(_run(v, rp, c, np.ones(n), x) - x) <= 2.0 ** -45 * np.abs(x)), v
+            assert np.all(np.abs(_run(v, rp, c, d, x) - d * x) <= 2.0 ** -43 * np.abs(d * x)), v
+        else:
+            assert np.array_equal(_run(v, rp, c, np.ones(n), x), x), v
+            assert np.array_equal(_run(v, rp, c, d, x), d * x), v
 
 
 def test_empty_rows_long_rows_and_block_straddles():
@@ -87,6 +92,30 @@ def test_all_empty_and_single_dense_row():
     r = np.random.Generator(np.random.PCG64(6))
     _check_all(np.array([0, n], dtype=np.int32), np.arange(n, dtype=np.int32), r.normal(size=n),
                r.uniform(-1, 1, n), "dense row")
+
+
+def test_operands_outside_the_float_pair_range():
+    """Rows holding zeros, values outside [2^-62, 2^62) or products whose
+    float sum overflows: the float-pair variants redo those rows in float64,
+    every variant matches the oracle."""
+    rng = np.random.Generator(np.random.PCG64(9))
+    rows, cols = 600, 700
+    lens = rng.integers(0, 60, rows)
+    lens[:4] = [4096 // 8, 50, 50, 50]
+    rp = np.zeros(rows + 1, dtype=np.int64)
+    rp[1:] = np.cumsum(lens)
+    nnz = int(rp[-1])
+    c = np.concatenate([np.sort(rng.choice(cols, int(L), replace=False)) for L in lens]).astype(np.int32)
+    val = rng.normal(size=nnz)
+    x = rng.uniform(-1, 1, cols)
+    val[: lens[0]] = 2.0 ** 61                              # row 0: 512 products of 2^122 overflow a float sum
+    x[c[: lens[0]]] = 2.0 ** 61
+    val[rp[1]] = 1e-25                                      # row 1: a tiny value
+    val[rp[2]] = 0.0                                        # row 2: an explicit zero
+    val[rp[3]] = -1e25                                      # row 3: a huge value
+    x[rng.integers(0, cols, 20)] = 0.0                      # zeros in x
+    x[c[rp[5]]] = 3e-30                                     # a tiny x entry
+    _check_all(rp.astype(np.int32), c, val, x, "range")
 
 
 def test_every_variant_is_deterministic():
