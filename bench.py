@@ -804,7 +804,7 @@ def run_mixed(args):
         times, _ = exhaustive(L, size, 2)
         regrets[L].append(times[v] / min(times) - 1.0)
     # --- fallback: exhaustive profiling of the low-confidence calls (counted, timed on a sample)
-    fb_sample = low[:16]
+    fb_sample = [low[q] for q in rng.choice(len(low), size=min(24, len(low)), replace=False)] if low else []
     t_fb = time.perf_counter()
     fb_ns = 0.0
     for q in fb_sample:

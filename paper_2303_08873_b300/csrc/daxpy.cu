@@ -80,10 +80,10 @@ int dispatch_ept(int e, int64_t n, double a, const double* x, double* y, cudaStr
 
 }  // namespace
 
-int daxpy_num_variants() { return 15; }
+int daxpy_num_variants() { return kDaxpyVariants; }
 
 int daxpy_variant_name(int v, char* buf, int len) {
-  if (v < 0 || v >= 15 || !buf || len <= 0) return AR_ERR_ARG;
+  if (v < 0 || v >= kDaxpyVariants || !buf || len <= 0) return AR_ERR_ARG;
   snprintf(buf, (size_t)len, "daxpy_b%d_e%d", kBlock[v / 3], kEpt[v % 3]);
   return AR_OK;
 }
@@ -98,7 +98,7 @@ int daxpy_launch(void* args, int variant, double, void* stream, void*) {
 
 extern "C" int ar_daxpy(int variant, int64_t n, double a, const double* x, double* y, void* stream) {
   using namespace ar;
-  if (variant < 0 || variant >= 15 || n < 0) return AR_ERR_ARG;
+  if (variant < 0 || variant >= kDaxpyVariants || n < 0) return AR_ERR_ARG;
   if (n == 0) return AR_OK;
   if (!x || !y) return AR_ERR_ARG;
   const int bi = variant / 3, e = variant % 3;

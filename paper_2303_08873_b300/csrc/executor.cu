@@ -26,7 +26,7 @@ constexpr uint32_t kDepSpin = 1u << 24;  // dependency polls (with backoff) befo
 constexpr int kMpPerTile = mp::kPerBlock;
 static_assert(mp::kThreads == T, "merge-path tiles use the executor's block size");
 
-__constant__ int c_nvar[4] = {15, 16, 8, 9};
+__constant__ int c_nvar[4] = {kDaxpyVariants, kJacobiVariants, kSpmvVariants, kNbodyVariants};
 __constant__ int c_default[4] = {6, 1, 0, 3};
 __constant__ int c_nfeat[4] = {1, 2, 5, 1};
 __constant__ int c_dx_block[5] = {64, 128, 256, 512, 1024};
@@ -698,7 +698,8 @@ extern "C" int ar_exec_batch(const ar_exec_call* calls, int ncalls, const ar_exe
   bool have = false;
   if (models) {
     if (models->H != 32 && models->H != 64) return AR_ERR_ARG;
-    const int nfeat[4] = {1, 2, 5, 1}, nvar[4] = {15, 16, 7, 9};
+    const int nfeat[4] = {1, 2, 5, 1};
+    const int nvar[4] = {kDaxpyVariants, kJacobiVariants, kSpmvVariants, kNbodyVariants};
     for (int L = 0; L < 4; ++L) {
       m.F[L] = models->F[L];
       m.V[L] = models->V[L];

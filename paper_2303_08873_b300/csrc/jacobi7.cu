@@ -412,10 +412,10 @@ bool encode_tensor_map_3d_f64(CUtensorMap* map, const void* base, uint64_t d0, u
   return r == CUDA_SUCCESS;
 }
 
-int jacobi7_num_variants() { return 16; }
+int jacobi7_num_variants() { return kJacobiVariants; }
 
 int jacobi7_variant_name(int v, char* buf, int len) {
-  if (v < 0 || v >= 16 || !buf || len <= 0) return AR_ERR_ARG;
+  if (v < 0 || v >= kJacobiVariants || !buf || len <= 0) return AR_ERR_ARG;
   snprintf(buf, (size_t)len, "jacobi7_%s_%dx%d", kFamily[v / 4], kShapeX[v % 4], kShapeY[v % 4]);
   return AR_OK;
 }
@@ -431,7 +431,7 @@ int jacobi7_launch(void* args, int variant, double, void* stream, void*) {
 extern "C" int ar_jacobi7(int variant, int N, int sweeps, const double* u0, double* out, double* work,
                           int* status, void* stream) {
   using namespace ar;
-  if (variant < 0 || variant >= 16 || N < 0 || sweeps < 0 || N > 65535) return AR_ERR_ARG;
+  if (variant < 0 || variant >= kJacobiVariants || N < 0 || sweeps < 0 || N > 65535) return AR_ERR_ARG;
   if (N == 0) return AR_OK;
   if (!u0 || !out || (sweeps > 1 && !work)) return AR_ERR_ARG;
   if (u0 == out || u0 == work || out == work) return AR_ERR_ARG;

@@ -184,10 +184,10 @@ size_t batch_ws(int count) { return (size_t)(2 * count + 2) * sizeof(int) + 256;
 
 }  // namespace
 
-int nbody_num_variants() { return 9; }
+int nbody_num_variants() { return kNbodyVariants; }
 
 int nbody_variant_name(int v, char* buf, int len) {
-  if (v < 0 || v >= 9 || !buf || len <= 0) return AR_ERR_ARG;
+  if (v < 0 || v >= kNbodyVariants || !buf || len <= 0) return AR_ERR_ARG;
   snprintf(buf, (size_t)len, "nbody_t%d_u%d", kTiles[v / 3], kUnroll[v % 3]);
   return AR_OK;
 }
@@ -203,7 +203,7 @@ int nbody_launch(void* args, int variant, double, void* stream, void*) {
 using namespace ar;
 
 extern "C" int ar_nbody(int variant, int64_t N, const float* pos4, float* acc4, float eps, void* stream) {
-  if (variant < 0 || variant >= 9 || N < 0 || !(eps > 0.f)) return AR_ERR_ARG;
+  if (variant < 0 || variant >= kNbodyVariants || N < 0 || !(eps > 0.f)) return AR_ERR_ARG;
   if (N == 0) return AR_OK;
   if (!pos4 || !acc4 || !aligned16(pos4) || !aligned16(acc4)) return AR_ERR_ARG;
   const float4* p = reinterpret_cast<const float4*>(pos4);

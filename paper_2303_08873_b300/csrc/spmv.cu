@@ -185,7 +185,7 @@ __global__ void csr_stats_final(int64_t rows, int nparts, const long long* __res
   }
 }
 
-constexpr int kNumVariants = 8;
+constexpr int kNumVariants = kSpmvVariants;
 const char* const kNames[kNumVariants] = {"spmv_thread_row", "spmv_warp_row", "spmv_vec2",       "spmv_vec4",
                                           "spmv_vec8",       "spmv_vec16",    "spmv_merge_path", "spmv_df_merge_path"};
 

@@ -29,6 +29,7 @@ def main():
     p.add_argument("--sweeps", type=int, default=1)
     p.add_argument("--reps", type=int, default=3)
     p.add_argument("--zipf", type=float, default=1.5, help="Zipf exponent of the spmv row lengths")
+    p.add_argument("--band", type=int, default=0, help="spmv: banded matrix of this (odd) width instead of Zipf")
     a = p.parse_args()
     dev = torch.device("cuda", 0)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -44,7 +45,10 @@ def main():
         run = lambda: ar.ar_jacobi7(a.variant, a.size, a.sweeps, u0, out, wk, st)  # noqa: E731
         work, unit = 16.0 * a.size ** 3 * a.sweeps, "GB/s"
     elif a.loop == "spmv":
-        rp, c, v = synth.csr_zipf(31, a.size, a.zipf, device="cuda")
+        if a.band:
+            rp, c, v = synth.csr_band(31, a.size, a.band, device="cuda")
+        else:
+            rp, c, v = synth.csr_zipf(31, a.size, a.zipf, device="cuda")
         x = synth.spmv_x(31, a.size, device="cuda")
         y = torch.empty(a.size, dtype=torch.float64, device=dev)
         nnz = int(rp[-1].item())

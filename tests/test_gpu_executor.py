@@ -161,8 +161,10 @@ def test_bad_variant_and_loop_are_reported_per_call():
 def _trained_models():
     """One MLP per loop, trained on the device from a deterministic cost model
     of the features (no timing involved)."""
-    specs = [(1, 15, lambda f: int(np.log2(f[0])) % 15), (2, 16, lambda f: (int(f[0]) // 40) % 16),
-             (5, 7, lambda f: 6 if f[2] > 20 else (1 if f[4] > 1000 else 3)), (1, 9, lambda f: int(f[0] > 2000) * 4)]
+    nv = [ar.loop_num_variants(L) for L in range(4)]
+    specs = [(1, nv[0], lambda f: int(np.log2(f[0])) % 15), (2, nv[1], lambda f: (int(f[0]) // 40) % 16),
+             (5, nv[2], lambda f: 7 if f[2] > 40 else (6 if f[2] > 20 else (1 if f[4] > 1000 else 3))),
+             (1, nv[3], lambda f: int(f[0] > 2000) * 4)]
     models = ar.ArExecModels()
     models.H = 64
     keep, regions = [], []
