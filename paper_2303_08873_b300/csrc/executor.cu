@@ -13,6 +13,7 @@
 
 #include "common.cuh"
 #include "merge_path.cuh"
+#include "nbody_math.cuh"
 #include "pairs.cuh"
 
 namespace ar {
@@ -513,62 +514,47 @@ __device__ void spmv_tile(const ar_exec_call& k, int v, int p, int64_t t, unsign
     mp::block<true>(rows, nnz, rp, col, val, x, y, db, i0, i1, carry_row + t, carry_val + t, smraw);
 }
 
-template <int U>
-__device__ __forceinline__ void nbody_accum(const float4* __restrict__ tile, int cnt, float4 pi, float eps2, float& ax,
-                                            float& ay, float& az) {
-  float tx = 0.f, ty = 0.f, tz = 0.f;
-#pragma unroll U
-  for (int q = 0; q < cnt; ++q) {
-    const float4 o = tile[q];
-    const float dx = o.x - pi.x, dy = o.y - pi.y, dz = o.z - pi.z;
-    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-    float inv;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(r2));  // r2 >= eps^2: never subnormal
-    const float s = o.w * inv * inv * inv;
-    tx = fmaf(dx, s, tx);
-    ty = fmaf(dy, s, ty);
-    tz = fmaf(dz, s, tz);
-  }
-  ax += tx;
-  ay += ty;
-  az += tz;
-}
-
+// An i-tile of Tt bodies (one or two per thread) against all N bodies, in
+// Tt-body j tiles held in the pair layout of nbody_math.cuh.
 __device__ void nbody_tile(const ar_exec_call& k, int v, int64_t t, unsigned char* smraw) {
   const int Tt = c_nb_tile[v / 3], uidx = v % 3;
   const float4* pos = static_cast<const float4*>(k.in0);
   float4* acc = static_cast<float4*>(k.out0);
   const int64_t N = k.n;
   const float eps2 = k.eps * k.eps;
+  const float2 eps2v = make_float2(eps2, eps2);
   float4* tile = reinterpret_cast<float4*>(smraw);
   const int nown = Tt > T ? 2 : 1;  // bodies per thread
-  float4 pi[2];
+  float2 npx[2][1], npy[2][1], npz[2][1];
   int64_t ii[2];
-  float ax[2] = {0.f, 0.f}, ay[2] = {0.f, 0.f}, az[2] = {0.f, 0.f};
+  float ax[2][1] = {{0.f}, {0.f}}, ay[2][1] = {{0.f}, {0.f}}, az[2][1] = {{0.f}, {0.f}};
   for (int o = 0; o < nown; ++o) {
     ii[o] = t * Tt + threadIdx.x + (int64_t)o * T;
     const bool own = threadIdx.x + o * T < Tt && ii[o] < N;
-    pi[o] = own ? pos[ii[o]] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 pi = own ? pos[ii[o]] : make_float4(0.f, 0.f, 0.f, 0.f);
+    npx[o][0] = make_float2(-pi.x, -pi.x);
+    npy[o][0] = make_float2(-pi.y, -pi.y);
+    npz[o][0] = make_float2(-pi.z, -pi.z);
   }
   for (int64_t j0 = 0; j0 < N; j0 += Tt) {
     __syncthreads();
     for (int q = threadIdx.x; q < Tt; q += T) {
       const int64_t jj = j0 + q;
-      tile[q] = jj < N ? pos[jj] : make_float4(0.f, 0.f, 0.f, 0.f);
+      tile_store(tile, q, jj < N ? pos[jj] : make_float4(0.f, 0.f, 0.f, 0.f));
     }
     __syncthreads();
     for (int o = 0; o < nown; ++o) {
       if (threadIdx.x + o * T >= Tt) continue;
       if (uidx == 0)
-        nbody_accum<1>(tile, Tt, pi[o], eps2, ax[o], ay[o], az[o]);
+        tile_accumulate<1, 1>(tile, Tt / 2, npx[o], npy[o], npz[o], eps2v, ax[o], ay[o], az[o]);
       else if (uidx == 1)
-        nbody_accum<4>(tile, Tt, pi[o], eps2, ax[o], ay[o], az[o]);
+        tile_accumulate<4, 1>(tile, Tt / 2, npx[o], npy[o], npz[o], eps2v, ax[o], ay[o], az[o]);
       else
-        nbody_accum<8>(tile, Tt, pi[o], eps2, ax[o], ay[o], az[o]);
+        tile_accumulate<8, 1>(tile, Tt / 2, npx[o], npy[o], npz[o], eps2v, ax[o], ay[o], az[o]);
     }
   }
   for (int o = 0; o < nown; ++o)
-    if (threadIdx.x + o * T < Tt && ii[o] < N) acc[ii[o]] = make_float4(ax[o], ay[o], az[o], 0.f);
+    if (threadIdx.x + o * T < Tt && ii[o] < N) acc[ii[o]] = make_float4(ax[o][0], ay[o][0], az[o][0], 0.f);
 }
 
 // ------------------------------------------------------------------ run

@@ -4,14 +4,18 @@
 //   j = i included (contributes exactly 0).
 //
 // Per interaction: 3 FADD + 3 FFMA (softened r^2) + 1 MUFU rsqrt + 3 FMUL +
-// 3 FFMA = 12 FP32-pipe instructions and one MUFU, plus one broadcast
-// shared-memory load of the j body shared by the thread's bodies.  Variants:
-// shared-memory tile of T bodies (T = threads per block, 128 / 256 / 512) x
-// unroll U (1 / 4 / 8) of the inner j loop; variant = 3*tile_index +
-// unroll_index.  Each thread integrates two bodies (i and i + T) when that
-// still leaves at least two blocks per SM, else one.  Each thread sums one tile
-// into a local partial before adding it to its running total, which keeps the
-// float32 rounding error near sqrt(T) + sqrt(N/T) additions instead of N.
+// 3 FFMA = 12 FP32 lane operations and one MUFU.  The FP32 operations of two
+// j bodies are issued together as packed pairs (FADD2 / FFMA2 / FMUL2 on
+// sm_100+), so a thread issues ~7.5 instructions per interaction instead of
+// ~14 and the FP32 pipe, not instruction issue, is the bound (nbody_math.cuh).
+// Variants: shared-memory tile of T bodies (T = threads per block, 128 / 256 /
+// 512) x unroll U (1 / 4 / 8) of the inner loop over j pairs; variant =
+// 3*tile_index + unroll_index.  Each thread integrates two bodies (i and
+// i + T) when that still leaves at least two blocks per SM, else one; its
+// bodies share every shared-memory load.  Each thread sums one tile into
+// local partials (even and odd j) before adding them to its running total,
+// which keeps the float32 rounding error near sqrt(T) + sqrt(N/T) additions
+// instead of N.
 //
 // The batched form runs `count` independent systems of uneven size in one
 // persistent launch: work items (system, i-tile) are ordered largest system
@@ -20,6 +24,7 @@
 #include <cstdio>
 
 #include "common.cuh"
+#include "nbody_math.cuh"
 
 namespace ar {
 namespace {
@@ -28,64 +33,30 @@ constexpr int kTiles[3] = {128, 256, 512};
 constexpr int kUnroll[3] = {1, 4, 8};
 constexpr int kBatchTile = 256;
 
-// 1/sqrt(x) by the hardware approximation (one MUFU instruction, relative
-// error about 2^-23); x = r^2 + eps^2 >= eps^2 is never subnormal, so the
-// flush-to-zero form loses nothing.
-__device__ __forceinline__ float rsqrt_hw(float x) {
-  float y;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-// R bodies per thread share every shared-memory load of a j body.
-template <int T, int U, int R>
-__device__ __forceinline__ void tile_accumulate(const float4* __restrict__ tile, const float4 (&pi)[R], float eps2,
-                                                float (&ax)[R], float (&ay)[R], float (&az)[R]) {
-  float tx[R], ty[R], tz[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) tx[r] = ty[r] = tz[r] = 0.f;
-#pragma unroll U
-  for (int k = 0; k < T; ++k) {
-    const float4 q = tile[k];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const float dx = q.x - pi[r].x, dy = q.y - pi[r].y, dz = q.z - pi[r].z;
-      const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-      const float inv = rsqrt_hw(r2);
-      const float s = q.w * inv * inv * inv;
-      tx[r] = fmaf(dx, s, tx[r]);
-      ty[r] = fmaf(dy, s, ty[r]);
-      tz[r] = fmaf(dz, s, tz[r]);
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    ax[r] += tx[r];
-    ay[r] += ty[r];
-    az[r] += tz[r];
-  }
-}
-
 // Bodies base + i_first + r*T (r < R) of [base, base+n) against all bodies of
 // the same range.  Padding bodies have zero mass and sit at the origin, so
 // they add exactly 0.
 template <int T, int U, int R>
 __device__ __forceinline__ void body_tile(const float4* __restrict__ p, float4* __restrict__ a, int64_t base,
                                           int64_t n, int64_t i_first, float eps2, float4* tile) {
-  float4 pi[R];
+  float2 npx[R], npy[R], npz[R];
   float ax[R], ay[R], az[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int64_t i = i_first + (int64_t)r * T;
-    pi[r] = i < n ? p[base + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 pi = i < n ? p[base + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    npx[r] = make_float2(-pi.x, -pi.x);
+    npy[r] = make_float2(-pi.y, -pi.y);
+    npz[r] = make_float2(-pi.z, -pi.z);
     ax[r] = ay[r] = az[r] = 0.f;
   }
+  const float2 eps2v = make_float2(eps2, eps2);
   for (int64_t j0 = 0; j0 < n; j0 += T) {
     __syncthreads();
     const int64_t j = j0 + threadIdx.x;
-    tile[threadIdx.x] = j < n ? p[base + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    tile_store(tile, threadIdx.x, j < n ? p[base + j] : make_float4(0.f, 0.f, 0.f, 0.f));
     __syncthreads();
-    tile_accumulate<T, U, R>(tile, pi, eps2, ax, ay, az);
+    tile_accumulate<U, R>(tile, T / 2, npx, npy, npz, eps2v, ax, ay, az);
   }
 #pragma unroll
   for (int r = 0; r < R; ++r) {

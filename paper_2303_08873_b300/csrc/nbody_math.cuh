@@ -1,0 +1,69 @@
+// All-pairs n-body interaction math (internal): shared by the stand-alone
+// kernels and the mixed-stream executor.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace ar {
+
+// 1/sqrt(x) by the hardware approximation (one MUFU instruction, relative
+// error about 2^-23); x = r^2 + eps^2 >= eps^2 is never subnormal, so the
+// flush-to-zero form loses nothing.
+__device__ __forceinline__ float rsqrt_hw(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Shared tile of T bodies in pair layout: entry 2m holds (x, x', y, y') and
+// entry 2m+1 (z, z', w, w') for bodies j = 2m and j' = 2m+1, so one 128-bit
+// load gives each coordinate of two j bodies as an adjacent float pair.
+__device__ __forceinline__ void tile_store(float4* tile, int t, float4 q) {
+  float* tf = reinterpret_cast<float*>(tile);
+  const int m = t >> 1, h = t & 1;
+  tf[8 * m + h] = q.x;
+  tf[8 * m + 2 + h] = q.y;
+  tf[8 * m + 4 + h] = q.z;
+  tf[8 * m + 6 + h] = q.w;
+}
+
+// R bodies per thread against the tile's 2 * npairs bodies, two j bodies per step:
+// every FP32 operation is a packed pair (FADD2 / FFMA2 / FMUL2, one issue for
+// two lanes' worth of work), so the FP32 pipe rather than instruction issue
+// bounds the loop; rsqrt stays scalar (one MUFU per interaction).  Per
+// interaction and lane the operations and their order are those of
+// the scalar formula: dx = q.x - p.x, r2 = fma(dz, dz, fma(dy, dy, fma(dx,
+// dx, eps^2))), s = ((m_j inv) inv) inv, t += d s.  The tile's even and odd
+// j bodies are summed in two partials, added once per tile.
+template <int U, int R>
+__device__ __forceinline__ void tile_accumulate(const float4* __restrict__ tile, int npairs, const float2 (&npx)[R],
+                                                const float2 (&npy)[R], const float2 (&npz)[R], float2 eps2v,
+                                                float (&ax)[R], float (&ay)[R], float (&az)[R]) {
+  float2 tx[R], ty[R], tz[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) tx[r] = ty[r] = tz[r] = make_float2(0.f, 0.f);
+#pragma unroll U
+  for (int m = 0; m < npairs; ++m) {
+    const float4 A = tile[2 * m], B = tile[2 * m + 1];
+    const float2 qx = make_float2(A.x, A.y), qy = make_float2(A.z, A.w);
+    const float2 qz = make_float2(B.x, B.y), qw = make_float2(B.z, B.w);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float2 dx = __fadd2_rn(qx, npx[r]), dy = __fadd2_rn(qy, npy[r]), dz = __fadd2_rn(qz, npz[r]);
+      const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, eps2v)));
+      const float2 inv = make_float2(rsqrt_hw(r2.x), rsqrt_hw(r2.y));
+      const float2 s = __fmul2_rn(__fmul2_rn(__fmul2_rn(qw, inv), inv), inv);
+      tx[r] = __ffma2_rn(dx, s, tx[r]);
+      ty[r] = __ffma2_rn(dy, s, ty[r]);
+      tz[r] = __ffma2_rn(dz, s, tz[r]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    ax[r] += tx[r].x + tx[r].y;
+    ay[r] += ty[r].x + ty[r].y;
+    az[r] += tz[r].x + tz[r].y;
+  }
+}
+
+}  // namespace ar
