@@ -21,7 +21,10 @@ namespace {
 
 constexpr int T = 256;                   // threads per executor block
 constexpr int PM = AR_EXEC_MAX_PHASES;   // phases per call
-constexpr int kJKC = 16;                 // Jacobi planes per tile
+constexpr int kJKC = 32;                 // Jacobi planes per tile
+constexpr int kJB = 4;                   // Jacobi planes whose loads are issued together
+constexpr int kDxTile = 16384;           // daxpy elements per tile
+constexpr int kSpPasses = 16;            // SpMV row groups per tile (thread-row, vector-k)
 constexpr int kCatchTiles = 512;         // tiles of a df call's catch-up phase
 constexpr uint32_t kDepSpin = 1u << 24;  // dependency polls (with backoff) before giving up
 constexpr int kMpPerTile = mp::kPerBlock;
@@ -63,21 +66,24 @@ __device__ __forceinline__ int phases_of(const ar_exec_call& c, int v) {
   return 1;
 }
 
+// n-body i-bodies per tile: one per thread, two for 512-body tiles.
+__device__ __forceinline__ int nb_bodies(int v) { return c_nb_tile[v / 3] > T ? c_nb_tile[v / 3] : T; }
+
 __device__ int64_t tiles_of(const ar_exec_call& c, int v, int p) {
   switch (c.loop) {
-    case AR_LOOP_DAXPY: return cdiv(c.n, (int64_t)c_dx_block[v / 3] * c_dx_ept[v % 3]);
+    case AR_LOOP_DAXPY: return cdiv(c.n, kDxTile);
     case AR_LOOP_JACOBI7: {
       const int64_t N = c.n;
       if (jacobi_pair_chain(c, v) && p == c.sweeps) return kCatchTiles;
       return cdiv(N, c_j_bx[v % 4]) * cdiv(N, c_j_by[v % 4]) * cdiv(N, kJKC);
     }
     case AR_LOOP_SPMV: {
-      if (v == 0) return cdiv(c.n, T);
-      if (v < 6) return cdiv(c.n, T / c_sp_k[v - 1]);
+      if (v == 0) return cdiv(c.n, (int64_t)T * kSpPasses);
+      if (v < 6) return cdiv(c.n, (int64_t)(T / c_sp_k[v - 1]) * kSpPasses);
       const int64_t nb = cdiv(c.n + c.nnz, kMpPerTile);
       return p == 0 ? nb : cdiv(nb, T);
     }
-    default: return cdiv(c.n, c_nb_tile[v / 3]);
+    default: return cdiv(c.n, nb_bodies(v));
   }
 }
 
@@ -268,14 +274,18 @@ __global__ void __launch_bounds__(T) exec_plan(const ar_exec_call* __restrict__ 
 }
 
 // ------------------------------------------------------------------ tiles
+// kDxTile elements; EPT consecutive elements per thread access (double2 for
+// EPT >= 2).  The variant's block size has no counterpart inside a
+// persistent 256-thread block, so variants differing only in it run alike.
 __device__ void daxpy_tile(const ar_exec_call& k, int v, int64_t t) {
-  const int BS = c_dx_block[v / 3], EPT = c_dx_ept[v % 3];
-  const int64_t n = k.n, base = t * (int64_t)BS * EPT;
+  const int EPT = c_dx_ept[v % 3];
+  const int64_t n = k.n, base = t * (int64_t)kDxTile;
   const double a = k.a;
   const double* x = static_cast<const double*>(k.in0);
   double* y = static_cast<double*>(k.out0);
   if (EPT == 1) {
-    for (int e = threadIdx.x; e < BS; e += T) {
+#pragma unroll 4
+    for (int e = threadIdx.x; e < kDxTile; e += T) {
       const int64_t i = base + e;
       if (i < n) y[i] = fma(a, __ldg(x + i), y[i]);
     }
@@ -283,19 +293,21 @@ __device__ void daxpy_tile(const ar_exec_call& k, int v, int64_t t) {
     const double2* x2 = reinterpret_cast<const double2*>(x);
     double2* y2 = reinterpret_cast<double2*>(y);
     const int64_t n2 = n >> 1, wb = base >> 1;
-    const int W = BS * EPT / 2;
-    for (int e = threadIdx.x; e < W; e += T) {
-      const int64_t w = wb + e;
-      if (w < n2) {
-        const double2 xv = __ldg(x2 + w);
-        double2 yv = y2[w];
-        yv.x = fma(a, xv.x, yv.x);
-        yv.y = fma(a, xv.y, yv.y);
-        y2[w] = yv;
+    const int W = kDxTile / 2, V2 = EPT / 2;  // double2 words per tile and per thread access
+#pragma unroll 2
+    for (int e = threadIdx.x * V2; e < W; e += T * V2) {
+      for (int u = 0; u < V2; ++u) {
+        const int64_t w = wb + e + u;
+        if (w < n2) {
+          const double2 xv = __ldg(x2 + w);
+          double2 yv = y2[w];
+          yv.x = fma(a, xv.x, yv.x);
+          yv.y = fma(a, xv.y, yv.y);
+          y2[w] = yv;
+        }
       }
     }
-    if ((n & 1) && threadIdx.x == 0 && n - 1 >= base && n - 1 < base + (int64_t)BS * EPT)
-      y[n - 1] = fma(a, x[n - 1], y[n - 1]);
+    if ((n & 1) && threadIdx.x == 0 && n - 1 >= base && n - 1 < base + kDxTile) y[n - 1] = fma(a, x[n - 1], y[n - 1]);
   }
 }
 
@@ -306,12 +318,123 @@ __device__ __forceinline__ double atcg(const double* __restrict__ u, int N, int 
   return __ldcg(u + ((int64_t)k * N + j) * N + i);
 }
 
+// Asynchronous 16-byte global -> shared copies (cp.async, L1 bypassed, so
+// data written earlier in the same launch by other SMs is seen); src_bytes 0
+// fills zeros.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int G>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(G) : "memory");
+}
+
 // One BX x BY x 16-plane tile of one sweep, 2.5D: an xy tile with halo in
 // shared memory (double buffered), z neighbours in registers.  Values are
 // float64 or float pairs in memory (src_pairs / dst_pairs); `pair_math`
 // selects float-pair arithmetic.  With float64 input and float-pair
 // arithmetic, inputs outside the pair range mark the point: it is redone in
 // float64 (dst float64) or, when dst holds pairs, reported through *flag.
+// Even N: planes kb-1 .. ke of the tile's column, x from i0-2 (16-byte
+// aligned) to i0+BX+1 and y from j0-1 to j0+BY, stream through a ring of
+// kRingPlanes shared-memory slots by cp.async, up to kRingPlanes-3 planes
+// ahead of the plane being computed; every value is loaded once per tile and
+// the z neighbours come from the ring.  Float-pair modes with float64 input
+// split each landed chunk in place (its copier does, after its own wait).
+constexpr int kRingPlanes = 8;
+__device__ void jacobi_ring_tile(int N, int BX, int BY, int bx, int by, int kb, int ke, const double* src, double* dst,
+                                 bool pair_math, bool src_pairs, bool dst_pairs, int* flag, unsigned char* smraw) {
+  const int i0 = bx * BX, j0 = by * BY;
+  const int PX = BX + 4, PL = PX * (BY + 2);
+  const int chunks_row = PX / 2, nchunk = chunks_row * (BY + 2);
+  double* ring = reinterpret_cast<double*>(smraw);
+  const bool active = threadIdx.x < BX * BY;
+  const int lx = threadIdx.x % BX, ly = threadIdx.x / BX;
+  const int i = i0 + lx, j = j0 + ly;
+  const bool inside = active && i < N && j < N;
+  const int64_t NN = (int64_t)N * N, col = (int64_t)j * N + i;
+  const int cidx = (ly + 1) * PX + lx + 2;
+  const bool split = pair_math && !src_pairs;
+  bool marker = false;
+  // plane kp (kb-1 <= kp) lives in slot (kp - kb + 1) % kRingPlanes
+  auto slot_of = [&](int kp) { return (kp - kb + 1) % kRingPlanes; };
+  auto issue = [&](int kp) {
+    if (kp <= ke) {
+      double* base = ring + slot_of(kp) * PL;
+      for (int c = threadIdx.x; c < nchunk; c += T) {
+        const int row = c / chunks_row, cx = c - row * chunks_row;
+        const int gy = j0 - 1 + row, gx = i0 - 2 + 2 * cx;  // gx even and N even: gx + 1 < N when gx < N
+        const bool in = kp >= 0 && kp < N && gy >= 0 && gy < N && gx >= 0 && gx < N;
+        cp_async16(base + row * PX + 2 * cx, in ? src + ((int64_t)kp * N + gy) * N + gx : src, in ? 16 : 0);
+      }
+    }
+    cp_async_commit();  // one group per plane, empty past ke, so the wait counts stay fixed
+  };
+  auto split_own = [&](int kp) {
+    double* base = ring + slot_of(kp) * PL;
+    for (int c = threadIdx.x; c < nchunk; c += T) {
+      const int row = c / chunks_row, cx = c - row * chunks_row;
+      double* e = base + row * PX + 2 * cx;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float2 f = df_split(e[h]);
+        marker |= (f.x != f.x);
+        reinterpret_cast<float2*>(e)[h] = f;
+      }
+    }
+  };
+  for (int q = 0; q < kRingPlanes - 1; ++q) issue(kb - 1 + q);
+  for (int kk = kb; kk < ke; ++kk) {
+    cp_async_wait<kRingPlanes - 4>();  // planes up to kk + 1 have landed (this thread's copies)
+    if (split) {
+      if (kk == kb) {
+        split_own(kb - 1);
+        split_own(kb);
+      }
+      split_own(kk + 1);
+    }
+    __syncthreads();
+    issue(kk + kRingPlanes - 2);  // into the slot of plane kk - 2, read last in the previous step
+    const int sb = slot_of(kk - 1) * PL, sc = slot_of(kk) * PL, sa = slot_of(kk + 1) * PL;
+    if (inside) {
+      if (!pair_math) {
+        const double* r = ring;
+        double s = r[sc + cidx - 1] + r[sc + cidx + 1];
+        s += r[sc + cidx - PX];
+        s += r[sc + cidx + PX];
+        s += r[sb + cidx];
+        s += r[sa + cidx];
+        dst[kk * NN + col] = s * kSixth;
+      } else {
+        const float2* r = reinterpret_cast<const float2*>(ring);
+        const float2 res =
+            df_avg6(r[sc + cidx - 1], r[sc + cidx + 1], r[sc + cidx - PX], r[sc + cidx + PX], r[sb + cidx], r[sa + cidx]);
+        if (dst_pairs) {
+          reinterpret_cast<float2*>(dst)[kk * NN + col] = res;
+        } else {
+          double dv = pair_to_double(res);
+          if (split && (__double_as_longlong(dv) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) {
+            // an input outside the float-pair range: redo this point in float64
+            double sd = atcg(src, N, i - 1, j, kk) + atcg(src, N, i + 1, j, kk);
+            sd += atcg(src, N, i, j - 1, kk);
+            sd += atcg(src, N, i, j + 1, kk);
+            sd += atcg(src, N, i, j, kk - 1);
+            sd += atcg(src, N, i, j, kk + 1);
+            dv = sd * kSixth;
+          }
+          dst[kk * NN + col] = dv;
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();  // no copy may land after the tile: the next item reuses the ring
+  __syncthreads();
+  if (dst_pairs && marker && flag) atomicOr(flag, 1);
+}
+
 __device__ void jacobi_sweep_tile(const ar_exec_call& k, int v, int64_t t, const double* src, double* dst,
                                   bool pair_math, bool src_pairs, bool dst_pairs, int* flag, unsigned char* smraw) {
   const int N = (int)k.n;
@@ -336,34 +459,64 @@ __device__ void jacobi_sweep_tile(const ar_exec_call& k, int v, int64_t t, const
     }
     return;
   }
+  if (!(N & 1)) {
+    jacobi_ring_tile(N, BX, BY, bx, by, kb, ke, src, dst, pair_math, src_pairs, dst_pairs, flag, smraw);
+    return;
+  }
   const int PXs = BX + 2, PL = PXs * (BY + 2);
   const int cidx = (ly + 1) * PXs + lx + 1;
-  if (!pair_math) {
-    double* tile = reinterpret_cast<double*>(smraw);
-    double below = inside ? atcg(src, N, i, j, kb - 1) : 0.0;
-    double cur = inside ? atcg(src, N, i, j, kb) : 0.0;
-    for (int kk = kb; kk < ke; ++kk) {
-      double* tb = tile + ((kk - kb) & 1) * PL;
-      const double above = inside ? atcg(src, N, i, j, kk + 1) : 0.0;
-      if (active) {
-        tb[cidx] = cur;
-        if (lx == 0) tb[cidx - 1] = atcg(src, N, i - 1, j, kk);
-        if (lx == BX - 1) tb[cidx + 1] = atcg(src, N, i + 1, j, kk);
-        if (ly == 0) tb[cidx - PXs] = atcg(src, N, i, j - 1, kk);
-        if (ly == BY - 1) tb[cidx + PXs] = atcg(src, N, i, j + 1, kk);
+  // halo role: the x-edge threads load the x halo, the y-edge threads the y
+  // halo (BX >= 32 and BY >= 2, so a thread has at most one of each)
+  const int hx = lx == 0 ? -1 : (lx == BX - 1 ? 1 : 0);
+  const int hy = ly == 0 ? -1 : (ly == BY - 1 ? 1 : 0);
+  // 2.5D over planes kb..ke-1: the xy tile with halo in shared memory (double
+  // buffered, one barrier per plane), z neighbours in registers.  The global
+  // loads of kJB planes (centre of the plane above, halos) are issued
+  // together before those planes are staged, so a thread has up to 3 kJB
+  // independent loads in flight instead of one or two.
+  auto sweep = [&](auto zero, auto ld, auto avg_store) {
+    using Val = decltype(zero);
+    Val* tile = reinterpret_cast<Val*>(smraw);
+    Val below = inside ? ld(i, j, kb - 1) : zero;
+    Val cur = inside ? ld(i, j, kb) : zero;
+    for (int kc = kb; kc < ke; kc += kJB) {
+      Val up[kJB], vx[kJB], vy[kJB];
+#pragma unroll
+      for (int q = 0; q < kJB; ++q) {
+        const int kk = kc + q;
+        up[q] = inside && kk < ke ? ld(i, j, kk + 1) : zero;
+        vx[q] = active && hx != 0 && kk < ke ? ld(i + hx, j, kk) : zero;
+        vy[q] = active && hy != 0 && kk < ke ? ld(i, j + hy, kk) : zero;
       }
-      __syncthreads();
-      if (inside) {
-        double s = tb[cidx - 1] + tb[cidx + 1];
-        s += tb[cidx - PXs];
-        s += tb[cidx + PXs];
-        s += below;
-        s += above;
-        dst[kk * NN + col] = s * kSixth;
+#pragma unroll
+      for (int q = 0; q < kJB; ++q) {
+        const int kk = kc + q;
+        if (kk < ke) {  // block-uniform
+          Val* tb = tile + ((kk - kb) & 1) * PL;
+          if (active) {
+            tb[cidx] = cur;
+            if (hx != 0) tb[cidx + hx] = vx[q];
+            if (hy != 0) tb[cidx + hy * PXs] = vy[q];
+          }
+          __syncthreads();
+          if (inside) avg_store(kk, tb[cidx - 1], tb[cidx + 1], tb[cidx - PXs], tb[cidx + PXs], below, up[q]);
+          below = cur;
+          cur = up[q];
+        }
       }
-      below = cur;
-      cur = above;
     }
+  };
+  if (!pair_math) {
+    sweep(
+        0.0, [&](int ii, int jj, int kk) { return atcg(src, N, ii, jj, kk); },
+        [&](int kk, double w, double e, double so, double no, double d, double u) {
+          double s = w + e;
+          s += so;
+          s += no;
+          s += d;
+          s += u;
+          dst[kk * NN + col] = s * kSixth;
+        });
     return;
   }
   // float-pair arithmetic; loads give pairs directly or split float64 values
@@ -378,41 +531,25 @@ __device__ void jacobi_sweep_tile(const ar_exec_call& k, int v, int64_t t, const
     marker |= (f.x != f.x);
     return f;
   };
-  float2* tile = reinterpret_cast<float2*>(smraw);
-  float2 below = inside ? ldp(i, j, kb - 1) : make_float2(0.f, 0.f);
-  float2 cur = inside ? ldp(i, j, kb) : make_float2(0.f, 0.f);
-  for (int kk = kb; kk < ke; ++kk) {
-    float2* tb = tile + ((kk - kb) & 1) * PL;
-    const float2 above = inside ? ldp(i, j, kk + 1) : make_float2(0.f, 0.f);
-    if (active) {
-      tb[cidx] = cur;
-      if (lx == 0) tb[cidx - 1] = ldp(i - 1, j, kk);
-      if (lx == BX - 1) tb[cidx + 1] = ldp(i + 1, j, kk);
-      if (ly == 0) tb[cidx - PXs] = ldp(i, j - 1, kk);
-      if (ly == BY - 1) tb[cidx + PXs] = ldp(i, j + 1, kk);
-    }
-    __syncthreads();
-    if (inside) {
-      const float2 r = df_avg6(tb[cidx - 1], tb[cidx + 1], tb[cidx - PXs], tb[cidx + PXs], below, above);
-      if (dst_pairs) {
-        reinterpret_cast<float2*>(dst)[kk * NN + col] = r;
-      } else {
-        double d = pair_to_double(r);
-        if (!src_pairs && (__double_as_longlong(d) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) {
-          // an input outside the float-pair range: redo this point in float64
-          double s = atcg(src, N, i - 1, j, kk) + atcg(src, N, i + 1, j, kk);
-          s += atcg(src, N, i, j - 1, kk);
-          s += atcg(src, N, i, j + 1, kk);
-          s += atcg(src, N, i, j, kk - 1);
-          s += atcg(src, N, i, j, kk + 1);
-          d = s * kSixth;
-        }
-        dst[kk * NN + col] = d;
-      }
-    }
-    below = cur;
-    cur = above;
-  }
+  sweep(make_float2(0.f, 0.f), ldp,
+        [&](int kk, float2 w, float2 e, float2 so, float2 no, float2 d, float2 u) {
+          const float2 r = df_avg6(w, e, so, no, d, u);
+          if (dst_pairs) {
+            reinterpret_cast<float2*>(dst)[kk * NN + col] = r;
+          } else {
+            double dv = pair_to_double(r);
+            if (!src_pairs && (__double_as_longlong(dv) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) {
+              // an input outside the float-pair range: redo this point in float64
+              double s = atcg(src, N, i - 1, j, kk) + atcg(src, N, i + 1, j, kk);
+              s += atcg(src, N, i, j - 1, kk);
+              s += atcg(src, N, i, j + 1, kk);
+              s += atcg(src, N, i, j, kk - 1);
+              s += atcg(src, N, i, j, kk + 1);
+              dv = s * kSixth;
+            }
+            dst[kk * NN + col] = dv;
+          }
+        });
   if (dst_pairs && marker && flag) atomicOr(flag, 1);
 }
 
@@ -466,24 +603,29 @@ __device__ void spmv_tile(const ar_exec_call& k, int v, int p, int64_t t, unsign
   const double* x = static_cast<const double*>(k.in3);
   double* y = static_cast<double*>(k.out0);
   const int64_t rows = k.n, nnz = k.nnz;
-  if (v == 0) {
-    const int64_t r = t * T + threadIdx.x;
-    if (r < rows) {
-      double s = 0.0;
-      for (int e = __ldg(rp + r); e < __ldg(rp + r + 1); ++e) s = fma(__ldg(val + e), __ldg(x + __ldg(col + e)), s);
-      y[r] = s;
+  if (v == 0) {  // kSpPasses groups of T rows, one row per thread
+    for (int g = 0; g < kSpPasses; ++g) {
+      const int64_t r = (t * kSpPasses + g) * T + threadIdx.x;
+      if (r < rows) {
+        double s = 0.0;
+        for (int e = __ldg(rp + r); e < __ldg(rp + r + 1); ++e) s = fma(__ldg(val + e), __ldg(x + __ldg(col + e)), s);
+        y[r] = s;
+      }
     }
     return;
   }
-  if (v < 6) {
+  if (v < 6) {  // kSpPasses groups of T/K rows, K lanes per row
     const int K = c_sp_k[v - 1];
-    const int64_t r = t * (T / K) + threadIdx.x / K;
     const int lane = threadIdx.x % K;
-    double s = 0.0;
-    if (r < rows)
-      for (int e = __ldg(rp + r) + lane; e < __ldg(rp + r + 1); e += K) s = fma(__ldg(val + e), __ldg(x + __ldg(col + e)), s);
-    for (int o = K / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, K);
-    if (r < rows && lane == 0) y[r] = s;
+    for (int g = 0; g < kSpPasses; ++g) {
+      const int64_t r = (t * kSpPasses + g) * (T / K) + threadIdx.x / K;
+      double s = 0.0;
+      if (r < rows)
+        for (int e = __ldg(rp + r) + lane; e < __ldg(rp + r + 1); e += K)
+          s = fma(__ldg(val + e), __ldg(x + __ldg(col + e)), s);
+      for (int o = K / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, K);
+      if (r < rows && lane == 0) y[r] = s;
+    }
     return;
   }
   const int64_t nb = cdiv(rows + nnz, kMpPerTile);
@@ -514,7 +656,7 @@ __device__ void spmv_tile(const ar_exec_call& k, int v, int p, int64_t t, unsign
     mp::block<true>(rows, nnz, rp, col, val, x, y, db, i0, i1, carry_row + t, carry_val + t, smraw);
 }
 
-// An i-tile of Tt bodies (one or two per thread) against all N bodies, in
+// nb_bodies(v) i-bodies (one or two per thread) against all N bodies, in
 // Tt-body j tiles held in the pair layout of nbody_math.cuh.
 __device__ void nbody_tile(const ar_exec_call& k, int v, int64_t t, unsigned char* smraw) {
   const int Tt = c_nb_tile[v / 3], uidx = v % 3;
@@ -524,13 +666,13 @@ __device__ void nbody_tile(const ar_exec_call& k, int v, int64_t t, unsigned cha
   const float eps2 = k.eps * k.eps;
   const float2 eps2v = make_float2(eps2, eps2);
   float4* tile = reinterpret_cast<float4*>(smraw);
-  const int nown = Tt > T ? 2 : 1;  // bodies per thread
+  const int nown = nb_bodies(v) / T;  // i-bodies per thread
   float2 npx[2][1], npy[2][1], npz[2][1];
   int64_t ii[2];
   float ax[2][1] = {{0.f}, {0.f}}, ay[2][1] = {{0.f}, {0.f}}, az[2][1] = {{0.f}, {0.f}};
   for (int o = 0; o < nown; ++o) {
-    ii[o] = t * Tt + threadIdx.x + (int64_t)o * T;
-    const bool own = threadIdx.x + o * T < Tt && ii[o] < N;
+    ii[o] = t * nb_bodies(v) + threadIdx.x + (int64_t)o * T;
+    const bool own = ii[o] < N;
     const float4 pi = own ? pos[ii[o]] : make_float4(0.f, 0.f, 0.f, 0.f);
     npx[o][0] = make_float2(-pi.x, -pi.x);
     npy[o][0] = make_float2(-pi.y, -pi.y);
@@ -544,7 +686,6 @@ __device__ void nbody_tile(const ar_exec_call& k, int v, int64_t t, unsigned cha
     }
     __syncthreads();
     for (int o = 0; o < nown; ++o) {
-      if (threadIdx.x + o * T >= Tt) continue;
       if (uidx == 0)
         tile_accumulate<1, 1>(tile, Tt / 2, npx[o], npy[o], npz[o], eps2v, ax[o], ay[o], az[o]);
       else if (uidx == 1)
@@ -554,7 +695,7 @@ __device__ void nbody_tile(const ar_exec_call& k, int v, int64_t t, unsigned cha
     }
   }
   for (int o = 0; o < nown; ++o)
-    if (threadIdx.x + o * T < Tt && ii[o] < N) acc[ii[o]] = make_float4(ax[o][0], ay[o][0], az[o][0], 0.f);
+    if (ii[o] < N) acc[ii[o]] = make_float4(ax[o][0], ay[o][0], az[o][0], 0.f);
 }
 
 // ------------------------------------------------------------------ run
@@ -573,12 +714,20 @@ __global__ void __launch_bounds__(T, 2) exec_run(const ar_exec_call* __restrict_
   __shared__ int s_c, s_p, s_ok;
   const int E = PM * ncalls;
   const long long total = prefix[E];
+  int pos = 0;  // thread 0: entry of this block's previous item
   for (;;) {
     if (threadIdx.x == 0) {
       const long long it = (long long)atomicAdd(counter, 1ull);
       s_item = it;
       if (it < total) {
-        int lo = 0, hi = E - 1;  // last entry whose range starts at or before it
+        // last entry whose range starts at or before it: this block's items
+        // only grow, so gallop forward from its previous entry, then bisect
+        int lo = pos, step = 1;
+        while (lo + step < E && prefix[lo + step] <= it) {
+          lo += step;
+          step <<= 1;
+        }
+        int hi = min(lo + step, E - 1);
         while (lo < hi) {
           const int mid = (lo + hi + 1) >> 1;
           if (prefix[mid] <= it)
@@ -586,6 +735,7 @@ __global__ void __launch_bounds__(T, 2) exec_run(const ar_exec_call* __restrict_
           else
             hi = mid - 1;
         }
+        pos = lo;
         const int p = lo / ncalls, c = lo % ncalls;
         int ok = 1;
         if (p > 0) {
