@@ -9,6 +9,10 @@ rate.
   python -m paper_2303_08873_b300.run_variant spmv 6 --size 2000000
   python -m paper_2303_08873_b300.run_variant nbody 4 --size 65536
   python -m paper_2303_08873_b300.run_variant daxpy 8 --size 33554432
+
+With ``--exec`` the same call also runs as a one-call batch of the persistent
+mixed-stream executor (``ar_exec_batch``, variant forced) and both rates are
+printed.
 """
 from __future__ import annotations
 
@@ -30,6 +34,7 @@ def main():
     p.add_argument("--reps", type=int, default=3)
     p.add_argument("--zipf", type=float, default=1.5, help="Zipf exponent of the spmv row lengths")
     p.add_argument("--band", type=int, default=0, help="spmv: banded matrix of this (odd) width instead of Zipf")
+    p.add_argument("--exec", action="store_true", help="also time the call through the executor (one-call batch)")
     a = p.parse_args()
     dev = torch.device("cuda", 0)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -37,12 +42,15 @@ def main():
         al, x, y = synth.daxpy_inputs(1, a.size)
         x, y = torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev)
         run = lambda: ar.ar_daxpy(a.variant, a.size, al, x, y)  # noqa: E731
+        call = ar.ArExecCall(loop=0, n=a.size, a=al, in0=x.data_ptr(), out0=y.data_ptr())
         work, unit = 24.0 * a.size, "GB/s"
     elif a.loop == "jacobi7":
         u0 = torch.from_numpy(synth.grid_inputs(1000 + a.size, a.size)).to(dev)
         out, wk = torch.empty_like(u0), torch.empty_like(u0)
         st = torch.zeros(2, dtype=torch.int32, device=dev)
         run = lambda: ar.ar_jacobi7(a.variant, a.size, a.sweeps, u0, out, wk, st)  # noqa: E731
+        call = ar.ArExecCall(loop=1, n=a.size, sweeps=a.sweeps, in0=u0.data_ptr(), out0=out.data_ptr(),
+                             out1=wk.data_ptr())
         work, unit = 16.0 * a.size ** 3 * a.sweeps, "GB/s"
     elif a.loop == "spmv":
         if a.band:
@@ -55,23 +63,43 @@ def main():
         wsb = ar.ar_spmv_workspace_bytes(a.variant, a.size, nnz)
         ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=dev)
         run = lambda: ar.ar_spmv(a.variant, a.size, nnz, rp, c, v, x, y, ws, wsb)  # noqa: E731
+        ews = torch.empty(16 * (-(-(a.size + nnz) // 4096)), dtype=torch.uint8, device=dev)
+        call = ar.ArExecCall(loop=2, n=a.size, nnz=nnz, in0=rp.data_ptr(), in1=c.data_ptr(), in2=v.data_ptr(),
+                             in3=x.data_ptr(), out0=y.data_ptr(), out1=ews.data_ptr(), out1_bytes=ews.numel())
         work, unit = 12.0 * nnz + 4.0 * (a.size + 1) + 16.0 * a.size, "GB/s"
     else:
         pos = torch.from_numpy(synth.nbody_inputs(4, a.size)).to(dev)
         acc = torch.empty_like(pos)
         run = lambda: ar.ar_nbody(a.variant, a.size, pos, acc, synth.NBODY_EPS)  # noqa: E731
+        call = ar.ArExecCall(loop=3, n=a.size, eps=synth.NBODY_EPS, in0=pos.data_ptr(), out0=acc.data_ptr())
         work, unit = 20.0 * a.size ** 2, "GFLOP/s"
-    run()
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(a.reps):
-        run()
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / a.reps
-    print(json.dumps({"loop": a.loop, "variant": a.variant, "name": ar.loop_variant_name(
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(a.reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / a.reps
+
+    ms = timed(run)
+    line = {"loop": a.loop, "variant": a.variant, "name": ar.loop_variant_name(
         ["daxpy", "jacobi7", "spmv", "nbody"].index(a.loop), a.variant), "size": a.size, "ms": ms,
-        "rate": work / (ms * 1e-3) / 1e9, "unit": unit}))
+        "rate": work / (ms * 1e-3) / 1e9, "unit": unit}
+    if a.exec:
+        table = torch.frombuffer(bytearray(ar.exec_table_bytes([call])), dtype=torch.uint8).to(dev)
+        outs = [torch.zeros(1, dtype=torch.int32, device=dev), torch.zeros(1, dtype=torch.float32, device=dev),
+                torch.zeros((1, 8), dtype=torch.float32, device=dev), torch.zeros(1, dtype=torch.int64, device=dev),
+                torch.zeros(1, dtype=torch.int64, device=dev), torch.zeros(1, dtype=torch.int32, device=dev)]
+        wsb = ar.ar_exec_workspace_bytes(1)
+        ews_all = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        force = torch.tensor([a.variant], dtype=torch.int32, device=dev)
+        ems = timed(lambda: ar.ar_exec_batch(table, 1, None, force, *outs, ews_all, wsb))
+        if int(outs[5][0]) != 0:
+            raise SystemExit(f"executor status {int(outs[5][0])}")
+        line.update({"exec_ms": ems, "exec_rate": work / (ems * 1e-3) / 1e9})
+    print(json.dumps(line))
 
 
 if __name__ == "__main__":
