@@ -104,7 +104,11 @@ struct TmaGeom {
   static constexpr int GROUP = PLANE * kDZ;      // elements per box
   static constexpr int RING = kRing * kDZ;       // planes resident
   static constexpr uint32_t BYTES = GROUP * 8u;
-  static constexpr size_t SMEM = (size_t)kRing * BYTES + 128;
+  // a tensor copy's shared-memory destination must be 128-byte aligned: slots
+  // start at multiples of SLOT elements from the 128-byte aligned ring base
+  static constexpr int SLOT = (GROUP + 15) / 16 * 16;
+  static constexpr size_t SMEM = (size_t)kRing * SLOT * 8 + 128;
+  static_assert(SLOT * 8 % 128 == 0, "TMA slots must stay 128-byte aligned");
 };
 
 // Sweep modes of the TMA kernel.  Buffers between the sweeps of one df call
@@ -155,7 +159,7 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
     const int slot = g % kRing;
     const uint32_t bar = smem_addr(&bars[slot]);
     mbar_arrive_expect_tx(bar, G::BYTES);
-    tma_load_3d(smem_addr(buf + (size_t)slot * G::GROUP), src_map, i0 - 2, j0 - 1, kb - 1 + g * kDZ, bar);
+    tma_load_3d(smem_addr(buf + (size_t)slot * G::SLOT), src_map, i0 - 2, j0 - 1, kb - 1 + g * kDZ, bar);
   };
   if (tid == 0)
     for (int g = 0; g < min(ngroups, kRing - 1); ++g) issue(g);
@@ -181,8 +185,8 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
       failed = true;
       break;
     }
-    double* box = buf + (size_t)slot * G::GROUP;
-    const double* prev = buf + (size_t)pslot * G::GROUP;
+    double* box = buf + (size_t)slot * G::SLOT;
+    const double* prev = buf + (size_t)pslot * G::SLOT;
     if (split_boxes) {
       bool marker = false;
       for (int e = tid; e < G::GROUP; e += BX * BY) {
