@@ -38,6 +38,9 @@ TRAIN_SWEEPS = [1, 5, 10, 20]
 BYTES_PER_POINT = 16.0          # one float64 read + one write per point per sweep
 FP64_OPS_PER_POINT = 6          # 5 adds + 1 multiply in the native families
 METRIC = "selected-variant GB/s (or GFLOP/s) vs exhaustive-best & fixed default; regret %"
+# DRAM bytes (read + write, ncu) of one spmv_df_merge_path main launch on the
+# 2e6-row Zipf(1.5) matrix of run_variant (97,990,829 nonzeros)
+SPMV_DF_MP_TRAFFIC_2M = 1200524000.0 + 7646976.0
 FALLBACK_HBM_GBS = 6400.0
 # DRAM bytes (read + write) of one pairs -> pairs sweep of jacobi7_df_32x8 at
 # N = 320 (ncu dram__bytes_read.sum + dram__bytes_write.sum, median of the 8
@@ -496,7 +499,7 @@ def kfold_protocol(table, V, F, epochs, shuffles=10, K=4, seed=77):
 
 
 def spmv_study(n_train, n_test, rows_max, epochs, kfold=False):
-    """Config 3: profile `n_train` seeded matrices (7 variants, 5 reps after a
+    """Config 3: profile `n_train` seeded matrices (8 variants, 5 reps after a
     warm-up, L2 flushed), train the MLP selector on the device and the depth-2
     tree on the same records, then compare their choices with the exhaustive
     argmin and the fixed default (thread per row) on `n_test` held-out
@@ -591,6 +594,18 @@ def spmv_study(n_train, n_test, rows_max, epochs, kfold=False):
         "cost": {"profiling_wall_s": t_prof, "profiling_gpu_ms": prof_ms, "train_mlp_s": t_mlp,
                  "train_records": len(mlp.records())},
     }
+    hbm_peak, peak_src = peaks()
+    # the variant most often fastest on the test set, and its DRAM bytes per
+    # launch on the 2e6-row Zipf(1.5) matrix from one ncu capture (1.2005 GB
+    # read + 7.6 MB written against 1.216 GB algorithmic)
+    dom = max(range(V), key=lambda v: sum(1 for p in per if p["best"] == v))
+    line["roofline"] = {"bound": "hbm", "achieved": res["mlp"]["gbs"], "peak": hbm_peak, "unit": "GB/s",
+                        "frac": res["mlp"]["gbs"] / hbm_peak, "peak_source": peak_src,
+                        "traffic": SPMV_DF_MP_TRAFFIC_2M if names[dom] == "spmv_df_merge_path" else None,
+                        "kernel": names[dom],
+                        "note": "achieved: the MLP-selected variants over the test matrices (sum of algorithmic "
+                                "bytes / sum of times); traffic: DRAM bytes of one launch of the dominant kernel "
+                                "on the 2e6-row Zipf(1.5) matrix"}
     if kfold:
         t2 = time.perf_counter()
         line["kfold_mean_regret_pct"] = kfold_protocol(table, V, 5, epochs)
@@ -841,6 +856,18 @@ def run_mixed(args):
                                       (chosen[q] for q in samp[:24]))
     learned = prof_ns * 1e-6 + len(low) * line["cost"]["fallback_profile_gpu_ms_per_call"]
     line["cost"]["profiling_cost_ratio"] = learned / (exh_per_call_ms * args.calls)
+    # both rates are over the same wall time: the stream's share of the machine
+    # is the sum of the two roofline fractions
+    hbm_peak, peak_src = peaks()
+    _, fp32_fma = ar.ar_measure_fma_rates()
+    fp32_roof = fp32_fma / 12.0 * NBODY_FLOPS / 1e9
+    mem_frac = line["value"] / hbm_peak
+    nb_frac = line["stream"]["nbody_gflops"] / fp32_roof
+    line["roofline"] = {"bound": "hbm", "achieved": line["value"], "peak": hbm_peak, "unit": "GB/s", "frac": mem_frac,
+                        "peak_source": peak_src, "traffic": None, "kernel": "exec_run (all loops in one launch)",
+                        "nbody": {"achieved_gflops": line["stream"]["nbody_gflops"], "peak_gflops": fp32_roof,
+                                  "frac": nb_frac},
+                        "machine_frac": mem_frac + nb_frac}
     print(json.dumps(line), flush=True)
 
 
