@@ -129,6 +129,35 @@ def test_every_variant_of_every_loop_in_one_batch():
     assert r["features"][0][0] == 100003 and tuple(r["features"][15][:2]) == (50.0, 3.0)
 
 
+def test_edge_sizes_of_every_loop_in_one_batch():
+    """Sizes at and just past the executor's tile edges (daxpy 16384-element
+    tiles, Jacobi 32-plane tiles and the even-N plane ring, SpMV row groups and
+    4096-item merge-path blocks, n-body 256/512-body tiles), and the degenerate
+    ones (one element, one unknown, one row, one body), every loop and family."""
+    b = Batch()
+    force = []
+    for n, v in [(1, 0), (2, 13), (3, 14), (16383, 1), (16385, 2), (32769, 7), (49152, 5)]:
+        b.daxpy(n, 200 + n % 97)
+        force.append(v)
+    for N, sweeps, v in [(1, 1, 1), (1, 3, 13), (2, 2, 13), (2, 1, 9), (3, 3, 15), (4, 2, 5), (6, 3, 14), (9, 2, 12),
+                         (34, 3, 13), (33, 2, 13), (64, 1, 0), (65, 2, 3)]:
+        b.jacobi(N, sweeps, 300 + N, None)
+        force.append(v)
+    tiny = synth.csr_zipf(11, 1, 1.5)
+    small = synth.csr_zipf(12, 4099, 1.5)
+    band = synth.csr_band(13, 5, 3)
+    for k, v in enumerate(range(8)):
+        b.spmv([tiny, small, band][k % 3], 400 + k)
+        force.append(v)
+    for N, v in [(1, 0), (2, 3), (3, 6), (129, 1), (257, 4), (513, 8), (255, 7)]:
+        b.nbody(N, 500 + N)
+        force.append(v)
+    r = b.run(force=force)
+    assert np.all(r["status"] == 0)
+    for k, ok in enumerate(b.check):
+        assert ok(), (k, b.calls[k].loop, force[k])
+
+
 def test_float_pair_chain_with_and_without_range_flag():
     """The float-pair Jacobi variants keep pairs between sweeps (float64 in,
     float64 out) and redo the call in float64 from the second phase on when an
