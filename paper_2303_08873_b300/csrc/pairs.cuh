@@ -1,5 +1,5 @@
-// Float-pair arithmetic shared by the Jacobi kernels and the mixed-stream
-// executor (internal).  A float64 value x is carried as an unevaluated pair
+// Float-pair arithmetic shared by the Jacobi kernels, the float-pair SpMV
+// merge path and the mixed-stream executor (internal).  A float64 value x is carried as an unevaluated pair
 // of floats (hi, lo) with x = hi + lo to ~2^-48 relative; conversions use
 // integer bit operations only, because float64<->float32 conversion
 // instructions issue on B300's slow float64 pipe.
@@ -125,14 +125,5 @@ __device__ __forceinline__ void pair_add(float& S, float& C, float p, float pe) 
   S = s + e;
   C = e - (S - s);
 }
-
-// A float64 value the float-pair path cannot carry to later sweeps.
-__device__ __forceinline__ bool outside_pair_range(double v) {
-  const long long b = __double_as_longlong(v);
-  if ((b << 1) == 0) return false;
-  const int e = (int)((b >> 52) & 0x7ff);
-  return e < 949 || e > 1140;
-}
-
 
 }  // namespace ar
