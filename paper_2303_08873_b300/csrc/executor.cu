@@ -15,6 +15,8 @@
 #include "merge_path.cuh"
 #include "nbody_math.cuh"
 #include "pairs.cuh"
+#include "jacobi_ring.cuh"
+#include "tma.cuh"
 
 namespace ar {
 namespace {
@@ -318,19 +320,6 @@ __device__ __forceinline__ double atcg(const double* __restrict__ u, int N, int 
   return __ldcg(u + ((int64_t)k * N + j) * N + i);
 }
 
-// Asynchronous 16-byte global -> shared copies (cp.async, L1 bypassed, so
-// data written earlier in the same launch by other SMs is seen); src_bytes 0
-// fills zeros.
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-               "l"(src), "r"(src_bytes)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int G>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(G) : "memory");
-}
 
 // One BX x BY x 16-plane tile of one sweep, 2.5D: an xy tile with halo in
 // shared memory (double buffered), z neighbours in registers.  Values are
@@ -338,103 +327,6 @@ __device__ __forceinline__ void cp_async_wait() {
 // selects float-pair arithmetic.  With float64 input and float-pair
 // arithmetic, inputs outside the pair range mark the point: it is redone in
 // float64 (dst float64) or, when dst holds pairs, reported through *flag.
-// Even N: planes kb-1 .. ke of the tile's column, x from i0-2 (16-byte
-// aligned) to i0+BX+1 and y from j0-1 to j0+BY, stream through a ring of
-// kRingPlanes shared-memory slots by cp.async, up to kRingPlanes-3 planes
-// ahead of the plane being computed; every value is loaded once per tile and
-// the z neighbours come from the ring.  Float-pair modes with float64 input
-// split each landed chunk in place (its copier does, after its own wait).
-constexpr int kRingPlanes = 8;
-__device__ void jacobi_ring_tile(int N, int BX, int BY, int bx, int by, int kb, int ke, const double* src, double* dst,
-                                 bool pair_math, bool src_pairs, bool dst_pairs, int* flag, unsigned char* smraw) {
-  const int i0 = bx * BX, j0 = by * BY;
-  const int PX = BX + 4, PL = PX * (BY + 2);
-  const int chunks_row = PX / 2, nchunk = chunks_row * (BY + 2);
-  double* ring = reinterpret_cast<double*>(smraw);
-  const bool active = threadIdx.x < BX * BY;
-  const int lx = threadIdx.x % BX, ly = threadIdx.x / BX;
-  const int i = i0 + lx, j = j0 + ly;
-  const bool inside = active && i < N && j < N;
-  const int64_t NN = (int64_t)N * N, col = (int64_t)j * N + i;
-  const int cidx = (ly + 1) * PX + lx + 2;
-  const bool split = pair_math && !src_pairs;
-  bool marker = false;
-  // plane kp (kb-1 <= kp) lives in slot (kp - kb + 1) % kRingPlanes
-  auto slot_of = [&](int kp) { return (kp - kb + 1) % kRingPlanes; };
-  auto issue = [&](int kp) {
-    if (kp <= ke) {
-      double* base = ring + slot_of(kp) * PL;
-      for (int c = threadIdx.x; c < nchunk; c += T) {
-        const int row = c / chunks_row, cx = c - row * chunks_row;
-        const int gy = j0 - 1 + row, gx = i0 - 2 + 2 * cx;  // gx even and N even: gx + 1 < N when gx < N
-        const bool in = kp >= 0 && kp < N && gy >= 0 && gy < N && gx >= 0 && gx < N;
-        cp_async16(base + row * PX + 2 * cx, in ? src + ((int64_t)kp * N + gy) * N + gx : src, in ? 16 : 0);
-      }
-    }
-    cp_async_commit();  // one group per plane, empty past ke, so the wait counts stay fixed
-  };
-  auto split_own = [&](int kp) {
-    double* base = ring + slot_of(kp) * PL;
-    for (int c = threadIdx.x; c < nchunk; c += T) {
-      const int row = c / chunks_row, cx = c - row * chunks_row;
-      double* e = base + row * PX + 2 * cx;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const float2 f = df_split(e[h]);
-        marker |= (f.x != f.x);
-        reinterpret_cast<float2*>(e)[h] = f;
-      }
-    }
-  };
-  for (int q = 0; q < kRingPlanes - 1; ++q) issue(kb - 1 + q);
-  for (int kk = kb; kk < ke; ++kk) {
-    cp_async_wait<kRingPlanes - 4>();  // planes up to kk + 1 have landed (this thread's copies)
-    if (split) {
-      if (kk == kb) {
-        split_own(kb - 1);
-        split_own(kb);
-      }
-      split_own(kk + 1);
-    }
-    __syncthreads();
-    issue(kk + kRingPlanes - 2);  // into the slot of plane kk - 2, read last in the previous step
-    const int sb = slot_of(kk - 1) * PL, sc = slot_of(kk) * PL, sa = slot_of(kk + 1) * PL;
-    if (inside) {
-      if (!pair_math) {
-        const double* r = ring;
-        double s = r[sc + cidx - 1] + r[sc + cidx + 1];
-        s += r[sc + cidx - PX];
-        s += r[sc + cidx + PX];
-        s += r[sb + cidx];
-        s += r[sa + cidx];
-        dst[kk * NN + col] = s * kSixth;
-      } else {
-        const float2* r = reinterpret_cast<const float2*>(ring);
-        const float2 res =
-            df_avg6(r[sc + cidx - 1], r[sc + cidx + 1], r[sc + cidx - PX], r[sc + cidx + PX], r[sb + cidx], r[sa + cidx]);
-        if (dst_pairs) {
-          reinterpret_cast<float2*>(dst)[kk * NN + col] = res;
-        } else {
-          double dv = pair_to_double(res);
-          if (split && (__double_as_longlong(dv) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) {
-            // an input outside the float-pair range: redo this point in float64
-            double sd = atcg(src, N, i - 1, j, kk) + atcg(src, N, i + 1, j, kk);
-            sd += atcg(src, N, i, j - 1, kk);
-            sd += atcg(src, N, i, j + 1, kk);
-            sd += atcg(src, N, i, j, kk - 1);
-            sd += atcg(src, N, i, j, kk + 1);
-            dv = sd * kSixth;
-          }
-          dst[kk * NN + col] = dv;
-        }
-      }
-    }
-  }
-  cp_async_wait<0>();  // no copy may land after the tile: the next item reuses the ring
-  __syncthreads();
-  if (dst_pairs && marker && flag) atomicOr(flag, 1);
-}
-
 __device__ void jacobi_sweep_tile(const ar_exec_call& k, int v, int64_t t, const double* src, double* dst,
                                   bool pair_math, bool src_pairs, bool dst_pairs, int* flag, unsigned char* smraw) {
   const int N = (int)k.n;
@@ -459,10 +351,11 @@ __device__ void jacobi_sweep_tile(const ar_exec_call& k, int v, int64_t t, const
     }
     return;
   }
-  if (!(N & 1)) {
+  if (((uintptr_t)src | (uintptr_t)dst) % 16 == 0) {
     jacobi_ring_tile(N, BX, BY, bx, by, kb, ke, src, dst, pair_math, src_pairs, dst_pairs, flag, smraw);
     return;
   }
+  // buffers not 16-byte aligned: global loads, those of 4 planes issued together
   const int PXs = BX + 2, PL = PXs * (BY + 2);
   const int cidx = (ly + 1) * PXs + lx + 1;
   // halo role: the x-edge threads load the x halo, the y-edge threads the y

@@ -29,6 +29,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "jacobi_ring.cuh"
 #include "pairs.cuh"
 #include "tma.cuh"
 
@@ -124,6 +125,8 @@ struct TmaGeom {
 //             out_alt, so the flagged chain ends one launch late (see the
 //             catch-up kernel)
 enum Mode { M_NATIVE = 0, M_DD = 1, M_DP = 2, M_PP = 3, M_PD = 4 };
+// How a tma / df sweep stages its planes.
+enum Staging { kStageSmem = 0, kStageTma = 1, kStageRing = 2 };
 
 template <int BX, int BY, int MODE>
 __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUtensorMap tmap,
@@ -287,6 +290,28 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
   }
 }
 
+// ------------------------------------------------------------------ cp.async ring
+// The df family when tensor copies cannot be used (odd N): each block streams
+// its column's planes through a shared-memory ring (jacobi_ring.cuh), in the
+// same sweep modes as jacobi_tma.
+template <int BX, int BY, int MODE>
+__global__ void __launch_bounds__(BX* BY) jacobi_ring(int N, int KC, const double* __restrict__ in, void* outv,
+                                                      const double* __restrict__ in_alt, double* out_alt, int* flag) {
+  extern __shared__ __align__(16) unsigned char ring_smem[];
+  const int kb = blockIdx.z * KC, ke = min(N, kb + KC);
+  // block-uniform: the flag was settled by an earlier launch on this stream
+  const bool flagged = (MODE == M_PP || MODE == M_PD) && flag != nullptr && *flag != 0;
+  if (flagged) {  // the previous sweep in float64, from the float64 data
+    jacobi_ring_tile(N, BX, BY, blockIdx.x, blockIdx.y, kb, ke, in_alt, out_alt, false, false, false, nullptr,
+                     ring_smem);
+    return;
+  }
+  constexpr bool src_pairs = MODE == M_PP || MODE == M_PD;
+  constexpr bool dst_pairs = MODE == M_DP || MODE == M_PP;
+  jacobi_ring_tile(N, BX, BY, blockIdx.x, blockIdx.y, kb, ke, in, static_cast<double*>(outv), MODE != M_NATIVE,
+                   src_pairs, dst_pairs, MODE == M_DP ? flag : nullptr, ring_smem);
+}
+
 // ------------------------------------------------------------------ host side
 template <int BX, int BY>
 int launch_naive(int N, const double* in, double* out, cudaStream_t s) {
@@ -366,11 +391,33 @@ int launch_tma(int N, const double* in, void* out, const double* in_alt, double*
   return launch_status();
 }
 
+template <int BX, int BY, int MODE>
+int launch_ring(int N, const double* in, void* out, const double* in_alt, double* out_alt, int* flag,
+                cudaStream_t s) {
+  constexpr int smem = ring_smem_bytes(BX, BY);
+  static_assert(smem <= 48 * 1024, "ring fits the default dynamic shared memory");
+  const int64_t cb = ceil_div(N, BX) * ceil_div(N, BY);
+  int resident = (227 * 1024) / smem;
+  if (resident > 2048 / (BX * BY)) resident = 2048 / (BX * BY);
+  const int KC = chunk_planes(N, cb, resident, 8, 64);
+  dim3 grid((unsigned)ceil_div(N, BX), (unsigned)ceil_div(N, BY), (unsigned)ceil_div(N, KC));
+  jacobi_ring<BX, BY, MODE><<<grid, BX * BY, smem, s>>>(N, KC, in, out, in_alt, out_alt, flag);
+  return launch_status();
+}
+
 template <int BX, int BY>
-int launch_family(int fam, int mode, bool tma, int N, const double* in, double* out, const double* in_alt,
+int launch_family(int fam, int mode, int staging, int N, const double* in, double* out, const double* in_alt,
                   double* out_alt, int* status, int* flag, cudaStream_t s) {
   if (fam == 0) return launch_naive<BX, BY>(N, in, out, s);
-  if (fam == 1 || !tma) return launch_smem<BX, BY>(N, in, out, s);
+  if (fam == 3 && staging == kStageRing) {
+    switch (mode) {
+      case M_DD: return launch_ring<BX, BY, M_DD>(N, in, out, nullptr, nullptr, nullptr, s);
+      case M_DP: return launch_ring<BX, BY, M_DP>(N, in, out, nullptr, nullptr, flag, s);
+      case M_PP: return launch_ring<BX, BY, M_PP>(N, in, out, in_alt, out_alt, flag, s);
+      default: return launch_ring<BX, BY, M_PD>(N, in, out, in_alt, out_alt, flag, s);
+    }
+  }
+  if (fam == 1 || staging != kStageTma) return launch_smem<BX, BY>(N, in, out, s);
   switch (mode) {
     case M_NATIVE: return launch_tma<BX, BY, M_NATIVE>(N, in, out, nullptr, nullptr, status, nullptr, s);
     case M_DD: return launch_tma<BX, BY, M_DD>(N, in, out, nullptr, nullptr, status, nullptr, s);
@@ -380,14 +427,14 @@ int launch_family(int fam, int mode, bool tma, int N, const double* in, double* 
   }
 }
 
-int sweep(int variant, int mode, bool tma, int N, const double* in, double* out, const double* in_alt,
+int sweep(int variant, int mode, int staging, int N, const double* in, double* out, const double* in_alt,
           double* out_alt, int* status, int* flag, cudaStream_t s) {
   const int fam = variant / 4;
   switch (variant % 4) {
-    case 0: return launch_family<32, 4>(fam, mode, tma, N, in, out, in_alt, out_alt, status, flag, s);
-    case 1: return launch_family<32, 8>(fam, mode, tma, N, in, out, in_alt, out_alt, status, flag, s);
-    case 2: return launch_family<64, 4>(fam, mode, tma, N, in, out, in_alt, out_alt, status, flag, s);
-    default: return launch_family<128, 2>(fam, mode, tma, N, in, out, in_alt, out_alt, status, flag, s);
+    case 0: return launch_family<32, 4>(fam, mode, staging, N, in, out, in_alt, out_alt, status, flag, s);
+    case 1: return launch_family<32, 8>(fam, mode, staging, N, in, out, in_alt, out_alt, status, flag, s);
+    case 2: return launch_family<64, 4>(fam, mode, staging, N, in, out, in_alt, out_alt, status, flag, s);
+    default: return launch_family<128, 2>(fam, mode, staging, N, in, out, in_alt, out_alt, status, flag, s);
   }
 }
 
@@ -447,13 +494,21 @@ extern "C" int ar_jacobi7(int variant, int N, int sweeps, const double* u0, doub
                : AR_ERR_CUDA;
   }
   const int fam = variant / 4;
-  const bool tma = fam >= 2 && tma_usable(variant % 4, N, u0, out, sweeps > 1 ? work : nullptr);
+  // tma and df stage planes by tensor copies when the grid allows it; the df
+  // family otherwise (odd N) streams them by cp.async; 16-byte aligned
+  // buffers are needed either way, else the shared-memory tile runs
+  const double* w = sweeps > 1 ? work : nullptr;
+  const int staging = fam < 2                                ? kStageSmem
+                      : tma_usable(variant % 4, N, u0, out, w) ? kStageTma
+                      : (fam == 3 && aligned16(u0) && aligned16(out) && (!w || aligned16(w))) ? kStageRing
+                                                                                               : kStageSmem;
+  const bool staged = staging != kStageSmem;
   auto dst_of = [&](int j) -> double* { return ((sweeps - 1 - j) % 2 == 0) ? out : work; };
   // df calls of 2+ sweeps keep float pairs between sweeps; status[1] records
   // whether the first sweep met an input outside the float-pair range, in
   // which case every later launch computes the previous sweep in float64 from
   // the float64 data and a final catch-up launch computes the last one
-  int* flag = (fam == 3 && tma && sweeps >= 2 && status) ? status + 1 : nullptr;
+  int* flag = (fam == 3 && staged && sweeps >= 2 && status) ? status + 1 : nullptr;
   if (flag && cudaMemsetAsync(flag, 0, sizeof(int), s) != cudaSuccess) return AR_ERR_CUDA;
   for (int sw = 0; sw < sweeps; ++sw) {
     const double* src = sw == 0 ? u0 : dst_of(sw - 1);
@@ -472,7 +527,7 @@ extern "C" int ar_jacobi7(int variant, int N, int sweeps, const double* u0, doub
         alt_dst = dst_of(sw - 1);
       }
     }
-    const int rc = sweep(variant, mode, tma, N, src, dst, alt_src, alt_dst, status, flag, s);
+    const int rc = sweep(variant, mode, staging, N, src, dst, alt_src, alt_dst, status, flag, s);
     if (rc != AR_OK) return rc;
   }
   if (flag) {

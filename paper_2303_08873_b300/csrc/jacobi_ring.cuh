@@ -1,0 +1,179 @@
+// One Jacobi sweep over a BX x BY x (ke - kb) tile whose planes stream through
+// a ring of shared-memory slots by 16-byte cp.async (internal): used by the
+// stand-alone float-pair kernel when tensor copies cannot be used (odd N:
+// rows are not 16-byte aligned) and by every Jacobi tile of the mixed-stream
+// executor.
+//
+// Slot rows hold x from i0 - 2 - o to i0 + BX + 1 - o in 16-byte chunks that
+// start at an even element index of the flat N^3 array; o = 0 for even N and
+// o = (k + y) & 1 for odd N (the parity of row (k, y)'s first element), so
+// element x of row (k, y) sits at column x - i0 + 2 + o.  A chunk half
+// outside the grid reads as zero: chunks wholly outside are zero-filled by
+// the copy, a chunk whose upper half lies past the row's end copies 8 bytes,
+// and a chunk whose lower half lies before the row's start (only possible
+// when o = 1, so that half is the previous row's last element, in bounds) is
+// copied whole and that half zeroed by its copier after landing.  Float-pair
+// sweeps with float64 input split every landed chunk in place the same way.
+// Every value is loaded once per tile; the z neighbours come from the ring.
+#pragma once
+
+#include "common.cuh"
+#include "pairs.cuh"
+#include "tma.cuh"
+
+namespace ar {
+
+constexpr int kRingPlanes = 8;
+constexpr int kRingChunks = 2;  // 16-byte chunks per thread and plane, at most (nchunk <= 2 * threads)
+
+// Shared memory of the ring for a BX x BY tile.
+__host__ __device__ constexpr int ring_smem_bytes(int BX, int BY) { return kRingPlanes * (BX + 4) * (BY + 2) * 8; }
+
+// src: float64 (pair_math false, or src_pairs false) or float pairs; dst:
+// float pairs if dst_pairs, else float64.  Threads: blockDim.x >= BX * BY
+// and 2 * blockDim.x >= (BX + 4) (BY + 2) / 2 (the chunks of one plane).
+// A float-pair sweep with float64 input and float64 output redoes in float64
+// every point whose inputs lie outside the float-pair range; with pairs out,
+// such inputs set *flag instead.  Buffers 16-byte aligned.
+__device__ __forceinline__ void jacobi_ring_tile(int N, int BX, int BY, int bx, int by, int kb, int ke,
+                                                 const double* src, double* dst, bool pair_math, bool src_pairs,
+                                                 bool dst_pairs, int* flag, unsigned char* smraw) {
+  const int nthr = blockDim.x;
+  const int i0 = bx * BX, j0 = by * BY;
+  const int PX = BX + 4, PL = PX * (BY + 2);
+  const int chunks_row = PX / 2, nchunk = chunks_row * (BY + 2);
+  double* ring = reinterpret_cast<double*>(smraw);
+  const bool active = threadIdx.x < BX * BY;
+  const int lx = threadIdx.x % BX, ly = threadIdx.x / BX;
+  const int i = i0 + lx, j = j0 + ly;
+  const bool inside = active && i < N && j < N;
+  const int64_t NN = (int64_t)N * N, col = (int64_t)j * N + i;
+  const bool odd = N & 1;
+  const bool split = pair_math && !src_pairs;
+  bool marker = false;
+  auto offset = [&](int kp, int y) { return odd ? ((kp + y) & 1) : 0; };
+  // plane kp (kb-1 <= kp) lives in slot (kp - kb + 1) % kRingPlanes
+  auto slot_of = [&](int kp) { return (kp - kb + 1) % kRingPlanes; };
+  // this thread's chunks (at most kRingChunks): row and column in the slot
+  int crow[kRingChunks], ccx[kRingChunks];
+  int nmine = 0;
+#pragma unroll
+  for (int m = 0; m < kRingChunks; ++m) {
+    const int c = threadIdx.x + m * nthr;
+    crow[m] = c / chunks_row;
+    ccx[m] = c - crow[m] * chunks_row;
+    if (c < nchunk) nmine = m + 1;
+  }
+  // chunk m of plane kp: its slot position and which halves hold grid values
+  auto chunk = [&](int kp, int m, double*& e, bool& v0, bool& v1, int64_t& L) {
+    const int row = crow[m], cx = ccx[m];
+    const int y = j0 - 1 + row;
+    const int x0 = i0 - 2 - offset(kp, y) + 2 * cx;
+    const bool rowin = kp >= 0 && kp < N && y >= 0 && y < N;
+    v0 = rowin && x0 >= 0 && x0 < N;
+    v1 = rowin && x0 + 1 >= 0 && x0 + 1 < N;
+    L = ((int64_t)kp * N + y) * N + x0;  // even
+    e = ring + slot_of(kp) * PL + row * PX + 2 * cx;
+  };
+  auto issue = [&](int kp) {
+    if (kp <= ke) {
+#pragma unroll
+      for (int m = 0; m < kRingChunks; ++m) {
+        if (m < nmine) {
+          double* e;
+          bool v0, v1;
+          int64_t L;
+          chunk(kp, m, e, v0, v1, L);
+          const int bytes = v1 ? 16 : (v0 ? 8 : 0);
+          cp_async16(e, bytes ? src + L : src, bytes);
+        }
+      }
+    }
+    cp_async_commit();  // one group per plane, empty past ke, so the wait counts stay fixed
+  };
+  // after this thread's copies of plane kp have landed: zero a copied half
+  // that lies before its row's start (odd N: only chunk column 1 of the first
+  // tile column, x0 = -1 when o = 1); split float64 values into pairs
+  const bool may_zero = odd && i0 == 0;
+  auto post = [&](int kp) {
+#pragma unroll
+    for (int m = 0; m < kRingChunks; ++m) {
+      if (m < nmine && (split || (may_zero && ccx[m] == 1))) {
+        double* e;
+        bool v0, v1;
+        int64_t L;
+        chunk(kp, m, e, v0, v1, L);
+        if (!v0 && v1) e[0] = 0.0;
+        if (split) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const float2 f = df_split(e[h]);
+            marker |= (f.x != f.x);
+            reinterpret_cast<float2*>(e)[h] = f;
+          }
+        }
+      }
+    }
+  };
+  const bool need_post = split || may_zero;
+  for (int q = 0; q < kRingPlanes - 1; ++q) issue(kb - 1 + q);
+  for (int kk = kb; kk < ke; ++kk) {
+    cp_async_wait<kRingPlanes - 4>();  // planes up to kk + 1 have landed (this thread's copies)
+    if (need_post) {
+      if (kk == kb) {
+        post(kb - 1);
+        post(kb);
+      }
+      post(kk + 1);
+    }
+    __syncthreads();
+    issue(kk + kRingPlanes - 2);  // into the slot of plane kk - 2, read last in the previous step
+    if (inside) {
+      // odd N: the neighbour rows (y +- 1 and planes k +- 1) have the other parity
+      const int o = offset(kk, j), on = odd ? 1 - o : 0;
+      const int rc = (ly + 1) * PX + lx + 2;
+      const int c0 = slot_of(kk) * PL + rc + o;
+      const int cs = slot_of(kk) * PL + rc - PX + on;
+      const int cn = slot_of(kk) * PL + rc + PX + on;
+      const int cb = slot_of(kk - 1) * PL + rc + on;
+      const int ca = slot_of(kk + 1) * PL + rc + on;
+      if (!pair_math) {
+        const double* r = ring;
+        double s = r[c0 - 1] + r[c0 + 1];
+        s += r[cs];
+        s += r[cn];
+        s += r[cb];
+        s += r[ca];
+        dst[kk * NN + col] = s * kSixth;
+      } else {
+        const float2* r = reinterpret_cast<const float2*>(ring);
+        const float2 res = df_avg6(r[c0 - 1], r[c0 + 1], r[cs], r[cn], r[cb], r[ca]);
+        if (dst_pairs) {
+          reinterpret_cast<float2*>(dst)[kk * NN + col] = res;
+        } else {
+          double dv = pair_to_double(res);
+          if (split && (__double_as_longlong(dv) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) {
+            // an input outside the float-pair range: redo this point in float64
+            // (L1-bypassing loads: src may have been written earlier in this launch)
+            auto g = [&](int ii, int jj, int kq) {
+              return ((unsigned)ii < (unsigned)N && (unsigned)jj < (unsigned)N && (unsigned)kq < (unsigned)N)
+                         ? __ldcg(src + ((int64_t)kq * N + jj) * N + ii)
+                         : 0.0;
+            };
+            double sd = g(i - 1, j, kk) + g(i + 1, j, kk);
+            sd += g(i, j - 1, kk);
+            sd += g(i, j + 1, kk);
+            sd += g(i, j, kk - 1);
+            sd += g(i, j, kk + 1);
+            dv = sd * kSixth;
+          }
+          dst[kk * NN + col] = dv;
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();  // no copy may land after the tile: the caller reuses the shared memory
+  if (__syncthreads_or(dst_pairs && marker) && threadIdx.x == 0 && flag) atomicOr(flag, 1);
+}
+
+}  // namespace ar

@@ -65,6 +65,21 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// Asynchronous 16-byte global -> shared copy (cp.async, L1 bypassed, so data
+// written earlier in the same launch by other SMs is seen): src_bytes (0, 8
+// or 16) are read, the rest of the 16 bytes is zero-filled.  Both addresses
+// 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int G>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(G) : "memory");
+}
+
 // Host: encode a 3D float64 tensor map over a dense (d2, d1, d0) array with
 // d0 fastest.  Returns false if the driver entry point is missing or the
 // encode call rejects the arguments.
