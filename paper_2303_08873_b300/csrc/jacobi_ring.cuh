@@ -47,63 +47,65 @@ __device__ __forceinline__ void jacobi_ring_tile(int N, int BX, int BY, int bx, 
   const int lx = threadIdx.x % BX, ly = threadIdx.x / BX;
   const int i = i0 + lx, j = j0 + ly;
   const bool inside = active && i < N && j < N;
-  const int64_t NN = (int64_t)N * N, col = (int64_t)j * N + i;
+  const int64_t NN = (int64_t)N * N;
   const bool odd = N & 1;
   const bool split = pair_math && !src_pairs;
+  const bool may_zero = odd && i0 == 0;
   bool marker = false;
-  auto offset = [&](int kp, int y) { return odd ? ((kp + y) & 1) : 0; };
-  // plane kp (kb-1 <= kp) lives in slot (kp - kb + 1) % kRingPlanes
-  auto slot_of = [&](int kp) { return (kp - kb + 1) % kRingPlanes; };
-  // this thread's chunks (at most kRingChunks): row and column in the slot
-  int crow[kRingChunks], ccx[kRingChunks];
+  // This thread's chunks (at most kRingChunks), fixed for the tile: slot
+  // offset, row y, and for each row parity o the flat offset y*N + x0 and the
+  // bytes to copy (16, 8 or 0 by which halves lie inside the row).
+  // (per parity: suffix 0 / 1; selected by value, not by index, so the
+  // arrays stay in registers)
+  int soff[kRingChunks], cy[kRingChunks], cb0[kRingChunks], cb1[kRingChunks];
+  bool z0[kRingChunks], z1[kRingChunks];  // a copied lower half to zero (x0 = -1)
+  int64_t cxy0[kRingChunks];              // y*N + x0 for parity 0; parity 1 is one less
   int nmine = 0;
 #pragma unroll
   for (int m = 0; m < kRingChunks; ++m) {
     const int c = threadIdx.x + m * nthr;
-    crow[m] = c / chunks_row;
-    ccx[m] = c - crow[m] * chunks_row;
+    const int row = c / chunks_row, cx = c - row * chunks_row;
     if (c < nchunk) nmine = m + 1;
-  }
-  // chunk m of plane kp: its slot position and which halves hold grid values
-  auto chunk = [&](int kp, int m, double*& e, bool& v0, bool& v1, int64_t& L) {
-    const int row = crow[m], cx = ccx[m];
+    soff[m] = row * PX + 2 * cx;
     const int y = j0 - 1 + row;
-    const int x0 = i0 - 2 - offset(kp, y) + 2 * cx;
-    const bool rowin = kp >= 0 && kp < N && y >= 0 && y < N;
-    v0 = rowin && x0 >= 0 && x0 < N;
-    v1 = rowin && x0 + 1 >= 0 && x0 + 1 < N;
-    L = ((int64_t)kp * N + y) * N + x0;  // even
-    e = ring + slot_of(kp) * PL + row * PX + 2 * cx;
-  };
+    cy[m] = y;
+    const bool yin = y >= 0 && y < N;
+    const int x0 = i0 - 2 + 2 * cx;  // parity 0; parity 1 starts one element earlier
+    const bool a0 = yin && x0 >= 0 && x0 < N, a1 = yin && x0 + 1 >= 0 && x0 + 1 < N;
+    const bool b0 = yin && x0 - 1 >= 0 && x0 - 1 < N;  // parity 1: halves x0 - 1, x0
+    cb0[m] = a1 ? 16 : (a0 ? 8 : 0);
+    cb1[m] = a0 ? 16 : (b0 ? 8 : 0);
+    z0[m] = !a0 && a1;
+    z1[m] = !b0 && a0;
+    cxy0[m] = (int64_t)y * N + x0;  // + kp * N^2
+  }
+  // plane kp (kb-1 <= kp) lives in slot (kp - kb + 1) % kRingPlanes
+  auto slot_of = [&](int kp) { return (kp - kb + 1) % kRingPlanes; };
   auto issue = [&](int kp) {
     if (kp <= ke) {
+      const bool kin = kp >= 0 && kp < N;
+      double* base = ring + slot_of(kp) * PL;
 #pragma unroll
       for (int m = 0; m < kRingChunks; ++m) {
         if (m < nmine) {
-          double* e;
-          bool v0, v1;
-          int64_t L;
-          chunk(kp, m, e, v0, v1, L);
-          const int bytes = v1 ? 16 : (v0 ? 8 : 0);
-          cp_async16(e, bytes ? src + L : src, bytes);
+          const bool o = odd && ((kp + cy[m]) & 1);
+          const int bytes = kin ? (o ? cb1[m] : cb0[m]) : 0;
+          cp_async16(base + soff[m], bytes ? src + (int64_t)kp * NN + cxy0[m] - (o ? 1 : 0) : src, bytes);
         }
       }
     }
     cp_async_commit();  // one group per plane, empty past ke, so the wait counts stay fixed
   };
   // after this thread's copies of plane kp have landed: zero a copied half
-  // that lies before its row's start (odd N: only chunk column 1 of the first
-  // tile column, x0 = -1 when o = 1); split float64 values into pairs
-  const bool may_zero = odd && i0 == 0;
+  // that lies before its row's start; split float64 values into pairs
   auto post = [&](int kp) {
+    const bool kin = kp >= 0 && kp < N;
+    double* base = ring + slot_of(kp) * PL;
 #pragma unroll
     for (int m = 0; m < kRingChunks; ++m) {
-      if (m < nmine && (split || (may_zero && ccx[m] == 1))) {
-        double* e;
-        bool v0, v1;
-        int64_t L;
-        chunk(kp, m, e, v0, v1, L);
-        if (!v0 && v1) e[0] = 0.0;
+      if (m < nmine) {
+        double* e = base + soff[m];
+        if (may_zero && kin && (((kp + cy[m]) & 1) ? z1[m] : z0[m])) e[0] = 0.0;
         if (split) {
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
@@ -117,6 +119,12 @@ __device__ __forceinline__ void jacobi_ring_tile(int N, int BX, int BY, int bx, 
   };
   const bool need_post = split || may_zero;
   for (int q = 0; q < kRingPlanes - 1; ++q) issue(kb - 1 + q);
+  // running state of the compute: slots of planes kk-1, kk, kk+1, this row's
+  // parity at plane kk, and the output offset of plane kk
+  int sb = slot_of(kb - 1), sc = slot_of(kb), sa = slot_of(kb + 1);
+  int o = odd ? ((kb + j) & 1) : 0;
+  int64_t outo = (int64_t)kb * NN + (int64_t)j * N + i;
+  const int rc = (ly + 1) * PX + lx + 2;
   for (int kk = kb; kk < ke; ++kk) {
     cp_async_wait<kRingPlanes - 4>();  // planes up to kk + 1 have landed (this thread's copies)
     if (need_post) {
@@ -130,13 +138,12 @@ __device__ __forceinline__ void jacobi_ring_tile(int N, int BX, int BY, int bx, 
     issue(kk + kRingPlanes - 2);  // into the slot of plane kk - 2, read last in the previous step
     if (inside) {
       // odd N: the neighbour rows (y +- 1 and planes k +- 1) have the other parity
-      const int o = offset(kk, j), on = odd ? 1 - o : 0;
-      const int rc = (ly + 1) * PX + lx + 2;
-      const int c0 = slot_of(kk) * PL + rc + o;
-      const int cs = slot_of(kk) * PL + rc - PX + on;
-      const int cn = slot_of(kk) * PL + rc + PX + on;
-      const int cb = slot_of(kk - 1) * PL + rc + on;
-      const int ca = slot_of(kk + 1) * PL + rc + on;
+      const int on = odd ? 1 - o : 0;
+      const int c0 = sc * PL + rc + o;
+      const int cs = sc * PL + rc - PX + on;
+      const int cn = sc * PL + rc + PX + on;
+      const int cb = sb * PL + rc + on;
+      const int ca = sa * PL + rc + on;
       if (!pair_math) {
         const double* r = ring;
         double s = r[c0 - 1] + r[c0 + 1];
@@ -144,12 +151,12 @@ __device__ __forceinline__ void jacobi_ring_tile(int N, int BX, int BY, int bx, 
         s += r[cn];
         s += r[cb];
         s += r[ca];
-        dst[kk * NN + col] = s * kSixth;
+        dst[outo] = s * kSixth;
       } else {
         const float2* r = reinterpret_cast<const float2*>(ring);
         const float2 res = df_avg6(r[c0 - 1], r[c0 + 1], r[cs], r[cn], r[cb], r[ca]);
         if (dst_pairs) {
-          reinterpret_cast<float2*>(dst)[kk * NN + col] = res;
+          reinterpret_cast<float2*>(dst)[outo] = res;
         } else {
           double dv = pair_to_double(res);
           if (split && (__double_as_longlong(dv) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) {
@@ -167,10 +174,15 @@ __device__ __forceinline__ void jacobi_ring_tile(int N, int BX, int BY, int bx, 
             sd += g(i, j, kk + 1);
             dv = sd * kSixth;
           }
-          dst[kk * NN + col] = dv;
+          dst[outo] = dv;
         }
       }
     }
+    sb = sc;
+    sc = sa;
+    sa = sa + 1 == kRingPlanes ? 0 : sa + 1;
+    o ^= odd ? 1 : 0;
+    outo += NN;
   }
   cp_async_wait<0>();  // no copy may land after the tile: the caller reuses the shared memory
   if (__syncthreads_or(dst_pairs && marker) && threadIdx.x == 0 && flag) atomicOr(flag, 1);
