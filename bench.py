@@ -56,9 +56,10 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--cpu-seconds", type=float, default=10.0)
-    p.add_argument("--workload", default="jacobi7", choices=["jacobi7", "spmv", "mixed", "daxpy", "nbody"],
+    p.add_argument("--workload", default="jacobi7", choices=["jacobi7", "spmv", "mixed", "daxpy", "nbody", "protocol"],
                    help="jacobi7: the headline line; spmv: the learned-selector study; mixed: the "
-                        "persistent mixed-stream executor (each prints one JSON line)")
+                        "persistent mixed-stream executor; protocol: K-fold and Online for daxpy, Jacobi and "
+                        "n-body (each prints one JSON line)")
     p.add_argument("--calls", type=int, default=10000, help="mixed: calls in the stream")
     p.add_argument("--tau", type=float, default=0.5, help="mixed: confidence below which a call is profiled")
     p.add_argument("--train", type=int, default=2000, help="spmv: profiled training matrices")
@@ -871,6 +872,109 @@ def run_mixed(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- evaluation protocol, all loops
+def run_protocol(args):
+    """The paper's evaluation protocol (Section 4.1: K-fold Adaptive-25/50/75,
+    Adaptive-100, Static,Best) and its Online mode (Section 4.2) for daxpy,
+    Jacobi and n-body, on profile tables of seeded feature points (the SpMV
+    tables are the selector study's: `--workload spmv --kfold`).  Profiles:
+    every variant of the stand-alone kernels, 3 timed runs after a warm-up,
+    512 MB L2 flush before each.  Online: one fresh region per loop with the
+    default min_train_data (= number of variants) and RoundRobin exploration,
+    invoked on the table's feature points in a seeded random order; after its
+    automatic training its choices are scored against the table's argmin."""
+    import torch
+
+    import paper_2303_08873_b300 as ar
+    import synth
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    rng = np.random.Generator(np.random.PCG64(4171))
+    status = torch.zeros(2, dtype=torch.int32, device=dev)
+    # largest inputs, used as prefixes for smaller feature points
+    nmax = 1 << 26
+    _, x, y = synth.daxpy_inputs(1, nmax)
+    xd, yd = torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev)
+    del x, y
+    Nmax = 512
+    u0 = torch.from_numpy(synth.grid_inputs(7, Nmax)).to(dev).reshape(-1)
+    out, work = torch.empty_like(u0), torch.empty_like(u0)
+    Bmax = 1 << 18
+    pos = torch.from_numpy(synth.nbody_inputs(4, Bmax)).to(dev)
+    acc = torch.empty_like(pos)
+
+    def log_uniform_ints(lo, hi, n):
+        # values exact in float32, the features' type inside the runtime
+        return sorted({int(np.float32(round(np.exp(rng.uniform(np.log(lo), np.log(hi)))))) for _ in range(n)})
+
+    def jacobi_args(f):
+        N = int(f[0])
+        return ar.ArJacobi7Args(N, int(f[1]), u0.data_ptr(), out.data_ptr(), work.data_ptr(), status.data_ptr())
+
+    loops = {
+        "daxpy": (ar.AR_LOOP_DAXPY, [[float(n)] for n in log_uniform_ints(1 << 10, nmax, 64)],
+                  lambda f: ar.ArDaxpyArgs(int(f[0]), 1.5, xd.data_ptr(), yd.data_ptr())),
+        "jacobi7": (ar.AR_LOOP_JACOBI7,
+                    [[float(N), float(rng.choice([1, 5, 10, 20]))] for N in log_uniform_ints(32, Nmax, 48)],
+                    jacobi_args),
+        "nbody": (ar.AR_LOOP_NBODY, [[float(n)] for n in log_uniform_ints(1 << 10, Bmax, 40)],
+                  lambda f: ar.ArNbodyArgs(int(f[0]), pos.data_ptr(), acc.data_ptr(), synth.NBODY_EPS)),
+    }
+    result = {}
+    for name, (L, points, make_args) in loops.items():
+        t0 = time.perf_counter()
+        F = len(points[0])
+        prof = ar.Region(f"protocol-{name}", F, "exhaustive,reps=3", 10 ** 9)
+        V = prof.add_builtin(L)
+        prof.set_l2_flush(flush, flush.numel())
+        table = []
+        for f in points:
+            ms, _ = prof.profile(f, make_args(f), stream=stream)
+            table.append((f, [float(m) for m in ms]))
+        t_prof = time.perf_counter() - t0
+        assert int(status[0].item()) == 0
+        t1 = time.perf_counter()
+        kf = kfold_protocol(table, V, F, args.epochs)
+        t_kfold = time.perf_counter() - t1
+        # Online mode
+        ro = ar.Region(f"online-{name}", F, "dtree,2")
+        ro.add_builtin(L)
+        order = rng.permutation(len(points))
+        calls = 0
+        while not ro.info()["trained"]:
+            f = points[order[calls % len(points)]]
+            ro.invoke(f, make_args(f), stream=stream)
+            calls += 1
+        stream.synchronize()
+        best = {tuple(f): min(ms) for f, ms in table}
+        msd = {tuple(f): ms for f, ms in table}
+        explore = [(tuple(ff[:F]), v, t) for ff, v, t in ro.records()]
+        online_regret = statistics.mean(msd[tuple(f)][ro.select(f)[0]] / best[tuple(f)] - 1.0 for f, _ in table)
+        names = [ar.loop_variant_name(L, v) for v in range(V)]
+        result[name] = {
+            "points": len(points), "variants": V, "features": F,
+            "kfold_mean_regret_pct": kf,
+            "online": {"explore_calls": calls, "mean_regret_pct": 100 * online_regret,
+                       "explore_overhead_pct": 100 * (sum(t for _, _, t in explore) /
+                                                      sum(best[tuple(float(x) for x in f)] for f, _, t in explore)
+                                                      - 1.0)},
+            "best_variant_histogram": {names[v]: sum(1 for _, ms in table if int(np.argmin(ms)) == v)
+                                       for v in range(V)},
+            "profiling_wall_s": t_prof, "kfold_wall_s": t_kfold}
+    line = {"metric": "mean regret % of the selected variant against the exhaustive argmin (paper Section 4.1-4.2)",
+            "value": statistics.mean(r["kfold_mean_regret_pct"]["mlp"]["adaptive_75"] for r in result.values()),
+            "unit": "%", "n_gpus": 1, "higher_is_better": False, "dtype": "f64 (daxpy, Jacobi) / f32 (n-body)",
+            "data": "synthetic", "vs_baseline": None,
+            "config": {"workload": "evaluation protocol: K = 4, f = 25/50/75 %, 10 shuffles, Adaptive-100, "
+                                   "Static,Best, Online; daxpy n in [2^10, 2^26] (64 points), Jacobi N in [32, 512] "
+                                   "x sweeps in {1,5,10,20} (48), n-body N in [1k, 256k] (40)",
+                       "value": "mean over the three loops of the MLP's Adaptive-75 regret"},
+            "loops": result}
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------- daxpy (config 1)
 def run_daxpy(args):
     """Config 1: daxpy n = 2^20, 15 variants, exhaustive profiling (5 reps after
@@ -1035,6 +1139,8 @@ def main():
         run_daxpy(args)
     elif args.workload == "nbody":
         run_nbody(args)
+    elif args.workload == "protocol":
+        run_protocol(args)
     else:
         run_ours(args)
 
