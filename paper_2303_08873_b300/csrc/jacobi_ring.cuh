@@ -81,6 +81,8 @@ __device__ __forceinline__ void jacobi_ring_tile(int N, int BX, int BY, int bx, 
   }
   // plane kp (kb-1 <= kp) lives in slot (kp - kb + 1) % kRingPlanes
   auto slot_of = [&](int kp) { return (kp - kb + 1) % kRingPlanes; };
+  // planes are issued in increasing order: kp * N^2 advances by N^2 per call
+  const double* plane_src = src + (int64_t)(kb - 1) * NN;
   auto issue = [&](int kp) {
     if (kp <= ke) {
       const bool kin = kp >= 0 && kp < N;
@@ -90,10 +92,11 @@ __device__ __forceinline__ void jacobi_ring_tile(int N, int BX, int BY, int bx, 
         if (m < nmine) {
           const bool o = odd && ((kp + cy[m]) & 1);
           const int bytes = kin ? (o ? cb1[m] : cb0[m]) : 0;
-          cp_async16(base + soff[m], bytes ? src + (int64_t)kp * NN + cxy0[m] - (o ? 1 : 0) : src, bytes);
+          cp_async16(base + soff[m], bytes ? plane_src + cxy0[m] - (o ? 1 : 0) : src, bytes);
         }
       }
     }
+    plane_src += NN;
     cp_async_commit();  // one group per plane, empty past ke, so the wait counts stay fixed
   };
   // after this thread's copies of plane kp have landed: zero a copied half
