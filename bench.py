@@ -141,6 +141,14 @@ def cpu_oracle_rate(seconds: float):
             "sample": f"jacobi7 float64 N in (32,64,128,256), 10 sweeps, {reps} passes, {dt:.1f} s"}
 
 
+def jacobi_config(ws):
+    """The Jacobi workload's `config`, shared by both arms."""
+    return {"workload": "jacobi7 float64 N in {32,64,128,256,384,512}, 10 sweeps, depth-2 tree on "
+                        "(N, sweeps) over 16 variants", "sizes": SIZES, "sweeps": SWEEPS,
+            "parallelism": "replicas" if ws > 1 else "single-gpu",
+            "l2": "inputs larger than L2: six grids, 3.2 GB read+written per step"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_info()
     if rank != 0:
@@ -164,8 +172,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "jacobi7 CPU oracle sample", "sizes": list(sizes),
-                                            "sweeps": SWEEPS},
+            "data": "synthetic", "config": jacobi_config(ws),
             "cpu_baseline": {"value": val, "unit": "GB/s", "cores": loops.num_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -402,10 +409,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "jacobi7 float64 N in {32,64,128,256,384,512}, 10 sweeps, depth-2 tree on "
-                               "(N, sweeps) over 16 variants", "sizes": SIZES, "sweeps": SWEEPS,
-                   "parallelism": "replicas" if ws > 1 else "single-gpu",
-                   "l2": "inputs larger than L2: six grids, 3.2 GB read+written per step"},
+        "config": jacobi_config(ws),
         "selection": {"exhaustive_best_gbs": step_bytes / t_best / 1e6, "default_gbs": step_bytes / t_def / 1e6,
                       "selected_table_gbs": step_bytes / t_sel / 1e6, "regret_pct": regret,
                       "default_variant": names[default], "per_N": per, "tree": tree,
