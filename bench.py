@@ -821,7 +821,7 @@ def run_mixed(args):
     regrets = {L: [] for L in range(4)}
     for q in samp:
         L, size, v = chosen[q]
-        times, _ = exhaustive(L, size, 2)
+        times, _ = exhaustive(L, size, 5)  # 5 timed runs per variant: regret is not measurement noise
         regrets[L].append(times[v] / min(times) - 1.0)
     # --- fallback: exhaustive profiling of the low-confidence calls (counted, timed on a sample)
     fb_sample = [low[q] for q in rng.choice(len(low), size=min(24, len(low)), replace=False)] if low else []

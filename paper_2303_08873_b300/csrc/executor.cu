@@ -30,6 +30,8 @@ constexpr int kSpPasses = 16;            // SpMV row groups per tile (thread-row
 constexpr int kCatchTiles = 512;         // tiles of a df call's catch-up phase
 constexpr uint32_t kDepSpin = 1u << 24;  // dependency polls (with backoff) before giving up
 constexpr int kMpPerTile = mp::kPerBlock;
+constexpr int kMpBatchExec = 4;  // merge-path loads in flight per thread inside the persistent kernel
+constexpr int kRunBlocksPerSm = 5;  // resident blocks of the persistent kernel per SM (registers spill; measured best)
 static_assert(mp::kThreads == T, "merge-path tiles use the executor's block size");
 
 __constant__ int c_nvar[4] = {kDaxpyVariants, kJacobiVariants, kSpmvVariants, kNbodyVariants};
@@ -544,9 +546,9 @@ __device__ void spmv_tile(const ar_exec_call& k, int v, int p, int64_t t, unsign
   __syncthreads();
   const int64_t i0 = sbounds[0], i1 = sbounds[1];
   if (v == 6)
-    mp::block<false>(rows, nnz, rp, col, val, x, y, db, i0, i1, carry_row + t, carry_val + t, smraw);
+    mp::block<false, kMpBatchExec>(rows, nnz, rp, col, val, x, y, db, i0, i1, carry_row + t, carry_val + t, smraw);
   else
-    mp::block<true>(rows, nnz, rp, col, val, x, y, db, i0, i1, carry_row + t, carry_val + t, smraw);
+    mp::block<true, kMpBatchExec>(rows, nnz, rp, col, val, x, y, db, i0, i1, carry_row + t, carry_val + t, smraw);
 }
 
 // nb_bodies(v) i-bodies (one or two per thread) against all N bodies, in
@@ -597,7 +599,7 @@ __device__ void nbody_tile(const ar_exec_call& k, int v, int64_t t, unsigned cha
 constexpr int kSmemBytes = mp::kSmemBytes + 16;
 static_assert(kSmemBytes >= 8448, "shared memory of the Jacobi and n-body tiles");
 
-__global__ void __launch_bounds__(T, 2) exec_run(const ar_exec_call* __restrict__ calls, int ncalls,
+__global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_call* __restrict__ calls, int ncalls,
                                                  const int* __restrict__ vint, const int* __restrict__ tiles,
                                                  const long long* __restrict__ prefix, int* done,
                                                  unsigned long long* counter, uint64_t* t0, uint64_t* t1,
@@ -755,7 +757,7 @@ extern "C" int ar_exec_batch(const ar_exec_call* calls, int ncalls, const ar_exe
   exec_features<<<dim3(64, (unsigned)ncalls), T, 0, s>>>(calls, features, part);
   exec_plan<<<1, T, 0, s>>>(calls, ncalls, m, have, force_variant, variant, conf, features, part, tiles, prefix,
                             done, counter, t_start, t_end, status, vint);
-  exec_run<<<device_sms() * 2, T, 0, s>>>(calls, ncalls, vint, tiles, prefix, done, counter, t_start, t_end, status,
+  exec_run<<<device_sms() * kRunBlocksPerSm, T, 0, s>>>(calls, ncalls, vint, tiles, prefix, done, counter, t_start, t_end, status,
                                           flags);
   return launch_status();
 }

@@ -69,18 +69,18 @@ __device__ __forceinline__ int64_t search(int64_t d, int64_t lo, int64_t hi, con
 // t + 256, ...; the column and value loads of a batch are issued together,
 // then its x gathers.  Returns false if an operand is outside the float-pair
 // split range (PAIRS only).
-template <bool PAIRS>
+template <bool PAIRS, int B = kBatch>
 __device__ __forceinline__ bool stage_products(int Z, int64_t j0, const int* __restrict__ col,
                                                const double* __restrict__ val, const double* __restrict__ x,
                                                double* sprod) {
   bool ok = true;
   const int t = threadIdx.x;
 #pragma unroll
-  for (int b0 = 0; b0 < kItems; b0 += kBatch) {
-    int cc[kBatch];
-    double vv[kBatch];
+  for (int b0 = 0; b0 < kItems; b0 += B) {
+    int cc[B];
+    double vv[B];
 #pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
+    for (int u = 0; u < B; ++u) {
       const int z = t + (b0 + u) * kThreads;
       if (z < Z) {
         cc[u] = ld_col(col + j0 + z);
@@ -88,7 +88,7 @@ __device__ __forceinline__ bool stage_products(int Z, int64_t j0, const int* __r
       }
     }
 #pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
+    for (int u = 0; u < B; ++u) {
       const int z = t + (b0 + u) * kThreads;
       if (z < Z) {
         const double xv = __ldg(x + cc[u]);
@@ -119,7 +119,7 @@ __device__ __forceinline__ bool pair_finite(float S, float C) {
 // 16-byte aligned shared memory.  Writes y for every row closed in the block
 // (the run totals included) and sets *carry_row / *carry_val to the open row
 // continuing into the next block and its partial sum, or *carry_row = -1.
-template <bool DF>
+template <bool DF, int B = kBatch>
 __device__ void block(int64_t rows, int64_t nnz, const int* __restrict__ rowptr, const int* __restrict__ col,
                       const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y,
                       int64_t db, int64_t i0, int64_t i1, int64_t* carry_row, double* carry_val,
@@ -140,7 +140,7 @@ __device__ void block(int64_t rows, int64_t nnz, const int* __restrict__ rowptr,
   if constexpr (!DF) {
     __syncthreads();  // the row ends are read by every thread's search below
   } else {
-    native = __syncthreads_or(!stage_products<true>(Z, j0, col, val, x, sprod));  // also publishes the row ends
+    native = __syncthreads_or(!stage_products<true, B>(Z, j0, col, val, x, sprod));  // also publishes the row ends
   }
   const int64_t d0 = min(db + (int64_t)t * kItems, de);
   const int n = (int)(min(d0 + kItems, de) - d0);
@@ -157,7 +157,7 @@ __device__ void block(int64_t rows, int64_t nnz, const int* __restrict__ rowptr,
   for (int pass = 0; pass < 2; ++pass) {
     if (native) {
       if (DF) __syncthreads();  // the float-pair products are read no more
-      stage_products<false>(Z, j0, col, val, x, sprod);
+      stage_products<false, B>(Z, j0, col, val, x, sprod);
     }
     __syncthreads();
     int ir = ir0, jr = jr0;
