@@ -76,7 +76,7 @@ __global__ void spmv_mp_partition(int64_t rows, int64_t nnz, int nblocks, const 
 // One path block per CTA (see merge_path.cuh); DF selects float-pair
 // arithmetic.
 template <bool DF>
-__global__ void __launch_bounds__(kMpThreads) spmv_mp_main(int64_t rows, int64_t nnz, const int* __restrict__ rowptr,
+__global__ void __launch_bounds__(kMpThreads, 5) spmv_mp_main(int64_t rows, int64_t nnz, const int* __restrict__ rowptr,
                                                            const int* __restrict__ col,
                                                            const double* __restrict__ val,
                                                            const double* __restrict__ x, double* __restrict__ y,
