@@ -598,6 +598,11 @@ __device__ void nbody_tile(const ar_exec_call& k, int v, int64_t t, unsigned cha
 // partial sums) plus its two path bounds; Jacobi needs 2 x 4 x 130 doubles
 constexpr int kSmemBytes = mp::kSmemBytes + 16;
 static_assert(kSmemBytes >= 8448, "shared memory of the Jacobi and n-body tiles");
+static_assert(ring_smem_bytes(32, 4) <= kSmemBytes && ring_smem_bytes(32, 8) <= kSmemBytes &&
+                  ring_smem_bytes(64, 4) <= kSmemBytes && ring_smem_bytes(128, 2) <= kSmemBytes,
+              "the Jacobi plane ring of every shape fits the tile shared memory");
+static_assert((128 + 4) / 2 * (2 + 2) <= 2 * T && (32 + 4) / 2 * (8 + 2) <= 2 * T,
+              "a plane's 16-byte chunks fit kRingChunks per thread");
 
 __global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_call* __restrict__ calls, int ncalls,
                                                  const int* __restrict__ vint, const int* __restrict__ tiles,

@@ -396,6 +396,7 @@ int launch_ring(int N, const double* in, void* out, const double* in_alt, double
                 cudaStream_t s) {
   constexpr int smem = ring_smem_bytes(BX, BY);
   static_assert(smem <= 48 * 1024, "ring fits the default dynamic shared memory");
+  static_assert((BX + 4) / 2 * (BY + 2) <= kRingChunks * BX * BY, "a plane's chunks fit kRingChunks per thread");
   const int64_t cb = ceil_div(N, BX) * ceil_div(N, BY);
   int resident = (227 * 1024) / smem;
   if (resident > 2048 / (BX * BY)) resident = 2048 / (BX * BY);
