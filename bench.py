@@ -38,9 +38,10 @@ TRAIN_SWEEPS = [1, 5, 10, 20]
 BYTES_PER_POINT = 16.0          # one float64 read + one write per point per sweep
 FP64_OPS_PER_POINT = 6          # 5 adds + 1 multiply in the native families
 METRIC = "selected-variant GB/s (or GFLOP/s) vs exhaustive-best & fixed default; regret %"
-# DRAM bytes (read + write, ncu) of one spmv_df_merge_path main launch on the
+# DRAM bytes (read + write, ncu) of one launch of the SpMV variants on the
 # 2e6-row Zipf(1.5) matrix of run_variant (97,990,829 nonzeros)
-SPMV_DF_MP_TRAFFIC_2M = 1200524000.0 + 7646976.0
+SPMV_TRAFFIC_2M = {"spmv_df_merge_path": 1200742000.0 + 7975680.0, "spmv_merge_path": 1200358000.0 + 7375360.0,
+                   "spmv_vec8": 1212000000.0 + 6400000.0, "spmv_vec16": 1205318000.0 + 7819008.0}
 FALLBACK_HBM_GBS = 6400.0
 # DRAM bytes (read + write) of one pairs -> pairs sweep of jacobi7_df_32x8 at
 # N = 320 (ncu dram__bytes_read.sum + dram__bytes_write.sum, median of the 8
@@ -601,12 +602,12 @@ def spmv_study(n_train, n_test, rows_max, epochs, kfold=False):
     }
     hbm_peak, peak_src = peaks()
     # the variant most often fastest on the test set, and its DRAM bytes per
-    # launch on the 2e6-row Zipf(1.5) matrix from one ncu capture (1.2005 GB
-    # read + 7.6 MB written against 1.216 GB algorithmic)
+    # launch on the 2e6-row Zipf(1.5) matrix from one ncu capture (~1.20 GB
+    # read + ~8 MB written against 1.216 GB algorithmic)
     dom = max(range(V), key=lambda v: sum(1 for p in per if p["best"] == v))
     line["roofline"] = {"bound": "hbm", "achieved": res["mlp"]["gbs"], "peak": hbm_peak, "unit": "GB/s",
                         "frac": res["mlp"]["gbs"] / hbm_peak, "peak_source": peak_src,
-                        "traffic": SPMV_DF_MP_TRAFFIC_2M if names[dom] == "spmv_df_merge_path" else None,
+                        "traffic": SPMV_TRAFFIC_2M.get(names[dom]),
                         "kernel": names[dom],
                         "note": "achieved: the MLP-selected variants over the test matrices (sum of algorithmic "
                                 "bytes / sum of times); traffic: DRAM bytes of one launch of the dominant kernel "
