@@ -12,7 +12,8 @@ rate.
 
 With ``--exec`` the same call also runs as a one-call batch of the persistent
 mixed-stream executor (``ar_exec_batch``, variant forced) and both rates are
-printed.
+printed.  Variant ``all`` runs every variant of the loop in turn (one line
+each), e.g. for a per-variant ncu launch list.
 """
 from __future__ import annotations
 
@@ -25,10 +26,13 @@ import paper_2303_08873_b300 as ar
 import synth
 
 
+LOOPS = ["daxpy", "jacobi7", "spmv", "nbody"]
+
+
 def main():
     p = argparse.ArgumentParser()
-    p.add_argument("loop", choices=["daxpy", "jacobi7", "spmv", "nbody"])
-    p.add_argument("variant", type=int)
+    p.add_argument("loop", choices=LOOPS)
+    p.add_argument("variant", help="variant index, or 'all' for every variant of the loop in turn")
     p.add_argument("--size", type=int, required=True, help="n (daxpy), N (jacobi7, nbody) or rows (spmv)")
     p.add_argument("--sweeps", type=int, default=1)
     p.add_argument("--reps", type=int, default=3)
@@ -36,19 +40,21 @@ def main():
     p.add_argument("--band", type=int, default=0, help="spmv: banded matrix of this (odd) width instead of Zipf")
     p.add_argument("--exec", action="store_true", help="also time the call through the executor (one-call batch)")
     a = p.parse_args()
+    L = LOOPS.index(a.loop)
+    variants = range(ar.loop_num_variants(L)) if a.variant == "all" else [int(a.variant)]
     dev = torch.device("cuda", 0)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if a.loop == "daxpy":
         al, x, y = synth.daxpy_inputs(1, a.size)
         x, y = torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev)
-        run = lambda: ar.ar_daxpy(a.variant, a.size, al, x, y)  # noqa: E731
+        make_run = lambda var: lambda: ar.ar_daxpy(var, a.size, al, x, y)  # noqa: E731
         call = ar.ArExecCall(loop=0, n=a.size, a=al, in0=x.data_ptr(), out0=y.data_ptr())
         work, unit = 24.0 * a.size, "GB/s"
     elif a.loop == "jacobi7":
         u0 = torch.from_numpy(synth.grid_inputs(1000 + a.size, a.size)).to(dev)
         out, wk = torch.empty_like(u0), torch.empty_like(u0)
         st = torch.zeros(2, dtype=torch.int32, device=dev)
-        run = lambda: ar.ar_jacobi7(a.variant, a.size, a.sweeps, u0, out, wk, st)  # noqa: E731
+        make_run = lambda var: lambda: ar.ar_jacobi7(var, a.size, a.sweeps, u0, out, wk, st)  # noqa: E731
         call = ar.ArExecCall(loop=1, n=a.size, sweeps=a.sweeps, in0=u0.data_ptr(), out0=out.data_ptr(),
                              out1=wk.data_ptr())
         work, unit = 16.0 * a.size ** 3 * a.sweeps, "GB/s"
@@ -60,9 +66,9 @@ def main():
         x = synth.spmv_x(31, a.size, device="cuda")
         y = torch.empty(a.size, dtype=torch.float64, device=dev)
         nnz = int(rp[-1].item())
-        wsb = ar.ar_spmv_workspace_bytes(a.variant, a.size, nnz)
+        wsb = max(ar.ar_spmv_workspace_bytes(var, a.size, nnz) for var in variants)
         ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=dev)
-        run = lambda: ar.ar_spmv(a.variant, a.size, nnz, rp, c, v, x, y, ws, wsb)  # noqa: E731
+        make_run = lambda var: lambda: ar.ar_spmv(var, a.size, nnz, rp, c, v, x, y, ws, wsb)  # noqa: E731
         ews = torch.empty(16 * (-(-(a.size + nnz) // 4096)), dtype=torch.uint8, device=dev)
         call = ar.ArExecCall(loop=2, n=a.size, nnz=nnz, in0=rp.data_ptr(), in1=c.data_ptr(), in2=v.data_ptr(),
                              in3=x.data_ptr(), out0=y.data_ptr(), out1=ews.data_ptr(), out1_bytes=ews.numel())
@@ -70,9 +76,10 @@ def main():
     else:
         pos = torch.from_numpy(synth.nbody_inputs(4, a.size)).to(dev)
         acc = torch.empty_like(pos)
-        run = lambda: ar.ar_nbody(a.variant, a.size, pos, acc, synth.NBODY_EPS)  # noqa: E731
+        make_run = lambda var: lambda: ar.ar_nbody(var, a.size, pos, acc, synth.NBODY_EPS)  # noqa: E731
         call = ar.ArExecCall(loop=3, n=a.size, eps=synth.NBODY_EPS, in0=pos.data_ptr(), out0=acc.data_ptr())
         work, unit = 20.0 * a.size ** 2, "GFLOP/s"
+
     def timed(fn):
         fn()
         torch.cuda.synchronize()
@@ -83,23 +90,24 @@ def main():
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / a.reps
 
-    ms = timed(run)
-    line = {"loop": a.loop, "variant": a.variant, "name": ar.loop_variant_name(
-        ["daxpy", "jacobi7", "spmv", "nbody"].index(a.loop), a.variant), "size": a.size, "ms": ms,
-        "rate": work / (ms * 1e-3) / 1e9, "unit": unit}
-    if a.exec:
-        table = torch.frombuffer(bytearray(ar.exec_table_bytes([call])), dtype=torch.uint8).to(dev)
-        outs = [torch.zeros(1, dtype=torch.int32, device=dev), torch.zeros(1, dtype=torch.float32, device=dev),
-                torch.zeros((1, 8), dtype=torch.float32, device=dev), torch.zeros(1, dtype=torch.int64, device=dev),
-                torch.zeros(1, dtype=torch.int64, device=dev), torch.zeros(1, dtype=torch.int32, device=dev)]
-        wsb = ar.ar_exec_workspace_bytes(1)
-        ews_all = torch.empty(wsb, dtype=torch.uint8, device=dev)
-        force = torch.tensor([a.variant], dtype=torch.int32, device=dev)
-        ems = timed(lambda: ar.ar_exec_batch(table, 1, None, force, *outs, ews_all, wsb))
-        if int(outs[5][0]) != 0:
-            raise SystemExit(f"executor status {int(outs[5][0])}")
-        line.update({"exec_ms": ems, "exec_rate": work / (ems * 1e-3) / 1e9})
-    print(json.dumps(line))
+    for var in variants:
+        ms = timed(make_run(var))
+        line = {"loop": a.loop, "variant": var, "name": ar.loop_variant_name(L, var), "size": a.size, "ms": ms,
+                "rate": work / (ms * 1e-3) / 1e9, "unit": unit}
+        if a.exec:
+            table = torch.frombuffer(bytearray(ar.exec_table_bytes([call])), dtype=torch.uint8).to(dev)
+            outs = [torch.zeros(1, dtype=torch.int32, device=dev), torch.zeros(1, dtype=torch.float32, device=dev),
+                    torch.zeros((1, 8), dtype=torch.float32, device=dev),
+                    torch.zeros(1, dtype=torch.int64, device=dev), torch.zeros(1, dtype=torch.int64, device=dev),
+                    torch.zeros(1, dtype=torch.int32, device=dev)]
+            ewsb = ar.ar_exec_workspace_bytes(1)
+            ews_all = torch.empty(ewsb, dtype=torch.uint8, device=dev)
+            force = torch.tensor([var], dtype=torch.int32, device=dev)
+            ems = timed(lambda: ar.ar_exec_batch(table, 1, None, force, *outs, ews_all, ewsb))
+            if int(outs[5][0]) != 0:
+                raise SystemExit(f"executor status {int(outs[5][0])}")
+            line.update({"exec_ms": ems, "exec_rate": work / (ems * 1e-3) / 1e9})
+        print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":
