@@ -442,7 +442,7 @@ def run_spmv(args):
     print(json.dumps(spmv_study(args.train, args.test, args.rows_max, args.epochs, kfold=args.kfold)), flush=True)
 
 
-def kfold_protocol(table, V, F, epochs, shuffles=10, K=4, seed=77):
+def kfold_protocol(table, V, F, epochs, shuffles=10, K=4, seed=77, models=("mlp", "dtree", "rfc", "static_best")):
     """The paper's evaluation protocol (Section 4.1): inputs split into K equal
     groups; a fraction f of the groups trains the model and the others test
     it (Adaptive-25/50/75; every group trains and tests across the K
@@ -476,7 +476,7 @@ def kfold_protocol(table, V, F, epochs, shuffles=10, K=4, seed=77):
         return 100.0 * statistics.mean(out)
 
     res = {}
-    for kind in ("mlp", "dtree", "rfc", "static_best"):
+    for kind in models:
         res[kind] = {}
         for frac in (1, 2, 3):
             vals = []
