@@ -177,13 +177,16 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
   // z queue: the values of planes p-1 and p at this thread's column
   double dm = 0.0, d0 = 0.0;
   float2 fm = make_float2(0.f, 0.f), f0 = make_float2(0.f, 0.f);
-  int64_t off = (int64_t)kb * NN + col;  // output offset of the next plane
+  // output element of the next plane (one pointer per output format)
+  double* od = outd + ((int64_t)kb * NN + col);
+  float2* op = outp + ((int64_t)kb * NN + col);
   int g = 0;
   bool failed = false;
-  for (; g < ngroups; ++g) {
-    const int slot = g % kRing;
-    const int pslot = slot == 0 ? kRing - 1 : slot - 1;
-    const bool ok = mbar_wait_bounded(smem_addr(&bars[slot]), (uint32_t)((g / kRing) & 1));
+  // slot of box g and the mbarrier phase it completes, advanced per box
+  int slot = 0, pslot = kRing - 1;
+  uint32_t phase = 0;
+  for (; g < ngroups; ++g, pslot = slot, slot = (slot + 1 == kRing) ? 0 : slot + 1, phase ^= (slot == 0)) {
+    const bool ok = mbar_wait_bounded(smem_addr(&bars[slot]), phase);
     if (__syncthreads_or(!ok)) {
       failed = true;
       break;
@@ -192,6 +195,7 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
     const double* prev = buf + (size_t)pslot * G::SLOT;
     if (split_boxes) {
       bool marker = false;
+#pragma unroll
       for (int e = tid; e < G::GROUP; e += BX * BY) {
         const float2 f = df_split(box[e]);
         marker |= (f.x != f.x);
@@ -222,8 +226,8 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
             s += pc[G::PX];
             s += dm;
             s += up;
-            if (inside) outd[off] = s * kSixth;
-            off += NN;
+            if (inside) *od = s * kSixth;
+            od += NN;
           }
           dm = d0;
           d0 = up;
@@ -236,7 +240,7 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
               if constexpr (MODE == M_DP || MODE == M_PP) {  // pairs out (the native case is above)
                 // stored unnormalised: the next sweep sums the hi parts exactly and
                 // the lo parts in float, so |lo| of a few ulps of hi costs ~2^-46
-                outp[off] = res;
+                *op = res;
               } else {
                 double v = pair_to_double(res);
                 // NaN test on the bit pattern (a float64 compare would use the float64 pipe)
@@ -250,10 +254,13 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
                   sd += at(in, N, i, j, k + 1);
                   v = sd * kSixth;
                 }
-                outd[off] = v;
+                *od = v;
               }
             }
-            off += NN;
+            if constexpr (MODE == M_DP || MODE == M_PP)
+              op += NN;
+            else
+              od += NN;
           }
           fm = f0;
           f0 = up;
