@@ -47,7 +47,7 @@ FALLBACK_HBM_GBS = 6400.0
 # N = 320 (ncu dram__bytes_read.sum + dram__bytes_write.sum, median of the 8
 # middle sweeps of a 10-sweep call), scaled to N = 512 by the unknowns; writes
 # still dirty in L2 when the kernel ends are not counted by ncu.
-DF_PP_TRAFFIC_N320 = 262360704.0 + 217589120.0
+DF_PP_TRAFFIC_N320 = 262379392.0 + 216399360.0
 
 
 def parse():

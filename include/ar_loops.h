@@ -67,7 +67,7 @@ int ar_daxpy(int variant, int64_t n, double a, const double *x, double *y, void 
  * doubles) as the ping-pong partner; u0, out and work must be distinct.
  * Variants: family {naive, smem (2.5D shared-memory z-march), tma
  * (cp.async.bulk.tensor tiles with mbarrier completion), df (tma staging plus
- * float-pair arithmetic on the FP32 pipe, ~2^-48 relative; points whose
+ * float-pair arithmetic on the FP32 pipe, ~2^-46 relative; points whose
  * inputs lie outside [2^-74, 2^118) in magnitude are recomputed in float64)}
  * x block shape {32x4, 32x8,
  * 64x4, 128x2}; variant = 4*family + shape.  The tma family needs even N

@@ -9,7 +9,7 @@
 // B300 the float64 pipe issues ~0.56e12 DFMA/s against 6.5e12 B/s of HBM, so
 // the 6 float64 operations per point (5 adds, 1 multiply) bound the native
 // families at ~1.5 TB/s.  The df family moves the arithmetic to the FP32 pipe
-// in float-pair form (hi + lo, ~2^-48 relative) and keeps one float64 add per
+// in float-pair form (hi + lo, ~2^-46 relative) and keeps one float64 add per
 // point.  Float64<->float32 conversions also issue on the float64 pipe on
 // B300, so the df family converts with integer bit operations only.
 //
@@ -242,7 +242,9 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
                 // the lo parts in float, so |lo| of a few ulps of hi costs ~2^-46
                 *op = res;
               } else {
-                double v = pair_to_double(res);
+                // a pairs -> float64 sweep only sees finite pairs (the first
+                // sweep of the chain checked the range)
+                double v = MODE == M_PD ? finite_pair_to_double(res) : pair_to_double(res);
                 // NaN test on the bit pattern (a float64 compare would use the float64 pipe)
                 if (MODE == M_DD && (__double_as_longlong(v) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) {
                   // an input outside the float-pair range: redo in float64

@@ -1,6 +1,6 @@
 // Float-pair arithmetic shared by the Jacobi kernels, the float-pair SpMV
 // merge path and the mixed-stream executor (internal).  A float64 value x is carried as an unevaluated pair
-// of floats (hi, lo) with x = hi + lo to ~2^-48 relative; conversions use
+// of floats (hi, lo) with x = hi + lo to ~2^-46 relative; conversions use
 // integer bit operations only, because float64<->float32 conversion
 // instructions issue on B300's slow float64 pipe.
 #pragma once
@@ -22,25 +22,27 @@ __device__ __forceinline__ double at(const double* __restrict__ u, int N, int i,
 constexpr float kSixthHi = 0.16666667163372039794921875f;           // RN(1/6)
 constexpr float kSixthLo = -4.967053740534411e-09f;  // RN(1/6 - kSixthHi)
 
-// Split x into (hi, lo) with hi = x rounded to 24 significant bits and
-// lo = the remainder, both floats: x = hi + lo to within 2^-48 |x|.  Works on
-// the bit pattern with integer operations (truncate the significand to 24
-// bits, round the 29-bit remainder up or down): on B300 a float64<->float32
-// conversion issues on the slow float64 pipe, int->float does not.  Values
-// outside the float-pair range (|x| < 2^-74, |x| >= 2^118, inf, NaN) give
-// hi = NaN as a marker; +-0 gives (0, 0).
+// Split x into floats (hi, lo): hi = x truncated to 24 significant bits,
+// lo = the next 23 bits of the remainder (same sign as x, |lo| < ulp(hi)),
+// so x = hi + lo to within 2^-46 |x|.  Integer operations plus one float add
+// and one float multiply: on B300 a float64<->float32 conversion issues on
+// the slow float64 pipe, and int->float conversion is avoided too (2^23 + q
+// is read as a float straight from its bits).  Values outside the float-pair
+// range (|x| < 2^-74, |x| >= 2^118, inf, NaN) give hi = NaN as a marker;
+// +-0 gives (0, 0).
 __device__ __forceinline__ float2 df_split(double x) {
   const long long b = __double_as_longlong(x);
   const unsigned h32 = (unsigned)((unsigned long long)b >> 32), l32 = (unsigned)b;
-  const int e = (int)((h32 >> 20) & 0x7ff);
+  const unsigned e = (h32 >> 20) & 0x7ffu;
   const unsigned sign = h32 & 0x80000000u;
-  const int rraw = (int)(l32 & 0x1FFFFFFFu);
-  const int up = rraw >= (1 << 28);  // round the remainder: hi one ulp away from zero
-  const unsigned hib = (sign | ((unsigned)(e - 896) << 23) | ((h32 & 0xfffffu) << 3) | (l32 >> 29)) + (unsigned)up;
-  const float lo = __int2float_rn(rraw - (up << 29)) * __int_as_float((e - 948) << 23);  // r * 2^(e-1075)
-  float2 out = make_float2(__uint_as_float(hib), __uint_as_float(__float_as_uint(lo) ^ sign));
+  // exponent bits 8..0 and the top 23 significand bits; adding 2^30 rebiases
+  // the 9-bit exponent field from 1023 to 127 (mod 512) for every e in range
+  const unsigned hib = (__funnelshift_l(l32, h32, 3) + 0x40000000u) | sign;
+  const float q = __uint_as_float(0x4b000000u | ((l32 >> 6) & 0x7fffffu)) - 8388608.0f;
+  const float lo = q * __uint_as_float(((e - 942u) << 23) | sign);  // q * +-2^(e-1069)
+  float2 out = make_float2(__uint_as_float(hib), lo);
   // branch-free selects: +-0 -> (0, 0); outside [2^-74, 2^118) or inf/NaN -> marker
-  if ((unsigned)(e - 949) > 191u) out = ((b << 1) == 0) ? make_float2(0.f, 0.f) : make_float2(__int_as_float(0x7fc00001), 0.f);
+  if (e - 949u > 191u) out = ((b << 1) == 0) ? make_float2(0.f, 0.f) : make_float2(__int_as_float(0x7fc00001), 0.f);
   return out;
 }
 
@@ -90,6 +92,17 @@ __device__ __forceinline__ float2 df_avg6(float2 v0, float2 v1, float2 v2, float
 }
 
 __device__ __forceinline__ double pair_to_double(float2 v) { return f2d_bits(v.x) + f2d_bits(v.y); }
+
+// f2d_bits for a finite float (no inf / NaN case): fewer operations.
+__device__ __forceinline__ double f2d_finite(float f) {
+  const unsigned u = __float_as_uint(f), a = u & 0x7fffffffu;
+  const bool normal = a >= 0x00800000u;  // zero and subnormals become signed zero
+  const unsigned hi = (u & 0x80000000u) | (normal ? (a >> 3) + 0x38000000u : 0u);
+  return __hiloint2double((int)hi, normal ? (int)(u << 29) : 0);
+}
+
+// pair_to_double for a pair of finite floats.
+__device__ __forceinline__ double finite_pair_to_double(float2 v) { return f2d_finite(v.x) + f2d_finite(v.y); }
 
 // Split a product operand x into floats hi + lo (hi = x truncated to 24
 // significant bits, 0 <= lo/x < 2^-23, x - hi - lo below 2^-46 |x|) with
