@@ -64,8 +64,10 @@ class Batch:
         self.check.append(lambda y=y, ref=ref, absum=absum: np.all(np.abs(host(y) - ref) <= 1e-10 * absum))
         return loops.csr_row_stats(rph)
 
-    def nbody(self, N, seed):
+    def nbody(self, N, seed, negate=None):
         p = synth.nbody_inputs(seed, N)
+        if negate is not None:
+            p[negate, 3] *= -1.0
         pd = dev(p)
         acc = torch.full((N, 4), np.nan, dtype=torch.float32, device="cuda")
         self.keep += [pd, acc]
@@ -151,6 +153,9 @@ def test_edge_sizes_of_every_loop_in_one_batch():
         force.append(v)
     for N, v in [(1, 0), (2, 3), (3, 6), (129, 1), (257, 4), (513, 8), (255, 7)]:
         b.nbody(N, 500 + N)
+        force.append(v)
+    for v in (1, 4, 7):  # negative masses in one tile
+        b.nbody(700, 600 + v, negate=slice(300, 303))
         force.append(v)
     r = b.run(force=force)
     assert np.all(r["status"] == 0)

@@ -52,6 +52,22 @@ def test_two_body_reaction_and_cube_centre():
         assert np.max(np.abs(c[-1, :3])) <= 1e-6 * np.max(np.abs(c[:-1, :3]))
 
 
+def test_signed_and_zero_masses():
+    """Negative masses in one tile (the weight keeps the mass's sign); zero
+    masses add nothing."""
+    N = 3000
+    p = synth.nbody_inputs(13, N)
+    p[::7, 3] = 0.0
+    p[1000:1010, 3] *= -1.0  # one tile of every tile size, and part of one body pair
+    ref = loops.nbody(p, EPS)
+    for v in range(V):
+        _check(_run(v, p), ref, ("signed masses", v))
+    q = p.copy()
+    q[:, 3] = 0.0
+    for v in range(V):
+        assert np.array_equal(_run(v, q), np.zeros((N, 4), np.float32)), v
+
+
 @pytest.mark.parametrize("N", [65536, 262144])
 def test_full_size_sampled(N):
     """Workload sizes: 2048 sampled bodies (plus the first and last) against
