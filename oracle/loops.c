@@ -12,6 +12,9 @@
  *   daxpy   y <- a*x + y
  *   jacobi7 u' = (sum of the 6 face neighbours) / 6 on N^3 unknowns, zero
  *           Dirichlet ghosts outside the cube
+ *   heat7   u' = u + alpha (sum of the 6 face neighbours - 6 u): one explicit
+ *           (forward Euler) step of the heat equation on the same grid, the
+ *           finite-difference scheme of Table 3's Heat, alpha = kappa dt / h^2
  *   spmv    y = A x for CSR A, each row summed in column-list order
  *   nbody   a_i = sum_j m_j (r_j - r_i) / (|r_j - r_i|^2 + eps^2)^(3/2)
  * The outer loops carry an OpenMP "parallel for" so the timed CPU baseline
@@ -94,6 +97,41 @@ void or_jacobi7(int64_t N, int sweeps, const double *u0, double *out, double *wo
   for (int s = 0; s < sweeps; ++s) {
     double *dst = ((sweeps - 1 - s) % 2 == 0) ? out : work;
     or_jacobi7_sweep(N, src, dst);
+    src = dst;
+  }
+}
+
+/* ---------------------------------------------------------------- Heat */
+/* One explicit step: out = u + alpha * (s - 6 u), s = W + E + S + N + D + U
+ * summed in that order, each operation rounded as written. */
+void or_heat7_step(int64_t N, double alpha, const double *in, double *out) {
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < N; ++k)
+    for (int64_t j = 0; j < N; ++j)
+      for (int64_t i = 0; i < N; ++i) {
+        double s = at(in, N, i - 1, j, k);
+        s = s + at(in, N, i + 1, j, k);
+        s = s + at(in, N, i, j - 1, k);
+        s = s + at(in, N, i, j + 1, k);
+        s = s + at(in, N, i, j, k - 1);
+        s = s + at(in, N, i, j, k + 1);
+        const double u = in[(k * N + j) * N + i];
+        out[(k * N + j) * N + i] = u + alpha * (s - 6.0 * u);
+      }
+}
+
+/* `steps` steps starting from u0, result in `out`; `work` holds N^3
+ * doubles; u0 is not modified. */
+void or_heat7(int64_t N, int steps, double alpha, const double *u0, double *out, double *work) {
+  const int64_t n3 = N * N * N;
+  if (steps <= 0) {
+    memcpy(out, u0, (size_t)n3 * sizeof(double));
+    return;
+  }
+  const double *src = u0;
+  for (int s = 0; s < steps; ++s) {
+    double *dst = ((steps - 1 - s) % 2 == 0) ? out : work;
+    or_heat7_step(N, alpha, src, dst);
     src = dst;
   }
 }

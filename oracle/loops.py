@@ -40,6 +40,7 @@ def lib():
         L.or_daxpy_fma.argtypes = [_i64, _dbl, _vp, _vp]
         L.or_jacobi7_sweep.argtypes = [_i64, _vp, _vp]
         L.or_jacobi7.argtypes = [_i64, ctypes.c_int, _vp, _vp, _vp]
+        L.or_heat7.argtypes = [_i64, ctypes.c_int, _dbl, _vp, _vp, _vp]
         L.or_spmv.argtypes = [_i64, _vp, _vp, _vp, _vp, _vp]
         L.or_spmv_rows.argtypes = [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.or_csr_row_stats.argtypes = [_i64, _vp, _vp]
@@ -82,6 +83,18 @@ def jacobi7(u0, sweeps: int) -> np.ndarray:
     out = np.empty_like(u0)
     work = np.empty_like(u0)
     lib().or_jacobi7(N, int(sweeps), _p(u0), _p(out), _p(work))
+    return out
+
+
+def heat7(u0, steps: int, alpha: float) -> np.ndarray:
+    """``steps`` explicit heat steps u + alpha (sum of the 6 neighbours - 6 u)
+    of the (N, N, N) grid u0 (zero Dirichlet ghosts)."""
+    u0 = _c(u0, np.float64)
+    N = u0.shape[0]
+    assert u0.shape == (N, N, N)
+    out = np.empty_like(u0)
+    work = np.empty_like(u0)
+    lib().or_heat7(N, int(steps), float(alpha), _p(u0), _p(out), _p(work))
     return out
 
 

@@ -109,6 +109,59 @@ def test_jacobi_zero_sweeps_is_copy():
     assert np.array_equal(loops.jacobi7(u0, 0), u0)
 
 
+# ------------------------------------------------------------------ Heat
+def test_heat_constant_field_faces_edges_corners():
+    # u = 8, alpha = 1/8: u + (m * 8 - 48) / 8 = m + 2 for a point with m
+    # in-cube neighbours (every operation exact in float64)
+    N = 7
+    out = loops.heat7(np.full((N, N, N), 8.0), 1, 0.125)
+    k, j, i = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+    nb = 6 - sum(((c == 0) | (c == N - 1)).astype(int) for c in (i, j, k))
+    assert np.array_equal(out, (nb + 2).astype(np.float64))
+
+
+@pytest.mark.parametrize("N,s,alpha", [(9, 1, 0.1), (16, 3, 1.0 / 6.0), (24, 10, 0.125)])
+def test_heat_eigenfunction_closed_form(N, s, alpha):
+    # the neighbour sum of the sine mode is 6 cos(pi h) u (one 2 cos(pi h)
+    # per axis), so a step multiplies it by 1 - 6 alpha (1 - cos(pi h))
+    u0 = synth.sine_mode(N)
+    out = loops.heat7(u0, s, alpha)
+    h = 1.0 / (N + 1)
+    lam = 1.0 - 6.0 * alpha * (1.0 - math.cos(math.pi * h))
+    assert np.max(np.abs(out - lam ** s * u0)) <= 1e-14 * s * np.max(np.abs(u0))
+
+
+@pytest.mark.parametrize("s", [1, 3])
+def test_heat_linear_field_unchanged_away_from_faces(s):
+    # the discrete Laplacian of an integer linear field is exactly 0
+    N = 14
+    u0 = synth.linear_field(N, 3, -2, 5)
+    out = loops.heat7(u0, s, 0.1)
+    core = (slice(s, N - s),) * 3
+    assert np.array_equal(out[core], u0[core])
+    assert not np.array_equal(out, u0)
+
+
+@pytest.mark.parametrize("N,s,alpha", [(5, 1, 0.1), (8, 4, 0.15), (11, 3, 1.0 / 7.0)])
+def test_heat_matches_kronecker_operator(N, s, alpha):
+    u0 = synth.grid_inputs(2, N)
+    L = _grid_operator(N) * 6.0 - 6.0 * sp.identity(N ** 3, format="csr")
+    v = u0.ravel()
+    for _ in range(s):
+        v = v + alpha * (L @ v)
+    out = loops.heat7(u0, s, alpha)
+    assert np.max(np.abs(out.ravel() - v)) <= 1e-15 * s * np.max(np.abs(u0)) * 16
+
+
+def test_heat_alpha_one_sixth_is_jacobi_and_zero_is_identity():
+    u0 = synth.grid_inputs(3, 12)
+    a = loops.heat7(u0, 4, 1.0 / 6.0)
+    b = loops.jacobi7(u0, 4)
+    assert np.max(np.abs(a - b)) <= 1e-15 * 4 * np.max(np.abs(u0)) * 8
+    assert np.array_equal(loops.heat7(u0, 3, 0.0), u0)
+    assert np.array_equal(loops.heat7(u0, 0, 0.1), u0)
+
+
 # ------------------------------------------------------------------ SpMV
 def test_spmv_identity_bitwise():
     n = 1000
