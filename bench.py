@@ -48,6 +48,28 @@ FALLBACK_HBM_GBS = 6400.0
 # middle sweeps of a 10-sweep call), scaled to N = 512 by the unknowns; writes
 # still dirty in L2 when the kernel ends are not counted by ncu.
 DF_PP_TRAFFIC_N320 = 262379392.0 + 216399360.0
+HEAT_ALPHA = 0.125              # alpha of the heat workload (stable: <= 1/6)
+
+# The two stencil workloads: the Jacobi region (the headline) and the explicit
+# heat step on the same grids.  fp64_ops: float64 operations per point of the
+# native families (the "alu" roof); pp_traffic: ncu DRAM bytes of one
+# pairs -> pairs sweep at N = 320 per df kernel (see DF_PP_TRAFFIC_N320).
+STENCILS = {
+    "jacobi7": {"loop": 1, "label": "jacobi7 float64", "fp64_ops": FP64_OPS_PER_POINT,
+                "pp_traffic": {"jacobi7_df_32x8": DF_PP_TRAFFIC_N320}},
+    "heat7": {"loop": 4, "label": f"heat7 float64 (alpha = {HEAT_ALPHA})", "fp64_ops": 7, "pp_traffic": {}},
+}
+
+
+def stencil_args(ar, kind, n, sweeps, ptrs, status_ptr):
+    """The loop's argument block for one call of `sweeps` sweeps (steps)."""
+    if kind == "heat7":
+        return ar.ArHeat7Args(n, sweeps, HEAT_ALPHA, *ptrs, status_ptr)
+    return ar.ArJacobi7Args(n, sweeps, *ptrs, status_ptr)
+
+
+def stencil_oracle(loops, kind, u, sweeps):
+    return loops.heat7(u, sweeps, HEAT_ALPHA) if kind == "heat7" else loops.jacobi7(u, sweeps)
 
 
 def parse():
@@ -57,10 +79,12 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--cpu-seconds", type=float, default=10.0)
-    p.add_argument("--workload", default="jacobi7", choices=["jacobi7", "spmv", "mixed", "daxpy", "nbody", "protocol"],
-                   help="jacobi7: the headline line; spmv: the learned-selector study; mixed: the "
-                        "persistent mixed-stream executor; protocol: K-fold and Online for daxpy, Jacobi and "
-                        "n-body (each prints one JSON line)")
+    p.add_argument("--workload", default="jacobi7",
+                   choices=["jacobi7", "heat7", "spmv", "mixed", "daxpy", "nbody", "protocol"],
+                   help="jacobi7: the headline line; heat7: the same region and grids with the explicit "
+                        "heat step; spmv: the learned-selector study; mixed: the persistent mixed-stream "
+                        "executor; protocol: K-fold and Online for daxpy, Jacobi and n-body (each prints one "
+                        "JSON line)")
     p.add_argument("--calls", type=int, default=10000, help="mixed: calls in the stream")
     p.add_argument("--tau", type=float, default=0.5, help="mixed: confidence below which a call is profiled")
     p.add_argument("--train", type=int, default=2000, help="spmv: profiled training matrices")
@@ -107,11 +131,11 @@ def job_rate(step_bytes: float, steps: int, world: int, ms: float) -> float:
 
 
 def jacobi_launches(name, N, sweeps):
-    """Kernel launches of one ar_jacobi7 call: one per sweep, plus the
-    catch-up launch of a df call that keeps float pairs between sweeps (TMA
-    staging usable: even N at least one box wide)."""
+    """Kernel launches of one ar_jacobi7 / ar_heat7 call: one per sweep, plus
+    the catch-up launch of a df call that keeps float pairs between sweeps
+    (TMA staging usable: even N at least one box wide)."""
     bx = int(name.split("_")[-1].split("x")[0])
-    df_chain = name.startswith("jacobi7_df") and N % 2 == 0 and N >= bx + 4 and N >= 10 and sweeps >= 2
+    df_chain = "_df_" in name and N % 2 == 0 and N >= bx + 4 and N >= 10 and sweeps >= 2
     return sweeps + (1 if df_chain else 0)
 
 
@@ -120,7 +144,7 @@ def workload_bytes(sizes, sweeps):
 
 
 # ---------------------------------------------------------------- CPU oracle
-def cpu_oracle_rate(seconds: float):
+def cpu_oracle_rate(seconds: float, kind: str = "jacobi7"):
     """GB/s of the float64 CPU oracle on a bounded sample of the workload:
     N in {32, 64, 128, 256} at 10 sweeps, repeated until `seconds` elapse."""
     import synth
@@ -132,19 +156,19 @@ def cpu_oracle_rate(seconds: float):
     reps = 0
     while True:
         for n, u in grids.items():
-            loops.jacobi7(u, SWEEPS)
+            stencil_oracle(loops, kind, u, SWEEPS)
             done += BYTES_PER_POINT * n ** 3 * SWEEPS
         reps += 1
         if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
     return {"value": done / dt / 1e9, "unit": "GB/s", "cores": loops.num_threads(), "kind": "oracle",
-            "sample": f"jacobi7 float64 N in (32,64,128,256), 10 sweeps, {reps} passes, {dt:.1f} s"}
+            "sample": f"{STENCILS[kind]['label']} N in (32,64,128,256), 10 sweeps, {reps} passes, {dt:.1f} s"}
 
 
-def jacobi_config(ws):
-    """The Jacobi workload's `config`, shared by both arms."""
-    return {"workload": "jacobi7 float64 N in {32,64,128,256,384,512}, 10 sweeps, depth-2 tree on "
+def jacobi_config(ws, kind="jacobi7"):
+    """The stencil workload's `config`, shared by both arms."""
+    return {"workload": f"{STENCILS[kind]['label']} N in {{32,64,128,256,384,512}}, 10 sweeps, depth-2 tree on "
                         "(N, sweeps) over 16 variants", "sizes": SIZES, "sweeps": SWEEPS,
             "parallelism": "replicas" if ws > 1 else "single-gpu",
             "l2": "inputs larger than L2: six grids, 3.2 GB read+written per step"}
@@ -156,24 +180,25 @@ def run_reference(args):
         return
     from oracle import loops
 
+    kind = args.workload if args.workload in STENCILS else "jacobi7"
     sizes = (32, 64, 128, 256)
     import synth
 
     grids = {n: synth.grid_inputs(1000 + n, n) for n in sizes}
     for _ in range(args.warmup):
         for n, u in grids.items():
-            loops.jacobi7(u, SWEEPS)
+            stencil_oracle(loops, kind, u, SWEEPS)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         for n, u in grids.items():
-            loops.jacobi7(u, SWEEPS)
+            stencil_oracle(loops, kind, u, SWEEPS)
     dt = time.perf_counter() - t0
     val = workload_bytes(sizes, SWEEPS) * args.steps / dt / 1e9
-    sample = f"jacobi7 float64 N in {sizes}, 10 sweeps per step (bounded sample of N up to 512)"
+    sample = f"{STENCILS[kind]['label']} N in {sizes}, 10 sweeps per step (bounded sample of N up to 512)"
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": jacobi_config(ws),
+            "data": "synthetic", "config": jacobi_config(ws, kind),
             "cpu_baseline": {"value": val, "unit": "GB/s", "cores": loops.num_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -235,6 +260,9 @@ def run_ours(args):
     import paper_2303_08873_b300 as ar
     import synth
 
+    kind = args.workload
+    spec = STENCILS[kind]
+    loop = spec["loop"]
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     hbm_peak, peak_src = peaks()
@@ -247,25 +275,25 @@ def run_ours(args):
         bufs[n] = (u0, torch.empty_like(u0), torch.empty_like(u0))
     status = torch.zeros(2, dtype=torch.int32, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    argblocks = {n: ar.ArJacobi7Args(n, SWEEPS, bufs[n][0].data_ptr(), bufs[n][1].data_ptr(),
-                                     bufs[n][2].data_ptr(), status.data_ptr()) for n in SIZES}
+    argblocks = {n: stencil_args(ar, kind, n, SWEEPS, [b.data_ptr() for b in bufs[n]], status.data_ptr())
+                 for n in SIZES}
 
     # --- profiling + training (untimed): exhaustive over N x sweeps
-    region = ar.Region("jacobi7", 2, "dtree,2,reps=5", 10 ** 9)
-    V = region.add_builtin(ar.AR_LOOP_JACOBI7)
+    region = ar.Region(kind, 2, "dtree,2,reps=5", 10 ** 9)
+    V = region.add_builtin(loop)
     region.set_l2_flush(flush, flush.numel())
     table = {}
     t_prof = time.perf_counter()
     for n in SIZES:
         for s in TRAIN_SWEEPS:
-            a = ar.ArJacobi7Args(n, s, *[bufs[n][i].data_ptr() for i in range(3)], status.data_ptr())
+            a = stencil_args(ar, kind, n, s, [b.data_ptr() for b in bufs[n]], status.data_ptr())
             ms, best = region.profile([n, s], a, stream=stream)
             table[(n, s)] = (ms, best)
     t_prof = time.perf_counter() - t_prof
     region.train()
     tree = region.tree()
-    default = ar.loop_default_variant(ar.AR_LOOP_JACOBI7)
-    names = [ar.loop_variant_name(ar.AR_LOOP_JACOBI7, v) for v in range(V)]
+    default = ar.loop_default_variant(loop)
+    names = [ar.loop_variant_name(loop, v) for v in range(V)]
     chosen = {n: region.select([n, SWEEPS])[0] for n in SIZES}
 
     def step():
@@ -309,18 +337,20 @@ def run_ours(args):
     big_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(k0, k1)) / SWEEPS
     achieved = BYTES_PER_POINT * big ** 3 / (big_ms * 1e-3) / 1e9
     vbig = chosen[big]
-    if names[vbig].startswith("jacobi7_df"):
-        traffic = DF_PP_TRAFFIC_N320 * (big / 320.0) ** 3 if names[vbig] == "jacobi7_df_32x8" else None
+    if "_df_" in names[vbig]:
+        pp = spec["pp_traffic"].get(names[vbig])
+        traffic = pp * (big / 320.0) ** 3 if pp else None
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic, "peak_source": peak_src,
                 "kernel": names[vbig],
                 "note": "achieved: the N=512 invocation's time per sweep (10 sweep launches + 1 catch-up); "
                         "traffic: DRAM bytes of one pairs->pairs sweep launch, measured at N=320 and scaled"}
     else:
-        alu_gbs = fp64_fma / FP64_OPS_PER_POINT * BYTES_PER_POINT / 1e9
+        alu_gbs = fp64_fma / spec["fp64_ops"] * BYTES_PER_POINT / 1e9
         roof = {"bound": "alu", "achieved": achieved, "peak": alu_gbs, "unit": "GB/s",
                 "frac": achieved / alu_gbs, "traffic": None,
-                "peak_source": "float64 issue rate measured by ar_measure_fma_rates x 16 B / 6 FP64 ops per point",
+                "peak_source": "float64 issue rate measured by ar_measure_fma_rates x 16 B / "
+                               f"{spec['fp64_ops']} FP64 ops per point",
                 "kernel": names[vbig], "hbm_frac": achieved / hbm_peak}
 
     # --- selection quality from the exhaustive table (sweeps = 10)
@@ -344,8 +374,8 @@ def run_ours(args):
     # exhaustive table above
     online = []
     for n in SIZES:
-        ro = ar.Region(f"jacobi7-online-{n}", 2, "dtree,2")
-        ro.add_builtin(ar.AR_LOOP_JACOBI7)
+        ro = ar.Region(f"{kind}-online-{n}", 2, "dtree,2")
+        ro.add_builtin(loop)
         explore_ms = 0.0
         calls = 0
         while not ro.info()["trained"]:
@@ -405,12 +435,12 @@ def run_ours(args):
 
     if rank != 0:
         return
-    cpu = cpu_oracle_rate(args.cpu_seconds) if ws == 1 else None
+    cpu = cpu_oracle_rate(args.cpu_seconds, kind) if ws == 1 else None
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": jacobi_config(ws),
+        "config": jacobi_config(ws, kind),
         "selection": {"exhaustive_best_gbs": step_bytes / t_best / 1e6, "default_gbs": step_bytes / t_def / 1e6,
                       "selected_table_gbs": step_bytes / t_sel / 1e6, "regret_pct": regret,
                       "default_variant": names[default], "per_N": per, "tree": tree,
@@ -1146,7 +1176,7 @@ def main():
         run_nbody(args)
     elif args.workload == "protocol":
         run_protocol(args)
-    else:
+    else:  # the stencil workloads: jacobi7 (default) and heat7
         run_ours(args)
 
 

@@ -31,8 +31,9 @@
 extern "C" {
 #endif
 
-/* Loop ids for ar_region_add_builtin. */
-enum { AR_LOOP_DAXPY = 0, AR_LOOP_JACOBI7 = 1, AR_LOOP_SPMV = 2, AR_LOOP_NBODY = 3 };
+/* Loop ids for ar_region_add_builtin.  The mixed-stream executor below runs
+ * the first four; AR_LOOP_HEAT7 is stand-alone and region use only. */
+enum { AR_LOOP_DAXPY = 0, AR_LOOP_JACOBI7 = 1, AR_LOOP_SPMV = 2, AR_LOOP_NBODY = 3, AR_LOOP_HEAT7 = 4 };
 
 /* Number of variants of a loop, its default variant (the fixed baseline the
  * selection is compared with) and a variant's name. */
@@ -91,6 +92,30 @@ typedef struct ar_jacobi7_args {
 } ar_jacobi7_args;
 int ar_jacobi7(int variant, int N, int sweeps, const double *u0, double *out, double *work,
                int *status, void *stream);
+
+/* ---------------------------------------------------------------- Heat ---
+ * `steps` explicit (forward Euler) steps of the heat equation on the same
+ * grid: u'(i,j,k) = u + alpha (u(i-1)+u(i+1)+u(j-1)+u(j+1)+u(k-1)+u(k+1) -
+ * 6u), zero outside the cube, alpha = kappa dt / h^2 with 0 <= alpha <= 1
+ * (AR_ERR_ARG otherwise, NaN included; the scheme is stable for alpha <=
+ * 1/6).  The finite-difference scheme of the paper's Heat benchmark
+ * (Table 3) on a 3D grid.  Layout, buffers, the 16 variants (same families
+ * and shapes as ar_jacobi7, named heat7_*), the tma/df requirements and the
+ * status array behave exactly as for ar_jacobi7; the df family carries
+ * alpha as a float pair and u + alpha (sum - 6u) to ~2^-46 of |u| +
+ * alpha sum|neighbours|.  Default: naive 32x8 (variant 1).  Not accepted by
+ * ar_exec_batch. */
+typedef struct ar_heat7_args {
+  int N;
+  int steps;
+  double alpha;
+  const double *u0;
+  double *out;
+  double *work;
+  int *status;
+} ar_heat7_args;
+int ar_heat7(int variant, int N, int steps, double alpha, const double *u0, double *out, double *work,
+             int *status, void *stream);
 
 /* ---------------------------------------------------------------- SpMV ---
  * y = A x for a CSR matrix of `rows` rows and nnz nonzeros: rowptr int32

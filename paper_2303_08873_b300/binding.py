@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "AR_OK", -1: "AR_ERR_ARG", -2: "AR_ERR_STATE", -3: "AR_ERR_CU
                 -5: "AR_ERR_IO", -6: "AR_ERR_TIMEOUT", -7: "AR_ERR_OOM"}
 AR_MAX_FEATURES = 8
 AR_MAX_VARIANTS = 64
-AR_LOOP_DAXPY, AR_LOOP_JACOBI7, AR_LOOP_SPMV, AR_LOOP_NBODY = 0, 1, 2, 3
+AR_LOOP_DAXPY, AR_LOOP_JACOBI7, AR_LOOP_SPMV, AR_LOOP_NBODY, AR_LOOP_HEAT7 = 0, 1, 2, 3, 4
 MODEL_KINDS = {0: "dtree", 1: "mlp", 2: "exhaustive", 3: "fixed", 4: "rfc"}
 
 
@@ -61,6 +61,11 @@ class ArDaxpyArgs(ctypes.Structure):
 
 class ArJacobi7Args(ctypes.Structure):
     _fields_ = [("N", _i), ("sweeps", _i), ("u0", _vp), ("out", _vp), ("work", _vp), ("status", _vp)]
+
+
+class ArHeat7Args(ctypes.Structure):
+    _fields_ = [("N", _i), ("steps", _i), ("alpha", _d), ("u0", _vp), ("out", _vp), ("work", _vp),
+                ("status", _vp)]
 
 
 class ArSpmvArgs(ctypes.Structure):
@@ -123,6 +128,7 @@ _SIGS = {
     "ar_region_add_builtin": (_i, [_vp, _i, _pi]),
     "ar_daxpy": (_i, [_i, _i64, _d, _vp, _vp, _vp]),
     "ar_jacobi7": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp, _vp]),
+    "ar_heat7": (_i, [_i, _i, _i, _d, _vp, _vp, _vp, _vp, _vp]),
     "ar_spmv_workspace_bytes": (_i, [_i, _i64, _i64, ctypes.POINTER(_sz)]),
     "ar_spmv": (_i, [_i, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "ar_spmv_merge_path_noalloc": (_i, [_i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -209,6 +215,11 @@ def ar_daxpy(variant, n, a, x, y, stream=None):
 def ar_jacobi7(variant, N, sweeps, u0, out, work, status=None, stream=None):
     return check(lib.ar_jacobi7(variant, N, sweeps, ptr(u0), ptr(out), ptr(work), ptr(status),
                                 stream_handle(stream)))
+
+
+def ar_heat7(variant, N, steps, alpha, u0, out, work, status=None, stream=None):
+    return check(lib.ar_heat7(variant, N, steps, alpha, ptr(u0), ptr(out), ptr(work), ptr(status),
+                              stream_handle(stream)))
 
 
 def ar_spmv_workspace_bytes(variant, rows, nnz):
@@ -492,11 +503,11 @@ class Region:
 
 
 __all__ = ["ArExecCall", "ArExecModels", "ar_exec_workspace_bytes", "ar_exec_batch", "exec_table_bytes",
-           "AR_EXEC_MAX_CALLS", "AR_EXEC_MAX_PHASES", "ArError", "Region", "ArDaxpyArgs", "ArJacobi7Args", "ArSpmvArgs", "ArNbodyArgs", "ar_spmv",
+           "AR_EXEC_MAX_CALLS", "AR_EXEC_MAX_PHASES", "ArError", "Region", "ArDaxpyArgs", "ArJacobi7Args", "ArHeat7Args", "ArSpmvArgs", "ArNbodyArgs", "ar_spmv",
            "ar_spmv_workspace_bytes", "ar_spmv_merge_path_noalloc", "ar_csr_features", "ar_csr_features_workspace_bytes", "ar_nbody",
            "ar_nbody_batched", "ar_nbody_batched_workspace_bytes", "LAUNCH_FN", "FAKE_TIME_FN", "lib", "ptr",
            "stream_handle", "check", "loop_num_variants", "loop_default_variant", "loop_variant_name", "ar_daxpy",
-           "ar_jacobi7", "ar_mlp_num_params", "ar_mlp_forward", "ar_mlp_grad", "ar_mlp_adam", "ar_mlp_train",
+           "ar_jacobi7", "ar_heat7", "ar_mlp_num_params", "ar_mlp_forward", "ar_mlp_grad", "ar_mlp_adam", "ar_mlp_train",
            "ar_measure_fma_rates", "EXPORTED", "AR_LOOP_DAXPY", "AR_LOOP_JACOBI7", "AR_LOOP_SPMV",
-           "AR_LOOP_NBODY", "AR_OK", "AR_ERR_ARG", "AR_ERR_STATE", "AR_ERR_CUDA", "AR_ERR_NOMODEL", "AR_ERR_IO",
+           "AR_LOOP_NBODY", "AR_LOOP_HEAT7", "AR_OK", "AR_ERR_ARG", "AR_ERR_STATE", "AR_ERR_CUDA", "AR_ERR_NOMODEL", "AR_ERR_IO",
            "AR_ERR_TIMEOUT", "AR_ERR_OOM", "AR_MAX_FEATURES", "AR_MAX_VARIANTS"]

@@ -1,5 +1,5 @@
 // Built-in loop table: variant counts, defaults, names and region launchers
-// for the four region bodies (ar_loops.h).
+// for the region bodies (ar_loops.h).
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -40,6 +40,7 @@ const LoopEntry* entry(int loop) {
       {jacobi7_num_variants, jacobi7_variant_name, jacobi7_launch, 1},
       {spmv_num_variants, spmv_variant_name, spmv_launch, 0},
       {nbody_num_variants, nbody_variant_name, nbody_launch, 3},
+      {heat7_num_variants, heat7_variant_name, heat7_launch, 1},
   };
   if (loop < 0 || loop >= (int)(sizeof table / sizeof table[0])) return nullptr;
   return &table[loop];

@@ -36,6 +36,9 @@ int daxpy_num_variants();
 int daxpy_variant_name(int v, char* buf, int len);
 int jacobi7_num_variants();
 int jacobi7_variant_name(int v, char* buf, int len);
+int heat7_launch(void* args, int variant, double value, void* stream, void* user);
+int heat7_num_variants();
+int heat7_variant_name(int v, char* buf, int len);
 int spmv_launch(void* args, int variant, double value, void* stream, void* user);
 int spmv_num_variants();
 int spmv_variant_name(int v, char* buf, int len);

@@ -43,9 +43,9 @@ constexpr int kShapeY[4] = {4, 8, 4, 2};
 const char* const kFamily[4] = {"naive", "smem", "tma", "df"};
 
 // ------------------------------------------------------------------ naive
-template <int BX, int BY>
+template <int BX, int BY, int ST>
 __global__ void __launch_bounds__(BX* BY) jacobi_naive(int N, const double* __restrict__ in,
-                                                       double* __restrict__ out) {
+                                                       double* __restrict__ out, StencilCoef cf) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z;
@@ -57,13 +57,13 @@ __global__ void __launch_bounds__(BX* BY) jacobi_naive(int N, const double* __re
   s += (j < N - 1 ? in[c + N] : 0.0);
   s += (k > 0 ? in[c - NN] : 0.0);
   s += (k < N - 1 ? in[c + NN] : 0.0);
-  out[c] = s * kSixth;
+  out[c] = stencil_f64<ST>(ST == kHeat ? in[c] : 0.0, s, cf);
 }
 
 // ------------------------------------------------------------------ 2.5D smem
-template <int BX, int BY>
+template <int BX, int BY, int ST>
 __global__ void __launch_bounds__(BX* BY) jacobi_smem(int N, int KC, const double* __restrict__ in,
-                                                      double* __restrict__ out) {
+                                                      double* __restrict__ out, StencilCoef cf) {
   __shared__ double tile[2][BY + 2][BX + 2];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int i = blockIdx.x * BX + tx, j = blockIdx.y * BY + ty;
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(BX* BY) jacobi_smem(int N, int KC, const doubl
       s += tile[b][ty + 2][tx + 1];
       s += below;
       s += above;
-      out[k * NN + col] = s * kSixth;
+      out[k * NN + col] = stencil_f64<ST>(cur, s, cf);
     }
     below = cur;
     cur = above;
@@ -128,11 +128,12 @@ enum Mode { M_NATIVE = 0, M_DD = 1, M_DP = 2, M_PP = 3, M_PD = 4 };
 // How a tma / df sweep stages its planes.
 enum Staging { kStageSmem = 0, kStageTma = 1, kStageRing = 2 };
 
-template <int BX, int BY, int MODE>
+template <int BX, int BY, int MODE, int ST>
 __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUtensorMap tmap,
                                                      const __grid_constant__ CUtensorMap tmap_alt, int N, int KC,
                                                      const double* __restrict__ in, void* __restrict__ outv,
-                                                     double* __restrict__ out_alt, int* status, int* flag) {
+                                                     double* __restrict__ out_alt, int* status, int* flag,
+                                                     StencilCoef cf) {
   using G = TmaGeom<BX, BY>;
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[kRing];
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
             s += pc[G::PX];
             s += dm;
             s += up;
-            if (inside) *od = s * kSixth;
+            if (inside) *od = stencil_f64<ST>(pc[0], s, cf);
             od += NN;
           }
           dm = d0;
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
           const float2* pc = reinterpret_cast<const float2*>(r == 0 ? prev : box) + cp;
           const float2 up = reinterpret_cast<const float2*>(box)[r * G::PLANE + c];
           if (live) {
-            const float2 res = df_avg6(pc[-1], pc[1], pc[-G::PX], pc[G::PX], fm, up);
+            const float2 res = stencil_pair<ST>(pc[0], pc[-1], pc[1], pc[-G::PX], pc[G::PX], fm, up, cf);
             if (inside) {
               if constexpr (MODE == M_DP || MODE == M_PP) {  // pairs out (the native case is above)
                 // stored unnormalised: the next sweep sums the hi parts exactly and
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
                   sd += at(in, N, i, j + 1, k);
                   sd += at(in, N, i, j, k - 1);
                   sd += at(in, N, i, j, k + 1);
-                  v = sd * kSixth;
+                  v = stencil_f64<ST>(at(in, N, i, j, k), sd, cf);
                 }
                 *od = v;
               }
@@ -303,29 +304,30 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
 // The df family when tensor copies cannot be used (odd N): each block streams
 // its column's planes through a shared-memory ring (jacobi_ring.cuh), in the
 // same sweep modes as jacobi_tma.
-template <int BX, int BY, int MODE>
+template <int BX, int BY, int MODE, int ST>
 __global__ void __launch_bounds__(BX* BY) jacobi_ring(int N, int KC, const double* __restrict__ in, void* outv,
-                                                      const double* __restrict__ in_alt, double* out_alt, int* flag) {
+                                                      const double* __restrict__ in_alt, double* out_alt, int* flag,
+                                                      StencilCoef cf) {
   extern __shared__ __align__(16) unsigned char ring_smem[];
   const int kb = blockIdx.z * KC, ke = min(N, kb + KC);
   // block-uniform: the flag was settled by an earlier launch on this stream
   const bool flagged = (MODE == M_PP || MODE == M_PD) && flag != nullptr && *flag != 0;
   if (flagged) {  // the previous sweep in float64, from the float64 data
-    jacobi_ring_tile(N, BX, BY, blockIdx.x, blockIdx.y, kb, ke, in_alt, out_alt, false, false, false, nullptr,
-                     ring_smem);
+    jacobi_ring_tile<ST>(N, BX, BY, blockIdx.x, blockIdx.y, kb, ke, in_alt, out_alt, false, false, false, nullptr,
+                         ring_smem, cf);
     return;
   }
   constexpr bool src_pairs = MODE == M_PP || MODE == M_PD;
   constexpr bool dst_pairs = MODE == M_DP || MODE == M_PP;
-  jacobi_ring_tile(N, BX, BY, blockIdx.x, blockIdx.y, kb, ke, in, static_cast<double*>(outv), MODE != M_NATIVE,
-                   src_pairs, dst_pairs, MODE == M_DP ? flag : nullptr, ring_smem);
+  jacobi_ring_tile<ST>(N, BX, BY, blockIdx.x, blockIdx.y, kb, ke, in, static_cast<double*>(outv), MODE != M_NATIVE,
+                       src_pairs, dst_pairs, MODE == M_DP ? flag : nullptr, ring_smem, cf);
 }
 
 // ------------------------------------------------------------------ host side
-template <int BX, int BY>
-int launch_naive(int N, const double* in, double* out, cudaStream_t s) {
+template <int BX, int BY, int ST>
+int launch_naive(int N, const double* in, double* out, const StencilCoef& cf, cudaStream_t s) {
   dim3 grid((unsigned)ceil_div(N, BX), (unsigned)ceil_div(N, BY), (unsigned)N);
-  jacobi_naive<BX, BY><<<grid, dim3(BX, BY), 0, s>>>(N, in, out);
+  jacobi_naive<BX, BY, ST><<<grid, dim3(BX, BY), 0, s>>>(N, in, out, cf);
   return launch_status();
 }
 
@@ -338,12 +340,12 @@ inline int chunk_planes(int N, int64_t colblocks, int resident_per_sm, int lo, i
   return (int)kc;
 }
 
-template <int BX, int BY>
-int launch_smem(int N, const double* in, double* out, cudaStream_t s) {
+template <int BX, int BY, int ST>
+int launch_smem(int N, const double* in, double* out, const StencilCoef& cf, cudaStream_t s) {
   const int64_t cb = ceil_div(N, BX) * ceil_div(N, BY);
   const int KC = chunk_planes(N, cb, 2048 / (BX * BY), 4, 1 << 30);
   dim3 grid((unsigned)ceil_div(N, BX), (unsigned)ceil_div(N, BY), (unsigned)ceil_div(N, KC));
-  jacobi_smem<BX, BY><<<grid, dim3(BX, BY), 0, s>>>(N, KC, in, out);
+  jacobi_smem<BX, BY, ST><<<grid, dim3(BX, BY), 0, s>>>(N, KC, in, out, cf);
   return launch_status();
 }
 
@@ -357,8 +359,10 @@ bool tma_usable(int shape, int N, const void* a, const void* b, const void* c) {
 
 // Float64 sweep of the flagged pair chain's last step: does nothing unless
 // the first sweep flagged an input outside the float-pair range.
+template <int ST>
 __global__ void __launch_bounds__(256) jacobi_catchup(int N, const int* __restrict__ flag,
-                                                      const double* __restrict__ in, double* __restrict__ out) {
+                                                      const double* __restrict__ in, double* __restrict__ out,
+                                                      StencilCoef cf) {
   if (*flag == 0) return;
   const int64_t n3 = (int64_t)N * N * N, NN = (int64_t)N * N;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n3; c += (int64_t)gridDim.x * blockDim.x) {
@@ -368,18 +372,18 @@ __global__ void __launch_bounds__(256) jacobi_catchup(int N, const int* __restri
     s += at(in, N, i, j + 1, k);
     s += at(in, N, i, j, k - 1);
     s += at(in, N, i, j, k + 1);
-    out[c] = s * kSixth;
+    out[c] = stencil_f64<ST>(in[c], s, cf);
   }
 }
 
-template <int BX, int BY, int MODE>
+template <int BX, int BY, int MODE, int ST>
 int launch_tma(int N, const double* in, void* out, const double* in_alt, double* out_alt, int* status, int* flag,
-               cudaStream_t s) {
+               const StencilCoef& cf, cudaStream_t s) {
   using G = TmaGeom<BX, BY>;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(jacobi_tma<BX, BY, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr_err = cudaFuncSetAttribute(jacobi_tma<BX, BY, MODE, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)G::SMEM);
   });
   if (attr_err != cudaSuccess) return AR_ERR_CUDA;
@@ -396,13 +400,14 @@ int launch_tma(int N, const double* in, void* out, const double* in_alt, double*
   int KC = chunk_planes(N, cb, resident, kDZ - 2, 8 * kDZ - 2);
   KC = (int)(ceil_div(KC + 2, kDZ) * kDZ - 2);
   dim3 grid((unsigned)ceil_div(N, BX), (unsigned)ceil_div(N, BY), (unsigned)ceil_div(N, KC));
-  jacobi_tma<BX, BY, MODE><<<grid, BX * BY, G::SMEM, s>>>(map, map_alt, N, KC, in, out, out_alt, status, flag);
+  jacobi_tma<BX, BY, MODE, ST><<<grid, BX * BY, G::SMEM, s>>>(map, map_alt, N, KC, in, out, out_alt, status, flag,
+                                                               cf);
   return launch_status();
 }
 
-template <int BX, int BY, int MODE>
+template <int BX, int BY, int MODE, int ST>
 int launch_ring(int N, const double* in, void* out, const double* in_alt, double* out_alt, int* flag,
-                cudaStream_t s) {
+                const StencilCoef& cf, cudaStream_t s) {
   constexpr int smem = ring_smem_bytes(BX, BY);
   static_assert(smem <= 48 * 1024, "ring fits the default dynamic shared memory");
   static_assert((BX + 4) / 2 * (BY + 2) <= kRingChunks * BX * BY, "a plane's chunks fit kRingChunks per thread");
@@ -411,40 +416,41 @@ int launch_ring(int N, const double* in, void* out, const double* in_alt, double
   if (resident > 2048 / (BX * BY)) resident = 2048 / (BX * BY);
   const int KC = chunk_planes(N, cb, resident, 8, 64);
   dim3 grid((unsigned)ceil_div(N, BX), (unsigned)ceil_div(N, BY), (unsigned)ceil_div(N, KC));
-  jacobi_ring<BX, BY, MODE><<<grid, BX * BY, smem, s>>>(N, KC, in, out, in_alt, out_alt, flag);
+  jacobi_ring<BX, BY, MODE, ST><<<grid, BX * BY, smem, s>>>(N, KC, in, out, in_alt, out_alt, flag, cf);
   return launch_status();
 }
 
-template <int BX, int BY>
+template <int BX, int BY, int ST>
 int launch_family(int fam, int mode, int staging, int N, const double* in, double* out, const double* in_alt,
-                  double* out_alt, int* status, int* flag, cudaStream_t s) {
-  if (fam == 0) return launch_naive<BX, BY>(N, in, out, s);
+                  double* out_alt, int* status, int* flag, const StencilCoef& cf, cudaStream_t s) {
+  if (fam == 0) return launch_naive<BX, BY, ST>(N, in, out, cf, s);
   if (fam == 3 && staging == kStageRing) {
     switch (mode) {
-      case M_DD: return launch_ring<BX, BY, M_DD>(N, in, out, nullptr, nullptr, nullptr, s);
-      case M_DP: return launch_ring<BX, BY, M_DP>(N, in, out, nullptr, nullptr, flag, s);
-      case M_PP: return launch_ring<BX, BY, M_PP>(N, in, out, in_alt, out_alt, flag, s);
-      default: return launch_ring<BX, BY, M_PD>(N, in, out, in_alt, out_alt, flag, s);
+      case M_DD: return launch_ring<BX, BY, M_DD, ST>(N, in, out, nullptr, nullptr, nullptr, cf, s);
+      case M_DP: return launch_ring<BX, BY, M_DP, ST>(N, in, out, nullptr, nullptr, flag, cf, s);
+      case M_PP: return launch_ring<BX, BY, M_PP, ST>(N, in, out, in_alt, out_alt, flag, cf, s);
+      default: return launch_ring<BX, BY, M_PD, ST>(N, in, out, in_alt, out_alt, flag, cf, s);
     }
   }
-  if (fam == 1 || staging != kStageTma) return launch_smem<BX, BY>(N, in, out, s);
+  if (fam == 1 || staging != kStageTma) return launch_smem<BX, BY, ST>(N, in, out, cf, s);
   switch (mode) {
-    case M_NATIVE: return launch_tma<BX, BY, M_NATIVE>(N, in, out, nullptr, nullptr, status, nullptr, s);
-    case M_DD: return launch_tma<BX, BY, M_DD>(N, in, out, nullptr, nullptr, status, nullptr, s);
-    case M_DP: return launch_tma<BX, BY, M_DP>(N, in, out, nullptr, nullptr, status, flag, s);
-    case M_PP: return launch_tma<BX, BY, M_PP>(N, in, out, in_alt, out_alt, status, flag, s);
-    default: return launch_tma<BX, BY, M_PD>(N, in, out, in_alt, out_alt, status, flag, s);
+    case M_NATIVE: return launch_tma<BX, BY, M_NATIVE, ST>(N, in, out, nullptr, nullptr, status, nullptr, cf, s);
+    case M_DD: return launch_tma<BX, BY, M_DD, ST>(N, in, out, nullptr, nullptr, status, nullptr, cf, s);
+    case M_DP: return launch_tma<BX, BY, M_DP, ST>(N, in, out, nullptr, nullptr, status, flag, cf, s);
+    case M_PP: return launch_tma<BX, BY, M_PP, ST>(N, in, out, in_alt, out_alt, status, flag, cf, s);
+    default: return launch_tma<BX, BY, M_PD, ST>(N, in, out, in_alt, out_alt, status, flag, cf, s);
   }
 }
 
+template <int ST>
 int sweep(int variant, int mode, int staging, int N, const double* in, double* out, const double* in_alt,
-          double* out_alt, int* status, int* flag, cudaStream_t s) {
+          double* out_alt, int* status, int* flag, const StencilCoef& cf, cudaStream_t s) {
   const int fam = variant / 4;
   switch (variant % 4) {
-    case 0: return launch_family<32, 4>(fam, mode, staging, N, in, out, in_alt, out_alt, status, flag, s);
-    case 1: return launch_family<32, 8>(fam, mode, staging, N, in, out, in_alt, out_alt, status, flag, s);
-    case 2: return launch_family<64, 4>(fam, mode, staging, N, in, out, in_alt, out_alt, status, flag, s);
-    default: return launch_family<128, 2>(fam, mode, staging, N, in, out, in_alt, out_alt, status, flag, s);
+    case 0: return launch_family<32, 4, ST>(fam, mode, staging, N, in, out, in_alt, out_alt, status, flag, cf, s);
+    case 1: return launch_family<32, 8, ST>(fam, mode, staging, N, in, out, in_alt, out_alt, status, flag, cf, s);
+    case 2: return launch_family<64, 4, ST>(fam, mode, staging, N, in, out, in_alt, out_alt, status, flag, cf, s);
+    default: return launch_family<128, 2, ST>(fam, mode, staging, N, in, out, in_alt, out_alt, status, flag, cf, s);
   }
 }
 
@@ -487,11 +493,26 @@ int jacobi7_launch(void* args, int variant, double, void* stream, void*) {
   return ar_jacobi7(variant, a->N, a->sweeps, a->u0, a->out, a->work, a->status, stream);
 }
 
-}  // namespace ar
+int heat7_num_variants() { return kJacobiVariants; }
 
-extern "C" int ar_jacobi7(int variant, int N, int sweeps, const double* u0, double* out, double* work,
-                          int* status, void* stream) {
-  using namespace ar;
+int heat7_variant_name(int v, char* buf, int len) {
+  if (v < 0 || v >= kJacobiVariants || !buf || len <= 0) return AR_ERR_ARG;
+  snprintf(buf, (size_t)len, "heat7_%s_%dx%d", kFamily[v / 4], kShapeX[v % 4], kShapeY[v % 4]);
+  return AR_OK;
+}
+
+int heat7_launch(void* args, int variant, double, void* stream, void*) {
+  const ar_heat7_args* a = static_cast<const ar_heat7_args*>(args);
+  if (!a) return AR_ERR_ARG;
+  return ar_heat7(variant, a->N, a->steps, a->alpha, a->u0, a->out, a->work, a->status, stream);
+}
+
+namespace {
+
+// `sweeps` applications of stencil ST from u0, the last one landing in out.
+template <int ST>
+int stencil_run(int variant, int N, int sweeps, const StencilCoef& cf, const double* u0, double* out, double* work,
+                int* status, void* stream) {
   if (variant < 0 || variant >= kJacobiVariants || N < 0 || sweeps < 0 || N > 65535) return AR_ERR_ARG;
   if (N == 0) return AR_OK;
   if (!u0 || !out || (sweeps > 1 && !work)) return AR_ERR_ARG;
@@ -537,13 +558,31 @@ extern "C" int ar_jacobi7(int variant, int N, int sweeps, const double* u0, doub
         alt_dst = dst_of(sw - 1);
       }
     }
-    const int rc = sweep(variant, mode, staging, N, src, dst, alt_src, alt_dst, status, flag, s);
+    const int rc = sweep<ST>(variant, mode, staging, N, src, dst, alt_src, alt_dst, status, flag, cf, s);
     if (rc != AR_OK) return rc;
   }
   if (flag) {
     const double* src = sweeps >= 2 ? dst_of(sweeps - 2) : u0;
-    jacobi_catchup<<<device_sms() * 4, 256, 0, s>>>(N, flag, src, dst_of(sweeps - 1));
+    jacobi_catchup<ST><<<device_sms() * 4, 256, 0, s>>>(N, flag, src, dst_of(sweeps - 1), cf);
     return launch_status();
   }
   return AR_OK;
+}
+
+}  // namespace
+}  // namespace ar
+
+extern "C" int ar_jacobi7(int variant, int N, int sweeps, const double* u0, double* out, double* work,
+                          int* status, void* stream) {
+  return ar::stencil_run<ar::kJacobi>(variant, N, sweeps, ar::StencilCoef{0.0, 0.f, 0.f}, u0, out, work, status,
+                                      stream);
+}
+
+extern "C" int ar_heat7(int variant, int N, int steps, double alpha, const double* u0, double* out, double* work,
+                        int* status, void* stream) {
+  if (!(alpha >= 0.0 && alpha <= 1.0)) return AR_ERR_ARG;  // NaN fails too
+  const float ahi = (float)alpha;
+  const float alo = (float)(alpha - (double)ahi);
+  return ar::stencil_run<ar::kHeat>(variant, N, steps, ar::StencilCoef{alpha, ahi, alo}, u0, out, work, status,
+                                    stream);
 }

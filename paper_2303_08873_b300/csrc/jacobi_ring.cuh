@@ -29,15 +29,18 @@ constexpr int kRingChunks = 2;  // 16-byte chunks per thread and plane, at most 
 // Shared memory of the ring for a BX x BY tile.
 __host__ __device__ constexpr int ring_smem_bytes(int BX, int BY) { return kRingPlanes * (BX + 4) * (BY + 2) * 8; }
 
-// src: float64 (pair_math false, or src_pairs false) or float pairs; dst:
-// float pairs if dst_pairs, else float64.  Threads: blockDim.x >= BX * BY
+// ST: the stencil (stencil_f64 / stencil_pair of pairs.cuh) with its
+// coefficients cf.  src: float64 (pair_math false, or src_pairs false) or
+// float pairs; dst: float pairs if dst_pairs, else float64.  Threads: blockDim.x >= BX * BY
 // and 2 * blockDim.x >= (BX + 4) (BY + 2) / 2 (the chunks of one plane).
 // A float-pair sweep with float64 input and float64 output redoes in float64
 // every point whose inputs lie outside the float-pair range; with pairs out,
 // such inputs set *flag instead.  Buffers 16-byte aligned.
+template <int ST>
 __device__ __forceinline__ void jacobi_ring_tile(int N, int BX, int BY, int bx, int by, int kb, int ke,
                                                  const double* src, double* dst, bool pair_math, bool src_pairs,
-                                                 bool dst_pairs, int* flag, unsigned char* smraw) {
+                                                 bool dst_pairs, int* flag, unsigned char* smraw,
+                                                 const StencilCoef& cf) {
   const int nthr = blockDim.x;
   const int i0 = bx * BX, j0 = by * BY;
   const int PX = BX + 4, PL = PX * (BY + 2);
@@ -154,10 +157,10 @@ __device__ __forceinline__ void jacobi_ring_tile(int N, int BX, int BY, int bx, 
         s += r[cn];
         s += r[cb];
         s += r[ca];
-        dst[outo] = s * kSixth;
+        dst[outo] = stencil_f64<ST>(r[c0], s, cf);
       } else {
         const float2* r = reinterpret_cast<const float2*>(ring);
-        const float2 res = df_avg6(r[c0 - 1], r[c0 + 1], r[cs], r[cn], r[cb], r[ca]);
+        const float2 res = stencil_pair<ST>(r[c0], r[c0 - 1], r[c0 + 1], r[cs], r[cn], r[cb], r[ca], cf);
         if (dst_pairs) {
           reinterpret_cast<float2*>(dst)[outo] = res;
         } else {
@@ -175,7 +178,7 @@ __device__ __forceinline__ void jacobi_ring_tile(int N, int BX, int BY, int bx, 
             sd += g(i, j + 1, kk);
             sd += g(i, j, kk - 1);
             sd += g(i, j, kk + 1);
-            dv = sd * kSixth;
+            dv = stencil_f64<ST>(g(i, j, kk), sd, cf);
           }
           dst[outo] = dv;
         }

@@ -68,12 +68,12 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
-// (v0 + ... + v5) / 6 in float-pair arithmetic: returns the unevaluated
-// pair (p, pe) with p + pe = the average to ~2^-46 relative.  The hi parts
-// are summed exactly by a TwoSum chain, the lo parts and the chain's errors
-// in plain float, then the sum is multiplied by 1/6 as a float pair.
-__device__ __forceinline__ float2 df_avg6(float2 v0, float2 v1, float2 v2, float2 v3, float2 v4, float2 v5) {
-  float s, c, e;
+// v0 + ... + v5 in float-pair arithmetic as the unevaluated pair (s, c): the
+// hi parts are summed exactly by a TwoSum chain, the chain's errors and the
+// lo parts in plain float.
+__device__ __forceinline__ void df_sum6(float2 v0, float2 v1, float2 v2, float2 v3, float2 v4, float2 v5, float& s,
+                                        float& c) {
+  float e;
   two_sum(v0.x, v1.x, s, c);
   two_sum(s, v2.x, s, e);
   c += e;
@@ -84,11 +84,69 @@ __device__ __forceinline__ float2 df_avg6(float2 v0, float2 v1, float2 v2, float
   two_sum(s, v5.x, s, e);
   c += e;
   c += ((v0.y + v1.y) + (v2.y + v3.y)) + (v4.y + v5.y);
+}
+
+// (v0 + ... + v5) / 6 in float-pair arithmetic: returns the unevaluated
+// pair (p, pe) with p + pe = the average to ~2^-46 relative; the sum is
+// multiplied by 1/6 as a float pair.
+__device__ __forceinline__ float2 df_avg6(float2 v0, float2 v1, float2 v2, float2 v3, float2 v4, float2 v5) {
+  float s, c;
+  df_sum6(v0, v1, v2, v3, v4, v5, s, c);
   const float p = s * kSixthHi;
   float pe = fmaf(s, kSixthHi, -p);
   pe = fmaf(s, kSixthLo, pe);
   pe = fmaf(c, kSixthHi, pe);
   return make_float2(p, pe);
+}
+
+// u + alpha (v0 + ... + v5 - 6 u), the explicit heat update, in float-pair
+// arithmetic with alpha = ahi + alo: d = sum - 6u by TwoSum (6 u.x's
+// rounding error recovered by FMA), alpha d as a pair product, u + alpha d
+// by TwoSum; absolute error ~2^-46 (|u| + |alpha| sum |v|).
+__device__ __forceinline__ float2 df_heat(float2 u, float2 v0, float2 v1, float2 v2, float2 v3, float2 v4, float2 v5,
+                                          float ahi, float alo) {
+  float s, c;
+  df_sum6(v0, v1, v2, v3, v4, v5, s, c);
+  const float p6 = 6.f * u.x;
+  const float p6e = fmaf(6.f, u.x, -p6) + 6.f * u.y;
+  float d, de;
+  two_sum(s, -p6, d, de);
+  de += c - p6e;
+  const float q = ahi * d;
+  float qe = fmaf(ahi, d, -q);
+  qe = fmaf(alo, d, qe);
+  qe = fmaf(ahi, de, qe);
+  float r, f;
+  two_sum(u.x, q, r, f);
+  f += u.y + qe;
+  return make_float2(r, f);
+}
+
+// The two 7-point stencils: the Jacobi average (W + E + S + N + D + U) / 6
+// and the explicit heat step u + alpha (W + E + S + N + D + U - 6 u).
+enum Stencil { kJacobi = 0, kHeat = 1 };
+struct StencilCoef {
+  double alpha;    // heat: the step's alpha = kappa dt / h^2
+  float ahi, alo;  // alpha as a float pair
+};
+
+// float64 form; s = W + E + S + N + D + U summed in that order, u the centre
+template <int ST>
+__device__ __forceinline__ double stencil_f64(double u, double s, const StencilCoef& k) {
+  if constexpr (ST == kJacobi)
+    return s * kSixth;
+  else
+    return u + k.alpha * (s - 6.0 * u);
+}
+
+// float-pair form of the same update
+template <int ST>
+__device__ __forceinline__ float2 stencil_pair(float2 u, float2 w, float2 e, float2 so, float2 no, float2 d,
+                                               float2 up, const StencilCoef& k) {
+  if constexpr (ST == kJacobi)
+    return df_avg6(w, e, so, no, d, up);
+  else
+    return df_heat(u, w, e, so, no, d, up, k.ahi, k.alo);
 }
 
 __device__ __forceinline__ double pair_to_double(float2 v) { return f2d_bits(v.x) + f2d_bits(v.y); }

@@ -6,6 +6,7 @@ the mean time per launch (CUDA events) and the algorithmic bandwidth or flop
 rate.
 
   python -m paper_2303_08873_b300.run_variant jacobi7 13 --size 320 --sweeps 1
+  python -m paper_2303_08873_b300.run_variant heat7 13 --size 320 --sweeps 10 --alpha 0.125
   python -m paper_2303_08873_b300.run_variant spmv 6 --size 2000000
   python -m paper_2303_08873_b300.run_variant nbody 4 --size 65536
   python -m paper_2303_08873_b300.run_variant daxpy 8 --size 33554432
@@ -26,20 +27,23 @@ import paper_2303_08873_b300 as ar
 import synth
 
 
-LOOPS = ["daxpy", "jacobi7", "spmv", "nbody"]
+LOOPS = ["daxpy", "jacobi7", "spmv", "nbody", "heat7"]  # index = loop id
 
 
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("loop", choices=LOOPS)
     p.add_argument("variant", help="variant index, or 'all' for every variant of the loop in turn")
-    p.add_argument("--size", type=int, required=True, help="n (daxpy), N (jacobi7, nbody) or rows (spmv)")
-    p.add_argument("--sweeps", type=int, default=1)
+    p.add_argument("--size", type=int, required=True, help="n (daxpy), N (jacobi7, heat7, nbody) or rows (spmv)")
+    p.add_argument("--sweeps", type=int, default=1, help="jacobi7 sweeps / heat7 steps")
+    p.add_argument("--alpha", type=float, default=0.125, help="heat7: alpha of the explicit step")
     p.add_argument("--reps", type=int, default=3)
     p.add_argument("--zipf", type=float, default=1.5, help="Zipf exponent of the spmv row lengths")
     p.add_argument("--band", type=int, default=0, help="spmv: banded matrix of this (odd) width instead of Zipf")
     p.add_argument("--exec", action="store_true", help="also time the call through the executor (one-call batch)")
     a = p.parse_args()
+    if a.exec and a.loop == "heat7":
+        raise SystemExit("--exec: the executor runs daxpy, jacobi7, spmv and nbody only")
     L = LOOPS.index(a.loop)
     variants = range(ar.loop_num_variants(L)) if a.variant == "all" else [int(a.variant)]
     dev = torch.device("cuda", 0)
@@ -57,6 +61,13 @@ def main():
         make_run = lambda var: lambda: ar.ar_jacobi7(var, a.size, a.sweeps, u0, out, wk, st)  # noqa: E731
         call = ar.ArExecCall(loop=1, n=a.size, sweeps=a.sweeps, in0=u0.data_ptr(), out0=out.data_ptr(),
                              out1=wk.data_ptr())
+        work, unit = 16.0 * a.size ** 3 * a.sweeps, "GB/s"
+    elif a.loop == "heat7":
+        u0 = torch.from_numpy(synth.grid_inputs(2000 + a.size, a.size)).to(dev)
+        out, wk = torch.empty_like(u0), torch.empty_like(u0)
+        st = torch.zeros(2, dtype=torch.int32, device=dev)
+        make_run = lambda var: lambda: ar.ar_heat7(var, a.size, a.sweeps, a.alpha, u0, out, wk, st)  # noqa: E731
+        call = None
         work, unit = 16.0 * a.size ** 3 * a.sweeps, "GB/s"
     elif a.loop == "spmv":
         if a.band:

@@ -273,6 +273,10 @@ def test_loop_tables():
     assert ar.loop_variant_name(ar.AR_LOOP_JACOBI7, 1) == "jacobi7_naive_32x8"
     r = ar.Region("j", 2)
     assert r.add_builtin(ar.AR_LOOP_JACOBI7) == 16
+    assert ar.loop_num_variants(ar.AR_LOOP_HEAT7) == 16
+    assert ar.loop_default_variant(ar.AR_LOOP_HEAT7) == 1
+    assert ar.loop_variant_name(ar.AR_LOOP_HEAT7, 13) == "heat7_df_32x8"
+    assert ar.Region("h", 2).add_builtin(ar.AR_LOOP_HEAT7) == 16
     with pytest.raises(ar.ArError):
         ar.loop_num_variants(17)
 
@@ -285,6 +289,10 @@ def test_kernel_entry_points_validate_before_launch():
     assert ar.lib.ar_daxpy(0, 0, 1.0, None, None, None) == 0  # empty: nothing launched
     assert ar.lib.ar_daxpy(1, 4, 1.0, 8, 16, None) == ar.AR_ERR_ARG  # misaligned double2
     assert ar.lib.ar_jacobi7(0, 8, 1, 64, 64, 128, None, None) == ar.AR_ERR_ARG  # aliasing
+    assert ar.lib.ar_heat7(0, 8, 1, 0.1, 64, 64, 128, None, None) == ar.AR_ERR_ARG  # aliasing
+    for bad in (-0.01, 1.5, float("nan"), float("inf")):  # alpha outside [0, 1]
+        assert ar.lib.ar_heat7(0, 8, 1, bad, 64, 128, 192, None, None) == ar.AR_ERR_ARG
+    assert ar.lib.ar_heat7(0, 0, 3, 0.1, None, None, None, None, None) == 0  # empty grid
     assert ar.lib.ar_mlp_num_params(5, 64, 7) == 5 * 64 + 64 + 64 * 64 + 64 + 7 * 64 + 7
     assert ar.lib.ar_mlp_num_params(5, 48, 7) == ar.AR_ERR_ARG
 
