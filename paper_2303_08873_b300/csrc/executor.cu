@@ -355,7 +355,7 @@ __device__ void jacobi_sweep_tile(const ar_exec_call& k, int v, int64_t t, const
   }
   if (((uintptr_t)src | (uintptr_t)dst) % 16 == 0) {
     jacobi_ring_tile<kJacobi>(N, BX, BY, bx, by, kb, ke, src, dst, pair_math, src_pairs, dst_pairs, flag, smraw,
-                              StencilCoef{0.0, 0.f, 0.f});
+                              StencilCoef{0.0, 0.f, 0.f, 0.f, 0.f});
     return;
   }
   // buffers not 16-byte aligned: global loads, those of 4 planes issued together

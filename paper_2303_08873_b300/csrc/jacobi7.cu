@@ -574,15 +574,15 @@ int stencil_run(int variant, int N, int sweeps, const StencilCoef& cf, const dou
 
 extern "C" int ar_jacobi7(int variant, int N, int sweeps, const double* u0, double* out, double* work,
                           int* status, void* stream) {
-  return ar::stencil_run<ar::kJacobi>(variant, N, sweeps, ar::StencilCoef{0.0, 0.f, 0.f}, u0, out, work, status,
-                                      stream);
+  return ar::stencil_run<ar::kJacobi>(variant, N, sweeps, ar::StencilCoef{0.0, 0.f, 0.f, 0.f, 0.f}, u0, out, work,
+                                      status, stream);
 }
 
 extern "C" int ar_heat7(int variant, int N, int steps, double alpha, const double* u0, double* out, double* work,
                         int* status, void* stream) {
   if (!(alpha >= 0.0 && alpha <= 1.0)) return AR_ERR_ARG;  // NaN fails too
-  const float ahi = (float)alpha;
-  const float alo = (float)(alpha - (double)ahi);
-  return ar::stencil_run<ar::kHeat>(variant, N, steps, ar::StencilCoef{alpha, ahi, alo}, u0, out, work, status,
-                                    stream);
+  const double beta = 1.0 - 6.0 * alpha;
+  const float ahi = (float)alpha, bhi = (float)beta;
+  const ar::StencilCoef cf{alpha, ahi, (float)(alpha - (double)ahi), bhi, (float)(beta - (double)bhi)};
+  return ar::stencil_run<ar::kHeat>(variant, N, steps, cf, u0, out, work, status, stream);
 }

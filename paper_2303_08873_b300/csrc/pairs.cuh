@@ -100,26 +100,26 @@ __device__ __forceinline__ float2 df_avg6(float2 v0, float2 v1, float2 v2, float
 }
 
 // u + alpha (v0 + ... + v5 - 6 u), the explicit heat update, in float-pair
-// arithmetic with alpha = ahi + alo: d = sum - 6u by TwoSum (6 u.x's
-// rounding error recovered by FMA), alpha d as a pair product, u + alpha d
-// by TwoSum; absolute error ~2^-46 (|u| + |alpha| sum |v|).
+// arithmetic as beta u + alpha sum with beta = 1 - 6 alpha: alpha = ahi + alo
+// and beta = bhi + blo are float pairs, each product a pair product (the lo x
+// lo term dropped), the two summed by TwoSum; absolute error ~2^-46 (|beta|
+// |u| + |alpha| sum |v|), at most ~2^-46 max |v| for 0 <= alpha <= 1/6.
 __device__ __forceinline__ float2 df_heat(float2 u, float2 v0, float2 v1, float2 v2, float2 v3, float2 v4, float2 v5,
-                                          float ahi, float alo) {
+                                          float ahi, float alo, float bhi, float blo) {
   float s, c;
   df_sum6(v0, v1, v2, v3, v4, v5, s, c);
-  const float p6 = 6.f * u.x;
-  const float p6e = fmaf(6.f, u.x, -p6) + 6.f * u.y;
-  float d, de;
-  two_sum(s, -p6, d, de);
-  de += c - p6e;
-  const float q = ahi * d;
-  float qe = fmaf(ahi, d, -q);
-  qe = fmaf(alo, d, qe);
-  qe = fmaf(ahi, de, qe);
-  float r, f;
-  two_sum(u.x, q, r, f);
-  f += u.y + qe;
-  return make_float2(r, f);
+  const float q = ahi * s;
+  float qe = fmaf(ahi, s, -q);
+  qe = fmaf(alo, s, qe);
+  qe = fmaf(ahi, c, qe);
+  const float r = bhi * u.x;
+  float re = fmaf(bhi, u.x, -r);
+  re = fmaf(blo, u.x, re);
+  re = fmaf(bhi, u.y, re);
+  float h, e;
+  two_sum(q, r, h, e);
+  e += qe + re;
+  return make_float2(h, e);
 }
 
 // The two 7-point stencils: the Jacobi average (W + E + S + N + D + U) / 6
@@ -128,6 +128,7 @@ enum Stencil { kJacobi = 0, kHeat = 1 };
 struct StencilCoef {
   double alpha;    // heat: the step's alpha = kappa dt / h^2
   float ahi, alo;  // alpha as a float pair
+  float bhi, blo;  // 1 - 6 alpha as a float pair
 };
 
 // float64 form; s = W + E + S + N + D + U summed in that order, u the centre
@@ -146,7 +147,7 @@ __device__ __forceinline__ float2 stencil_pair(float2 u, float2 w, float2 e, flo
   if constexpr (ST == kJacobi)
     return df_avg6(w, e, so, no, d, up);
   else
-    return df_heat(u, w, e, so, no, d, up, k.ahi, k.alo);
+    return df_heat(u, w, e, so, no, d, up, k.ahi, k.alo, k.bhi, k.blo);
 }
 
 __device__ __forceinline__ double pair_to_double(float2 v) { return f2d_bits(v.x) + f2d_bits(v.y); }
