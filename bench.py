@@ -778,7 +778,7 @@ def run_mixed(args):
     regions, keep = {}, []
     models = ar.ArExecModels()
     models.H = 64
-    nfeat = {0: 1, 1: 2, 2: 5, 3: 1}
+    nfeat = {0: 1, 1: 3, 2: 5, 3: 1}  # the executor's features per loop (ar_loops.h)
     prof_ns = 0.0
     t0w = time.perf_counter()
     for L in range(4):

@@ -210,8 +210,9 @@ int ar_nbody_batched(int count, const int32_t *offs, const float *pos4, float *a
  * Persistent execution of a batch of region invocations of the four loops
  * (up to AR_EXEC_MAX_CALLS per batch) in three launches on `stream`:
  *   1. features: per call, the selector's features (daxpy: n; Jacobi: N,
- *      sweeps; SpMV: rows, nnz, mean, variance, max of the row lengths,
- *      reduced from rowptr on the device; n-body: N);
+ *      sweeps, 1 if N is even else 0 (a 16-byte row pitch, which tensor
+ *      copies need); SpMV: rows, nnz, mean, variance, max of the row
+ *      lengths, reduced from rowptr on the device; n-body: N);
  *   2. plan (one block): per call, the variant -- force_variant[c] if given,
  *      else the argmax of the loop's MLP (models->theta[loop]; the loop's
  *      default variant if that is NULL) with its confidence -- and the
@@ -223,9 +224,16 @@ int ar_nbody_batched(int count, const int32_t *offs, const float *pos4, float *a
  *      done; items are handed out phase-major, so every awaited item was
  *      handed out earlier.
  * The tiles compute exactly what the stand-alone variants compute (same
- * data, same tolerances); the tma family runs the smem tile inside the
- * executor.  EPT 2/4 daxpy variants on buffers that are not 16-byte aligned
- * run with one element per thread.
+ * data, same tolerances).  Jacobi tiles of the tma and df families with
+ * shapes 32x4 and 32x8 stage their planes by tensor copies when N is even,
+ * N >= 36 and u0/out/work are 16-byte aligned (through tensor maps the plan
+ * kernel makes on the device from host-encoded templates; the first batch
+ * of a process checks, once and synchronously on `stream`, that a
+ * device-made map equals the host encoding, and uses the cp.async plane ring
+ * instead while the check fails or while `stream` is capturing before it
+ * ran); the other Jacobi tiles stream planes by cp.async.  EPT 2/4 daxpy
+ * variants on buffers that are not 16-byte aligned run with one element per
+ * thread.
  * All arrays are device memory.  Per call c: variant[c], conf[c] (1 when
  * forced or defaulted), features[8c..8c+7], t_start[c] / t_end[c] (%globaltimer
  * ns of the first tile's start and the last tile's end), status[c] (AR_OK,
@@ -237,7 +245,7 @@ int ar_nbody_batched(int count, const int32_t *offs, const float *pos4, float *a
  * synchronisation and can be captured in a CUDA graph together with the copy
  * that refreshes `calls` (a captured graph replays on the stream it is
  * launched on, which must be the one other batches using the workspace run
- * on). */
+ * on); the one exception is the first batch's tensor-map check above. */
 #define AR_EXEC_MAX_CALLS 256
 #define AR_EXEC_MAX_PHASES 64
 typedef struct ar_exec_call {
@@ -253,7 +261,7 @@ typedef struct ar_exec_call {
   uint64_t out1_bytes;               /* SpMV: merge-path workspace bytes (16 per 4096 rows+nnz) */
 } ar_exec_call;
 typedef struct ar_exec_models {
-  int32_t F[4], V[4], H; /* per loop: features, variants (must match the loop); hidden width 32/64 */
+  int32_t F[4], V[4], H; /* per loop: features (1, 3, 5, 1), variants (must match the loop); hidden 32/64 */
   const float *theta[4], *mu[4], *sd[4];
 } ar_exec_models;
 int ar_exec_workspace_bytes(int max_calls, size_t *bytes);

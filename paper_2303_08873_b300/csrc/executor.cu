@@ -9,7 +9,12 @@
 // blocks that are already running; the wait is bounded and reports
 // AR_ERR_TIMEOUT per call.  Data written inside this launch (Jacobi sweeps,
 // merge-path carries) are read with L1-bypassing loads (ld.global.cg).
+#include <cudaTypedefs.h>
+
 #include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 #include "merge_path.cuh"
@@ -36,7 +41,7 @@ static_assert(mp::kThreads == T, "merge-path tiles use the executor's block size
 
 __constant__ int c_nvar[4] = {kDaxpyVariants, kJacobiVariants, kSpmvVariants, kNbodyVariants};
 __constant__ int c_default[4] = {6, 1, 0, 3};
-__constant__ int c_nfeat[4] = {1, 2, 5, 1};
+__constant__ int c_nfeat[4] = {1, 3, 5, 1};
 __constant__ int c_dx_block[5] = {64, 128, 256, 512, 1024};
 __constant__ int c_dx_ept[3] = {1, 2, 4};
 __constant__ int c_j_bx[4] = {32, 32, 64, 128};
@@ -137,6 +142,9 @@ __global__ void __launch_bounds__(T) exec_features(const ar_exec_call* __restric
     float v = 0.f;
     if (threadIdx.x == 0) v = (float)k.n;
     if (threadIdx.x == 1 && k.loop == AR_LOOP_JACOBI7) v = (float)k.sweeps;
+    // Jacobi: 1 when the row pitch is a multiple of 16 bytes (even N), the
+    // condition for staging planes by tensor copies
+    if (threadIdx.x == 2 && k.loop == AR_LOOP_JACOBI7) v = (k.n % 2 == 0) ? 1.f : 0.f;
     feats[8 * c + threadIdx.x] = v;
   }
 }
@@ -193,6 +201,30 @@ __device__ int mlp_choose(const ModelsDev& m, int L, const float* f, float* conf
   return best;
 }
 
+// Writes a tensor map of the N^3 float64 grid at `base` into `dst` (global,
+// 128-byte aligned): the template `tm` (encoded on the host with the right
+// box) with its address, extents and strides replaced.
+__device__ void make_grid_map(CUtensorMap* dst, const CUtensorMap& tm, const void* base, int N) {
+  const uint4* s4 = reinterpret_cast<const uint4*>(&tm);
+  uint4* d4 = reinterpret_cast<uint4*>(dst);
+  for (int q = 0; q < (int)(sizeof(CUtensorMap) / sizeof(uint4)); ++q) d4[q] = s4[q];
+  tmap_set_address(dst, base);
+  tmap_set_dim<0>(dst, N);
+  tmap_set_dim<1>(dst, N);
+  tmap_set_dim<2>(dst, N);
+  tmap_set_stride<0>(dst, (unsigned long long)N * 8ull);
+  tmap_set_stride<1>(dst, (unsigned long long)N * N * 8ull);
+}
+
+// One-time check of the device-made maps against the host encoding (see
+// tma_templates_ready).
+__global__ void exec_tmap_check(const __grid_constant__ CUtensorMap tm, CUtensorMap* out, const void* base, int N) {
+  if (threadIdx.x == 0) {
+    make_grid_map(out, tm, base, N);
+    tmap_release();
+  }
+}
+
 __global__ void __launch_bounds__(T) exec_plan(const ar_exec_call* __restrict__ calls, int ncalls, ModelsDev m,
                                                bool have_models, const int* __restrict__ force,
                                                int* __restrict__ variant, float* __restrict__ conf,
@@ -200,7 +232,10 @@ __global__ void __launch_bounds__(T) exec_plan(const ar_exec_call* __restrict__ 
                                                int* __restrict__ tiles, long long* __restrict__ prefix,
                                                int* __restrict__ done, unsigned long long* __restrict__ counter,
                                                uint64_t* __restrict__ t0, uint64_t* __restrict__ t1,
-                                               int* __restrict__ status, int* __restrict__ vint) {
+                                               int* __restrict__ status, int* __restrict__ vint,
+                                               const __grid_constant__ CUtensorMap tm4,
+                                               const __grid_constant__ CUtensorMap tm8, bool tma_ok,
+                                               CUtensorMap* __restrict__ maps, int* __restrict__ usetma) {
   __shared__ long long scan[T];
   const int c = threadIdx.x;
   if (c < ncalls) {
@@ -243,6 +278,23 @@ __global__ void __launch_bounds__(T) exec_plan(const ar_exec_call* __restrict__ 
       tiles[c * PM + p] = p < ph ? (int)tiles_of(k, v, p) : 0;
       done[c * PM + p] = 0;
     }
+    // tensor maps of u0, out and work for the tensor-copy Jacobi tiles (tma
+    // and df families, shapes 32x4 and 32x8): even N at least one box wide,
+    // 16-byte aligned buffers
+    int use = 0;
+    if (tma_ok && st == AR_OK && k.loop == AR_LOOP_JACOBI7 && v / 4 >= 2 && v % 4 <= 1) {
+      const bool two = k.sweeps > 1;
+      const uintptr_t al = (uintptr_t)k.in0 | (uintptr_t)k.out0 | (two ? (uintptr_t)k.out1 : 0);
+      if (k.n % 2 == 0 && k.n >= 36 && k.n <= 65535 && (al & 15) == 0 && k.in0 && k.out0 && (!two || k.out1)) {
+        const CUtensorMap& tm = v % 4 == 0 ? tm4 : tm8;
+        make_grid_map(maps + 3 * c, tm, k.in0, (int)k.n);
+        make_grid_map(maps + 3 * c + 1, tm, k.out0, (int)k.n);
+        if (two) make_grid_map(maps + 3 * c + 2, tm, k.out1, (int)k.n);
+        tmap_release();
+        use = 1;
+      }
+    }
+    usetma[c] = use;
     t0[c] = ~0ull;
     t1[c] = 0ull;
     status[c] = st;
@@ -323,26 +375,200 @@ __device__ __forceinline__ double atcg(const double* __restrict__ u, int N, int 
 }
 
 
+// ---------------------------------------------------------------- Jacobi by TMA
+// Box geometry of the tensor-copy tiles (shapes 32x4 and 32x8): boxes of
+// (BX+4) x (BY+2) x kXDZ float64 in a kXRing-slot ring at a 128-byte aligned
+// base inside the block's shared memory, one mbarrier per slot.
+constexpr int kXDZ = 4, kXRing = 3;
+template <int BX, int BY>
+struct XGeom {
+  static constexpr int PX = BX + 4, PY = BY + 2, PLANE = PX * PY, GROUP = PLANE * kXDZ;
+  static constexpr int SLOT = (GROUP + 15) / 16 * 16;
+  static constexpr uint32_t BYTES = GROUP * 8u;
+  static constexpr int SMEM = kXRing * SLOT * 8 + 128;
+  static_assert(SLOT * 8 % 128 == 0, "tensor-copy slots stay 128-byte aligned");
+};
+
+// One BX x BY x (ke - kb) tile of one sweep with its planes staged by tensor
+// copies through `map` (a map of src, made by the plan kernel): box g holds
+// planes kb-1+4g .. kb+2+4g (zero outside the grid) and completes output
+// planes kb+4g-1 .. kb+4g+2.  Values and arithmetic as in jacobi_ring_tile:
+// pair_math with float64 input splits each landed box in place (a value
+// outside the pair range marks the point: redone in float64 for float64
+// output, reported through *flag for pair output).  The caller's barrier
+// after the tile orders its stores; returns false if a wait gave up (the
+// copies in flight were drained).
+template <int BX, int BY>
+__device__ bool jacobi_tma_tile(const CUtensorMap* map, int N, int bx, int by, int kb, int ke, const double* src,
+                                double* dst, bool pair_math, bool src_pairs, bool dst_pairs, int* flag,
+                                unsigned char* smraw, uint64_t* bars) {
+  using G = XGeom<BX, BY>;
+  double* buf = reinterpret_cast<double*>(smraw + ((128u - (smem_addr(smraw) & 127u)) & 127u));
+  const int tid = threadIdx.x;
+  const bool active = tid < BX * BY;
+  const int tx = tid % BX, ty = active ? tid / BX : 0;  // idle threads read a valid slot entry
+  const int i0 = bx * BX, j0 = by * BY;
+  const int kc = ke - kb;
+  const int ngroups = (kc + 2 + kXDZ - 1) / kXDZ;
+  const bool split = pair_math && !src_pairs;
+  if (tid == 0) {
+    for (int r = 0; r < kXRing; ++r) mbar_init(smem_addr(&bars[r]), 1);
+    mbar_fence_init();
+    fence_proxy_async_global();  // the previous sweep's stores before these tensor copies
+    tmap_acquire(map);
+  }
+  __syncthreads();
+  auto issue = [&](int g) {
+    const int slot = g % kXRing;
+    const uint32_t bar = smem_addr(&bars[slot]);
+    mbar_arrive_expect_tx(bar, G::BYTES);
+    tma_load_3d(smem_addr(buf + (size_t)slot * G::SLOT), map, i0 - 2, j0 - 1, kb - 1 + g * kXDZ, bar);
+  };
+  if (tid == 0)
+    for (int g = 0; g < min(ngroups, kXRing - 1); ++g) issue(g);
+  const int i = i0 + tx, j = j0 + ty;
+  const bool inside = active && i < N && j < N;
+  const int64_t NN = (int64_t)N * N;
+  const int c = (ty + 1) * G::PX + tx + 2;
+  double* od = dst + ((int64_t)kb * NN + (int64_t)j * N + i);
+  float2* op = reinterpret_cast<float2*>(dst) + ((int64_t)kb * NN + (int64_t)j * N + i);
+  double dm = 0.0, d0 = 0.0;
+  float2 fm = make_float2(0.f, 0.f), f0 = make_float2(0.f, 0.f);
+  bool marker_any = false;
+  int g = 0, slot = 0, pslot = kXRing - 1;
+  uint32_t phase = 0;
+  bool failed = false;
+  for (; g < ngroups; ++g, pslot = slot, slot = (slot + 1 == kXRing) ? 0 : slot + 1, phase ^= (slot == 0)) {
+    const bool ok = mbar_wait_bounded(smem_addr(&bars[slot]), phase);
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    double* box = buf + (size_t)slot * G::SLOT;
+    const double* prev = buf + (size_t)pslot * G::SLOT;
+    if (split) {
+      bool marker = false;
+      for (int e = tid; e < G::GROUP; e += T) {
+        const float2 f = df_split(box[e]);
+        marker |= (f.x != f.x);
+        reinterpret_cast<float2*>(box)[e] = f;
+      }
+      marker_any |= __syncthreads_or(marker);
+    }
+    auto planes = [&](auto native_c, auto guard_c) {
+      constexpr bool NAT = decltype(native_c)::value;
+      constexpr bool GUARD = decltype(guard_c)::value;
+#pragma unroll
+      for (int r = 0; r < kXDZ; ++r) {
+        const int p = g * kXDZ - 1 + r;
+        const bool live = !GUARD || (p >= 1 && p <= kc);  // block-uniform
+        const int cp = (r == 0 ? (kXDZ - 1) * G::PLANE : (r - 1) * G::PLANE) + c;
+        if constexpr (NAT) {
+          const double* pc = (r == 0 ? prev : box) + cp;
+          const double up = box[r * G::PLANE + c];
+          if (live) {
+            double s = pc[-1] + pc[1];
+            s += pc[-G::PX];
+            s += pc[G::PX];
+            s += dm;
+            s += up;
+            if (inside) *od = s * kSixth;
+            od += NN;
+          }
+          dm = d0;
+          d0 = up;
+        } else {
+          const float2* pc = reinterpret_cast<const float2*>(r == 0 ? prev : box) + cp;
+          const float2 up = reinterpret_cast<const float2*>(box)[r * G::PLANE + c];
+          if (live) {
+            const float2 res = df_avg6(pc[-1], pc[1], pc[-G::PX], pc[G::PX], fm, up);
+            if (inside) {
+              if (dst_pairs) {
+                *op = res;
+              } else {
+                double v = src_pairs ? finite_pair_to_double(res) : pair_to_double(res);
+                if (!src_pairs && (__double_as_longlong(v) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) {
+                  // an input outside the float-pair range: redo in float64
+                  const int k = kb + p - 1;
+                  double sd = atcg(src, N, i - 1, j, k) + atcg(src, N, i + 1, j, k);
+                  sd += atcg(src, N, i, j - 1, k);
+                  sd += atcg(src, N, i, j + 1, k);
+                  sd += atcg(src, N, i, j, k - 1);
+                  sd += atcg(src, N, i, j, k + 1);
+                  v = sd * kSixth;
+                }
+                *od = v;
+              }
+            }
+            op += NN;
+            od += NN;
+          }
+          fm = f0;
+          f0 = up;
+        }
+      }
+    };
+    using T_ = std::true_type;
+    using F_ = std::false_type;
+    const bool guard = g == 0 || g * kXDZ + kXDZ - 2 > kc;
+    if (!pair_math) {
+      if (guard)
+        planes(T_{}, T_{});
+      else
+        planes(T_{}, F_{});
+    } else {
+      if (guard)
+        planes(F_{}, T_{});
+      else
+        planes(F_{}, F_{});
+    }
+    // every reader of box g-1 is past this barrier: its slot takes box g+2
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0 && g + kXRing - 1 < ngroups) issue(g + kXRing - 1);
+  }
+  if (failed && tid == 0) {  // drain the boxes still in flight (bounded) before the slots are reused
+    const int issued = min(ngroups, g + kXRing - 1);
+    for (int h = g; h < issued; ++h) (void)mbar_wait_bounded(smem_addr(&bars[h % kXRing]), (uint32_t)((h / kXRing) & 1));
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int r = 0; r < kXRing; ++r) mbar_inval(smem_addr(&bars[r]));
+  if (dst_pairs && split && marker_any && tid == 0 && flag) atomicOr(flag, 1);
+  fence_proxy_async_global();  // these stores before later tensor copies of dst
+  return !failed;
+}
+
 // One BX x BY x 16-plane tile of one sweep, 2.5D: an xy tile with halo in
 // shared memory (double buffered), z neighbours in registers.  Values are
 // float64 or float pairs in memory (src_pairs / dst_pairs); `pair_math`
 // selects float-pair arithmetic.  With float64 input and float-pair
 // arithmetic, inputs outside the pair range mark the point: it is redone in
 // float64 (dst float64) or, when dst holds pairs, reported through *flag.
-__device__ void jacobi_sweep_tile(const ar_exec_call& k, int v, int64_t t, const double* src, double* dst,
-                                  bool pair_math, bool src_pairs, bool dst_pairs, int* flag, unsigned char* smraw) {
+// `map`: a tensor map of src (tma and df families, shapes 32x4 and 32x8,
+// when the plan made one), else nullptr.  Returns false if a bounded wait
+// gave up.
+__device__ bool jacobi_sweep_tile(const ar_exec_call& k, int v, int64_t t, const double* src, double* dst,
+                                  bool pair_math, bool src_pairs, bool dst_pairs, int* flag, unsigned char* smraw,
+                                  const CUtensorMap* map, uint64_t* bars) {
   const int N = (int)k.n;
   const int fam = v / 4, BX = c_j_bx[v % 4], BY = c_j_by[v % 4];
   const int64_t gx = (N + BX - 1) / BX, gy = (N + BY - 1) / BY;
   const int bx = (int)(t % gx), by = (int)((t / gx) % gy), bz = (int)(t / (gx * gy));
   const int kb = bz * kJKC, ke = min(N, kb + kJKC);
+  if (map && fam >= 2 && v % 4 <= 1) {
+    return v % 4 == 0 ? jacobi_tma_tile<32, 4>(map, N, bx, by, kb, ke, src, dst, pair_math, src_pairs, dst_pairs,
+                                               flag, smraw, bars)
+                      : jacobi_tma_tile<32, 8>(map, N, bx, by, kb, ke, src, dst, pair_math, src_pairs, dst_pairs,
+                                               flag, smraw, bars);
+  }
   const bool active = threadIdx.x < BX * BY;
   const int lx = threadIdx.x % BX, ly = threadIdx.x / BX;
   const int i = bx * BX + lx, j = by * BY + ly;
   const bool inside = active && i < N && j < N;
   const int64_t NN = (int64_t)N * N, col = (int64_t)j * N + i;
   if (fam == 0) {  // naive: 6 loads per point
-    if (!inside) return;
+    if (!inside) return true;
     for (int kk = kb; kk < ke; ++kk) {
       double s = atcg(src, N, i - 1, j, kk) + atcg(src, N, i + 1, j, kk);
       s += atcg(src, N, i, j - 1, kk);
@@ -351,12 +577,12 @@ __device__ void jacobi_sweep_tile(const ar_exec_call& k, int v, int64_t t, const
       s += atcg(src, N, i, j, kk + 1);
       dst[kk * NN + col] = s * kSixth;
     }
-    return;
+    return true;
   }
   if (((uintptr_t)src | (uintptr_t)dst) % 16 == 0) {
     jacobi_ring_tile<kJacobi>(N, BX, BY, bx, by, kb, ke, src, dst, pair_math, src_pairs, dst_pairs, flag, smraw,
                               StencilCoef{0.0, 0.f, 0.f, 0.f, 0.f});
-    return;
+    return true;
   }
   // buffers not 16-byte aligned: global loads, those of 4 planes issued together
   const int PXs = BX + 2, PL = PXs * (BY + 2);
@@ -413,7 +639,7 @@ __device__ void jacobi_sweep_tile(const ar_exec_call& k, int v, int64_t t, const
           s += u;
           dst[kk * NN + col] = s * kSixth;
         });
-    return;
+    return true;
   }
   // float-pair arithmetic; loads give pairs directly or split float64 values
   const float2* srcp = reinterpret_cast<const float2*>(src);
@@ -447,29 +673,35 @@ __device__ void jacobi_sweep_tile(const ar_exec_call& k, int v, int64_t t, const
           }
         });
   if (dst_pairs && marker && flag) atomicOr(flag, 1);
+  return true;
 }
 
 // Phase p of a Jacobi call.  Buffers ping-pong so that the last sweep lands in
 // `out`.  A df call with a pair chain: phase 0 float64 -> pairs, phases
 // 1..S-2 pairs -> pairs, phase S-1 pairs -> float64, phase S the catch-up;
 // once the call's flag is set, phase p >= 1 computes sweep p-1 in float64
-// from float64 data and the catch-up computes sweep S-1.
-__device__ void jacobi_tile(const ar_exec_call& k, int v, int p, int64_t t, int* flag, unsigned char* smraw) {
+// from float64 data and the catch-up computes sweep S-1.  maps: the call's
+// tensor maps of (u0, out, work), or nullptr.  Returns false if a bounded
+// wait gave up.
+__device__ bool jacobi_tile(const ar_exec_call& k, int v, int p, int64_t t, int* flag, unsigned char* smraw,
+                            const CUtensorMap* maps, uint64_t* bars) {
   const int S = k.sweeps, N = (int)k.n;
   const double* u0 = static_cast<const double*>(k.in0);
   double* out = static_cast<double*>(k.out0);
   double* work = static_cast<double*>(k.out1);
   auto dst_of = [&](int sw) -> double* { return ((S - 1 - sw) % 2 == 0) ? out : work; };
   auto src_of = [&](int sw) -> const double* { return sw == 0 ? u0 : dst_of(sw - 1); };
+  auto map_of = [&](const double* b) -> const CUtensorMap* {
+    return !maps ? nullptr : b == u0 ? maps : b == out ? maps + 1 : maps + 2;
+  };
   const int fam = v / 4;
-  if (!jacobi_pair_chain(k, v)) {
-    jacobi_sweep_tile(k, v, t, src_of(p), dst_of(p), fam == 3, false, false, nullptr, smraw);
-    return;
-  }
+  if (!jacobi_pair_chain(k, v))
+    return jacobi_sweep_tile(k, v, t, src_of(p), dst_of(p), fam == 3, false, false, nullptr, smraw,
+                             map_of(src_of(p)), bars);
   // block-uniform: the tile bodies below hold barriers
   const bool flagged = __syncthreads_or(p >= 1 && __ldcg(flag) != 0);
   if (p == S) {  // catch-up: float64 sweep S-1 over a contiguous chunk of unknowns
-    if (!flagged) return;
+    if (!flagged) return true;
     const double* src = src_of(S - 1);
     double* dst = dst_of(S - 1);
     const int64_t n3 = (int64_t)N * N * N, NN = (int64_t)N * N;
@@ -483,13 +715,13 @@ __device__ void jacobi_tile(const ar_exec_call& k, int v, int p, int64_t t, int*
       s += atcg(src, N, i, j, kk + 1);
       dst[c] = s * kSixth;
     }
-    return;
+    return true;
   }
-  if (flagged) {  // one sweep late, in float64
-    jacobi_sweep_tile(k, v, t, src_of(p - 1), dst_of(p - 1), false, false, false, nullptr, smraw);
-    return;
-  }
-  jacobi_sweep_tile(k, v, t, src_of(p), dst_of(p), true, p > 0, p < S - 1, flag, smraw);
+  if (flagged)  // one sweep late, in float64
+    return jacobi_sweep_tile(k, v, t, src_of(p - 1), dst_of(p - 1), false, false, false, nullptr, smraw,
+                             map_of(src_of(p - 1)), bars);
+  return jacobi_sweep_tile(k, v, t, src_of(p), dst_of(p), true, p > 0, p < S - 1, flag, smraw, map_of(src_of(p)),
+                           bars);
 }
 
 __device__ void spmv_tile(const ar_exec_call& k, int v, int p, int64_t t, unsigned char* smraw) {
@@ -598,6 +830,8 @@ __device__ void nbody_tile(const ar_exec_call& k, int v, int64_t t, unsigned cha
 // largest tile: a merge-path block (staged products and row ends, open rows,
 // partial sums) plus its two path bounds; Jacobi needs 2 x 4 x 130 doubles
 constexpr int kSmemBytes = mp::kSmemBytes + 16;
+static_assert(XGeom<32, 4>::SMEM <= kSmemBytes && XGeom<32, 8>::SMEM <= kSmemBytes,
+              "the tensor-copy box ring fits the tile shared memory");
 static_assert(kSmemBytes >= 8448, "shared memory of the Jacobi and n-body tiles");
 static_assert(ring_smem_bytes(32, 4) <= kSmemBytes && ring_smem_bytes(32, 8) <= kSmemBytes &&
                   ring_smem_bytes(64, 4) <= kSmemBytes && ring_smem_bytes(128, 2) <= kSmemBytes,
@@ -609,8 +843,10 @@ __global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_cal
                                                  const int* __restrict__ vint, const int* __restrict__ tiles,
                                                  const long long* __restrict__ prefix, int* done,
                                                  unsigned long long* counter, uint64_t* t0, uint64_t* t1,
-                                                 int* status, int* flags) {
+                                                 int* status, int* flags, const CUtensorMap* __restrict__ maps,
+                                                 const int* __restrict__ usetma) {
   __shared__ __align__(16) unsigned char smraw[kSmemBytes];
+  __shared__ __align__(8) uint64_t s_bars[kXRing];
   __shared__ long long s_item, s_t;
   __shared__ int s_c, s_p, s_ok;
   const int E = PM * ncalls;
@@ -671,7 +907,11 @@ __global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_cal
     if (s_ok && k.loop >= 0 && k.loop < 4 && v >= 0 && v < c_nvar[k.loop]) {
       switch (k.loop) {
         case AR_LOOP_DAXPY: daxpy_tile(k, v, t); break;
-        case AR_LOOP_JACOBI7: jacobi_tile(k, v, p, t, flags + c, smraw); break;
+        case AR_LOOP_JACOBI7:
+          if (!jacobi_tile(k, v, p, t, flags + c, smraw, usetma[c] ? maps + 3 * c : nullptr, s_bars) &&
+              threadIdx.x == 0)
+            atomicExch(status + c, (int)AR_ERR_TIMEOUT);
+          break;
         case AR_LOOP_SPMV: spmv_tile(k, v, p, t, smraw); break;
         default: nbody_tile(k, v, t, smraw); break;
       }
@@ -686,7 +926,7 @@ __global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_cal
 }
 
 struct WsLayout {
-  size_t part, tiles, prefix, done, counter, vint, flags, total;
+  size_t part, tiles, prefix, done, counter, vint, flags, usetma, maps, total;
 };
 
 WsLayout layout(int max_calls) {
@@ -707,8 +947,54 @@ WsLayout layout(int max_calls) {
   o = up(o + (size_t)max_calls * 4);
   w.flags = o;
   o = up(o + (size_t)max_calls * 4);
+  w.usetma = o;
+  o = up(o + (size_t)max_calls * 4);
+  w.maps = o;  // 3 tensor maps (u0, out, work) per call, 128-byte aligned
+  o = up(o + (size_t)max_calls * 3 * sizeof(CUtensorMap));
   w.total = o + 256;
   return w;
+}
+
+// Templates of the Jacobi tiles' tensor maps (box 36 x 6 x 4 for shape 32x4,
+// 36 x 10 x 4 for 32x8), encoded once; the plan kernel copies one per grid
+// and replaces its address, extents and strides on the device.  Before the
+// first use a check compares a device-made map with the host encoding of the
+// same grid, byte for byte, on `s` (synchronous; not while `s` is capturing,
+// in which case this batch stages Jacobi planes by cp.async instead).  Any
+// mismatch or encode failure turns tensor copies off for the process.
+struct MapTemplates {
+  CUtensorMap tm4, tm8;
+};
+bool tma_templates_ready(unsigned char* scratch, cudaStream_t s, MapTemplates* out) {
+  static std::mutex mu;
+  static int state = 0;  // 0 unchecked, 1 usable, -1 off
+  static MapTemplates tm;
+  std::lock_guard<std::mutex> lock(mu);
+  if (state == 0) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
+    state = -1;
+    if (encode_tensor_map_3d_f64(&tm.tm4, scratch, 64, 64, 64, 36, 6, kXDZ) &&
+        encode_tensor_map_3d_f64(&tm.tm8, scratch, 64, 64, 64, 36, 10, kXDZ)) {
+      bool same = true;
+      const int Ns[2] = {96, 512};
+      for (int q = 0; q < 2 && same; ++q) {
+        const CUtensorMap& t = q == 0 ? tm.tm4 : tm.tm8;
+        const unsigned char* base = scratch + 1024 * (q + 1);
+        CUtensorMap want, got;
+        if (!encode_tensor_map_3d_f64(&want, base, Ns[q], Ns[q], Ns[q], 36, q == 0 ? 6 : 10, kXDZ)) {
+          same = false;
+          break;
+        }
+        exec_tmap_check<<<1, 32, 0, s>>>(t, reinterpret_cast<CUtensorMap*>(scratch), base, Ns[q]);
+        same = cudaMemcpyAsync(&got, scratch, sizeof got, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+               cudaStreamSynchronize(s) == cudaSuccess && std::memcmp(&want, &got, sizeof got) == 0;
+      }
+      if (same) state = 1;
+    }
+  }
+  *out = tm;
+  return state == 1;
 }
 
 }  // namespace
@@ -735,7 +1021,7 @@ extern "C" int ar_exec_batch(const ar_exec_call* calls, int ncalls, const ar_exe
   bool have = false;
   if (models) {
     if (models->H != 32 && models->H != 64) return AR_ERR_ARG;
-    const int nfeat[4] = {1, 2, 5, 1};
+    const int nfeat[4] = {1, 3, 5, 1};
     const int nvar[4] = {kDaxpyVariants, kJacobiVariants, kSpmvVariants, kNbodyVariants};
     for (int L = 0; L < 4; ++L) {
       m.F[L] = models->F[L];
@@ -757,13 +1043,18 @@ extern "C" int ar_exec_batch(const ar_exec_call* calls, int ncalls, const ar_exe
   unsigned long long* counter = reinterpret_cast<unsigned long long*>(base + w.counter);
   int* vint = reinterpret_cast<int*>(base + w.vint);
   int* flags = reinterpret_cast<int*>(base + w.flags);
+  int* usetma = reinterpret_cast<int*>(base + w.usetma);
+  CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(base + w.maps);
   cudaStream_t s = as_stream(stream);
+  MapTemplates tmt{};
+  const bool tma_ok = tma_templates_ready(reinterpret_cast<unsigned char*>(maps), s, &tmt);
   if (cudaMemsetAsync(part, 0, (size_t)ncalls * 3 * 8, s) != cudaSuccess) return AR_ERR_CUDA;
   if (cudaMemsetAsync(flags, 0, (size_t)ncalls * 4, s) != cudaSuccess) return AR_ERR_CUDA;
   exec_features<<<dim3(64, (unsigned)ncalls), T, 0, s>>>(calls, features, part);
   exec_plan<<<1, T, 0, s>>>(calls, ncalls, m, have, force_variant, variant, conf, features, part, tiles, prefix,
-                            done, counter, t_start, t_end, status, vint);
+                            done, counter, t_start, t_end, status, vint, tmt.tm4, tmt.tm8, tma_ok, maps,
+                            usetma);
   exec_run<<<device_sms() * kRunBlocksPerSm, T, 0, s>>>(calls, ncalls, vint, tiles, prefix, done, counter, t_start, t_end, status,
-                                          flags);
+                                          flags, maps, usetma);
   return launch_status();
 }

@@ -80,6 +80,43 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(G) : "memory");
 }
 
+__device__ __forceinline__ void mbar_inval(uint32_t bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Order this thread's earlier generic-proxy global accesses (stores of a
+// previous sweep, the acquire of a dependency counter) with later
+// async-proxy (TMA) accesses of global memory.
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Device-side edits of a tensor map in global memory (64-byte aligned):
+// tensormap.replace writes one field in the driver's encoding.  The writer
+// then releases the map to the tensor-map proxy; a reader acquires it
+// before its first tensor copy through it.
+__device__ __forceinline__ void tmap_set_address(void* map, const void* addr) {
+  asm volatile("tensormap.replace.tile.global_address.global.b1024.b64 [%0], %1;" ::"l"(map), "l"(addr)
+               : "memory");
+}
+template <int ORD>
+__device__ __forceinline__ void tmap_set_dim(void* map, int v) {
+  asm volatile("tensormap.replace.tile.global_dim.global.b1024.b32 [%0], %1, %2;" ::"l"(map), "n"(ORD), "r"(v)
+               : "memory");
+}
+template <int ORD>  // the byte stride of dimension ORD + 1
+__device__ __forceinline__ void tmap_set_stride(void* map, unsigned long long bytes) {
+  asm volatile("tensormap.replace.tile.global_stride.global.b1024.b64 [%0], %1, %2;" ::"l"(map), "n"(ORD),
+               "l"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tmap_release() {
+  asm volatile("fence.proxy.tensormap::generic.release.gpu;" ::: "memory");
+}
+__device__ __forceinline__ void tmap_acquire(const void* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+}
+
 // Host: encode a 3D float64 tensor map over a dense (d2, d1, d0) array with
 // d0 fastest.  Returns false if the driver entry point is missing or the
 // encode call rejects the arguments.

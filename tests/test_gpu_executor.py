@@ -128,7 +128,8 @@ def test_every_variant_of_every_loop_in_one_batch():
         f = r["features"][k]
         assert f[0] == np.float32(st[0]) and f[1] == np.float32(st[1]) and f[4] == st[4]
         assert f[2] == pytest.approx(st[2], rel=1e-6) and f[3] == pytest.approx(st[3], rel=1e-5)
-    assert r["features"][0][0] == 100003 and tuple(r["features"][15][:2]) == (50.0, 3.0)
+    assert r["features"][0][0] == 100003 and tuple(r["features"][15][:3]) == (50.0, 3.0, 1.0)
+    assert tuple(r["features"][16][:3]) == (37.0, 3.0, 0.0)
 
 
 def test_edge_sizes_of_every_loop_in_one_batch():
@@ -181,6 +182,27 @@ def test_float_pair_chain_with_and_without_range_flag():
         assert ok(), (k, force[k])
 
 
+def test_jacobi_tensor_copy_tiles():
+    """tma and df variants of shapes 32x4 and 32x8 on even N >= 36 stage
+    their planes by tensor copies through maps the plan kernel makes on the
+    device: every mode of the pair chain, the float64 and float-pair forms,
+    ragged x, y and z tile edges, an input outside the pair range, next to
+    calls of the other loops in the same batch."""
+    b = Batch()
+    force = []
+    for k, (N, sweeps, v, plant) in enumerate([(36, 1, 8, None), (40, 2, 9, None), (66, 3, 12, None),
+                                               (100, 5, 13, None), (70, 10, 13, None), (38, 4, 12, 3e39),
+                                               (44, 3, 13, 1e-30), (36, 2, 9, 5e40), (98, 1, 13, None)]):
+        b.jacobi(N, sweeps, 700 + k, plant)
+        force.append(v)
+        b.nbody(600 + 50 * k, 720 + k)
+        force.append(k % 9)
+    r = b.run(force=force)
+    assert np.all(r["status"] == 0)
+    for k, ok in enumerate(b.check):
+        assert ok(), (k, b.calls[k].loop, force[k])
+
+
 def test_bad_variant_and_loop_are_reported_per_call():
     b = Batch()
     b.daxpy(1000, 1)
@@ -196,7 +218,8 @@ def _trained_models():
     """One MLP per loop, trained on the device from a deterministic cost model
     of the features (no timing involved)."""
     nv = [ar.loop_num_variants(L) for L in range(4)]
-    specs = [(1, nv[0], lambda f: int(np.log2(f[0])) % 15), (2, nv[1], lambda f: (int(f[0]) // 40) % 16),
+    specs = [(1, nv[0], lambda f: int(np.log2(f[0])) % 15),
+             (3, nv[1], lambda f: ((int(f[0]) // 40) % 8) * 2 + int(f[2])),
              (5, nv[2], lambda f: 7 if f[2] > 40 else (6 if f[2] > 20 else (1 if f[4] > 1000 else 3))),
              (1, nv[3], lambda f: int(f[0] > 2000) * 4)]
     models = ar.ArExecModels()
@@ -204,7 +227,7 @@ def _trained_models():
     keep, regions = [], []
     rng = np.random.Generator(np.random.PCG64(9))
     samples = {0: [[float(2 ** rng.uniform(10, 24))] for _ in range(300)],
-               1: [[float(rng.integers(8, 600)), 3.0] for _ in range(300)],
+               1: [[float(n), 3.0, float(n % 2 == 0)] for n in rng.integers(8, 600, 300)],
                2: [[float(rng.integers(1e3, 1e6)), 1e6, float(rng.uniform(1, 60)), 5.0, float(rng.integers(1, 4096))]
                    for _ in range(300)],
                3: [[float(rng.integers(500, 5000))] for _ in range(300)]}
