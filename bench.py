@@ -147,24 +147,38 @@ def workload_bytes(sizes, sweeps):
 # ---------------------------------------------------------------- CPU oracle
 def cpu_oracle_rate(seconds: float, kind: str = "jacobi7"):
     """GB/s of the float64 CPU oracle on a bounded sample of the workload:
-    N in {32, 64, 128, 256} at 10 sweeps, repeated until `seconds` elapse."""
+    N in {32, 64, 128, 256} at 10 sweeps on all host threads, repeated until
+    `seconds` elapse, then N in {32, 64, 128} on one thread for a quarter of
+    that (reported as `single_thread`)."""
     import synth
     from oracle import loops
 
-    grids = {n: synth.grid_inputs(1000 + n, n) for n in (32, 64, 128, 256)}
-    t0 = time.perf_counter()
-    done = 0.0
-    reps = 0
-    while True:
-        for n, u in grids.items():
-            stencil_oracle(loops, kind, u, SWEEPS)
-            done += BYTES_PER_POINT * n ** 3 * SWEEPS
-        reps += 1
-        if time.perf_counter() - t0 >= seconds:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": done / dt / 1e9, "unit": "GB/s", "cores": loops.num_threads(), "kind": "oracle",
-            "sample": f"{STENCILS[kind]['label']} N in (32,64,128,256), 10 sweeps, {reps} passes, {dt:.1f} s"}
+    def rate(sizes, budget):
+        grids = {n: synth.grid_inputs(1000 + n, n) for n in sizes}
+        t0 = time.perf_counter()
+        done, reps = 0.0, 0
+        while True:
+            for n, u in grids.items():
+                stencil_oracle(loops, kind, u, SWEEPS)
+                done += BYTES_PER_POINT * n ** 3 * SWEEPS
+            reps += 1
+            if time.perf_counter() - t0 >= budget:
+                break
+        dt = time.perf_counter() - t0
+        return done / dt / 1e9, reps, dt
+
+    cores = loops.num_threads()
+    val, reps, dt = rate((32, 64, 128, 256), seconds)
+    loops.set_threads(1)
+    try:
+        one, reps1, dt1 = rate((32, 64, 128), seconds / 4)
+    finally:
+        loops.set_threads(cores)
+    return {"value": val, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": f"{STENCILS[kind]['label']} N in (32,64,128,256), 10 sweeps, {reps} passes, {dt:.1f} s",
+            "single_thread": {"value": one, "unit": "GB/s", "cores": 1,
+                              "sample": f"N in (32,64,128), 10 sweeps, {reps1} passes, {dt1:.1f} s"},
+            "host_cpus": os.cpu_count()}
 
 
 def jacobi_config(ws, kind="jacobi7"):
