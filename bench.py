@@ -56,9 +56,11 @@ HEAT_ALPHA = 0.125              # alpha of the heat workload (stable: <= 1/6)
 # pairs -> pairs sweep at N = 320 per df kernel (see DF_PP_TRAFFIC_N320).
 STENCILS = {
     "jacobi7": {"loop": 1, "label": "jacobi7 float64", "fp64_ops": FP64_OPS_PER_POINT,
-                "pp_traffic": {"jacobi7_df_32x8": DF_PP_TRAFFIC_N320}},
+                "pp_traffic": {"jacobi7_df_32x8": DF_PP_TRAFFIC_N320,
+                               "jacobi7_df_32x4": 262180096.0 + 218679040.0}},
     "heat7": {"loop": 4, "label": f"heat7 float64 (alpha = {HEAT_ALPHA})", "fp64_ops": 7,
-              "pp_traffic": {"heat7_df_32x8": 262293632.0 + 218051328.0}},
+              "pp_traffic": {"heat7_df_32x8": 262293632.0 + 218051328.0,
+                             "heat7_df_32x4": 262183552.0 + 219656064.0}},
 }
 
 
