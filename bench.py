@@ -569,6 +569,24 @@ def spmv_study(n_train, n_test, rows_max, epochs, kfold=False):
     fwsb = ar.ar_csr_features_workspace_bytes(0)
     fws = torch.empty(fwsb, dtype=torch.uint8, device=dev)
     f5 = torch.zeros(5, dtype=torch.float32, device=dev)
+    sink = torch.empty(1, dtype=torch.int64, device=dev)
+    fe0, fe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def floor_ms(keep, nnz):
+        """Mean time of the gather-floor kernel on one matrix (3 runs after a
+        warm-up, L2 flushed before each, like the variants' profiles)."""
+        _, c, v, x, _ = keep
+        t = []
+        with torch.cuda.stream(stream):
+            ar.ar_spmv_gather_floor(nnz, c, v, x, sink, stream=stream)
+            for _ in range(3):
+                flush.fill_(1)
+                fe0.record(stream)
+                ar.ar_spmv_gather_floor(nnz, c, v, x, sink, stream=stream)
+                fe1.record(stream)
+                stream.synchronize()
+                t.append(fe0.elapsed_time(fe1))
+        return statistics.mean(t)
 
     def case(seed):
         prm = synth.spmv_matrix_params(seed, rows_max=rows_max)
@@ -582,7 +600,7 @@ def spmv_study(n_train, n_test, rows_max, epochs, kfold=False):
         feats = f5.cpu().tolist()
         a = ar.ArSpmvArgs(rows, nnz, rp.data_ptr(), c.data_ptr(), v.data_ptr(), x.data_ptr(), y.data_ptr(),
                           ws.data_ptr(), ws.numel())
-        return feats, a, (rp, c, v, x, y), rows, nnz
+        return feats, a, (rp, c, v, x, y), rows, nnz, prm["kind"]
 
     mlp = ar.Region("spmv-mlp", 5, f"mlp,64,epochs={epochs},seed=7", 10 ** 9)
     tree = ar.Region("spmv-dtree", 5, "dtree,2", 10 ** 9)
@@ -599,7 +617,7 @@ def spmv_study(n_train, n_test, rows_max, epochs, kfold=False):
     prof_ms = 0.0
     table = []
     for k in range(n_train):
-        feats, a, keep, rows, nnz = case(1000 + k)
+        feats, a, keep, rows, nnz, _ = case(1000 + k)
         ms, _ = mlp.profile(feats, a, stream=stream)
         prof_ms += 6 * sum(ms)  # warm-up + 5 timed runs of every variant
         table.append((feats, ms))
@@ -614,12 +632,12 @@ def spmv_study(n_train, n_test, rows_max, epochs, kfold=False):
 
     per = []
     for k in range(n_test):
-        feats, a, keep, rows, nnz = case(3000 + k)
+        feats, a, keep, rows, nnz, kind = case(3000 + k)
         ms, best = exh.profile(feats, a, stream=stream)
         vm, conf = mlp.select(feats)
         vt, _ = tree.select(feats)
         per.append({"rows": rows, "nnz": nnz, "bytes": spmv_bytes(rows, nnz), "ms": ms, "best": best,
-                    "mlp": vm, "conf": conf, "dtree": vt})
+                    "mlp": vm, "conf": conf, "dtree": vt, "floor_ms": floor_ms(keep, nnz), "kind": kind})
         table.append((feats, ms))
         del keep
 
@@ -659,11 +677,30 @@ def spmv_study(n_train, n_test, rows_max, epochs, kfold=False):
                         "note": "achieved: the MLP-selected variants over the test matrices (sum of algorithmic "
                                 "bytes / sum of times); traffic: DRAM bytes of one launch of the dominant kernel "
                                 "on the 2e6-row Zipf(1.5) matrix"}
+    # the memory-side floor of every test matrix (ar_spmv_gather_floor: col and
+    # val streamed, x gathered, no row logic, no float64 arithmetic)
+    floor_gbs = sum(p["bytes"] for p in per) / (sum(p["floor_ms"] for p in per) * 1e-3) / 1e9
+    line["gather_floor"] = {"gbs": floor_gbs, "mlp_frac": res["mlp"]["gbs"] / floor_gbs,
+                            "exhaustive_best_frac": best_gbs / floor_gbs,
+                            "zipf_mlp_frac": _floor_frac(per, "mlp", lambda p: p["kind"] == "zipf"),
+                            "band_mlp_frac": _floor_frac(per, "mlp", lambda p: p["kind"] == "band"),
+                            "note": "algorithmic bytes over the time of a kernel that only streams col and val and "
+                                    "gathers x[col] (8 in flight per thread): the bound random 8-byte gathers "
+                                    "(32-byte sectors) set on power-law matrices"}
     if kfold:
         t2 = time.perf_counter()
         line["kfold_mean_regret_pct"] = kfold_protocol(table, V, 5, epochs)
         line["kfold_wall_s"] = time.perf_counter() - t2
     return line
+
+
+def _floor_frac(per, key, keep):
+    """Selected time's share of the gather floor over the matrices `keep`
+    admits (None if none)."""
+    sel = [p for p in per if keep(p)]
+    if not sel:
+        return None
+    return sum(p["floor_ms"] for p in sel) / sum(p["ms"][p[key]] for p in sel)
 
 
 # ---------------------------------------------------------------- mixed stream

@@ -180,6 +180,17 @@ int ar_spmv_merge_path_noalloc(int64_t rows, int64_t nnz, const int32_t *rowptr,
  * formed in float64.  workspace: ar_csr_features_workspace_bytes of device
  * memory (no initialisation needed). */
 int ar_csr_features_workspace_bytes(int64_t rows, size_t *bytes);
+
+/* Measurement kernel, not an SpMV: streams col and val of all nnz nonzeros
+ * and gathers x[col[j]], 8 nonzeros in flight per thread, with no row logic
+ * and no float64 arithmetic, so its time is the memory-side floor of any
+ * CSR SpMV variant on the matrix (for power-law rows, random 8-byte gathers
+ * that each cost a 32-byte sector, not HBM bytes, set it).  sink8: 8 bytes
+ * of device memory that the kernel may write (its result is meaningless).
+ * Returns AR_OK, AR_ERR_ARG (nnz outside [0, 2^31), NULL pointers) or
+ * AR_ERR_CUDA. */
+int ar_spmv_gather_floor(int64_t nnz, const int32_t *col, const double *val, const double *x, void *sink8,
+                         void *stream);
 int ar_csr_features(int64_t rows, const int32_t *rowptr, float *out5, void *workspace, size_t workspace_bytes,
                     void *stream);
 

@@ -133,6 +133,7 @@ _SIGS = {
     "ar_spmv": (_i, [_i, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "ar_spmv_merge_path_noalloc": (_i, [_i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "ar_csr_features_workspace_bytes": (_i, [_i64, ctypes.POINTER(_sz)]),
+    "ar_spmv_gather_floor": (_i, [_i64, _vp, _vp, _vp, _vp, _vp]),
     "ar_csr_features": (_i, [_i64, _vp, _vp, _vp, _sz, _vp]),
     "ar_nbody": (_i, [_i, _i64, _vp, _vp, _f, _vp]),
     "ar_nbody_batched_workspace_bytes": (_i, [_i, ctypes.POINTER(_sz)]),
@@ -215,6 +216,10 @@ def ar_daxpy(variant, n, a, x, y, stream=None):
 def ar_jacobi7(variant, N, sweeps, u0, out, work, status=None, stream=None):
     return check(lib.ar_jacobi7(variant, N, sweeps, ptr(u0), ptr(out), ptr(work), ptr(status),
                                 stream_handle(stream)))
+
+
+def ar_spmv_gather_floor(nnz, col, val, x, sink8, stream=None):
+    return check(lib.ar_spmv_gather_floor(nnz, ptr(col), ptr(val), ptr(x), ptr(sink8), stream_handle(stream)))
 
 
 def ar_heat7(variant, N, steps, alpha, u0, out, work, status=None, stream=None):
@@ -504,7 +509,7 @@ class Region:
 
 __all__ = ["ArExecCall", "ArExecModels", "ar_exec_workspace_bytes", "ar_exec_batch", "exec_table_bytes",
            "AR_EXEC_MAX_CALLS", "AR_EXEC_MAX_PHASES", "ArError", "Region", "ArDaxpyArgs", "ArJacobi7Args", "ArHeat7Args", "ArSpmvArgs", "ArNbodyArgs", "ar_spmv",
-           "ar_spmv_workspace_bytes", "ar_spmv_merge_path_noalloc", "ar_csr_features", "ar_csr_features_workspace_bytes", "ar_nbody",
+           "ar_spmv_workspace_bytes", "ar_spmv_merge_path_noalloc", "ar_spmv_gather_floor", "ar_csr_features", "ar_csr_features_workspace_bytes", "ar_nbody",
            "ar_nbody_batched", "ar_nbody_batched_workspace_bytes", "LAUNCH_FN", "FAKE_TIME_FN", "lib", "ptr",
            "stream_handle", "check", "loop_num_variants", "loop_default_variant", "loop_variant_name", "ar_daxpy",
            "ar_jacobi7", "ar_heat7", "ar_mlp_num_params", "ar_mlp_forward", "ar_mlp_grad", "ar_mlp_adam", "ar_mlp_train",

@@ -265,6 +265,41 @@ extern "C" int ar_spmv(int variant, int64_t rows, int64_t nnz, const int32_t* ro
   }
 }
 
+namespace ar {
+namespace {
+
+// Memory-side floor of a CSR SpMV: every nonzero's column and value are
+// streamed and x[col] gathered, 8 nonzeros per thread in flight, with no row
+// logic and no float64 arithmetic (the loaded bits are XORed into an integer
+// that is stored only if it matches a constant, which keeps the loads live).
+__global__ void __launch_bounds__(256) spmv_gather_floor(int64_t nnz, const int* __restrict__ col,
+                                                         const double* __restrict__ val,
+                                                         const double* __restrict__ x,
+                                                         unsigned long long* __restrict__ sink) {
+  unsigned long long acc = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+#pragma unroll 8
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nnz; j += stride) {
+    const int c = __ldg(col + j);
+    acc += (unsigned long long)__double_as_longlong(__ldg(val + j)) ^
+           (unsigned long long)__double_as_longlong(__ldg(x + c));
+  }
+  if (acc == 0x5bd1e9955bd1e995ull) *sink = acc;
+}
+
+}  // namespace
+}  // namespace ar
+
+extern "C" int ar_spmv_gather_floor(int64_t nnz, const int32_t* col, const double* val, const double* x,
+                                    void* sink8, void* stream) {
+  using namespace ar;
+  if (nnz < 0 || nnz > 0x7fffffffLL || (nnz > 0 && (!col || !val || !x || !sink8))) return AR_ERR_ARG;
+  if (nnz == 0) return AR_OK;
+  spmv_gather_floor<<<(unsigned)(device_sms() * 4), 256, 0, as_stream(stream)>>>(
+      nnz, reinterpret_cast<const int*>(col), val, x, static_cast<unsigned long long*>(sink8));
+  return launch_status();
+}
+
 extern "C" int ar_csr_features_workspace_bytes(int64_t rows, size_t* bytes) {
   if (rows < 0 || !bytes) return AR_ERR_ARG;
   *bytes = (size_t)kFeatBlocks * 3 * sizeof(long long);

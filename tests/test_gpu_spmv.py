@@ -171,3 +171,32 @@ def test_row_features_match_oracle(rows, kind):
     assert got[0] == np.float32(ref[0]) and got[1] == np.float32(ref[1]) and got[4] == ref[4]
     assert got[2] == pytest.approx(ref[2], rel=1e-6)
     assert got[3] == pytest.approx(ref[3], rel=1e-5, abs=1e-6)
+
+
+def test_gather_floor_is_below_every_variant():
+    """ar_spmv_gather_floor does a subset of every variant's memory work (no
+    row logic, no float64 arithmetic), so on a power-law matrix it is not
+    slower than the fastest variant (mean of 5 runs, 10 % slack for noise)."""
+    rows = 2_000_000
+    rp, c, v = synth.csr_zipf(31, rows, 1.5, device="cuda")
+    x = synth.spmv_x(31, rows, device="cuda")
+    nnz = int(rp[-1].item())
+    y = torch.empty(rows, dtype=torch.float64, device="cuda")
+    sink = torch.empty(1, dtype=torch.int64, device="cuda")
+    wsb = max(ar.ar_spmv_workspace_bytes(var, rows, nnz) for var in range(V))
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(5):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 5
+
+    floor = timed(lambda: ar.ar_spmv_gather_floor(nnz, c, v, x, sink))
+    best = min(timed(lambda var=var: ar.ar_spmv(var, rows, nnz, rp, c, v, x, y, ws, wsb)) for var in range(V))
+    assert floor <= 1.1 * best, (floor, best)

@@ -293,6 +293,9 @@ def test_kernel_entry_points_validate_before_launch():
     for bad in (-0.01, 1.5, float("nan"), float("inf")):  # alpha outside [0, 1]
         assert ar.lib.ar_heat7(0, 8, 1, bad, 64, 128, 192, None, None) == ar.AR_ERR_ARG
     assert ar.lib.ar_heat7(0, 0, 3, 0.1, None, None, None, None, None) == 0  # empty grid
+    assert ar.lib.ar_spmv_gather_floor(-1, 8, 8, 8, 8, None) == ar.AR_ERR_ARG
+    assert ar.lib.ar_spmv_gather_floor(10, None, 8, 8, 8, None) == ar.AR_ERR_ARG
+    assert ar.lib.ar_spmv_gather_floor(0, None, None, None, None, None) == 0  # nothing to stream
     assert ar.lib.ar_mlp_num_params(5, 64, 7) == 5 * 64 + 64 + 64 * 64 + 64 + 7 * 64 + 7
     assert ar.lib.ar_mlp_num_params(5, 48, 7) == ar.AR_ERR_ARG
 
