@@ -248,7 +248,9 @@ int ar_nbody_batched(int count, const int32_t *offs, const float *pos4, float *a
  * All arrays are device memory.  Per call c: variant[c], conf[c] (1 when
  * forced or defaulted), features[8c..8c+7], t_start[c] / t_end[c] (%globaltimer
  * ns of the first tile's start and the last tile's end), status[c] (AR_OK,
- * AR_ERR_ARG for a bad loop/variant, AR_ERR_TIMEOUT if a dependency wait gave
+ * AR_ERR_ARG for a bad loop/variant or, for Jacobi, sweeps outside [1,
+ * AR_EXEC_MAX_PHASES], N > 65535 or u0/out/work missing or not distinct
+ * (work only for 2+ sweeps), AR_ERR_TIMEOUT if a dependency wait gave
  * up).  The call table and models must stay valid until the work completes.
  * workspace: ar_exec_workspace_bytes(max_calls) bytes, no initialisation
  * needed.  Two batches that share a workspace (or a call table) must not

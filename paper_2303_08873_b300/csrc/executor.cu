@@ -255,7 +255,13 @@ __global__ void __launch_bounds__(T) exec_plan(const ar_exec_call* __restrict__ 
       f[4] = (float)part[3 * c + 2];
       f[5] = f[6] = f[7] = 0.f;
     }
-    if (!loop_ok || (k.loop == AR_LOOP_JACOBI7 && (k.sweeps < 1 || k.sweeps > PM)) || k.n < 0) {
+    // Jacobi: u0, out and (for 2+ sweeps) work present and distinct, N < 2^16
+    const bool jac_bad =
+        k.loop == AR_LOOP_JACOBI7 &&
+        (k.sweeps < 1 || k.sweeps > PM || k.n > 65535 ||
+         (k.n > 0 && (!k.in0 || !k.out0 || k.in0 == k.out0 ||
+                      (k.sweeps > 1 && (!k.out1 || k.out1 == k.out0 || k.out1 == k.in0)))));
+    if (!loop_ok || jac_bad || k.n < 0) {
       st = AR_ERR_ARG;
     } else if (force) {
       v = force[c];

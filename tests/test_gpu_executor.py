@@ -209,8 +209,18 @@ def test_bad_variant_and_loop_are_reported_per_call():
     b.daxpy(1000, 2)
     b.calls.append(ar.ArExecCall(loop=7, n=10))
     b.check.append(lambda: True)
-    r = b.run(force=[3, 15, 0])
+    # Jacobi calls with aliased or missing buffers, and an empty one
+    u = torch.zeros(8 ** 3, dtype=torch.float64, device="cuda")
+    w = torch.zeros_like(u)
+    b.keep += [u, w]
+    b.calls.append(ar.ArExecCall(loop=1, n=8, sweeps=2, in0=u.data_ptr(), out0=w.data_ptr(), out1=w.data_ptr()))
+    b.calls.append(ar.ArExecCall(loop=1, n=8, sweeps=1, in0=u.data_ptr(), out0=u.data_ptr()))
+    b.calls.append(ar.ArExecCall(loop=1, n=8, sweeps=3, in0=u.data_ptr(), out0=w.data_ptr()))
+    b.calls.append(ar.ArExecCall(loop=1, n=0, sweeps=1))
+    b.check += [lambda: True] * 4
+    r = b.run(force=[3, 15, 0, 13, 1, 5, 13])
     assert r["status"][0] == 0 and r["status"][1] == ar.AR_ERR_ARG and r["status"][2] == ar.AR_ERR_ARG
+    assert list(r["status"][3:6]) == [ar.AR_ERR_ARG] * 3 and r["status"][6] == 0
     assert b.check[0]()
 
 
