@@ -41,8 +41,6 @@ static_assert(mp::kThreads == T, "merge-path tiles use the executor's block size
 
 __constant__ int c_nvar[4] = {kDaxpyVariants, kJacobiVariants, kSpmvVariants, kNbodyVariants};
 __constant__ int c_default[4] = {6, 1, 0, 3};
-__constant__ int c_nfeat[4] = {1, 3, 5, 1};
-__constant__ int c_dx_block[5] = {64, 128, 256, 512, 1024};
 __constant__ int c_dx_ept[3] = {1, 2, 4};
 __constant__ int c_j_bx[4] = {32, 32, 64, 128};
 __constant__ int c_j_by[4] = {4, 8, 4, 2};
@@ -372,8 +370,6 @@ __device__ void daxpy_tile(const ar_exec_call& k, int v, int64_t t) {
     if ((n & 1) && threadIdx.x == 0 && n - 1 >= base && n - 1 < base + kDxTile) y[n - 1] = fma(a, x[n - 1], y[n - 1]);
   }
 }
-
-__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 
 __device__ __forceinline__ double atcg(const double* __restrict__ u, int N, int i, int j, int k) {
   if ((unsigned)i >= (unsigned)N || (unsigned)j >= (unsigned)N || (unsigned)k >= (unsigned)N) return 0.0;

@@ -103,7 +103,6 @@ struct TmaGeom {
   static constexpr int PY = BY + 2;
   static constexpr int PLANE = PX * PY;          // elements per plane
   static constexpr int GROUP = PLANE * kDZ;      // elements per box
-  static constexpr int RING = kRing * kDZ;       // planes resident
   static constexpr uint32_t BYTES = GROUP * 8u;
   // a tensor copy's shared-memory destination must be 128-byte aligned: slots
   // start at multiples of SLOT elements from the 128-byte aligned ring base
