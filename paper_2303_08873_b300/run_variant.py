@@ -13,8 +13,10 @@ rate.
 
 With ``--exec`` the same call also runs as a one-call batch of the persistent
 mixed-stream executor (``ar_exec_batch``, variant forced) and both rates are
-printed.  Variant ``all`` runs every variant of the loop in turn (one line
-each), e.g. for a per-variant ncu launch list.
+printed.  With ``--floor`` (spmv) the gather-floor measurement kernel
+(``ar_spmv_gather_floor``) is timed on the same matrix.  Variant ``all`` runs
+every variant of the loop in turn (one line each), e.g. for a per-variant ncu
+launch list.
 """
 from __future__ import annotations
 
@@ -41,6 +43,8 @@ def main():
     p.add_argument("--zipf", type=float, default=1.5, help="Zipf exponent of the spmv row lengths")
     p.add_argument("--band", type=int, default=0, help="spmv: banded matrix of this (odd) width instead of Zipf")
     p.add_argument("--exec", action="store_true", help="also time the call through the executor (one-call batch)")
+    p.add_argument("--floor", action="store_true",
+                   help="spmv: also time ar_spmv_gather_floor (the memory-side floor) on the same matrix")
     a = p.parse_args()
     if a.exec and a.loop == "heat7":
         raise SystemExit("--exec: the executor runs daxpy, jacobi7, spmv and nbody only")
@@ -105,6 +109,11 @@ def main():
         ms = timed(make_run(var))
         line = {"loop": a.loop, "variant": var, "name": ar.loop_variant_name(L, var), "size": a.size, "ms": ms,
                 "rate": work / (ms * 1e-3) / 1e9, "unit": unit}
+        if a.floor and a.loop == "spmv":
+            sink = torch.empty(1, dtype=torch.int64, device=dev)
+            fms = timed(lambda: ar.ar_spmv_gather_floor(nnz, c, v, x, sink))
+            line.update({"floor_ms": fms, "floor_rate": work / (fms * 1e-3) / 1e9,
+                         "floor_gathers_per_s": nnz / (fms * 1e-3)})
         if a.exec:
             table = torch.frombuffer(bytearray(ar.exec_table_bytes([call])), dtype=torch.uint8).to(dev)
             outs = [torch.zeros(1, dtype=torch.int32, device=dev), torch.zeros(1, dtype=torch.float32, device=dev),
