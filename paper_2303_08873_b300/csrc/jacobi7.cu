@@ -125,7 +125,7 @@ struct TmaGeom {
 //             catch-up kernel)
 enum Mode { M_NATIVE = 0, M_DD = 1, M_DP = 2, M_PP = 3, M_PD = 4 };
 // How a tma / df sweep stages its planes.
-enum Staging { kStageSmem = 0, kStageTma = 1, kStageRing = 2 };
+enum Staging { kStageSmem = 0, kStageTma = 1, kStageRing = 2, kStageTmaOdd = 3 };
 
 template <int BX, int BY, int MODE, int ST>
 __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUtensorMap tmap,
@@ -299,6 +299,244 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
   }
 }
 
+// ------------------------------------------------------------------ TMA, odd N
+// Odd N: the row pitch N*8 is not a multiple of 16 bytes, so no 3D tensor map
+// exists.  The grid is viewed instead as a 2D tensor of width 2N (pitch 16N
+// bytes) and height (N^2 - 1) / 2: grid row R = kN + y (flat RN .. RN + N)
+// sits in 2D row R >> 1 at columns (R & 1) N + x.  A tile's BY + 2 rows of
+// one plane alternate between the two halves, so each plane is staged as two
+// half-boxes of (BX + 4) x (BY + 2) / 2: half b holds the rows with
+// (k + y) & 1 == b, copied from x = i0 - 2 - b (an even 2D column in both
+// halves, as a tensor copy needs), so element x of such a row sits at column
+// x - i0 + 2 + b.  TMA zero fill supplies the planes outside the grid; on
+// edge tiles the rows outside [0, N) and the columns outside [0, N) hold
+// neighbouring grid rows and are zeroed after landing, and the grid's last
+// row (flat N^3 - N .. N^3, past the 2D view's last full row) is loaded by
+// the threads.  Everything else is the jacobi_tma kernel: 4-plane groups in a
+// 3-slot ring, the same sweep modes, flag and catch-up.
+template <int BX, int BY>
+struct OddGeom {
+  static constexpr int PX = BX + 4;
+  static constexpr int HB = (BY + 2) / 2;          // rows per half-box
+  static constexpr int HALF = (PX * HB + 15) / 16 * 16;  // half-box stride: 128-byte aligned copies
+  static constexpr int PLANE = 2 * HALF;
+  static constexpr int GROUP = PLANE * kDZ;
+  static constexpr uint32_t BYTES = 2u * kDZ * PX * HB * 8u;  // bytes landed per group
+  static constexpr size_t SMEM = (size_t)kRing * GROUP * 8 + 128;
+  static_assert((BY + 2) % 2 == 0, "tile rows split evenly between the halves");
+  static_assert(HALF * 8 % 128 == 0 && GROUP * 8 % 128 == 0, "tensor-copy destinations stay 128-byte aligned");
+};
+
+template <int BX, int BY, int MODE, int ST>
+__global__ void __launch_bounds__(BX* BY) jacobi_tma_odd(const __grid_constant__ CUtensorMap tmap,
+                                                         const __grid_constant__ CUtensorMap tmap_alt, int N, int KC,
+                                                         const double* __restrict__ in, void* __restrict__ outv,
+                                                         const double* __restrict__ in_alt,
+                                                         double* __restrict__ out_alt, int* status, int* flag,
+                                                         StencilCoef cf) {
+  using G = OddGeom<BX, BY>;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[kRing];
+  double* buf = reinterpret_cast<double*>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
+
+  const int tid = threadIdx.x;
+  const int tx = tid % BX, ty = tid / BX;
+  const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY, y0 = j0 - 1;
+  const int kb = blockIdx.z * KC;
+  const int kc = min(KC, N - kb);
+  const int ngroups = (kc + 2 + kDZ - 1) / kDZ;
+  const bool flagged = (MODE == M_PP || MODE == M_PD) && flag != nullptr && *flag != 0;
+  const bool native = (MODE == M_NATIVE) || flagged;
+  const bool split_boxes = !native && (MODE == M_DD || MODE == M_DP);
+  const CUtensorMap* src_map = flagged ? &tmap_alt : &tmap;
+  const double* src = flagged ? in_alt : in;  // the staged data (for the edge fix-ups)
+  // block-uniform: a tile that meets the grid's x or y faces holds copied
+  // values of neighbouring grid rows to zero (and maybe the last row to load)
+  const bool edge = i0 == 0 || i0 + BX + 2 > N || j0 == 0 || j0 + BY + 1 >= N;
+
+  if (tid == 0) {
+    for (int r = 0; r < kRing; ++r) mbar_init(smem_addr(&bars[r]), 1);
+    mbar_fence_init();
+  }
+  // the padding after each half-box is never copied: zero it once, so that
+  // splitting a landed group in place reads no garbage (which would mark it)
+  constexpr int kPad = G::HALF - G::PX * G::HB;
+  for (int e = tid; e < kRing * kDZ * 2 * kPad; e += BX * BY)
+    buf[(e / kPad) * G::HALF + G::PX * G::HB + e % kPad] = 0.0;
+  fence_proxy_async_smem();
+  __syncthreads();
+
+  auto issue = [&](int g) {
+    const int slot = g % kRing;
+    const uint32_t bar = smem_addr(&bars[slot]);
+    mbar_arrive_expect_tx(bar, G::BYTES);
+    double* sb = buf + (size_t)slot * G::GROUP;
+#pragma unroll
+    for (int r = 0; r < kDZ; ++r) {
+      const int k = kb - 1 + g * kDZ + r;
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const int yb = y0 + ((((k + y0) & 1) == b) ? 0 : 1);  // first tile row of parity b
+        const long long R = (long long)k * N + yb;
+        const int yrow = (int)((R - b) >> 1);                  // R - b is even: exact, also below 0
+        tma_load_2d(smem_addr(sb + r * G::PLANE + b * G::HALF), src_map, b * N + i0 - 2 - b, yrow, bar);
+      }
+    }
+  };
+  if (tid == 0)
+    for (int g = 0; g < min(ngroups, kRing - 1); ++g) issue(g);
+
+  const int i = i0 + tx, j = j0 + ty;
+  const bool inside = i < N && j < N;
+  const int64_t NN = (int64_t)N * N;
+  const int64_t col = (int64_t)j * N + i;
+  // offsets in a plane: the centre row lies in half bc = (k + j) & 1 at
+  // column tx + 2 + bc; the rows j -+ 1 and the centres of the planes k -+ 1
+  // lie in the other half.  Output plane p of group g has its centre in
+  // group plane r - 1 with bc = q ^ (r & 1), q = (kb + j) & 1: bundle A (bc = q)
+  // for even r, bundle B (bc = 1 - q) for odd r.
+  const int q = (kb + j) & 1;
+  const int idc = (ty + 1) >> 1, ids = ty >> 1, idn = (ty + 2) >> 1;
+  auto cen = [&](int bc) { return bc * G::HALF + idc * G::PX + tx + 2 + bc; };
+  auto oth = [&](int bc, int id) { return (1 - bc) * G::HALF + id * G::PX + tx + 2 + (1 - bc); };
+  const int cA = cen(q), sA = oth(q, ids), nA = oth(q, idn), uA = oth(q, idc);
+  const int cB = cen(1 - q), sB = oth(1 - q, ids), nB = oth(1 - q, idn), uB = oth(1 - q, idc);
+  double* outd = flagged ? out_alt : static_cast<double*>(outv);
+  float2* outp = static_cast<float2*>(outv);
+  double dm = 0.0, d0 = 0.0;
+  float2 fm = make_float2(0.f, 0.f), f0 = make_float2(0.f, 0.f);
+  double* od = outd + ((int64_t)kb * NN + col);
+  float2* op = outp + ((int64_t)kb * NN + col);
+  int g = 0;
+  bool failed = false;
+  int slot = 0, pslot = kRing - 1;
+  uint32_t phase = 0;
+  for (; g < ngroups; ++g, pslot = slot, slot = (slot + 1 == kRing) ? 0 : slot + 1, phase ^= (slot == 0)) {
+    const bool ok = mbar_wait_bounded(smem_addr(&bars[slot]), phase);
+    double* box = buf + (size_t)slot * G::GROUP;
+    const double* prev = buf + (size_t)pslot * G::GROUP;
+    if (edge && ok) {
+      // one staged row per thread: zero it if it lies outside the grid, else
+      // zero its columns outside [0, N); load the grid's last row
+      for (int rr = tid; rr < kDZ * 2 * G::HB; rr += BX * BY) {
+        const int idx = rr % G::HB, b = (rr / G::HB) & 1, r = rr / (2 * G::HB);
+        const int k = kb - 1 + g * kDZ + r;
+        const int y = y0 + 2 * idx + ((((k + y0) & 1) == b) ? 0 : 1);
+        const int xb = i0 - 2 - b;  // x of the row's first column
+        double* d = box + r * G::PLANE + b * G::HALF + idx * G::PX;
+        if ((unsigned)y >= (unsigned)N || (unsigned)k >= (unsigned)N) {
+          for (int c = 0; c < G::PX; ++c) d[c] = 0.0;
+        } else {
+          const int c0 = max(0, -xb), c1 = min(G::PX, N - xb);  // columns inside the grid
+          for (int c = 0; c < c0; ++c) d[c] = 0.0;
+          for (int c = c1; c < G::PX; ++c) d[c] = 0.0;
+          if (k == N - 1 && y == N - 1) {
+            const double* row = src + ((int64_t)k * N + y) * N + xb;
+            for (int c = c0; c < c1; ++c) d[c] = __ldcg(row + c);
+          }
+        }
+      }
+    }
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    if (split_boxes) {
+      bool marker = false;
+#pragma unroll
+      for (int e = tid; e < G::GROUP; e += BX * BY) {
+        const float2 f = df_split(box[e]);
+        marker |= (f.x != f.x);
+        reinterpret_cast<float2*>(box)[e] = f;
+      }
+      if (__syncthreads_or(marker) && MODE == M_DP && tid == 0 && flag) atomicOr(flag, 1);
+    }
+    auto planes = [&](auto native_c, auto guard_c) {
+      constexpr bool NAT = decltype(native_c)::value;
+      constexpr bool GUARD = decltype(guard_c)::value;
+#pragma unroll
+      for (int r = 0; r < kDZ; ++r) {
+        const int p = g * kDZ - 1 + r;
+        const bool live = !GUARD || (p >= 1 && p <= kc);  // block-uniform
+        const int cc = (r & 1) ? cB : cA, cs = (r & 1) ? sB : sA, cn = (r & 1) ? nB : nA;
+        const int cu = (r & 1) ? uB : uA;
+        const int pb = r == 0 ? (kDZ - 1) * G::PLANE : (r - 1) * G::PLANE;
+        if constexpr (NAT) {
+          const double* pp = r == 0 ? prev : box;
+          const double up = box[r * G::PLANE + cu];
+          if (live) {
+            double s = pp[pb + cc - 1] + pp[pb + cc + 1];
+            s += pp[pb + cs];
+            s += pp[pb + cn];
+            s += dm;
+            s += up;
+            if (inside) *od = stencil_f64<ST>(pp[pb + cc], s, cf);
+            od += NN;
+          }
+          dm = d0;
+          d0 = up;
+        } else {
+          const float2* pp = reinterpret_cast<const float2*>(r == 0 ? prev : box);
+          const float2 up = reinterpret_cast<const float2*>(box)[r * G::PLANE + cu];
+          if (live) {
+            const float2 res =
+                stencil_pair<ST>(pp[pb + cc], pp[pb + cc - 1], pp[pb + cc + 1], pp[pb + cs], pp[pb + cn], fm, up, cf);
+            if (inside) {
+              if constexpr (MODE == M_DP || MODE == M_PP) {
+                *op = res;
+              } else {
+                double v = MODE == M_PD ? finite_pair_to_double(res) : pair_to_double(res);
+                if (MODE == M_DD && (__double_as_longlong(v) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) {
+                  const int k = kb + p - 1;
+                  double sd = at(in, N, i - 1, j, k) + at(in, N, i + 1, j, k);
+                  sd += at(in, N, i, j - 1, k);
+                  sd += at(in, N, i, j + 1, k);
+                  sd += at(in, N, i, j, k - 1);
+                  sd += at(in, N, i, j, k + 1);
+                  v = stencil_f64<ST>(at(in, N, i, j, k), sd, cf);
+                }
+                *od = v;
+              }
+            }
+            if constexpr (MODE == M_DP || MODE == M_PP)
+              op += NN;
+            else
+              od += NN;
+          }
+          fm = f0;
+          f0 = up;
+        }
+      }
+    };
+    using T_ = std::true_type;
+    using F_ = std::false_type;
+    const bool guard = g == 0 || g * kDZ + kDZ - 2 > kc;
+    if (native) {
+      if (guard)
+        planes(T_{}, T_{});
+      else
+        planes(T_{}, F_{});
+    } else {
+      if (guard)
+        planes(F_{}, T_{});
+      else
+        planes(F_{}, F_{});
+    }
+    // every reader of group g-1 is past this barrier: its slot takes group g+2
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0 && g + kRing - 1 < ngroups) issue(g + kRing - 1);
+  }
+  if (failed) {
+    if (tid == 0) {
+      if (status) atomicExch(status, (int)AR_ERR_TIMEOUT);
+      const int issued = min(ngroups, g + kRing - 1);
+      for (int h = g; h < issued; ++h) (void)mbar_wait_bounded(smem_addr(&bars[h % kRing]), (uint32_t)((h / kRing) & 1));
+    }
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ cp.async ring
 // The df family when tensor copies cannot be used (odd N): each block streams
 // its column's planes through a shared-memory ring (jacobi_ring.cuh), in the
@@ -356,6 +594,12 @@ bool tma_usable(int shape, int N, const void* a, const void* b, const void* c) {
   return !(N & 1) && N >= PX && N >= PY && N >= kDZ && aligned16(a) && (!b || aligned16(b)) && (!c || aligned16(c));
 }
 
+// Odd N: tensor copies through the 2N-wide view (jacobi_tma_odd).
+bool tma_odd_usable(int shape, int N, const void* a, const void* b, const void* c) {
+  const int PX = kShapeX[shape] + 4;
+  return (N & 1) && N >= PX && N >= 5 && aligned16(a) && (!b || aligned16(b)) && (!c || aligned16(c));
+}
+
 // Float64 sweep of the flagged pair chain's last step: does nothing unless
 // the first sweep flagged an input outside the float-pair range.
 template <int ST>
@@ -405,6 +649,36 @@ int launch_tma(int N, const double* in, void* out, const double* in_alt, double*
 }
 
 template <int BX, int BY, int MODE, int ST>
+int launch_tma_odd(int N, const double* in, void* out, const double* in_alt, double* out_alt, int* status,
+                   int* flag, const StencilCoef& cf, cudaStream_t s) {
+  using G = OddGeom<BX, BY>;
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(jacobi_tma_odd<BX, BY, MODE, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)G::SMEM);
+  });
+  if (attr_err != cudaSuccess) return AR_ERR_CUDA;
+  // the grid as 2N-wide rows: (N^2 - 1) / 2 full rows (the last grid row is
+  // loaded by the kernel)
+  const uint64_t W = 2ull * (uint64_t)N, H = ((uint64_t)N * N - 1) / 2;
+  CUtensorMap map, map_alt;
+  if (!encode_tensor_map_2d_f64(&map, in, W, H, W * 8, G::PX, G::HB) ||
+      !encode_tensor_map_2d_f64(&map_alt, in_alt ? in_alt : in, W, H, W * 8, G::PX, G::HB))
+    return AR_ERR_CUDA;
+  const int64_t cb = ceil_div(N, BX) * ceil_div(N, BY);
+  int resident = (int)((227 * 1024) / G::SMEM);
+  if (resident > 2048 / (BX * BY)) resident = 2048 / (BX * BY);
+  if (resident < 1) resident = 1;
+  int KC = chunk_planes(N, cb, resident, kDZ - 2, 8 * kDZ - 2);
+  KC = (int)(ceil_div(KC + 2, kDZ) * kDZ - 2);
+  dim3 grid((unsigned)ceil_div(N, BX), (unsigned)ceil_div(N, BY), (unsigned)ceil_div(N, KC));
+  jacobi_tma_odd<BX, BY, MODE, ST><<<grid, BX * BY, G::SMEM, s>>>(map, map_alt, N, KC, in, out, in_alt, out_alt,
+                                                                  status, flag, cf);
+  return launch_status();
+}
+
+template <int BX, int BY, int MODE, int ST>
 int launch_ring(int N, const double* in, void* out, const double* in_alt, double* out_alt, int* flag,
                 const StencilCoef& cf, cudaStream_t s) {
   constexpr int smem = ring_smem_bytes(BX, BY);
@@ -431,6 +705,15 @@ int launch_family(int fam, int mode, int staging, int N, const double* in, doubl
       default: return launch_ring<BX, BY, M_PD, ST>(N, in, out, in_alt, out_alt, flag, cf, s);
     }
   }
+  if (staging == kStageTmaOdd) {
+    switch (mode) {
+      case M_NATIVE: return launch_tma_odd<BX, BY, M_NATIVE, ST>(N, in, out, nullptr, nullptr, status, nullptr, cf, s);
+      case M_DD: return launch_tma_odd<BX, BY, M_DD, ST>(N, in, out, nullptr, nullptr, status, nullptr, cf, s);
+      case M_DP: return launch_tma_odd<BX, BY, M_DP, ST>(N, in, out, nullptr, nullptr, status, flag, cf, s);
+      case M_PP: return launch_tma_odd<BX, BY, M_PP, ST>(N, in, out, in_alt, out_alt, status, flag, cf, s);
+      default: return launch_tma_odd<BX, BY, M_PD, ST>(N, in, out, in_alt, out_alt, status, flag, cf, s);
+    }
+  }
   if (fam == 1 || staging != kStageTma) return launch_smem<BX, BY, ST>(N, in, out, cf, s);
   switch (mode) {
     case M_NATIVE: return launch_tma<BX, BY, M_NATIVE, ST>(N, in, out, nullptr, nullptr, status, nullptr, cf, s);
@@ -455,8 +738,8 @@ int sweep(int variant, int mode, int staging, int N, const double* in, double* o
 
 }  // namespace
 
-bool encode_tensor_map_3d_f64(CUtensorMap* map, const void* base, uint64_t d0, uint64_t d1, uint64_t d2,
-                              uint32_t b0, uint32_t b1, uint32_t b2) {
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   static std::once_flag once;
   std::call_once(once, [] {
@@ -467,12 +750,33 @@ bool encode_tensor_map_3d_f64(CUtensorMap* map, const void* base, uint64_t d0, u
         q == cudaDriverEntryPointSuccess)
       encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   });
+  return encode;
+}
+}  // namespace
+
+bool encode_tensor_map_3d_f64(CUtensorMap* map, const void* base, uint64_t d0, uint64_t d1, uint64_t d2,
+                              uint32_t b0, uint32_t b1, uint32_t b2) {
+  auto encode = tensor_map_encoder();
   if (!encode) return false;
   cuuint64_t dims[3] = {d0, d1, d2};
   cuuint64_t strides[2] = {d0 * 8, d0 * d1 * 8};
   cuuint32_t box[3] = {b0, b1, b2};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<void*>(base), dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+bool encode_tensor_map_2d_f64(CUtensorMap* map, const void* base, uint64_t d0, uint64_t d1, uint64_t pitch_bytes,
+                              uint32_t b0, uint32_t b1) {
+  auto encode = tensor_map_encoder();
+  if (!encode) return false;
+  cuuint64_t dims[2] = {d0, d1};
+  cuuint64_t strides[1] = {pitch_bytes};
+  cuuint32_t box[2] = {b0, b1};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void*>(base), dims, strides, box, estr,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -528,8 +832,9 @@ int stencil_run(int variant, int N, int sweeps, const StencilCoef& cf, const dou
   // family otherwise (odd N) streams them by cp.async; 16-byte aligned
   // buffers are needed either way, else the shared-memory tile runs
   const double* w = sweeps > 1 ? work : nullptr;
-  const int staging = fam < 2                                ? kStageSmem
-                      : tma_usable(variant % 4, N, u0, out, w) ? kStageTma
+  const int staging = fam < 2                                    ? kStageSmem
+                      : tma_usable(variant % 4, N, u0, out, w)     ? kStageTma
+                      : tma_odd_usable(variant % 4, N, u0, out, w) ? kStageTmaOdd
                       : (fam == 3 && aligned16(u0) && aligned16(out) && (!w || aligned16(w))) ? kStageRing
                                                                                                : kStageSmem;
   const bool staged = staging != kStageSmem;

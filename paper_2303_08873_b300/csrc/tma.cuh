@@ -65,6 +65,16 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// 2D tiled TMA load of one box at element coordinates (x, y); the same rules
+// as tma_load_3d.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
 // Asynchronous 16-byte global -> shared copy (cp.async, L1 bypassed, so data
 // written earlier in the same launch by other SMs is seen): src_bytes (0, 8
 // or 16) are read, the rest of the 16 bytes is zero-filled.  Both addresses
@@ -122,5 +132,9 @@ __device__ __forceinline__ void tmap_acquire(const void* map) {
 // encode call rejects the arguments.
 bool encode_tensor_map_3d_f64(CUtensorMap* map, const void* base, uint64_t d0, uint64_t d1, uint64_t d2,
                               uint32_t b0, uint32_t b1, uint32_t b2);
+// Host: the same for a dense 2D (d1, d0) float64 array with row pitch
+// `pitch_bytes` (a multiple of 16).
+bool encode_tensor_map_2d_f64(CUtensorMap* map, const void* base, uint64_t d0, uint64_t d1, uint64_t pitch_bytes,
+                              uint32_t b0, uint32_t b1);
 
 }  // namespace ar

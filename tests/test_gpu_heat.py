@@ -157,3 +157,12 @@ def test_region_selects_among_heat_variants():
         seen.add(v)
         _check(host(out), ref, ("region", v))
     assert seen == set(range(V))
+
+
+@pytest.mark.parametrize("N", [37, 133])
+def test_odd_n_tensor_copies(N):
+    u0 = synth.grid_inputs(60 + N, N)
+    ref = loops.heat7(u0, 4, 0.125)
+    for v in range(8, 16):
+        _check(_run(v, u0, 4, 0.125), ref, (ar.loop_variant_name(HEAT, v), N), u0)
+

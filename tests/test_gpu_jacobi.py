@@ -148,3 +148,35 @@ def test_two_sweep_pair_chain_with_flagged_input():
     st = torch.zeros(2, dtype=torch.int32, device="cuda")
     for v in range(12, 16):
         _check(_run(v, u0, 2, st), ref, ("flagged 2 sweeps", v))
+
+
+@pytest.mark.parametrize("N", [37, 71, 135])
+@pytest.mark.parametrize("sweeps", [1, 2, 5])
+def test_odd_n_tensor_copies(N, sweeps):
+    """Odd N >= BX + 4: the tma and df families stage planes through the
+    2N-wide view of the grid (two half-boxes per plane, zeroed edges, the last
+    grid row loaded by the threads)."""
+    u0 = synth.grid_inputs(40 + N, N)
+    ref = loops.jacobi7(u0, sweeps)
+    status = torch.zeros(2, dtype=torch.int32, device="cuda")
+    for v in range(8, 16):
+        _check(_run(v, u0, sweeps, status), ref, (ar.loop_variant_name(1, v), N, sweeps))
+        assert int(status[0].item()) == 0
+    for v in range(12, 16):
+        _check(_run(v, u0, sweeps, None), ref, (ar.loop_variant_name(1, v), N, sweeps, "no status"))
+
+
+def test_odd_n_range_guard():
+    N = 41
+    u0 = synth.grid_inputs(48, N)
+    u0[5, 6, 7] = 1e-30
+    u0[20, 20, 20] = 3e40
+    u0[N - 1, N - 1, N - 1] = 2.5  # the grid's last row, past the 2N-wide view
+    ref = loops.jacobi7(u0, 3)
+    big = np.abs(ref) > 1e3
+    st = torch.zeros(2, dtype=torch.int32, device="cuda")
+    for v in range(12, 16):
+        out = _run(v, u0, 3, st)
+        _check(out[~big], ref[~big], ("odd df mixed", v))
+        assert np.all(np.abs(out[big] - ref[big]) <= 1e-15 * np.abs(ref[big]) * 8)
+
