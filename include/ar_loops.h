@@ -71,9 +71,11 @@ int ar_daxpy(int variant, int64_t n, double a, const double *x, double *y, void 
  * float-pair arithmetic on the FP32 pipe, ~2^-46 relative; points whose
  * inputs lie outside [2^-74, 2^118) in magnitude are recomputed in float64)}
  * x block shape {32x4, 32x8,
- * 64x4, 128x2}; variant = 4*family + shape.  The tma family needs even N
- * (16-byte row pitch), N >= BX+4 and 16-byte aligned buffers; otherwise the
- * tma and df families run the smem kernel of the same shape.  Default: naive 32x8 (variant 1).
+ * 64x4, 128x2}; variant = 4*family + shape.  The tma family needs N >= BX+4
+ * and 16-byte aligned buffers (odd N: tensor copies through a 2N-wide view of
+ * the grid); otherwise the tma family runs the smem kernel of the same shape
+ * and the df family a cp.async plane ring (aligned buffers) or the smem
+ * kernel.  Default: naive 32x8 (variant 1).
  * `status` (device int[2], may be NULL): status[0] receives AR_ERR_TIMEOUT if
  * a bounded wait inside a tma/df kernel gave up (the caller zeroes it);
  * status[1] is scratch for the df family, which with a status array and 2+
