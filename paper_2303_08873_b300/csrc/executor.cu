@@ -214,11 +214,27 @@ __device__ void make_grid_map(CUtensorMap* dst, const CUtensorMap& tm, const voi
   tmap_set_stride<1>(dst, (unsigned long long)N * N * 8ull);
 }
 
+// Odd N: the map of the grid's 2N-wide 2D view (rows of 2N float64, pitch
+// 16N bytes, (N^2 - 1) / 2 rows; see jacobi_tma_odd_tile).
+__device__ void make_grid_map_2d(CUtensorMap* dst, const CUtensorMap& tm, const void* base, int N) {
+  const uint4* s4 = reinterpret_cast<const uint4*>(&tm);
+  uint4* d4 = reinterpret_cast<uint4*>(dst);
+  for (int q = 0; q < (int)(sizeof(CUtensorMap) / sizeof(uint4)); ++q) d4[q] = s4[q];
+  tmap_set_address(dst, base);
+  tmap_set_dim<0>(dst, 2 * N);
+  tmap_set_dim<1>(dst, (int)(((long long)N * N - 1) / 2));
+  tmap_set_stride<0>(dst, (unsigned long long)N * 16ull);
+}
+
 // One-time check of the device-made maps against the host encoding (see
-// tma_templates_ready).
-__global__ void exec_tmap_check(const __grid_constant__ CUtensorMap tm, CUtensorMap* out, const void* base, int N) {
+// tma_templates_ready); twod selects the 2D view of odd N.
+__global__ void exec_tmap_check(const __grid_constant__ CUtensorMap tm, CUtensorMap* out, const void* base, int N,
+                                bool twod) {
   if (threadIdx.x == 0) {
-    make_grid_map(out, tm, base, N);
+    if (twod)
+      make_grid_map_2d(out, tm, base, N);
+    else
+      make_grid_map(out, tm, base, N);
     tmap_release();
   }
 }
@@ -232,7 +248,9 @@ __global__ void __launch_bounds__(T) exec_plan(const ar_exec_call* __restrict__ 
                                                uint64_t* __restrict__ t0, uint64_t* __restrict__ t1,
                                                int* __restrict__ status, int* __restrict__ vint,
                                                const __grid_constant__ CUtensorMap tm4,
-                                               const __grid_constant__ CUtensorMap tm8, bool tma_ok,
+                                               const __grid_constant__ CUtensorMap tm8,
+                                               const __grid_constant__ CUtensorMap to4,
+                                               const __grid_constant__ CUtensorMap to8, bool tma_ok, bool tma_odd_ok,
                                                CUtensorMap* __restrict__ maps, int* __restrict__ usetma) {
   __shared__ long long scan[T];
   const int c = threadIdx.x;
@@ -285,15 +303,21 @@ __global__ void __launch_bounds__(T) exec_plan(const ar_exec_call* __restrict__ 
     // tensor maps of u0, out and work for the tensor-copy Jacobi tiles (tma
     // and df families, shapes 32x4 and 32x8): even N at least one box wide,
     // 16-byte aligned buffers
+    // (odd N: maps of the grid's 2N-wide 2D view)
     int use = 0;
-    if (tma_ok && st == AR_OK && k.loop == AR_LOOP_JACOBI7 && v / 4 >= 2 && v % 4 <= 1) {
+    const bool odd = k.n % 2 != 0;
+    if ((odd ? tma_odd_ok : tma_ok) && st == AR_OK && k.loop == AR_LOOP_JACOBI7 && v / 4 >= 2 && v % 4 <= 1) {
       const bool two = k.sweeps > 1;
       const uintptr_t al = (uintptr_t)k.in0 | (uintptr_t)k.out0 | (two ? (uintptr_t)k.out1 : 0);
-      if (k.n % 2 == 0 && k.n >= 36 && k.n <= 65535 && (al & 15) == 0 && k.in0 && k.out0 && (!two || k.out1)) {
-        const CUtensorMap& tm = v % 4 == 0 ? tm4 : tm8;
-        make_grid_map(maps + 3 * c, tm, k.in0, (int)k.n);
-        make_grid_map(maps + 3 * c + 1, tm, k.out0, (int)k.n);
-        if (two) make_grid_map(maps + 3 * c + 2, tm, k.out1, (int)k.n);
+      if (k.n >= 36 && k.n <= 65535 && (al & 15) == 0 && k.in0 && k.out0 && (!two || k.out1)) {
+        const void* bufs[3] = {k.in0, k.out0, two ? k.out1 : nullptr};
+        for (int q = 0; q < 3; ++q) {
+          if (!bufs[q]) continue;
+          if (odd)
+            make_grid_map_2d(maps + 3 * c + q, v % 4 == 0 ? to4 : to8, bufs[q], (int)k.n);
+          else
+            make_grid_map(maps + 3 * c + q, v % 4 == 0 ? tm4 : tm8, bufs[q], (int)k.n);
+        }
         tmap_release();
         use = 1;
       }
@@ -541,6 +565,201 @@ __device__ bool jacobi_tma_tile(const CUtensorMap* map, int N, int bx, int by, i
   return !failed;
 }
 
+// Odd N: the same tile through the grid's 2N-wide 2D view (`map` made by
+// make_grid_map_2d): each plane lands as two half-boxes of 36 x (BY+2)/2,
+// half b holding the rows with (k + y) & 1 == b from x = i0 - 2 - b, so
+// element x sits at column x - i0 + 2 + b; rows and columns outside the grid
+// are zeroed on edge tiles and the grid's last row (past the view) is loaded
+// by the threads -- the staging of the stand-alone jacobi_tma_odd kernel.
+template <int BX, int BY>
+struct XOddGeom {
+  static constexpr int PX = BX + 4, HB = (BY + 2) / 2;
+  static constexpr int HALF = (PX * HB + 15) / 16 * 16;  // 128-byte aligned half-boxes
+  static constexpr int PLANE = 2 * HALF, GROUP = PLANE * kXDZ;
+  static constexpr uint32_t BYTES = 2u * kXDZ * PX * HB * 8u;
+  static constexpr int SMEM = kXRing * GROUP * 8;  // the tile shared memory is 128-byte aligned
+};
+
+template <int BX, int BY>
+__device__ bool jacobi_tma_odd_tile(const CUtensorMap* map, int N, int bx, int by, int kb, int ke, const double* src,
+                                    double* dst, bool pair_math, bool src_pairs, bool dst_pairs, int* flag,
+                                    unsigned char* smraw, uint64_t* bars) {
+  using G = XOddGeom<BX, BY>;
+  double* buf = reinterpret_cast<double*>(smraw);
+  const int tid = threadIdx.x;
+  const bool active = tid < BX * BY;
+  const int tx = tid % BX, ty = active ? tid / BX : 0;  // idle threads read valid slot entries
+  const int i0 = bx * BX, j0 = by * BY, y0 = j0 - 1;
+  const int kc = ke - kb;
+  const int ngroups = (kc + 2 + kXDZ - 1) / kXDZ;
+  const bool split = pair_math && !src_pairs;
+  const bool edge = i0 == 0 || i0 + BX + 2 > N || j0 == 0 || j0 + BY + 1 >= N;
+  constexpr int kPad = G::HALF - G::PX * G::HB;
+  for (int e = tid; e < kXRing * kXDZ * 2 * kPad; e += T)  // never copied: keep the splits clean
+    buf[(e / kPad) * G::HALF + G::PX * G::HB + e % kPad] = 0.0;
+  if (tid == 0) {
+    for (int r = 0; r < kXRing; ++r) mbar_init(smem_addr(&bars[r]), 1);
+    mbar_fence_init();
+    fence_proxy_async_global();  // the previous sweep's stores before these tensor copies
+    tmap_acquire(map);
+  }
+  fence_proxy_async_smem();
+  __syncthreads();
+  auto issue = [&](int g) {
+    const int slot = g % kXRing;
+    const uint32_t bar = smem_addr(&bars[slot]);
+    mbar_arrive_expect_tx(bar, G::BYTES);
+    double* sb = buf + (size_t)slot * G::GROUP;
+#pragma unroll
+    for (int r = 0; r < kXDZ; ++r) {
+      const int k = kb - 1 + g * kXDZ + r;
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const int yb = y0 + ((((k + y0) & 1) == b) ? 0 : 1);
+        const long long R = (long long)k * N + yb;
+        tma_load_2d(smem_addr(sb + r * G::PLANE + b * G::HALF), map, b * N + i0 - 2 - b, (int)((R - b) >> 1), bar);
+      }
+    }
+  };
+  if (tid == 0)
+    for (int g = 0; g < min(ngroups, kXRing - 1); ++g) issue(g);
+  const int i = i0 + tx, j = j0 + ty;
+  const bool inside = active && i < N && j < N;
+  const int64_t NN = (int64_t)N * N;
+  const int q = (kb + j) & 1;
+  const int idc = (ty + 1) >> 1, ids = ty >> 1, idn = (ty + 2) >> 1;
+  auto cen = [&](int bc) { return bc * G::HALF + idc * G::PX + tx + 2 + bc; };
+  auto oth = [&](int bc, int id) { return (1 - bc) * G::HALF + id * G::PX + tx + 2 + (1 - bc); };
+  const int cA = cen(q), sA = oth(q, ids), nA = oth(q, idn), uA = oth(q, idc);
+  const int cB = cen(1 - q), sB = oth(1 - q, ids), nB = oth(1 - q, idn), uB = oth(1 - q, idc);
+  double* od = dst + ((int64_t)kb * NN + (int64_t)j * N + i);
+  float2* op = reinterpret_cast<float2*>(dst) + ((int64_t)kb * NN + (int64_t)j * N + i);
+  double dm = 0.0, d0 = 0.0;
+  float2 fm = make_float2(0.f, 0.f), f0 = make_float2(0.f, 0.f);
+  bool marker_any = false;
+  int g = 0, slot = 0, pslot = kXRing - 1;
+  uint32_t phase = 0;
+  bool failed = false;
+  for (; g < ngroups; ++g, pslot = slot, slot = (slot + 1 == kXRing) ? 0 : slot + 1, phase ^= (slot == 0)) {
+    const bool ok = mbar_wait_bounded(smem_addr(&bars[slot]), phase);
+    double* box = buf + (size_t)slot * G::GROUP;
+    const double* prev = buf + (size_t)pslot * G::GROUP;
+    if (edge && ok) {
+      for (int rr = tid; rr < kXDZ * 2 * G::HB; rr += T) {
+        const int idx = rr % G::HB, b = (rr / G::HB) & 1, r = rr / (2 * G::HB);
+        const int k = kb - 1 + g * kXDZ + r;
+        const int y = y0 + 2 * idx + ((((k + y0) & 1) == b) ? 0 : 1);
+        const int xb = i0 - 2 - b;
+        double* d = box + r * G::PLANE + b * G::HALF + idx * G::PX;
+        if ((unsigned)y >= (unsigned)N || (unsigned)k >= (unsigned)N) {
+          for (int c = 0; c < G::PX; ++c) d[c] = 0.0;
+        } else {
+          const int c0 = max(0, -xb), c1 = min(G::PX, N - xb);
+          for (int c = 0; c < c0; ++c) d[c] = 0.0;
+          for (int c = c1; c < G::PX; ++c) d[c] = 0.0;
+          if (k == N - 1 && y == N - 1) {
+            const double* row = src + ((int64_t)k * N + y) * N + xb;
+            for (int c = c0; c < c1; ++c) d[c] = __ldcg(row + c);
+          }
+        }
+      }
+    }
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    if (split) {
+      bool marker = false;
+      for (int e = tid; e < G::GROUP; e += T) {
+        const float2 f = df_split(box[e]);
+        marker |= (f.x != f.x);
+        reinterpret_cast<float2*>(box)[e] = f;
+      }
+      marker_any |= __syncthreads_or(marker);
+    }
+    auto planes = [&](auto native_c, auto guard_c) {
+      constexpr bool NAT = decltype(native_c)::value;
+      constexpr bool GUARD = decltype(guard_c)::value;
+#pragma unroll
+      for (int r = 0; r < kXDZ; ++r) {
+        const int p = g * kXDZ - 1 + r;
+        const bool live = !GUARD || (p >= 1 && p <= kc);  // block-uniform
+        const int cc = (r & 1) ? cB : cA, cs = (r & 1) ? sB : sA, cn = (r & 1) ? nB : nA, cu = (r & 1) ? uB : uA;
+        const int pb = r == 0 ? (kXDZ - 1) * G::PLANE : (r - 1) * G::PLANE;
+        if constexpr (NAT) {
+          const double* pp = r == 0 ? prev : box;
+          const double up = box[r * G::PLANE + cu];
+          if (live) {
+            double s = pp[pb + cc - 1] + pp[pb + cc + 1];
+            s += pp[pb + cs];
+            s += pp[pb + cn];
+            s += dm;
+            s += up;
+            if (inside) *od = s * kSixth;
+            od += NN;
+          }
+          dm = d0;
+          d0 = up;
+        } else {
+          const float2* pp = reinterpret_cast<const float2*>(r == 0 ? prev : box);
+          const float2 up = reinterpret_cast<const float2*>(box)[r * G::PLANE + cu];
+          if (live) {
+            const float2 res = df_avg6(pp[pb + cc - 1], pp[pb + cc + 1], pp[pb + cs], pp[pb + cn], fm, up);
+            if (inside) {
+              if (dst_pairs) {
+                *op = res;
+              } else {
+                double v = src_pairs ? finite_pair_to_double(res) : pair_to_double(res);
+                if (!src_pairs && (__double_as_longlong(v) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) {
+                  const int k = kb + p - 1;
+                  double sd = atcg(src, N, i - 1, j, k) + atcg(src, N, i + 1, j, k);
+                  sd += atcg(src, N, i, j - 1, k);
+                  sd += atcg(src, N, i, j + 1, k);
+                  sd += atcg(src, N, i, j, k - 1);
+                  sd += atcg(src, N, i, j, k + 1);
+                  v = sd * kSixth;
+                }
+                *od = v;
+              }
+            }
+            op += NN;
+            od += NN;
+          }
+          fm = f0;
+          f0 = up;
+        }
+      }
+    };
+    using T_ = std::true_type;
+    using F_ = std::false_type;
+    const bool guard = g == 0 || g * kXDZ + kXDZ - 2 > kc;
+    if (!pair_math) {
+      if (guard)
+        planes(T_{}, T_{});
+      else
+        planes(T_{}, F_{});
+    } else {
+      if (guard)
+        planes(F_{}, T_{});
+      else
+        planes(F_{}, F_{});
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0 && g + kXRing - 1 < ngroups) issue(g + kXRing - 1);
+  }
+  if (failed && tid == 0) {
+    const int issued = min(ngroups, g + kXRing - 1);
+    for (int h = g; h < issued; ++h) (void)mbar_wait_bounded(smem_addr(&bars[h % kXRing]), (uint32_t)((h / kXRing) & 1));
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int r = 0; r < kXRing; ++r) mbar_inval(smem_addr(&bars[r]));
+  if (dst_pairs && split && marker_any && tid == 0 && flag) atomicOr(flag, 1);
+  fence_proxy_async_global();  // these stores before later tensor copies of dst
+  return !failed;
+}
+
 // One BX x BY x 16-plane tile of one sweep, 2.5D: an xy tile with halo in
 // shared memory (double buffered), z neighbours in registers.  Values are
 // float64 or float pairs in memory (src_pairs / dst_pairs); `pair_math`
@@ -559,6 +778,11 @@ __device__ bool jacobi_sweep_tile(const ar_exec_call& k, int v, int64_t t, const
   const int bx = (int)(t % gx), by = (int)((t / gx) % gy), bz = (int)(t / (gx * gy));
   const int kb = bz * kJKC, ke = min(N, kb + kJKC);
   if (map && fam >= 2 && v % 4 <= 1) {
+    if (N & 1)
+      return v % 4 == 0 ? jacobi_tma_odd_tile<32, 4>(map, N, bx, by, kb, ke, src, dst, pair_math, src_pairs,
+                                                     dst_pairs, flag, smraw, bars)
+                        : jacobi_tma_odd_tile<32, 8>(map, N, bx, by, kb, ke, src, dst, pair_math, src_pairs,
+                                                     dst_pairs, flag, smraw, bars);
     return v % 4 == 0 ? jacobi_tma_tile<32, 4>(map, N, bx, by, kb, ke, src, dst, pair_math, src_pairs, dst_pairs,
                                                flag, smraw, bars)
                       : jacobi_tma_tile<32, 8>(map, N, bx, by, kb, ke, src, dst, pair_math, src_pairs, dst_pairs,
@@ -832,8 +1056,9 @@ __device__ void nbody_tile(const ar_exec_call& k, int v, int64_t t, unsigned cha
 // largest tile: a merge-path block (staged products and row ends, open rows,
 // partial sums) plus its two path bounds; Jacobi needs 2 x 4 x 130 doubles
 constexpr int kSmemBytes = mp::kSmemBytes + 16;
-static_assert(XGeom<32, 4>::SMEM <= kSmemBytes && XGeom<32, 8>::SMEM <= kSmemBytes,
-              "the tensor-copy box ring fits the tile shared memory");
+static_assert(XGeom<32, 4>::SMEM <= kSmemBytes && XGeom<32, 8>::SMEM <= kSmemBytes &&
+                  XOddGeom<32, 4>::SMEM <= kSmemBytes && XOddGeom<32, 8>::SMEM <= kSmemBytes,
+              "the tensor-copy box rings fit the tile shared memory");
 static_assert(kSmemBytes >= 8448, "shared memory of the Jacobi and n-body tiles");
 static_assert(ring_smem_bytes(32, 4) <= kSmemBytes && ring_smem_bytes(32, 8) <= kSmemBytes &&
                   ring_smem_bytes(64, 4) <= kSmemBytes && ring_smem_bytes(128, 2) <= kSmemBytes,
@@ -847,7 +1072,7 @@ __global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_cal
                                                  unsigned long long* counter, uint64_t* t0, uint64_t* t1,
                                                  int* status, int* flags, const CUtensorMap* __restrict__ maps,
                                                  const int* __restrict__ usetma) {
-  __shared__ __align__(16) unsigned char smraw[kSmemBytes];
+  __shared__ __align__(128) unsigned char smraw[kSmemBytes];  // tensor-copy destinations
   __shared__ __align__(8) uint64_t s_bars[kXRing];
   __shared__ long long s_item, s_t;
   __shared__ int s_c, s_p, s_ok;
@@ -965,38 +1190,47 @@ WsLayout layout(int max_calls) {
 // in which case this batch stages Jacobi planes by cp.async instead).  Any
 // mismatch or encode failure turns tensor copies off for the process.
 struct MapTemplates {
-  CUtensorMap tm4, tm8;
+  CUtensorMap tm4, tm8;  // 3D, even N
+  CUtensorMap to4, to8;  // 2D view, odd N
+  bool even_ok, odd_ok;
 };
+// One template check: a device-made map of a test grid against the host
+// encoding of the same grid.
+bool template_matches(const CUtensorMap& t, bool twod, int N, int box_rows, unsigned char* scratch, int slot,
+                      cudaStream_t s) {
+  const unsigned char* base = scratch + 1024 * (slot + 1);
+  CUtensorMap want, got;
+  const bool enc = twod ? encode_tensor_map_2d_f64(&want, base, 2ull * N, ((uint64_t)N * N - 1) / 2, 16ull * N, 36,
+                                                   (uint32_t)box_rows)
+                        : encode_tensor_map_3d_f64(&want, base, N, N, N, 36, (uint32_t)box_rows, kXDZ);
+  if (!enc) return false;
+  exec_tmap_check<<<1, 32, 0, s>>>(t, reinterpret_cast<CUtensorMap*>(scratch), base, N, twod);
+  return cudaMemcpyAsync(&got, scratch, sizeof got, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+         cudaStreamSynchronize(s) == cudaSuccess && std::memcmp(&want, &got, sizeof got) == 0;
+}
 bool tma_templates_ready(unsigned char* scratch, cudaStream_t s, MapTemplates* out) {
   static std::mutex mu;
-  static int state = 0;  // 0 unchecked, 1 usable, -1 off
-  static MapTemplates tm;
+  static int state = 0;  // 0 unchecked, 1 checked
+  static MapTemplates tm{};
   std::lock_guard<std::mutex> lock(mu);
   if (state == 0) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
-    state = -1;
-    if (encode_tensor_map_3d_f64(&tm.tm4, scratch, 64, 64, 64, 36, 6, kXDZ) &&
-        encode_tensor_map_3d_f64(&tm.tm8, scratch, 64, 64, 64, 36, 10, kXDZ)) {
-      bool same = true;
-      const int Ns[2] = {96, 512};
-      for (int q = 0; q < 2 && same; ++q) {
-        const CUtensorMap& t = q == 0 ? tm.tm4 : tm.tm8;
-        const unsigned char* base = scratch + 1024 * (q + 1);
-        CUtensorMap want, got;
-        if (!encode_tensor_map_3d_f64(&want, base, Ns[q], Ns[q], Ns[q], 36, q == 0 ? 6 : 10, kXDZ)) {
-          same = false;
-          break;
-        }
-        exec_tmap_check<<<1, 32, 0, s>>>(t, reinterpret_cast<CUtensorMap*>(scratch), base, Ns[q]);
-        same = cudaMemcpyAsync(&got, scratch, sizeof got, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
-               cudaStreamSynchronize(s) == cudaSuccess && std::memcmp(&want, &got, sizeof got) == 0;
-      }
-      if (same) state = 1;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+      *out = MapTemplates{};
+      return false;
     }
+    state = 1;
+    tm.even_ok = encode_tensor_map_3d_f64(&tm.tm4, scratch, 64, 64, 64, 36, 6, kXDZ) &&
+                 encode_tensor_map_3d_f64(&tm.tm8, scratch, 64, 64, 64, 36, 10, kXDZ) &&
+                 template_matches(tm.tm4, false, 96, 6, scratch, 0, s) &&
+                 template_matches(tm.tm8, false, 512, 10, scratch, 1, s);
+    tm.odd_ok = encode_tensor_map_2d_f64(&tm.to4, scratch, 130, 2112, 1040, 36, 3) &&
+                encode_tensor_map_2d_f64(&tm.to8, scratch, 130, 2112, 1040, 36, 5) &&
+                template_matches(tm.to4, true, 97, 3, scratch, 2, s) &&
+                template_matches(tm.to8, true, 511, 5, scratch, 3, s);
   }
   *out = tm;
-  return state == 1;
+  return tm.even_ok || tm.odd_ok;
 }
 
 }  // namespace
@@ -1054,8 +1288,8 @@ extern "C" int ar_exec_batch(const ar_exec_call* calls, int ncalls, const ar_exe
   if (cudaMemsetAsync(flags, 0, (size_t)ncalls * 4, s) != cudaSuccess) return AR_ERR_CUDA;
   exec_features<<<dim3(64, (unsigned)ncalls), T, 0, s>>>(calls, features, part);
   exec_plan<<<1, T, 0, s>>>(calls, ncalls, m, have, force_variant, variant, conf, features, part, tiles, prefix,
-                            done, counter, t_start, t_end, status, vint, tmt.tm4, tmt.tm8, tma_ok, maps,
-                            usetma);
+                            done, counter, t_start, t_end, status, vint, tmt.tm4, tmt.tm8, tmt.to4, tmt.to8,
+                            tma_ok && tmt.even_ok, tma_ok && tmt.odd_ok, maps, usetma);
   exec_run<<<device_sms() * kRunBlocksPerSm, T, 0, s>>>(calls, ncalls, vint, tiles, prefix, done, counter, t_start, t_end, status,
                                           flags, maps, usetma);
   return launch_status();

@@ -183,16 +183,19 @@ def test_float_pair_chain_with_and_without_range_flag():
 
 
 def test_jacobi_tensor_copy_tiles():
-    """tma and df variants of shapes 32x4 and 32x8 on even N >= 36 stage
-    their planes by tensor copies through maps the plan kernel makes on the
-    device: every mode of the pair chain, the float64 and float-pair forms,
-    ragged x, y and z tile edges, an input outside the pair range, next to
-    calls of the other loops in the same batch."""
+    """tma and df variants of shapes 32x4 and 32x8 on N >= 36 stage their
+    planes by tensor copies through maps the plan kernel makes on the device
+    (odd N: through the grid's 2N-wide 2D view): every mode of the pair
+    chain, the float64 and float-pair forms, ragged x, y and z tile edges, an
+    input outside the pair range, next to calls of the other loops in the
+    same batch."""
     b = Batch()
     force = []
     for k, (N, sweeps, v, plant) in enumerate([(36, 1, 8, None), (40, 2, 9, None), (66, 3, 12, None),
                                                (100, 5, 13, None), (70, 10, 13, None), (38, 4, 12, 3e39),
-                                               (44, 3, 13, 1e-30), (36, 2, 9, 5e40), (98, 1, 13, None)]):
+                                               (44, 3, 13, 1e-30), (36, 2, 9, 5e40), (98, 1, 13, None),
+                                               (37, 1, 8, None), (41, 2, 9, None), (67, 3, 12, None),
+                                               (101, 5, 13, None), (39, 4, 12, 3e39), (45, 3, 13, 1e-30)]):
         b.jacobi(N, sweeps, 700 + k, plant)
         force.append(v)
         b.nbody(600 + 50 * k, 720 + k)
