@@ -967,7 +967,7 @@ def run_protocol(args):
     Adaptive-100, Static,Best) and its Online mode (Section 4.2) for daxpy,
     Jacobi and n-body, on profile tables of seeded feature points (the SpMV
     tables are the selector study's: `--workload spmv --kfold`).  Profiles:
-    every variant of the stand-alone kernels, 3 timed runs after a warm-up,
+    every variant of the stand-alone kernels, 5 timed runs after a warm-up,
     512 MB L2 flush before each.  Online: one fresh region per loop with the
     default min_train_data (= number of variants) and RoundRobin exploration,
     invoked on the table's feature points in a seeded random order; after its
@@ -1015,7 +1015,7 @@ def run_protocol(args):
     for name, (L, points, make_args) in loops.items():
         t0 = time.perf_counter()
         F = len(points[0])
-        prof = ar.Region(f"protocol-{name}", F, "exhaustive,reps=3", 10 ** 9)
+        prof = ar.Region(f"protocol-{name}", F, "exhaustive,reps=5", 10 ** 9)
         V = prof.add_builtin(L)
         prof.set_l2_flush(flush, flush.numel())
         table = []
