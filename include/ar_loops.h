@@ -280,6 +280,15 @@ typedef struct ar_exec_models {
   const float *theta[4], *mu[4], *sd[4];
 } ar_exec_models;
 int ar_exec_workspace_bytes(int max_calls, size_t *bytes);
+
+/* Self-test of the bounded device waits that every kernel here uses (the
+ * executor's dependency wait and the tensor-copy mbarrier wait): kind 0
+ * waits on a counter that nothing raises and kind 1 on an mbarrier phase
+ * that nothing completes, each for at most `limit` polls (1 .. 2^24), then
+ * gives up; kinds 2 and 3 wait on ones already satisfied.  status: one
+ * device int32, set to AR_ERR_TIMEOUT (kinds 0, 1) or AR_OK (kinds 2, 3).
+ * One block, no fault, no hang; AR_ERR_ARG for a bad kind or limit. */
+int ar_wait_selftest(int kind, unsigned int limit, int32_t *status, void *stream);
 int ar_exec_batch(const ar_exec_call *calls, int ncalls, const ar_exec_models *models, const int32_t *force_variant,
                   int32_t *variant, float *conf, float *features, uint64_t *t_start, uint64_t *t_end,
                   int32_t *status, void *workspace, size_t workspace_bytes, void *stream);

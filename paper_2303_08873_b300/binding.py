@@ -139,6 +139,7 @@ _SIGS = {
     "ar_nbody_batched_workspace_bytes": (_i, [_i, ctypes.POINTER(_sz)]),
     "ar_nbody_batched": (_i, [_i, _vp, _vp, _vp, _f, _vp, _sz, _vp]),
     "ar_exec_workspace_bytes": (_i, [_i, ctypes.POINTER(_sz)]),
+    "ar_wait_selftest": (_i, [_i, ctypes.c_uint, _vp, _vp]),
     "ar_exec_batch": (_i, [_vp, _i, ctypes.POINTER(ArExecModels), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "ar_mlp_num_params": (_i, [_i, _i, _i]),
     "ar_mlp_forward": (_i, [_vp, _vp, _vp, _i, _i, _i, _i64, _vp, _vp, _vp, _vp, _vp]),

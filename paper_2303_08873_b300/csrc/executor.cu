@@ -60,6 +60,16 @@ __device__ __forceinline__ uint64_t gtimer() {
 
 __device__ __forceinline__ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Bounded wait until *d >= need (polls with a 100 ns back-off); false if the
+// limit ran out first.
+__device__ __forceinline__ bool dep_wait(const volatile int* d, int need, uint32_t limit) {
+  for (uint32_t spins = 0; *d < need;) {
+    if (++spins > limit) return false;
+    __nanosleep(100);
+  }
+  return true;
+}
+
 // A df Jacobi call of 2+ sweeps keeps float pairs in out/work between sweeps
 // and ends with a catch-up phase (a float64 sweep that only runs when the
 // first sweep met an input outside the float-pair range).
@@ -1103,16 +1113,9 @@ __global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_cal
         const int p = lo / ncalls, c = lo % ncalls;
         int ok = 1;
         if (p > 0) {
-          const volatile int* d = done + c * PM + p - 1;
-          const int need = tiles[c * PM + p - 1];
-          uint32_t spins = 0;
-          while (*d < need) {
-            if (++spins > kDepSpin) {
-              ok = 0;
-              atomicExch(status + c, (int)AR_ERR_TIMEOUT);
-              break;
-            }
-            __nanosleep(100);
+          if (!dep_wait(done + c * PM + p - 1, tiles[c * PM + p - 1], kDepSpin)) {
+            ok = 0;
+            atomicExch(status + c, (int)AR_ERR_TIMEOUT);
           }
           __threadfence();
         }
@@ -1233,10 +1236,38 @@ bool tma_templates_ready(unsigned char* scratch, cudaStream_t s, MapTemplates* o
   return tm.even_ok || tm.odd_ok;
 }
 
+// Self-test of the bounded waits: kind 0 waits on a counter that nothing
+// raises, kind 1 on an mbarrier phase that nothing completes, kinds 2 and 3
+// on ones already satisfied; each writes AR_ERR_TIMEOUT or AR_OK to *status.
+__global__ void wait_selftest(int kind, uint32_t limit, int* status) {
+  __shared__ int counter;
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  bool ok;
+  if (kind == 0 || kind == 2) {
+    counter = kind == 2 ? 1 : 0;
+    ok = dep_wait(&counter, 1, limit);
+  } else {
+    const uint32_t b = smem_addr(&bar);
+    mbar_init(b, 1);
+    mbar_fence_init();
+    if (kind == 3) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
+    ok = mbar_wait_bounded(b, 0, limit);
+    mbar_inval(b);
+  }
+  *status = ok ? AR_OK : AR_ERR_TIMEOUT;
+}
+
 }  // namespace
 }  // namespace ar
 
 using namespace ar;
+
+extern "C" int ar_wait_selftest(int kind, unsigned int limit, int32_t* status, void* stream) {
+  if (kind < 0 || kind > 3 || limit == 0 || limit > (1u << 24) || !status) return AR_ERR_ARG;
+  wait_selftest<<<1, 32, 0, as_stream(stream)>>>(kind, limit, status);
+  return launch_status();
+}
 
 extern "C" int ar_exec_workspace_bytes(int max_calls, size_t* bytes) {
   if (max_calls < 1 || max_calls > AR_EXEC_MAX_CALLS || !bytes) return AR_ERR_ARG;

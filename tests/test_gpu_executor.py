@@ -311,3 +311,18 @@ def test_graph_capture_and_replay_with_new_table():
         assert np.all(outs[5].cpu().numpy() == 0)
         for k, ok in enumerate(b.check):
             assert ok(), k
+
+
+def test_bounded_waits_give_up_with_a_status():
+    """A wait that nothing satisfies ends after its poll limit with
+    AR_ERR_TIMEOUT (a counter nothing raises, an mbarrier phase nothing
+    completes); satisfied ones return AR_OK.  Nothing faults or hangs."""
+    import time
+    st = torch.full((4,), 99, dtype=torch.int32, device="cuda")
+    t0 = time.perf_counter()
+    for kind in range(4):
+        ar.lib.ar_wait_selftest(kind, 1000, st[kind:].data_ptr(), None)
+    torch.cuda.synchronize()
+    assert time.perf_counter() - t0 < 5.0
+    assert st.cpu().tolist() == [ar.AR_ERR_TIMEOUT, ar.AR_ERR_TIMEOUT, ar.AR_OK, ar.AR_OK]
+
