@@ -1185,6 +1185,7 @@ def run_nbody(args):
     big_ms = k0.elapsed_time(k1)
     inter_s = Ns[-1] ** 2 / (big_ms * 1e-3)
     peak_inter = fp32_fma / 12.0  # 12 FP32 lane operations per interaction (6 packed pairs per 2)
+    packed_inter = ar.ar_measure_fp32x2_rate() / 12.0  # the same lanes issued as packed pairs
     # batched form
     bodies, offs = synth.nbody_batch_inputs(40)
     bd, od = torch.from_numpy(bodies).to(dev), torch.from_numpy(offs).to(dev)
@@ -1210,7 +1211,10 @@ def run_nbody(args):
             "roofline": {"bound": "alu", "achieved": inter_s * NBODY_FLOPS / 1e9, "unit": "GFLOP/s",
                          "peak": peak_inter * NBODY_FLOPS / 1e9, "frac": inter_s / peak_inter,
                          "peak_source": "float32 FMA lane rate (ar_measure_fma_rates) / 12 FP32 lane operations "
-                                        "per interaction", "kernel": per[-1]["best"]},
+                                        "per interaction", "kernel": per[-1]["best"],
+                         "packed": {"peak": packed_inter * NBODY_FLOPS / 1e9, "frac": inter_s / packed_inter,
+                                    "peak_source": "packed float32 pair FMA lane rate (ar_measure_fp32x2_rate) / "
+                                                   "12 FP32 lane operations per interaction"}},
             "batched": {"systems": int(offs.size - 1), "bodies": int(sizes.sum()), "ms": bms,
                         "gflops": bflops / (bms * 1e-3) / 1e9}}
     print(json.dumps(line), flush=True)

@@ -337,6 +337,11 @@ int ar_mlp_train(float *theta, float *adam_m, float *adam_v, const float *mu, co
  * second for float64 and float32. */
 int ar_measure_fma_rates(double *fp64_fma_per_s, double *fp32_fma_per_s);
 
+/* The same microbenchmark with packed float32 pairs (one FFMA2 instruction =
+ * two float32 lanes' FMAs): float32 lane FMAs per second, the ceiling of the
+ * n-body kernels' packed arithmetic.  AR_ERR_ARG if the pointer is null. */
+int ar_measure_fp32x2_rate(double *fp32_lane_fma_per_s);
+
 #ifdef __cplusplus
 }
 #endif

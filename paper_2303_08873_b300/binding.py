@@ -147,6 +147,7 @@ _SIGS = {
     "ar_mlp_adam": (_i, [_vp, _vp, _vp, _vp, _i64, _i, _f, _vp]),
     "ar_mlp_train": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp, _i, _i, _f, _vp, _vp]),
     "ar_measure_fma_rates": (_i, [_pd, _pd]),
+    "ar_measure_fp32x2_rate": (_i, [_pd]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -320,6 +321,13 @@ def ar_measure_fma_rates():
     a, b = ctypes.c_double(), ctypes.c_double()
     check(lib.ar_measure_fma_rates(ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def ar_measure_fp32x2_rate():
+    """float32 lane FMAs per second issued as packed pairs (FFMA2)."""
+    a = ctypes.c_double()
+    check(lib.ar_measure_fp32x2_rate(ctypes.byref(a)))
+    return a.value
 
 
 # ------------------------------------------------------------------ regions
@@ -514,6 +522,6 @@ __all__ = ["ArExecCall", "ArExecModels", "ar_exec_workspace_bytes", "ar_exec_bat
            "ar_nbody_batched", "ar_nbody_batched_workspace_bytes", "LAUNCH_FN", "FAKE_TIME_FN", "lib", "ptr",
            "stream_handle", "check", "loop_num_variants", "loop_default_variant", "loop_variant_name", "ar_daxpy",
            "ar_jacobi7", "ar_heat7", "ar_mlp_num_params", "ar_mlp_forward", "ar_mlp_grad", "ar_mlp_adam", "ar_mlp_train",
-           "ar_measure_fma_rates", "EXPORTED", "AR_LOOP_DAXPY", "AR_LOOP_JACOBI7", "AR_LOOP_SPMV",
+           "ar_measure_fma_rates", "ar_measure_fp32x2_rate", "EXPORTED", "AR_LOOP_DAXPY", "AR_LOOP_JACOBI7", "AR_LOOP_SPMV",
            "AR_LOOP_NBODY", "AR_LOOP_HEAT7", "AR_OK", "AR_ERR_ARG", "AR_ERR_STATE", "AR_ERR_CUDA", "AR_ERR_NOMODEL", "AR_ERR_IO",
            "AR_ERR_TIMEOUT", "AR_ERR_OOM", "AR_MAX_FEATURES", "AR_MAX_VARIANTS"]

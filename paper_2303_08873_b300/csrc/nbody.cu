@@ -15,12 +15,16 @@
 // bodies share every shared-memory load.  Each thread sums one tile into
 // local partials (even and odd j) before adding them to its running total,
 // which keeps the float32 rounding error near sqrt(T) + sqrt(N/T) additions
-// instead of N.
+// instead of N.  The kernels declare a minimum of one resident block so the
+// compiler keeps the unrolled interactions' operands in registers (92-110 a
+// thread for unroll 4 and 8): held to 34-64 registers, the same variants ran
+// at half the rate for N <= 16k and 8 % slower at 64k.
 //
 // The batched form runs `count` independent systems of uneven size in one
 // persistent launch: work items (system, i-tile) are ordered largest system
 // first (an i-tile costs the system's size) and pulled from an atomic counter
-// by resident blocks, so the long items start first and the tail is short.
+// by resident blocks (as many as fit at the kernel's register count), so the
+// long items start first and the tail is short.
 #include <cstdio>
 
 #include "common.cuh"
@@ -31,11 +35,15 @@ namespace {
 
 constexpr int kTiles[3] = {128, 256, 512};
 constexpr int kUnroll[3] = {1, 4, 8};
-constexpr int kBatchTile = 256;
+constexpr int kBatchTile = 128;
 
 // Bodies base + i_first + r*T (r < R) of [base, base+n) against all bodies of
 // the same range.  Padding bodies have zero mass and sit at the origin, so
-// they add exactly 0.
+// they add exactly 0.  `tile` holds two tiles of T bodies: each thread loads
+// its body of the next tile into a register before the current tile's
+// interactions and stores it into the other half after them, so the load's
+// latency is hidden and one barrier per tile suffices (the half written in
+// step k was last read in step k - 1, before the barrier that opens step k).
 template <int T, int U, int R>
 __device__ __forceinline__ void body_tile(const float4* __restrict__ p, float4* __restrict__ a, int64_t base,
                                           int64_t n, int64_t i_first, float eps2, float4* tile) {
@@ -51,12 +59,17 @@ __device__ __forceinline__ void body_tile(const float4* __restrict__ p, float4* 
     ax[r] = ay[r] = az[r] = 0.f;
   }
   const float2 eps2v = make_float2(eps2, eps2);
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();  // the previous item's last tile has been read by every thread
+  tile_store(tile, threadIdx.x, threadIdx.x < n ? p[base + threadIdx.x] : zero);
+  int cur = 0;
   for (int64_t j0 = 0; j0 < n; j0 += T) {
     __syncthreads();
-    const int64_t j = j0 + threadIdx.x;
-    tile_store(tile, threadIdx.x, j < n ? p[base + j] : make_float4(0.f, 0.f, 0.f, 0.f));
-    __syncthreads();
-    tile_accumulate<U, R>(tile, T / 2, npx, npy, npz, eps2v, ax, ay, az);
+    const int64_t j = j0 + T + threadIdx.x;
+    const float4 q = j < n ? p[base + j] : zero;
+    tile_accumulate<U, R>(tile + cur * T, T / 2, npx, npy, npz, eps2v, ax, ay, az);
+    cur ^= 1;
+    if (j0 + T < n) tile_store(tile + cur * T, threadIdx.x, q);
   }
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -66,9 +79,9 @@ __device__ __forceinline__ void body_tile(const float4* __restrict__ p, float4* 
 }
 
 template <int T, int U, int R>
-__global__ void __launch_bounds__(T) nbody_tile(int64_t N, const float4* __restrict__ p, float4* __restrict__ a,
+__global__ void __launch_bounds__(T, 1) nbody_tile(int64_t N, const float4* __restrict__ p, float4* __restrict__ a,
                                                 float eps2) {
-  __shared__ float4 tile[T];
+  __shared__ float4 tile[2 * T];
   body_tile<T, U, R>(p, a, 0, N, (int64_t)blockIdx.x * (T * R) + threadIdx.x, eps2, tile);
 }
 
@@ -100,11 +113,11 @@ __global__ void nbody_batch_plan(int count, const int* __restrict__ offs, int* _
   }
 }
 
-__global__ void __launch_bounds__(kBatchTile) nbody_batched(int count, const int* __restrict__ offs,
+__global__ void __launch_bounds__(kBatchTile, 1) nbody_batched(int count, const int* __restrict__ offs,
                                                             const float4* __restrict__ p, float4* __restrict__ a,
                                                             float eps2, const int* __restrict__ order,
                                                             const int* __restrict__ prefix, int* __restrict__ counter) {
-  __shared__ float4 tile[kBatchTile];
+  __shared__ float4 tile[2 * kBatchTile];
   __shared__ int item_s;
   const int total = prefix[count];
   for (;;) {
@@ -124,7 +137,7 @@ __global__ void __launch_bounds__(kBatchTile) nbody_batched(int count, const int
     const int b = order[lo];
     const int t = item - prefix[lo];
     const int64_t base = offs[b], n = offs[b + 1] - offs[b];
-    body_tile<kBatchTile, 4, 1>(p, a, base, n, (int64_t)t * kBatchTile + threadIdx.x, eps2, tile);
+    body_tile<kBatchTile, 8, 1>(p, a, base, n, (int64_t)t * kBatchTile + threadIdx.x, eps2, tile);
   }
 }
 
@@ -207,7 +220,11 @@ extern "C" int ar_nbody_batched(int count, const int32_t* offs, const float* pos
   int* counter = prefix + count + 1;
   const int* o = reinterpret_cast<const int*>(offs);
   nbody_batch_plan<<<1, 256, count * sizeof(int), s>>>(count, o, order, prefix, counter);
-  const int grid = device_sms() * 4;
+  static int resident = 0;  // blocks per SM at the kernel's register count
+  if (resident == 0 &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, nbody_batched, kBatchTile, 0) != cudaSuccess)
+    return AR_ERR_CUDA;
+  const int grid = device_sms() * (resident > 0 ? resident : 1);
   nbody_batched<<<grid, kBatchTile, 0, s>>>(count, o, reinterpret_cast<const float4*>(pos4),
                                             reinterpret_cast<float4*>(acc4), eps * eps, order, prefix, counter);
   return launch_status();

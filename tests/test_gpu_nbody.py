@@ -121,3 +121,13 @@ def test_every_variant_is_deterministic():
     p = synth.nbody_inputs(12, 70000)
     for v in range(V):
         assert np.array_equal(_run(v, p), _run(v, p)), v
+
+
+def test_roofline_denominators_are_plausible():
+    # the issue-rate microbenchmarks behind the n-body and float64 roofs:
+    # float64 is a small fraction of float32 on B300, and packed float32
+    # pairs cannot beat the scalar float32 lane rate by more than noise
+    fp64, fp32 = ar.ar_measure_fma_rates()
+    packed = ar.ar_measure_fp32x2_rate()
+    assert 0 < fp64 < 0.2 * fp32
+    assert 0.5 * fp32 < packed < 1.1 * fp32

@@ -299,6 +299,7 @@ def test_kernel_entry_points_validate_before_launch():
     for kind, limit in ((4, 10), (-1, 10), (0, 0), (1, (1 << 24) + 1)):
         assert ar.lib.ar_wait_selftest(kind, limit, 64, None) == ar.AR_ERR_ARG
     assert ar.lib.ar_wait_selftest(0, 10, None, None) == ar.AR_ERR_ARG
+    assert ar.lib.ar_measure_fp32x2_rate(None) == ar.AR_ERR_ARG
     assert ar.lib.ar_mlp_num_params(5, 64, 7) == 5 * 64 + 64 + 64 * 64 + 64 + 7 * 64 + 7
     assert ar.lib.ar_mlp_num_params(5, 48, 7) == ar.AR_ERR_ARG
 
