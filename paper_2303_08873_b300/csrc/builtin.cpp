@@ -9,15 +9,13 @@
 namespace ar {
 
 int device_sms() {
-  static int sms = 0;
-  if (sms == 0) {
+  static const int sms = [] {  // initialised once, thread-safe
     int dev = 0, v = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
-      sms = v;
-    else
-      sms = kNumSMs;
-  }
+      return v;
+    return kNumSMs;
+  }();
   return sms;
 }
 

@@ -220,11 +220,13 @@ extern "C" int ar_nbody_batched(int count, const int32_t* offs, const float* pos
   int* counter = prefix + count + 1;
   const int* o = reinterpret_cast<const int*>(offs);
   nbody_batch_plan<<<1, 256, count * sizeof(int), s>>>(count, o, order, prefix, counter);
-  static int resident = 0;  // blocks per SM at the kernel's register count
-  if (resident == 0 &&
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, nbody_batched, kBatchTile, 0) != cudaSuccess)
-    return AR_ERR_CUDA;
-  const int grid = device_sms() * (resident > 0 ? resident : 1);
+  static const int resident = [] {  // blocks per SM at the kernel's register count
+    int r = 0;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, nbody_batched, kBatchTile, 0) == cudaSuccess && r > 0
+               ? r
+               : 1;
+  }();
+  const int grid = device_sms() * resident;
   nbody_batched<<<grid, kBatchTile, 0, s>>>(count, o, reinterpret_cast<const float4*>(pos4),
                                             reinterpret_cast<float4*>(acc4), eps * eps, order, prefix, counter);
   return launch_status();
