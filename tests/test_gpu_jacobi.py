@@ -84,7 +84,7 @@ def test_df_range_guard_falls_back_to_float64():
     reft = loops.jacobi7(tiny, 4)
     for v in range(12, 16):
         _check(_run(v, tiny, 4), reft, ("df tiny", v))
-    # the first sweep's verdict: float64 storage between sweeps when a value
+    # the first sweep's decision: float64 storage between sweeps when a value
     # leaves the float-pair range, float pairs otherwise
     st = torch.zeros(2, dtype=torch.int32, device="cuda")
     _run(13, u0, 3, st)
