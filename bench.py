@@ -188,7 +188,8 @@ def jacobi_config(ws, kind="jacobi7"):
     return {"workload": f"{STENCILS[kind]['label']} N in {{32,64,128,256,384,512}}, 10 sweeps, depth-2 tree on "
                         "(N, sweeps) over 16 variants", "sizes": SIZES, "sweeps": SWEEPS,
             "parallelism": "replicas" if ws > 1 else "single-gpu",
-            "l2": "inputs larger than L2: six grids, 3.2 GB read+written per step"}
+            "l2": "inputs larger than L2: six grids of 1.68 GB in all; each sweep reads and writes "
+                  "3.36 GB, 33.6 GB per step"}
 
 
 def run_reference(args):
