@@ -15,7 +15,9 @@
 // bodies share every shared-memory load.  Each thread sums one tile into
 // local partials (even and odd j) before adding them to its running total,
 // which keeps the float32 rounding error near sqrt(T) + sqrt(N/T) additions
-// instead of N.  The kernels declare a minimum of one resident block so the
+// instead of N.  Small N, whose one-body-per-thread grid leaves fewer than
+// two blocks per SM, splits each i-tile's j range over a thread-block
+// cluster (nbody_tile_split).  The kernels declare a minimum of one resident block so the
 // compiler keeps the unrolled interactions' operands in registers (92-110 a
 // thread for unroll 4 and 8): held to 34-64 registers, the same variants ran
 // at half the rate for N <= 16k and 8 % slower at 64k.
@@ -25,10 +27,13 @@
 // first (an i-tile costs the system's size) and pulled from an atomic counter
 // by resident blocks (as many as fit at the kernel's register count), so the
 // long items start first and the tail is short.
+#include <algorithm>
+#include <atomic>
 #include <cstdio>
 
 #include "common.cuh"
 #include "nbody_math.cuh"
+#include "tma.cuh"
 
 namespace ar {
 namespace {
@@ -36,6 +41,7 @@ namespace {
 constexpr int kTiles[3] = {128, 256, 512};
 constexpr int kUnroll[3] = {1, 4, 8};
 constexpr int kBatchTile = 128;
+constexpr int kMaxCluster = 8;  // portable thread-block cluster size
 
 // Bodies base + i_first + r*T (r < R) of [base, base+n) against all bodies of
 // the same range.  Padding bodies have zero mass and sit at the origin, so
@@ -44,11 +50,13 @@ constexpr int kBatchTile = 128;
 // interactions and stores it into the other half after them, so the load's
 // latency is hidden and one barrier per tile suffices (the half written in
 // step k was last read in step k - 1, before the barrier that opens step k).
+// The j range is [jb, je) within the n bodies (the whole range, or one
+// cluster block's chunk); the partial sums are left in ax, ay, az.
 template <int T, int U, int R>
-__device__ __forceinline__ void body_tile(const float4* __restrict__ p, float4* __restrict__ a, int64_t base,
-                                          int64_t n, int64_t i_first, float eps2, float4* tile) {
+__device__ __forceinline__ void body_partials(const float4* __restrict__ p, int64_t base, int64_t n,
+                                              int64_t i_first, int64_t jb, int64_t je, float eps2, float4* tile,
+                                              float (&ax)[R], float (&ay)[R], float (&az)[R]) {
   float2 npx[R], npy[R], npz[R];
-  float ax[R], ay[R], az[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int64_t i = i_first + (int64_t)r * T;
@@ -61,16 +69,23 @@ __device__ __forceinline__ void body_tile(const float4* __restrict__ p, float4* 
   const float2 eps2v = make_float2(eps2, eps2);
   const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncthreads();  // the previous item's last tile has been read by every thread
-  tile_store(tile, threadIdx.x, threadIdx.x < n ? p[base + threadIdx.x] : zero);
+  if (jb < je) tile_store(tile, threadIdx.x, jb + threadIdx.x < je ? p[base + jb + threadIdx.x] : zero);
   int cur = 0;
-  for (int64_t j0 = 0; j0 < n; j0 += T) {
+  for (int64_t j0 = jb; j0 < je; j0 += T) {
     __syncthreads();
     const int64_t j = j0 + T + threadIdx.x;
-    const float4 q = j < n ? p[base + j] : zero;
+    const float4 q = j < je ? p[base + j] : zero;
     tile_accumulate<U, R>(tile + cur * T, T / 2, npx, npy, npz, eps2v, ax, ay, az);
     cur ^= 1;
-    if (j0 + T < n) tile_store(tile + cur * T, threadIdx.x, q);
+    if (j0 + T < je) tile_store(tile + cur * T, threadIdx.x, q);
   }
+}
+
+template <int T, int U, int R>
+__device__ __forceinline__ void body_tile(const float4* __restrict__ p, float4* __restrict__ a, int64_t base,
+                                          int64_t n, int64_t i_first, float eps2, float4* tile) {
+  float ax[R], ay[R], az[R];
+  body_partials<T, U, R>(p, base, n, i_first, 0, n, eps2, tile, ax, ay, az);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int64_t i = i_first + (int64_t)r * T;
@@ -83,6 +98,59 @@ __global__ void __launch_bounds__(T, 1) nbody_tile(int64_t N, const float4* __re
                                                 float eps2) {
   __shared__ float4 tile[2 * T];
   body_tile<T, U, R>(p, a, 0, N, (int64_t)blockIdx.x * (T * R) + threadIdx.x, eps2, tile);
+}
+
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// float4 at the same shared-memory offset in block `rank` of this cluster
+__device__ __forceinline__ float4 ld_cluster_f4(const float4* local, unsigned rank) {
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(smem_addr(local)), "r"(rank));
+  float4 v;
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(remote)
+               : "memory");
+  return v;
+}
+
+// Small N: the grid of i-tiles underfills the GPU, so each i-tile is split
+// over a thread-block cluster of CS blocks (CS = gridDim.x / i-tiles, set at
+// launch): block rank q takes the j bodies [q chunk, (q + 1) chunk), chunk a
+// multiple of T, and leaves its partial sums in shared memory; after a
+// cluster barrier rank 0 adds the CS partials in rank order from the other
+// blocks' shared memory (distributed shared memory) and writes the result,
+// and a second barrier keeps every block's shared memory alive until then.
+// Both barriers are reached by every thread of every block.
+template <int T, int U>
+__global__ void __launch_bounds__(T, 1) nbody_tile_split(int64_t N, const float4* __restrict__ p,
+                                                      float4* __restrict__ a, float eps2, int cs, int64_t chunk) {
+  __shared__ float4 tile[2 * T];
+  __shared__ float4 part[T];
+  const unsigned q = cluster_rank();
+  const int64_t i = (int64_t)(blockIdx.x / cs) * T + threadIdx.x;
+  const int64_t jb = min((int64_t)q * chunk, N), je = min(jb + chunk, N);
+  float ax[1], ay[1], az[1];
+  body_partials<T, U, 1>(p, 0, N, i, jb, je, eps2, tile, ax, ay, az);
+  part[threadIdx.x] = make_float4(ax[0], ay[0], az[0], 0.f);
+  cluster_barrier();
+  if (q == 0) {
+    float4 s = part[threadIdx.x];
+    for (int r = 1; r < cs; ++r) {
+      const float4 o = ld_cluster_f4(&part[threadIdx.x], (unsigned)r);
+      s.x += o.x;
+      s.y += o.y;
+      s.z += o.z;
+    }
+    if (i < N) a[i] = make_float4(s.x, s.y, s.z, 0.f);
+  }
+  cluster_barrier();
 }
 
 // ------------------------------------------------------------ batched
@@ -141,17 +209,62 @@ __global__ void __launch_bounds__(kBatchTile, 1) nbody_batched(int count, const 
   }
 }
 
+// Whether clusters of cs blocks of nbody_tile_split<T, U> fit on the device
+// (asked once per cluster size).
+template <int T, int U>
+bool split_fits(int cs) {
+  static std::atomic<int> known[kMaxCluster + 1];  // 0 not asked, 1 fits, 2 does not
+  int k = known[cs].load(std::memory_order_relaxed);
+  if (k == 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)cs);
+    cfg.blockDim = dim3(T);
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = (unsigned)cs;
+    at.val.clusterDim.y = at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    k = cudaOccupancyMaxActiveClusters(&n, nbody_tile_split<T, U>, &cfg) == cudaSuccess && n > 0 ? 1 : 2;
+    (void)cudaGetLastError();
+    known[cs].store(k, std::memory_order_relaxed);
+  }
+  return k == 1;
+}
+
 // Two bodies per thread when the grid still fills the GPU twice over,
-// otherwise one (small N keeps all its blocks).
+// otherwise one; and when even one body per thread leaves fewer than two
+// blocks per SM, the j range is split over a cluster of up to kMaxCluster
+// blocks per i-tile (nbody_tile_split).
 template <int T, int U>
 int launch_r(int64_t N, const float4* p, float4* a, float eps2, cudaStream_t s) {
-  const bool two = ceil_div(N, 2 * T) >= 2LL * device_sms();
+  const int64_t want = 2LL * device_sms();
+  const bool two = ceil_div(N, 2 * T) >= want;
   const int64_t grid = ceil_div(N, two ? 2 * T : T);
   if (grid > 0x7fffffffLL) return AR_ERR_ARG;
-  if (two)
+  if (two) {
     nbody_tile<T, U, 2><<<(unsigned)grid, T, 0, s>>>(N, p, a, eps2);
-  else
-    nbody_tile<T, U, 1><<<(unsigned)grid, T, 0, s>>>(N, p, a, eps2);
+    return launch_status();
+  }
+  const int cs = (int)std::min<int64_t>({(int64_t)kMaxCluster, ceil_div(want, grid), grid});
+  if (cs >= 2 && split_fits<T, U>(cs)) {
+    const int64_t chunk = ceil_div(ceil_div(N, cs), T) * T;  // j bodies per block, whole tiles
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(grid * cs));
+    cfg.blockDim = dim3(T);
+    cfg.stream = s;
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = (unsigned)cs;
+    at.val.clusterDim.y = at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, nbody_tile_split<T, U>, N, p, a, eps2, cs, chunk) != cudaSuccess)
+      return AR_ERR_CUDA;
+    return launch_status();
+  }
+  nbody_tile<T, U, 1><<<(unsigned)grid, T, 0, s>>>(N, p, a, eps2);
   return launch_status();
 }
 

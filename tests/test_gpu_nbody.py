@@ -117,10 +117,28 @@ def test_batched_workload_sampled():
         assert err <= TOL * np.max(np.linalg.norm(ref, axis=1)) * 4, b
 
 
-def test_every_variant_is_deterministic():
-    p = synth.nbody_inputs(12, 70000)
+@pytest.mark.parametrize("N", [5000, 70000])
+def test_every_variant_is_deterministic(N):
+    # 5000 bodies: the j range is split over thread-block clusters and the
+    # partials are added in rank order, so repeated runs agree bit for bit
+    p = synth.nbody_inputs(12, N)
     for v in range(V):
         assert np.array_equal(_run(v, p), _run(v, p)), v
+
+
+@pytest.mark.parametrize("N", [16384, 30000])
+def test_cluster_split_sizes_match_oracle(N):
+    # sizes whose grid of one body per thread underfills the GPU: every tile
+    # splits its j range over a cluster (some ranks of the 512 tiles empty)
+    p = synth.nbody_inputs(13, N)
+    rows = np.arange(0, N, 97)
+    ref = loops.nbody_rows(p, rows, EPS)
+    scale = np.max(np.linalg.norm(ref, axis=1))
+    for v in range(V):
+        a = _run(v, p)[rows]
+        assert np.all(a[:, 3] == 0.0), v
+        err = np.max(np.linalg.norm(a[:, :3].astype(np.float64) - ref, axis=1))
+        assert err <= TOL * scale, (ar.loop_variant_name(3, v), N, err, scale)
 
 
 def test_roofline_denominators_are_plausible():
