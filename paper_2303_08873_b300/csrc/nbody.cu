@@ -17,10 +17,11 @@
 // which keeps the float32 rounding error near sqrt(T) + sqrt(N/T) additions
 // instead of N.  Small N, whose one-body-per-thread grid leaves fewer than
 // two blocks per SM, splits each i-tile's j range over a thread-block
-// cluster (nbody_tile_split).  The kernels declare a minimum of one resident block so the
-// compiler keeps the unrolled interactions' operands in registers (92-110 a
-// thread for unroll 4 and 8): held to 34-64 registers, the same variants ran
-// at half the rate for N <= 16k and 8 % slower at 64k.
+// cluster (nbody_tile_split).  The kernels declare a minimum of one
+// resident block so the compiler keeps the unrolled interactions' operands
+// in registers (92-110 a thread for unroll 4 and 8): held to 34-64
+// registers, the same variants ran at half the rate for N <= 16k and 8 %
+// slower at 64k.
 //
 // The batched form runs `count` independent systems of uneven size in one
 // persistent launch: work items (system, i-tile) are ordered largest system
