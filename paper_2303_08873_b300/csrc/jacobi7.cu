@@ -46,6 +46,7 @@ const char* const kFamily[4] = {"naive", "smem", "tma", "df"};
 template <int BX, int BY, int ST>
 __global__ void __launch_bounds__(BX* BY) jacobi_naive(int N, const double* __restrict__ in,
                                                        double* __restrict__ out, StencilCoef cf) {
+  pdl_begin();  // the previous sweep of the chain is complete and visible
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z;
@@ -64,6 +65,7 @@ __global__ void __launch_bounds__(BX* BY) jacobi_naive(int N, const double* __re
 template <int BX, int BY, int ST>
 __global__ void __launch_bounds__(BX* BY) jacobi_smem(int N, int KC, const double* __restrict__ in,
                                                       double* __restrict__ out, StencilCoef cf) {
+  pdl_begin();  // the previous sweep of the chain is complete and visible
   __shared__ double tile[2][BY + 2][BX + 2];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int i = blockIdx.x * BX + tx, j = blockIdx.y * BY + ty;
@@ -133,6 +135,7 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
                                                      const double* __restrict__ in, void* __restrict__ outv,
                                                      double* __restrict__ out_alt, int* status, int* flag,
                                                      StencilCoef cf) {
+  pdl_begin();  // the previous sweep of the chain is complete and visible
   using G = TmaGeom<BX, BY>;
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[kRing];
@@ -334,6 +337,7 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma_odd(const __grid_constant__
                                                          const double* __restrict__ in_alt,
                                                          double* __restrict__ out_alt, int* status, int* flag,
                                                          StencilCoef cf) {
+  pdl_begin();  // the previous sweep of the chain is complete and visible
   using G = OddGeom<BX, BY>;
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[kRing];
@@ -545,6 +549,7 @@ template <int BX, int BY, int MODE, int ST>
 __global__ void __launch_bounds__(BX* BY) jacobi_ring(int N, int KC, const double* __restrict__ in, void* outv,
                                                       const double* __restrict__ in_alt, double* out_alt, int* flag,
                                                       StencilCoef cf) {
+  pdl_begin();  // the previous sweep of the chain is complete and visible
   extern __shared__ __align__(16) unsigned char ring_smem[];
   const int kb = blockIdx.z * KC, ke = min(N, kb + KC);
   // block-uniform: the flag was settled by an earlier launch on this stream
@@ -564,8 +569,7 @@ __global__ void __launch_bounds__(BX* BY) jacobi_ring(int N, int KC, const doubl
 template <int BX, int BY, int ST>
 int launch_naive(int N, const double* in, double* out, const StencilCoef& cf, cudaStream_t s) {
   dim3 grid((unsigned)ceil_div(N, BX), (unsigned)ceil_div(N, BY), (unsigned)N);
-  jacobi_naive<BX, BY, ST><<<grid, dim3(BX, BY), 0, s>>>(N, in, out, cf);
-  return launch_status();
+  return launch_pdl(jacobi_naive<BX, BY, ST>, grid, dim3(BX, BY), 0, s, N, in, out, cf);
 }
 
 inline int chunk_planes(int N, int64_t colblocks, int resident_per_sm, int lo, int hi) {
@@ -582,8 +586,7 @@ int launch_smem(int N, const double* in, double* out, const StencilCoef& cf, cud
   const int64_t cb = ceil_div(N, BX) * ceil_div(N, BY);
   const int KC = chunk_planes(N, cb, 2048 / (BX * BY), 4, 1 << 30);
   dim3 grid((unsigned)ceil_div(N, BX), (unsigned)ceil_div(N, BY), (unsigned)ceil_div(N, KC));
-  jacobi_smem<BX, BY, ST><<<grid, dim3(BX, BY), 0, s>>>(N, KC, in, out, cf);
-  return launch_status();
+  return launch_pdl(jacobi_smem<BX, BY, ST>, grid, dim3(BX, BY), 0, s, N, KC, in, out, cf);
 }
 
 // TMA staging needs a 16-byte row pitch (even N), a grid at least one box wide
@@ -606,6 +609,7 @@ template <int ST>
 __global__ void __launch_bounds__(256) jacobi_catchup(int N, const int* __restrict__ flag,
                                                       const double* __restrict__ in, double* __restrict__ out,
                                                       StencilCoef cf) {
+  pdl_begin();  // the previous sweep of the chain is complete and visible
   if (*flag == 0) return;
   const int64_t n3 = (int64_t)N * N * N, NN = (int64_t)N * N;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n3; c += (int64_t)gridDim.x * blockDim.x) {
@@ -643,9 +647,8 @@ int launch_tma(int N, const double* in, void* out, const double* in_alt, double*
   int KC = chunk_planes(N, cb, resident, kDZ - 2, 8 * kDZ - 2);
   KC = (int)(ceil_div(KC + 2, kDZ) * kDZ - 2);
   dim3 grid((unsigned)ceil_div(N, BX), (unsigned)ceil_div(N, BY), (unsigned)ceil_div(N, KC));
-  jacobi_tma<BX, BY, MODE, ST><<<grid, BX * BY, G::SMEM, s>>>(map, map_alt, N, KC, in, out, out_alt, status, flag,
-                                                               cf);
-  return launch_status();
+  return launch_pdl(jacobi_tma<BX, BY, MODE, ST>, grid, dim3(BX * BY), G::SMEM, s, map, map_alt, N, KC, in, out,
+                    out_alt, status, flag, cf);
 }
 
 template <int BX, int BY, int MODE, int ST>
@@ -673,9 +676,8 @@ int launch_tma_odd(int N, const double* in, void* out, const double* in_alt, dou
   int KC = chunk_planes(N, cb, resident, kDZ - 2, 8 * kDZ - 2);
   KC = (int)(ceil_div(KC + 2, kDZ) * kDZ - 2);
   dim3 grid((unsigned)ceil_div(N, BX), (unsigned)ceil_div(N, BY), (unsigned)ceil_div(N, KC));
-  jacobi_tma_odd<BX, BY, MODE, ST><<<grid, BX * BY, G::SMEM, s>>>(map, map_alt, N, KC, in, out, in_alt, out_alt,
-                                                                  status, flag, cf);
-  return launch_status();
+  return launch_pdl(jacobi_tma_odd<BX, BY, MODE, ST>, grid, dim3(BX * BY), G::SMEM, s, map, map_alt, N, KC, in, out,
+                    in_alt, out_alt, status, flag, cf);
 }
 
 template <int BX, int BY, int MODE, int ST>
@@ -689,8 +691,8 @@ int launch_ring(int N, const double* in, void* out, const double* in_alt, double
   if (resident > 2048 / (BX * BY)) resident = 2048 / (BX * BY);
   const int KC = chunk_planes(N, cb, resident, 8, 64);
   dim3 grid((unsigned)ceil_div(N, BX), (unsigned)ceil_div(N, BY), (unsigned)ceil_div(N, KC));
-  jacobi_ring<BX, BY, MODE, ST><<<grid, BX * BY, smem, s>>>(N, KC, in, out, in_alt, out_alt, flag, cf);
-  return launch_status();
+  return launch_pdl(jacobi_ring<BX, BY, MODE, ST>, grid, dim3(BX * BY), smem, s, N, KC, in, out, in_alt, out_alt,
+                    flag, cf);
 }
 
 template <int BX, int BY, int ST>
@@ -867,8 +869,8 @@ int stencil_run(int variant, int N, int sweeps, const StencilCoef& cf, const dou
   }
   if (flag) {
     const double* src = sweeps >= 2 ? dst_of(sweeps - 2) : u0;
-    jacobi_catchup<ST><<<device_sms() * 4, 256, 0, s>>>(N, flag, src, dst_of(sweeps - 1), cf);
-    return launch_status();
+    return launch_pdl(jacobi_catchup<ST>, dim3(device_sms() * 4), dim3(256), 0, s, N, flag, src, dst_of(sweeps - 1),
+                      cf);
   }
   return AR_OK;
 }
