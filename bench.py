@@ -47,7 +47,7 @@ FALLBACK_HBM_GBS = 6400.0
 # N = 320 (ncu dram__bytes_read.sum + dram__bytes_write.sum, median of the 8
 # middle sweeps of a 10-sweep call), scaled to N = 512 by the unknowns; writes
 # still dirty in L2 when the kernel ends are not counted by ncu.
-DF_PP_TRAFFIC_N320 = 262379392.0 + 216399360.0
+DF_PP_TRAFFIC_N320 = 262383232.0 + 216723200.0
 HEAT_ALPHA = 0.125              # alpha of the heat workload (stable: <= 1/6)
 
 # The two stencil workloads: the Jacobi region (the headline) and the explicit
@@ -57,10 +57,10 @@ HEAT_ALPHA = 0.125              # alpha of the heat workload (stable: <= 1/6)
 STENCILS = {
     "jacobi7": {"loop": 1, "label": "jacobi7 float64", "fp64_ops": FP64_OPS_PER_POINT,
                 "pp_traffic": {"jacobi7_df_32x8": DF_PP_TRAFFIC_N320,
-                               "jacobi7_df_32x4": 262180096.0 + 218679040.0}},
+                               "jacobi7_df_32x4": 262181376.0 + 218752000.0}},
     "heat7": {"loop": 4, "label": f"heat7 float64 (alpha = {HEAT_ALPHA})", "fp64_ops": 7,
-              "pp_traffic": {"heat7_df_32x8": 262293632.0 + 218051328.0,
-                             "heat7_df_32x4": 262183552.0 + 219656064.0}},
+              "pp_traffic": {"heat7_df_32x8": 262317568.0 + 218154624.0,
+                             "heat7_df_32x4": 262190848.0 + 219815424.0}},
 }
 
 
