@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(256) spmv_vector(int64_t rows, const int* __re
 // ------------------------------------------------------------ merge path
 __global__ void spmv_mp_partition(int64_t rows, int64_t nnz, int nblocks, const int* __restrict__ rowptr,
                                   int64_t* __restrict__ start_row) {
+  pdl_begin();  // lets the main pass launch; the partition itself is launched in order
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b > nblocks) return;
   const int64_t L = rows + nnz;
@@ -83,6 +84,7 @@ __global__ void __launch_bounds__(kMpThreads, 5) spmv_mp_main(int64_t rows, int6
                                                            const int64_t* __restrict__ start_row,
                                                            int64_t* __restrict__ carry_row,
                                                            double* __restrict__ carry_val) {
+  pdl_begin();  // the partition of this call is complete and visible
   __shared__ __align__(16) unsigned char smem[mp::kSmemBytes];
   const int b = blockIdx.x;
   mp::block<DF>(rows, nnz, rowptr, col, val, x, y, (int64_t)b * kMpPerBlock, start_row[b], start_row[b + 1],
@@ -94,6 +96,7 @@ __global__ void __launch_bounds__(kMpThreads, 5) spmv_mp_main(int64_t rows, int6
 // a later block, which has already written y[row] in spmv_mp_main.
 __global__ void spmv_mp_fixup(int nblocks, const int64_t* __restrict__ carry_row,
                               const double* __restrict__ carry_val, double* __restrict__ y) {
+  pdl_begin();  // the main pass of this call is complete and visible
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nblocks) return;
   const int64_t r = carry_row[b];
@@ -253,14 +256,12 @@ extern "C" int ar_spmv(int variant, int64_t rows, int64_t nnz, const int32_t* ro
       int64_t* carry_row = start_row + (nb + 1);
       double* carry_val = reinterpret_cast<double*>(carry_row + nb);
       spmv_mp_partition<<<(unsigned)ceil_div(nb + 1, 256), 256, 0, s>>>(rows, nnz, (int)nb, rp, start_row);
-      if (variant == 6)
-        spmv_mp_main<false><<<(unsigned)nb, kMpThreads, 0, s>>>(rows, nnz, rp, c, val, x, y, start_row, carry_row,
-                                                                carry_val);
-      else
-        spmv_mp_main<true><<<(unsigned)nb, kMpThreads, 0, s>>>(rows, nnz, rp, c, val, x, y, start_row, carry_row,
-                                                               carry_val);
-      spmv_mp_fixup<<<(unsigned)ceil_div(nb, 256), 256, 0, s>>>((int)nb, carry_row, carry_val, y);
-      return launch_status();
+      if (launch_status() != AR_OK) return AR_ERR_CUDA;
+      const int rc = launch_pdl(variant == 6 ? spmv_mp_main<false> : spmv_mp_main<true>, dim3((unsigned)nb),
+                                dim3(kMpThreads), 0, s, rows, nnz, rp, c, val, x, y, start_row, carry_row, carry_val);
+      if (rc != AR_OK) return rc;
+      return launch_pdl(spmv_mp_fixup, dim3((unsigned)ceil_div(nb, 256)), dim3(256), 0, s, (int)nb, carry_row,
+                        carry_val, y);
     }
   }
 }
@@ -372,8 +373,10 @@ extern "C" int ar_spmv_merge_path_noalloc(int64_t rows, int64_t nnz, const int32
   const int* rp = reinterpret_cast<const int*>(rowptr);
   const int* c = reinterpret_cast<const int*>(col);
   spmv_mp_partition<<<(unsigned)ceil_div(nb + 1, 256), 256, 0, s>>>(rows, nnz, (int)nb, rp, start_row);
-  spmv_mp_main<false><<<(unsigned)nb, kMpThreads, 0, s>>>(rows, nnz, rp, c, val, x, y, start_row, carry_row,
-                                                          carry_val);
-  spmv_mp_fixup<<<(unsigned)ceil_div(nb, 256), 256, 0, s>>>((int)nb, carry_row, carry_val, y);
-  return launch_status();
+  if (launch_status() != AR_OK) return AR_ERR_CUDA;
+  const int rc = launch_pdl(spmv_mp_main<false>, dim3((unsigned)nb), dim3(kMpThreads), 0, s, rows, nnz, rp, c, val,
+                            x, y, start_row, carry_row, carry_val);
+  if (rc != AR_OK) return rc;
+  return launch_pdl(spmv_mp_fixup, dim3((unsigned)ceil_div(nb, 256)), dim3(256), 0, s, (int)nb, carry_row, carry_val,
+                    y);
 }
