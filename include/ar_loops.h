@@ -83,7 +83,10 @@ int ar_daxpy(int variant, int64_t n, double a, const double *x, double *y, void 
  * and, when an input lies outside the float-pair range, recomputes the whole
  * call in float64 (one extra launch at the end, which otherwise exits at
  * once).  Without a status array every df sweep converts from and to
- * float64 and redoes out-of-range points in float64. */
+ * float64 and redoes out-of-range points in float64.  The sweeps of one call
+ * are chained by programmatic dependent launch (each waits for the previous
+ * one before its first global access), so a caller's next operation on
+ * `stream` is ordered after the whole call as usual. */
 typedef struct ar_jacobi7_args {
   int N;
   int sweeps;
@@ -201,7 +204,10 @@ int ar_csr_features(int64_t rows, const int32_t *rowptr, float *out5, void *work
  * over all N bodies (j = i adds 0), float32.  pos4 holds (x, y, z, m) per
  * body; both arrays 16-byte aligned.  eps > 0.  Variants: shared-memory tile
  * {128, 256, 512} bodies x inner unroll {1, 4, 8}; variant = 3*tile + unroll.
- * Default: tile 256, unroll 1 (variant 3). */
+ * Default: tile 256, unroll 1 (variant 3).  Small N (fewer than two blocks
+ * per SM even at one body per thread) splits each tile's j range over a
+ * thread-block cluster of up to 8 blocks and adds the partial sums in a
+ * fixed order: results are bit-identical from run to run at every N. */
 typedef struct ar_nbody_args {
   int64_t N;
   const float *pos4;
