@@ -86,7 +86,11 @@ int ar_daxpy(int variant, int64_t n, double a, const double *x, double *y, void 
  * float64 and redoes out-of-range points in float64.  The sweeps of one call
  * are chained by programmatic dependent launch (each waits for the previous
  * one before its first global access), so a caller's next operation on
- * `stream` is ordered after the whole call as usual. */
+ * `stream` is ordered after the whole call as usual; a kernel the caller
+ * itself launches next with programmatic dependent launch must execute
+ * griddepcontrol.wait before reading the output (the last kernel of the
+ * call lets dependents launch early).  The merge-path SpMV variants chain
+ * their launches the same way. */
 typedef struct ar_jacobi7_args {
   int N;
   int sweeps;
