@@ -248,7 +248,17 @@ int launch_r(int64_t N, const float4* p, float4* a, float eps2, cudaStream_t s) 
     nbody_tile<T, U, 2><<<(unsigned)grid, T, 0, s>>>(N, p, a, eps2);
     return launch_status();
   }
-  const int cs = (int)std::min<int64_t>({(int64_t)kMaxCluster, ceil_div(want, grid), grid});
+  // the largest cluster whose blocks still fit in one wave of resident
+  // slots; when not even two do, enough clusters for two blocks per SM
+  static const int resident = [] {
+    int r = 0;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, nbody_tile_split<T, U>, T, 0) == cudaSuccess && r > 0
+               ? r
+               : 1;
+  }();
+  const int64_t fit = (int64_t)resident * device_sms() / grid;
+  const int cs = fit >= 2 ? (int)std::min<int64_t>({(int64_t)kMaxCluster, fit, grid})
+                          : (int)std::min<int64_t>({(int64_t)kMaxCluster, ceil_div(want, grid), grid});
   if (cs >= 2 && split_fits<T, U>(cs)) {
     const int64_t chunk = ceil_div(ceil_div(N, cs), T) * T;  // j bodies per block, whole tiles
     cudaLaunchConfig_t cfg = {};
