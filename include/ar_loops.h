@@ -171,7 +171,9 @@ int ar_spmv(int variant, int64_t rows, int64_t nnz, const int32_t *rowptr, const
  *  - Memory: every GPU that loads the library holds the 8 MiB array until the
  *    process exits.  The first call on a device looks up the array's device
  *    address (cudaGetSymbolAddress, once per device, with that device
- *    current); make that first call before any stream capture.
+ *    current); make that first call before any stream capture.  The cached
+ *    address does not survive cudaDeviceReset: do not call this entry point
+ *    after resetting the device in the same process.
  *  - No allocation: calls no cudaMalloc, cudaFree or allocating routine.
  *  - Sharing: all calls on a device use the same array; the kernels write
  *    every scratch word before reading it, so nothing needs clearing, but two
@@ -179,6 +181,8 @@ int ar_spmv(int variant, int64_t rows, int64_t nnz, const int32_t *rowptr, const
  *    the scratch and give wrong results.  Order them on one stream.
  * Returns AR_OK, AR_ERR_ARG (bad arguments or over capacity) or AR_ERR_CUDA. */
 #define AR_SPMV_NOALLOC_SCRATCH_BYTES (8u << 20)
+/* 24 bytes per 4096-item path block plus 8 (checked against the kernels'
+ * block size by a static_assert in the library's source) */
 #define AR_SPMV_NOALLOC_MAX_PATH ((long long)(((AR_SPMV_NOALLOC_SCRATCH_BYTES - 8u) / 24u) * 4096u))
 int ar_spmv_merge_path_noalloc(int64_t rows, int64_t nnz, const int32_t *rowptr, const int32_t *col,
                                const double *val, const double *x, double *y, void *stream);

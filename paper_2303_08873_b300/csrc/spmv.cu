@@ -327,6 +327,12 @@ namespace {
 
 constexpr size_t kNoAllocScratchBytes = (size_t)AR_SPMV_NOALLOC_SCRATCH_BYTES;
 static __device__ __align__(256) unsigned char g_spmv_scratch[kNoAllocScratchBytes];
+// Layout for nb path blocks: start_row int64[nb + 1], carry_row int64[nb],
+// carry_val double[nb] = 24 nb + 8 bytes.  The header's capacity must be the
+// largest path whose block count fits that layout in the array.
+static_assert(AR_SPMV_NOALLOC_MAX_PATH ==
+                  (long long)((kNoAllocScratchBytes - 8) / 24) * (long long)kMpPerBlock,
+              "AR_SPMV_NOALLOC_MAX_PATH out of step with the merge-path block size or scratch layout");
 
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
@@ -334,7 +340,9 @@ void* g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of g_spmv_scratch on the current device, looked up once per
 // device (in host code the symbol names a host-side stand-in, not device
-// memory).  Returns nullptr if the lookup fails.
+// memory).  Returns nullptr if the lookup fails.  The cached address belongs
+// to the device's primary context: it does not survive cudaDeviceReset, after
+// which this entry point must not be called again in the process.
 void* scratch_on_current_device() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
@@ -354,11 +362,13 @@ extern "C" int ar_spmv_merge_path_noalloc(int64_t rows, int64_t nnz, const int32
   if (rows < 0 || nnz < 0 || nnz > 0x7fffffffLL) return AR_ERR_ARG;
   if (rows == 0) return AR_OK;
   if (!rowptr || !y || (nnz > 0 && (!col || !val || !x))) return AR_ERR_ARG;
-  if (rows + nnz > (int64_t)AR_SPMV_NOALLOC_MAX_PATH) {
+  // bound each term before forming the sum, so the sum cannot overflow
+  constexpr int64_t kMax = (int64_t)AR_SPMV_NOALLOC_MAX_PATH;
+  if (rows > kMax || nnz > kMax - rows) {
     fprintf(stderr,
-            "ar_spmv_merge_path_noalloc: rows + nnz = %lld exceeds the fixed scratch limit %lld; "
+            "ar_spmv_merge_path_noalloc: rows + nnz >= %lld exceeds the fixed scratch limit %lld; "
             "use ar_spmv with a caller-provided workspace\n",
-            (long long)(rows + nnz), (long long)AR_SPMV_NOALLOC_MAX_PATH);
+            (long long)(rows > kMax ? rows : rows + nnz), (long long)kMax);
     return AR_ERR_ARG;
   }
   void* base = scratch_on_current_device();

@@ -176,3 +176,91 @@ def test_rfc_single_feature_bootstrap_of_all_identical_rows():
 def test_rfc_vote_ties_go_to_lowest_label():
     forest = [[(-1, 0.0, -1, -1, 4)], [(-1, 0.0, -1, -1, 1)]]
     assert select.rfc_predict(forest, [0.0]) == (1, 0.5)
+
+
+# ------------------------------------------------------------ forest worked example
+# A 2-tree, depth-2 forest on 6 rows and 4 features (mtry = floor(sqrt 4) = 2),
+# seed 0, worked out by hand from the SplitMix64 stream.  Every draw below is
+# a literal derived from the stream, and every split from exact Gini scores
+# (score = sum_c cL^2/nL + sum_c cR^2/nR, higher is better).
+RFC_X = [[1.0, 2.0, 3.0, 3.0], [0.0, 0.0, 3.0, 3.0], [0.0, 1.0, 3.0, 1.0],
+         [1.0, 3.0, 1.0, 1.0], [2.0, 2.0, 0.0, 0.0], [3.0, 3.0, 3.0, 2.0]]
+RFC_Y = [2, 0, 1, 2, 0, 0]
+# the first 20 outputs of SplitMix64 from state 0 (0..7 also in the golden file)
+RFC_STREAM = [
+    0xe220a8397b1dcdaf, 0x6e789e6aa1b965f4, 0x06c45d188009454f, 0xf88bb8a8724c81ec,
+    0x1b39896a51a8749b, 0x53cb9f0c747ea2ea, 0x2c829abe1f4532e1, 0xc584133ac916ab3c,
+    0x3ee5789041c98ac3, 0xf3b8488c368cb0a6, 0x657eecdd3cb13d09, 0xc2d326e0055bdef6,
+    0x8621a03fe0bbdb7b, 0x8e1f7555983aa92f, 0xb54e0f1600cc4d19, 0x84bb3f97971d80ab,
+    0x7d29825c75521255, 0xc3cf17102b7f7f86, 0x3466e9a083914f64, 0xd81a8d2b5a4485ac,
+]
+# Tree 1 consumes outputs 0..9:
+#   bootstrap = outputs 0..5 mod 6 = [1, 0, 1, 4, 1, 0] (row 1 x3, row 0 x2, row 4)
+#   root draw: output 6 mod 4 = 1 swaps slots 0,1 -> [1,0,2,3]; 1 + output 7 mod 3
+#     = 3 swaps slots 1,3 -> [1,3,2,0]: features {1, 3}.  Feature 1 at 1.0 scores
+#     9/3 + 5/3 = 14/3, feature 3 at 1.5 scores 1 + 13/5 = 18/5: split (1, 1.0).
+#   left child = row 1 x3, pure: a leaf, no draw.
+#   right child = row 0 x2 (label 2), row 4 (label 0): draw outputs 8, 9 ->
+#     [3,1,2,0] -> [3,0,2,1]: features {0, 3}; both score 4/2 + 1 = 3, the tie
+#     goes to feature 0: split (0, 1.5).  (A draw made once per tree would offer
+#     {1, 3} here, where feature 1 does not vary: split (3, 1.5) instead.)
+# Tree 2 consumes outputs 10..19:
+#   bootstrap = outputs 10..15 mod 6 = [1, 4, 3, 3, 5, 1]
+#   root draw: outputs 16, 17 -> [1,0,2,3] -> [1,3,2,0]: features {1, 3}.
+#     Feature 1 at 2.5 and feature 3 at 1.5 both score 3 + 5/3 = 14/3 (best);
+#     the tie goes to feature 1: split (1, 2.5).
+#   left child = row 1 x2, row 4: all label 0, a leaf.
+#   right child = row 3 x2 (label 2), row 5 (label 0): outputs 18, 19 ->
+#     [0,1,2,3] -> [0,2,1,3]: features {0, 2}, both score 3: split (0, 2.0).
+RFC_BOOT = [[1, 0, 1, 4, 1, 0], [1, 4, 3, 3, 5, 1]]
+RFC_DRAWS = [[[1, 3], [0, 3]], [[1, 3], [0, 2]]]
+RFC_FOREST = [
+    [(1, 1.0, 1, 2, 0), (-1, 0.0, -1, -1, 0), (0, 1.5, 3, 4, 2), (-1, 0.0, -1, -1, 2),
+     (-1, 0.0, -1, -1, 0)],
+    [(1, 2.5, 1, 2, 0), (-1, 0.0, -1, -1, 0), (0, 2.0, 3, 4, 2), (-1, 0.0, -1, -1, 2),
+     (-1, 0.0, -1, -1, 0)],
+]
+
+
+def test_rfc_stream_and_derived_draws():
+    r = select.SplitMix64(0)
+    assert [r.next() for _ in RFC_STREAM] == RFC_STREAM
+    # the literal bootstrap indices and subsets restate the stream arithmetic
+    assert [o % 6 for o in RFC_STREAM[0:6]] == RFC_BOOT[0]
+    assert [o % 6 for o in RFC_STREAM[10:16]] == RFC_BOOT[1]
+
+
+def test_rfc_worked_example_forest():
+    forest = select.rfc_fit(RFC_X, RFC_Y, ntrees=2, max_depth=2, seed=0)
+    assert forest == RFC_FOREST
+    # the same trees from the (separately pinned) CART with the hand-derived
+    # bootstrap samples and per-split feature subsets
+    for t in range(2):
+        draws = iter(RFC_DRAWS[t])
+        tree = select.cart_fit(RFC_X, RFC_Y, 2, samples=RFC_BOOT[t], feature_draw=lambda: next(draws))
+        assert tree == RFC_FOREST[t]
+        assert next(draws, None) is None  # exactly one draw per split attempt
+
+
+def _mutated_rfc(old: str, new: str):
+    """rfc_fit with one planted mistake (a textual edit of its source)."""
+    import inspect
+    import textwrap
+
+    src = textwrap.dedent(inspect.getsource(select.rfc_fit))
+    assert old in src, old
+    ns = dict(vars(select))
+    exec(compile(src.replace(old, new), "<mutant>", "exec"), ns)
+    return ns["rfc_fit"]
+
+
+@pytest.mark.parametrize("old,new", [
+    ("for _ in range(n)]", "for _ in range(n - 1)]"),                 # bootstrap of n-1
+    ("rng.next() % n ", "rng.next() % (n - 1) "),                     # indices mod n-1
+    ("feature_draw=draw", "feature_draw=(lambda s=draw(): (lambda: s))()"),  # one draw per tree
+    ("for a in range(mtry):", "for a in range(F - 1):"),              # full shuffle
+    ("int(math.floor(math.sqrt(F)))", "F"),                           # every feature
+])
+def test_rfc_worked_example_rejects_planted_mistakes(old, new):
+    forest = _mutated_rfc(old, new)(RFC_X, RFC_Y, ntrees=2, max_depth=2, seed=0)
+    assert forest != RFC_FOREST
