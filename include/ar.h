@@ -149,6 +149,32 @@ int ar_end(ar_region *r, void *stream);
 int ar_invoke(ar_region *r, const float *features, int nf, void *args, void *stream,
               int *out_variant, double *out_value);
 
+/* One block of host memory and its device counterpart, for ar_invoke_host. */
+typedef struct ar_host_copy {
+  void *host;   /* host address; pinned (cudaHostAlloc / cudaHostRegister)
+                   for the copy to run asynchronously */
+  void *device; /* device address (caller-owned) */
+  size_t bytes;
+} ar_host_copy;
+
+/* End-to-end execution on host data (the region's execution of Table 1 with
+ * its inputs and results in host memory): on `stream`, copy every `in`
+ * block host -> device (one cudaMemcpyAsync each, in order), then ar_invoke
+ * (features -> the model's or the exploration's variant -> its launcher ->
+ * the profiling record, which times the variant only), then copy every `out`
+ * block device -> host.  `args` holds the device addresses the variant
+ * reads and writes (the `device` sides of the copies and any scratch the
+ * caller owns).  Nothing blocks the host when the host blocks are pinned;
+ * the results are in host memory once `stream` completes (pageable host
+ * memory also works, with copies that block the host).  Independent
+ * invocations on different streams overlap their copies with each other's
+ * kernels.  Errors: as ar_invoke; AR_ERR_ARG for a bad copy list (NULL
+ * pointer with a non-zero size, negative count) before anything is
+ * enqueued; AR_ERR_CUDA if a copy cannot be enqueued. */
+int ar_invoke_host(ar_region *r, const float *features, int nf, void *args, void *stream,
+                   const ar_host_copy *in, int n_in, const ar_host_copy *out, int n_out, int *out_variant,
+                   double *out_value);
+
 /* Prediction only (no execution): the trained model's variant and its
  * confidence (MLP: max softmax probability; dtree: fraction of training
  * labels agreeing in the leaf; exhaustive/fixed: 1).  AR_ERR_NOMODEL if

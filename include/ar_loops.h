@@ -307,6 +307,48 @@ int ar_exec_batch(const ar_exec_call *calls, int ncalls, const ar_exec_models *m
                   int32_t *variant, float *conf, float *features, uint64_t *t_start, uint64_t *t_end,
                   int32_t *status, void *workspace, size_t workspace_bytes, void *stream);
 
+/* Confidence fallback of a mixed-stream batch.  The region learns from its
+ * profiled executions (Section 2: every execution's features, policy and time
+ * are recorded, and the model trained on them maps features to the fastest
+ * policy; Table 1, __apollo_region_train); a call the device MLP was unsure
+ * of is profiled exhaustively and its executions join the records of its
+ * loop's region.  For each call c in [0, ncalls) with conf[c] < tau:
+ *  - if the loop's region already holds records of every variant for the
+ *    call's exact feature vector, nothing runs: best[c] is the fastest mean
+ *    of those records (ties within 0.5 % to the lowest index);
+ *  - otherwise every variant runs as a one-call ar_exec_batch forced to it,
+ *    once untimed and `reps` times timed by the executor's own per-call time
+ *    (t_end - t_start), each timed run preceded by the region's L2 flush
+ *    (ar_set_l2_flush) if it has one; each timed run is appended to the
+ *    region as a record (features, variant, ms), so a profiled call adds
+ *    exactly V x reps records, and best[c] is the fastest mean.  The call's
+ *    outputs end as its best variant computes them: one more untimed run of
+ *    best[c], except for daxpy, whose y (updated in place by every run) is
+ *    saved in the workspace before profiling and restored after (every daxpy
+ *    variant computes the same fused multiply-add per element, so the saved
+ *    y is the best variant's result too).
+ * Other calls get best[c] = -1.  With retrain != 0 every region that received
+ * records is trained again (ar_train) and, when `models` is given and the
+ * region's model is an MLP, its new parameters are copied into that loop's
+ * device buffers models->theta/mu/sd (same F, H and V), ready for the next
+ * batch.
+ *  calls, features (8 floats per call, as ar_exec_batch writes them), conf:
+ *    HOST copies of the batch's table and outputs; the calls' device buffers
+ *    must still be valid.
+ *  regions[4]: one region per loop (NULL skips that loop's calls) with the
+ *    loop's variant count and the executor's feature count (1, 3, 5, 1);
+ *    AR_ERR_STATE otherwise.  reps: 1 .. 16.
+ *  workspace: device memory of ar_exec_fallback_workspace_bytes(n), n the
+ *    largest daxpy n that may fall back (AR_ERR_ARG for a larger one).
+ *  best: HOST int32[ncalls]; *num_profiled (may be NULL): calls profiled.
+ * Blocking: synchronises `stream` once per profiled call and before return.
+ * Returns AR_OK, AR_ERR_ARG, AR_ERR_STATE, AR_ERR_CUDA, or the first failing
+ * execution's status (e.g. AR_ERR_TIMEOUT). */
+int ar_exec_fallback_workspace_bytes(int64_t max_daxpy_n, size_t *bytes);
+int ar_exec_fallback(const ar_exec_call *calls, int ncalls, const float *features, const float *conf, float tau,
+                     ar_region *const *regions, int reps, const ar_exec_models *models, int retrain, void *workspace,
+                     size_t workspace_bytes, void *stream, int32_t *best, int *num_profiled);
+
 /* ------------------------------------------------------------ MLP selector ---
  * The learned selector of the adaptive region: the paper's model kinds are
  * decision trees and random forests and it names neural networks as a

@@ -83,6 +83,10 @@ class ArExecCall(ctypes.Structure):
                 ("out0", _vp), ("out1", _vp), ("out1_bytes", ctypes.c_uint64)]
 
 
+class ArHostCopy(ctypes.Structure):
+    _fields_ = [("host", _vp), ("device", _vp), ("bytes", _sz)]
+
+
 class ArExecModels(ctypes.Structure):
     _fields_ = [("F", ctypes.c_int32 * 4), ("V", ctypes.c_int32 * 4), ("H", ctypes.c_int32),
                 ("theta", _vp * 4), ("mu", _vp * 4), ("sd", _vp * 4)]
@@ -105,6 +109,8 @@ _SIGS = {
     "ar_get_policy": (_i, [_vp, _pi]),
     "ar_end": (_i, [_vp, _vp]),
     "ar_invoke": (_i, [_vp, _pf, _i, _vp, _vp, _pi, _pd]),
+    "ar_invoke_host": (_i, [_vp, _pf, _i, _vp, _vp, ctypes.POINTER(ArHostCopy), _i, ctypes.POINTER(ArHostCopy), _i,
+                            _pi, _pd]),
     "ar_select": (_i, [_vp, _pf, _i, _pi, _pf]),
     "ar_profile": (_i, [_vp, _pf, _i, _vp, _vp, _i, _pf, _pi]),
     "ar_train": (_i, [_vp]),
@@ -141,6 +147,9 @@ _SIGS = {
     "ar_exec_workspace_bytes": (_i, [_i, ctypes.POINTER(_sz)]),
     "ar_wait_selftest": (_i, [_i, ctypes.c_uint, _vp, _vp]),
     "ar_exec_batch": (_i, [_vp, _i, ctypes.POINTER(ArExecModels), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "ar_exec_fallback_workspace_bytes": (_i, [_i64, ctypes.POINTER(_sz)]),
+    "ar_exec_fallback": (_i, [_vp, _i, _pf, _pf, _f, ctypes.POINTER(_vp), _i, ctypes.POINTER(ArExecModels), _i, _vp,
+                              _sz, _vp, ctypes.POINTER(ctypes.c_int32), _pi]),
     "ar_mlp_num_params": (_i, [_i, _i, _i]),
     "ar_mlp_forward": (_i, [_vp, _vp, _vp, _i, _i, _i, _i64, _vp, _vp, _vp, _vp, _vp]),
     "ar_mlp_grad": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp]),
@@ -287,6 +296,32 @@ def ar_exec_batch(calls, ncalls, models, force_variant, variant, conf, features,
                                    stream_handle(stream)))
 
 
+def ar_exec_fallback_workspace_bytes(max_daxpy_n):
+    b = ctypes.c_size_t()
+    check(lib.ar_exec_fallback_workspace_bytes(max_daxpy_n, ctypes.byref(b)))
+    return b.value
+
+
+def ar_exec_fallback(calls, features, conf, tau, regions, reps, models, retrain, workspace, workspace_bytes,
+                     stream=None):
+    """calls: list of ArExecCall (host); features: (n, 8) float32 and conf:
+    (n,) float32 host arrays (the batch's outputs); regions: four Region
+    objects or None.  Returns (best variant per call, -1 if not profiled;
+    number of calls profiled)."""
+    n = len(calls)
+    arr = (ArExecCall * max(n, 1))(*calls)
+    f = np.ascontiguousarray(np.asarray(features, dtype=np.float32).reshape(n, 8) if n else np.zeros((1, 8), np.float32))
+    c = np.ascontiguousarray(np.asarray(conf, dtype=np.float32).reshape(n) if n else np.zeros(1, np.float32))
+    regs = (_vp * 4)(*[r.h if r is not None else None for r in regions])
+    best = np.full(max(n, 1), -1, dtype=np.int32)
+    cnt = ctypes.c_int()
+    mp = ctypes.byref(models) if models is not None else None
+    check(lib.ar_exec_fallback(ctypes.addressof(arr), n, f.ctypes.data_as(_pf), c.ctypes.data_as(_pf), tau, regs, reps,
+                               mp, int(retrain), ptr(workspace), workspace_bytes, stream_handle(stream),
+                               best.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(cnt)))
+    return best[:n], cnt.value
+
+
 def exec_table_bytes(calls) -> bytes:
     """Pack a list of ArExecCall into the byte image of the device call table."""
     arr = (ArExecCall * len(calls))(*calls)
@@ -407,6 +442,18 @@ class Region:
         self._ck(lib.ar_invoke(self.h, fp, n, a, stream_handle(stream), ctypes.byref(v), ctypes.byref(val)))
         return v.value, val.value
 
+    def invoke_host(self, features, args, copies_in, copies_out, stream=None):
+        """ar_invoke_host: copies_in / copies_out are lists of (host, device,
+        bytes) with host and device given as tensors, arrays or addresses."""
+        f, fp, n = _floats(features)
+        cin = (ArHostCopy * max(1, len(copies_in)))(*[ArHostCopy(ptr(h), ptr(d), b) for h, d, b in copies_in])
+        cout = (ArHostCopy * max(1, len(copies_out)))(*[ArHostCopy(ptr(h), ptr(d), b) for h, d, b in copies_out])
+        v, val = ctypes.c_int(), ctypes.c_double()
+        a = ctypes.cast(ctypes.pointer(args), _vp) if args is not None else None
+        self._ck(lib.ar_invoke_host(self.h, fp, n, a, stream_handle(stream), cin, len(copies_in), cout,
+                                    len(copies_out), ctypes.byref(v), ctypes.byref(val)))
+        return v.value, val.value
+
     def select(self, features):
         f, fp, n = _floats(features)
         v, c = ctypes.c_int(), ctypes.c_float()
@@ -437,15 +484,16 @@ class Region:
         self._ck(lib.ar_record_counts(self.h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
 
-    def records(self):
-        """Resolved records as a list of (features tuple, variant, ms)."""
+    def records(self, first: int = 0):
+        """Resolved records [first, end) as a list of (features tuple, variant, ms)."""
         n, _ = self.counts()
-        if n == 0:
+        n -= first
+        if n <= 0:
             return []
         F = np.zeros((n, AR_MAX_FEATURES), dtype=np.float32)
         V = np.zeros(n, dtype=np.int32)
         M = np.zeros(n, dtype=np.float32)
-        self._ck(lib.ar_get_records(self.h, 0, n, F.ctypes.data_as(_pf), V.ctypes.data_as(_pi),
+        self._ck(lib.ar_get_records(self.h, first, n, F.ctypes.data_as(_pf), V.ctypes.data_as(_pi),
                                     M.ctypes.data_as(_pf)))
         return [(tuple(float(x) for x in F[i, :self.nf]), int(V[i]), float(M[i])) for i in range(n)]
 
@@ -517,6 +565,7 @@ class Region:
 
 
 __all__ = ["ArExecCall", "ArExecModels", "ar_exec_workspace_bytes", "ar_exec_batch", "exec_table_bytes",
+           "ar_exec_fallback", "ar_exec_fallback_workspace_bytes", "ArHostCopy",
            "AR_EXEC_MAX_CALLS", "AR_EXEC_MAX_PHASES", "ArError", "Region", "ArDaxpyArgs", "ArJacobi7Args", "ArHeat7Args", "ArSpmvArgs", "ArNbodyArgs", "ar_spmv",
            "ar_spmv_workspace_bytes", "ar_spmv_merge_path_noalloc", "ar_spmv_gather_floor", "ar_csr_features", "ar_csr_features_workspace_bytes", "ar_nbody",
            "ar_nbody_batched", "ar_nbody_batched_workspace_bytes", "LAUNCH_FN", "FAKE_TIME_FN", "lib", "ptr",

@@ -87,6 +87,14 @@ struct SplitMix64 {
 
 uint64_t fnv1a(const uint8_t* p, size_t n);
 
+// Region internals used by other parts of the library (runtime.cpp).
+// Per-variant mean ms over the region's resolved records of one exact feature
+// vector (+inf where a variant has none); returns the number of variants that
+// have at least one record (0 if the vector was never recorded).
+int region_key_means(const ar_region* r, const float* f, int nf, std::vector<double>* mean);
+// The region's L2 flush buffer (ar_set_l2_flush), or nullptr / 0.
+void region_flush_buffer(const ar_region* r, void** buf, size_t* bytes);
+
 struct Blob {
   std::vector<uint8_t> data;
   void put_bytes(const void* p, size_t n) {

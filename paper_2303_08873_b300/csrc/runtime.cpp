@@ -74,6 +74,8 @@ struct ar_region {
 
   uint64_t explore_counter = 0;
   std::vector<ar::Record> records;
+  // per exact feature vector: (sum of ms, count) of each variant's records
+  std::map<FKey, std::vector<std::pair<double, int64_t>>> agg;
   std::deque<Pending> pending;
   std::vector<cudaEvent_t> event_pool;
   std::set<std::pair<FKey, int>> unique;
@@ -235,6 +237,12 @@ void add_record(ar_region* r, const FKey& key, int variant, float ms) {
   rec.variant = variant;
   rec.ms = ms;
   r->records.push_back(rec);
+  auto& a = r->agg[key];
+  if (a.size() < r->variants.size()) a.resize(r->variants.size(), {0.0, 0});
+  if (variant >= 0 && variant < (int)a.size()) {
+    a[variant].first += ms;
+    a[variant].second += 1;
+  }
 }
 
 // Resolve completed pending executions in order; block on them if `wait`.
@@ -517,6 +525,37 @@ int ar_invoke(ar_region* r, const float* features, int nf, void* args, void* str
   if (rc != AR_OK) return rc;
   if (out_variant) *out_variant = v;
   if (out_value) *out_value = var.value;
+  return AR_OK;
+}
+
+int ar_invoke_host(ar_region* r, const float* features, int nf, void* args, void* stream, const ar_host_copy* in,
+                   int n_in, const ar_host_copy* out, int n_out, int* out_variant, double* out_value) {
+  if (!r) return AR_ERR_ARG;
+  // the checks of ar_invoke first, so that nothing is enqueued for a call it rejects
+  if (nf != r->nf) return fail(r, AR_ERR_STATE, "expected %d features, got %d", r->nf, nf);
+  if (nf > 0 && !features) return fail(r, AR_ERR_ARG, "NULL features");
+  if (!finite_all(features, nf)) return fail(r, AR_ERR_ARG, "feature is NaN or inf");
+  if (r->open) return fail(r, AR_ERR_STATE, "an execution is already open");
+  if (r->variants.empty()) return fail(r, AR_ERR_STATE, "region has no variants");
+  if (n_in < 0 || n_out < 0 || (n_in > 0 && !in) || (n_out > 0 && !out))
+    return fail(r, AR_ERR_ARG, "bad copy list");
+  for (int i = 0; i < n_in + n_out; ++i) {
+    const ar_host_copy& c = i < n_in ? in[i] : out[i - n_in];
+    if (c.bytes > 0 && (!c.host || !c.device)) return fail(r, AR_ERR_ARG, "copy %d has a NULL pointer", i);
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  for (int i = 0; i < n_in; ++i) {
+    if (!in[i].bytes) continue;
+    const cudaError_t e = cudaMemcpyAsync(in[i].device, in[i].host, in[i].bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(r, e, "host-to-device copy");
+  }
+  int rc = ar_invoke(r, features, nf, args, stream, out_variant, out_value);
+  if (rc != AR_OK) return rc;
+  for (int i = 0; i < n_out; ++i) {
+    if (!out[i].bytes) continue;
+    const cudaError_t e = cudaMemcpyAsync(out[i].host, out[i].device, out[i].bytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(r, e, "device-to-host copy");
+  }
   return AR_OK;
 }
 
@@ -944,7 +983,15 @@ int ar_region_load(ar_region* r, const char* path) {
   freeze(r);
   r->records.swap(recs);
   r->unique.clear();
-  for (const auto& rec : r->records) r->unique.insert({ar::record_key(rec), rec.variant});
+  r->agg.clear();
+  for (const auto& rec : r->records) {
+    const FKey k = ar::record_key(rec);
+    r->unique.insert({k, rec.variant});
+    auto& a = r->agg[k];
+    if (a.size() < r->variants.size()) a.resize(r->variants.size(), {0.0, 0});
+    a[rec.variant].first += rec.ms;
+    a[rec.variant].second += 1;
+  }
   r->tree.swap(tree);
   r->forest.swap(forest);
   r->mlp = std::move(m);
@@ -955,3 +1002,28 @@ int ar_region_load(ar_region* r, const char* path) {
 }
 
 }  // extern "C"
+
+namespace ar {
+
+int region_key_means(const ar_region* r, const float* f, int nf, std::vector<double>* mean) {
+  const int V = (int)r->variants.size();
+  mean->assign(V, INFINITY);
+  float g[AR_MAX_FEATURES] = {};
+  for (int i = 0; i < nf && i < AR_MAX_FEATURES; ++i) g[i] = f[i];
+  auto it = r->agg.find(make_key(g, nf));
+  if (it == r->agg.end()) return 0;
+  int have = 0;
+  for (int v = 0; v < V && v < (int)it->second.size(); ++v)
+    if (it->second[v].second > 0) {
+      (*mean)[v] = it->second[v].first / (double)it->second[v].second;
+      ++have;
+    }
+  return have;
+}
+
+void region_flush_buffer(const ar_region* r, void** buf, size_t* bytes) {
+  *buf = r->flush_buf;
+  *bytes = r->flush_bytes;
+}
+
+}  // namespace ar

@@ -326,3 +326,129 @@ def test_bounded_waits_give_up_with_a_status():
     assert time.perf_counter() - t0 < 5.0
     assert st.cpu().tolist() == [ar.AR_ERR_TIMEOUT, ar.AR_ERR_TIMEOUT, ar.AR_OK, ar.AR_OK]
 
+
+
+def test_plan_kernel_mlp_matches_oracle_forward():
+    """The plan kernel's per-call MLP (variant, confidence) against the float64
+    oracle forward at the float32-rounded weights and statistics, on the
+    features the executor computed for each call."""
+    from oracle import mlp
+
+    models, keep, regions = _trained_models()
+    b = Batch()
+    rng = np.random.Generator(np.random.PCG64(21))
+    for n in np.exp(rng.uniform(np.log(1000), np.log(400000), 14)).astype(int):
+        b.daxpy(int(n), int(n) % 97)
+    for N in (33, 40, 48, 71, 96, 130):
+        b.jacobi(N, 2, N)
+    for rows, s in ((5000, 1.5), (20000, 2.2), (60000, 1.8)):
+        b.spmv(synth.csr_zipf(rows % 13, rows, s), rows % 17)
+    b.spmv(synth.csr_band(3, 15000, 33), 8)
+    for N in (600, 1500, 2100, 3700):
+        b.nbody(N, N % 11)
+    r = b.run(models=models)
+    assert np.all(r["status"] == 0)
+    checked = 0
+    for k, call in enumerate(b.calls):
+        L = call.loop
+        F, V = models.F[L], models.V[L]
+        m = regions[L].mlp()
+        th32, mu32, sd32 = (np.asarray(m[q], dtype=np.float32) for q in ("theta", "mu", "sd"))
+        f32 = r["features"][k][:F].astype(np.float32)
+        p, _ = mlp.forward(th32.astype(np.float64), f32[None, :].astype(np.float64), mu32.astype(np.float64),
+                           sd32.astype(np.float64), 64, V)
+        p = p[0]
+        assert abs(float(r["conf"][k]) - p.max()) <= 1e-5, (k, L)
+        top2 = np.sort(p)[-2:]
+        if top2[1] - top2[0] > 1e-4:
+            assert r["variant"][k] == int(np.argmax(p)), (k, L)
+            checked += 1
+        assert b.check[k](), k
+    assert checked >= len(b.calls) // 2
+
+
+def _fallback_regions(spec):
+    regions = []
+    for L, nf in enumerate((1, 3, 5, 1)):
+        r = ar.Region(f"fb{L}", nf, spec, 10 ** 9)
+        r.add_builtin(L)
+        regions.append(r)
+    return regions
+
+
+def _fallback_batch():
+    b = Batch()
+    b.daxpy(70001, 3)
+    b.jacobi(45, 2, 4)
+    b.spmv(synth.csr_zipf(5, 30000, 1.6), 6)
+    b.nbody(1500, 7)
+    return b
+
+
+def test_fallback_profiles_low_confidence_calls_into_records():
+    """Calls planted below the confidence threshold are profiled through the
+    executor: V x reps records each, best = the fastest recorded mean (the
+    oracle's label rule), outputs still the loop's result; a second fallback
+    on the same features profiles nothing and returns the same choices."""
+    from oracle import select
+
+    b = _fallback_batch()
+    r = b.run()
+    assert np.all(r["status"] == 0)
+    regions = _fallback_regions("dtree")
+    conf = np.array([0.2, 0.9, 0.3, 0.1], dtype=np.float32)
+    reps = 2
+    wsb = ar.ar_exec_fallback_workspace_bytes(70001)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    best, cnt = ar.ar_exec_fallback(b.calls, r["features"], conf, 0.5, regions, reps, None, False, ws, wsb)
+    assert cnt == 3 and best[1] == -1
+    for k, L in ((0, 0), (2, 2), (3, 3)):
+        V = ar.loop_num_variants(L)
+        recs = regions[L].records()
+        assert len(recs) == V * reps
+        nf = regions[L].nf
+        for f, v, ms in recs:
+            assert np.array_equal(np.asarray(f[:nf], dtype=np.float32), r["features"][k][:nf])
+            assert ms >= 0
+        assert sorted(v for _, v, _ in recs) == sorted(list(range(V)) * reps)
+        assert best[k] == select.labels([(tuple(f), v, ms) for f, v, ms in recs])[0][1]
+    assert regions[1].counts()[0] == 0
+    for k, ok in enumerate(b.check):
+        assert ok(), k  # daxpy applied once, the rest recomputed by the best variant
+    best2, cnt2 = ar.ar_exec_fallback(b.calls, r["features"], conf, 0.5, regions, reps, None, False, ws, wsb)
+    assert cnt2 == 0 and np.array_equal(best, best2)
+    assert [rg.counts()[0] for rg in regions] == [15 * reps, 0, 8 * reps, 9 * reps]
+    for k, ok in enumerate(b.check):
+        assert ok(), k
+
+
+def test_fallback_retrains_and_refreshes_device_models():
+    b = _fallback_batch()
+    r = b.run()
+    regions = _fallback_regions("mlp,64,epochs=30,seed=2")
+    models = ar.ArExecModels()
+    models.H = 64
+    keep = []
+    for L, F in enumerate((1, 3, 5, 1)):
+        V = ar.loop_num_variants(L)
+        th = torch.zeros(ar.ar_mlp_num_params(F, 64, V), dtype=torch.float32, device="cuda")
+        mu = torch.zeros(F, dtype=torch.float32, device="cuda")
+        sd = torch.ones(F, dtype=torch.float32, device="cuda")
+        keep += [th, mu, sd]
+        models.F[L], models.V[L] = F, V
+        models.theta[L], models.mu[L], models.sd[L] = th.data_ptr(), mu.data_ptr(), sd.data_ptr()
+    wsb = ar.ar_exec_fallback_workspace_bytes(70001)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    conf = np.zeros(4, dtype=np.float32)
+    best, cnt = ar.ar_exec_fallback(b.calls, r["features"], conf, 0.5, regions, 1, models, True, ws, wsb)
+    assert cnt == 4 and np.all(best >= 0)
+    for L in range(4):
+        m = regions[L].mlp()
+        assert np.array_equal(host(keep[3 * L]), np.asarray(m["theta"], dtype=np.float32))
+        assert np.array_equal(host(keep[3 * L + 1]), np.asarray(m["mu"], dtype=np.float32))
+        assert np.array_equal(host(keep[3 * L + 2]), np.asarray(m["sd"], dtype=np.float32))
+    # the refreshed device models choose what the retrained regions choose
+    r2 = b.run(models=models)
+    for k, call in enumerate(b.calls):
+        want, _ = regions[call.loop].select(list(r2["features"][k][:regions[call.loop].nf]))
+        assert r2["variant"][k] == want, k

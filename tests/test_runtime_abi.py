@@ -341,3 +341,45 @@ def test_random_forest_save_load(tmp_path):
     q, _ = _region(V=3, spec="rfc,5,2")
     q.load(p)
     assert q.forest() == r.forest() and q.select([5000]) == r.select([5000])
+
+
+def test_exec_fallback_checks_region_shapes_before_device_work():
+    ws = 256  # a dummy device address: every case below returns before any device work
+    daxpy_like = ar.Region("fb-shape", 1, "dtree", 10 ** 9)
+    daxpy_like.add_builtin(ar.AR_LOOP_JACOBI7)  # 16 variants where daxpy has 15
+    bad = [daxpy_like, None, None, None]
+    call = ar.ArExecCall(loop=0, n=10)
+    with pytest.raises(ar.ArError) as e:
+        ar.ar_exec_fallback([call], np.zeros((1, 8)), [0.0], 0.5, bad, 1, None, False, ws, 1 << 20)
+    assert e.value.code == ar.AR_ERR_STATE
+    wrong_nf = ar.Region("fb-nf", 2, "dtree", 10 ** 9)
+    wrong_nf.add_builtin(ar.AR_LOOP_DAXPY)
+    with pytest.raises(ar.ArError) as e:
+        ar.ar_exec_fallback([call], np.zeros((1, 8)), [0.0], 0.5, [wrong_nf, None, None, None], 1, None, False,
+                            ws, 1 << 20)
+    assert e.value.code == ar.AR_ERR_STATE
+    for reps in (0, 17):
+        with pytest.raises(ar.ArError) as e:
+            ar.ar_exec_fallback([call], np.zeros((1, 8)), [0.0], 0.5, [None] * 4, reps, None, False, ws, 1 << 20)
+        assert e.value.code == ar.AR_ERR_ARG
+    with pytest.raises(ar.ArError) as e:  # workspace smaller than the fixed part
+        ar.ar_exec_fallback([call], np.zeros((1, 8)), [0.0], 0.5, [None] * 4, 1, None, False, ws, 64)
+    assert e.value.code == ar.AR_ERR_ARG
+
+
+def test_invoke_host_rejects_bad_copy_lists_before_enqueuing():
+    r = ar.Region("host-copy", 1, "fixed,0", 0)
+    r.register("v0", 0.0, _noop)
+    with pytest.raises(ar.ArError) as e:
+        r.invoke_host([1.0], None, [(0, 64, 8)], [])  # NULL host pointer with bytes
+    assert e.value.code == ar.AR_ERR_ARG
+    with pytest.raises(ar.ArError) as e:
+        r.invoke_host([1.0], None, [], [(64, 0, 8)])  # NULL device pointer with bytes
+    assert e.value.code == ar.AR_ERR_ARG
+    with pytest.raises(ar.ArError) as e:
+        r.invoke_host([1.0, 2.0], None, [], [])  # wrong feature count
+    assert e.value.code == ar.AR_ERR_STATE
+    with pytest.raises(ar.ArError) as e:
+        r.invoke_host([float("nan")], None, [], [])
+    assert e.value.code == ar.AR_ERR_ARG
+    assert r.counts() == (0, 0)
