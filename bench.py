@@ -94,6 +94,8 @@ def parse():
     p.add_argument("--test", type=int, default=500, help="spmv: held-out test matrices")
     p.add_argument("--rows-max", type=float, default=1e7, help="spmv: largest row count")
     p.add_argument("--epochs", type=int, default=200, help="spmv: MLP epochs")
+    p.add_argument("--no-configs", action="store_true",
+                   help="jacobi7: skip the bounded records of the other configurations on the line")
     p.add_argument("--kfold", action="store_true",
                    help="spmv: also run the paper's K-fold protocol (K=4, f = 25/50/75 %%, 10 shuffles) and "
                         "Adaptive-100 on all profiled matrices")
@@ -177,7 +179,8 @@ def cpu_oracle_rate(seconds: float, kind: str = "jacobi7"):
     finally:
         loops.set_threads(cores)
     return {"value": val, "unit": "GB/s", "cores": cores, "kind": "oracle",
-            "sample": f"{STENCILS[kind]['label']} N in (32,64,128,256), 10 sweeps, {reps} passes, {dt:.1f} s",
+            "sample": f"{STENCILS[kind]['label']} N in (32,64,128,256), 10 sweeps, {reps} passes, {dt:.1f} s "
+                      "(the GPU value covers N up to 512)",
             "single_thread": {"value": one, "unit": "GB/s", "cores": 1,
                               "sample": f"N in (32,64,128), 10 sweeps, {reps1} passes, {dt1:.1f} s"},
             "host_cpus": os.cpu_count()}
@@ -266,6 +269,49 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- GPU arm
+def other_configs(args):
+    """The other configurations of the workload, each bounded so that the
+    default run stays within a few minutes, as compact records for the
+    headline line: daxpy (exhaustive selection), SpMV selection (MLP vs tree
+    vs default on 300 training and 100 held-out matrices), n-body per N with
+    the batched form, and a 2,560-call mixed stream with the confidence
+    fallback."""
+    import torch
+
+    out = {}
+    t = time.perf_counter()
+    d = daxpy_record(50, 5)
+    out["daxpy"] = {"value": d["value"], "unit": "GB/s", "selection": d["selection"], "roofline": d["roofline"],
+                    "warm_graph": d["warm_graph"], "config": d["config"]["workload"],
+                    "wall_s": time.perf_counter() - t}
+    out["daxpy"]["selection"].pop("profile_gbs", None)
+    torch.cuda.empty_cache()
+    t = time.perf_counter()
+    sp = spmv_study(300, 100, 1e7, 200)
+    sel = sp["selection"]
+    out["spmv"] = {"value": sp["value"], "unit": "GB/s", "config": sp["config"]["workload"],
+                   "selection": {k: sel[k] for k in ("exhaustive_best_gbs", "mlp_gbs", "dtree_gbs", "default_gbs",
+                                                    "mlp_mean_regret_pct", "dtree_mean_regret_pct",
+                                                    "default_mean_regret_pct", "mlp_exact_pct",
+                                                    "mlp_low_confidence_calls")},
+                   "roofline": sp["roofline"], "gather_floor": sp["gather_floor"], "cost": sp["cost"],
+                   "wall_s": time.perf_counter() - t}
+    torch.cuda.empty_cache()
+    t = time.perf_counter()
+    nb = nbody_record(3, 2)
+    out["nbody"] = {"value": nb["value"], "unit": "GFLOP/s", "config": nb["config"]["workload"],
+                    "per_N": nb["selection"]["per_N"], "roofline": nb["roofline"], "batched": nb["batched"],
+                    "wall_s": time.perf_counter() - t}
+    torch.cuda.empty_cache()
+    t = time.perf_counter()
+    mx = mixed_record(2560, args.tau)
+    out["mixed"] = {"value": mx["value"], "unit": "GB/s", "config": mx["config"]["workload"],
+                    "stream": mx["stream"], "selection": mx["selection"], "fallback": mx["fallback"],
+                    "cost": mx["cost"], "roofline": mx["roofline"], "wall_s": time.perf_counter() - t}
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -386,6 +432,36 @@ def run_ours(args):
                     "default_gbs": BYTES_PER_POINT * n ** 3 * SWEEPS / ms_n[default] / 1e6})
     regret = statistics.mean(p["regret_pct"] for p in per)
 
+    # --- the tree's regret on points it was not trained on: (a) sweeps = 10
+    # held out (trained on sweeps 1, 5, 20); (b) leave one N out (trained on
+    # the other five sizes, every sweep count)
+    def tree_regret(train_keys, test_n):
+        rt = ar.Region(f"{kind}-heldout", 2, "dtree,2", 10 ** 9)
+        for v in range(V):
+            rt.register(names[v], float(v), lambda a_, v_, x_, s_, u_: 0)
+        for key in train_keys:
+            for v in range(V):
+                rt.add_record(list(key), v, table[key][0][v])
+        rt.train()
+        out = []
+        for n in test_n:
+            ms_n, best = table[(n, SWEEPS)]
+            out.append(100 * (ms_n[rt.select([n, SWEEPS])[0]] / ms_n[best] - 1))
+        return out
+
+    held_sweeps = tree_regret([k for k in table if k[1] != SWEEPS], SIZES)
+    held_n = [tree_regret([k for k in table if k[0] != n], [n])[0] for n in SIZES]
+
+    # --- the best native float64 variant (families naive, smem, tma) at N = 512
+    ms_big = table[(big, SWEEPS)][0]
+    v64 = min(range(12), key=lambda v: ms_big[v])
+    gbs64 = BYTES_PER_POINT * big ** 3 * SWEEPS / ms_big[v64] / 1e6
+    alu64 = fp64_fma / spec["fp64_ops"] * BYTES_PER_POINT / 1e9
+    native64 = {"kernel": names[v64], "gbs": gbs64, "alu_roof_gbs": alu64, "alu_frac": gbs64 / alu64,
+                "hbm_frac": gbs64 / hbm_peak,
+                "note": "best of the native float64 families (naive, smem, tma) at N = 512, 10 sweeps, from the "
+                        "profile table; roof: measured float64 FMA issue rate / 6 float64 ops per point x 16 B"}
+
     # --- the paper's Online mode (Section 4.2): one fresh region per N, default
     # min_train_data (= number of variants), RoundRobin exploration over real
     # invocations, automatic training, then the tree's choice; regret from the
@@ -407,49 +483,43 @@ def run_ours(args):
                        "regret_pct": 100 * (ms_n[v_on] / ms_n[best] - 1),
                        "explore_overhead_pct": 100 * (explore_ms / (calls * ms_n[best]) - 1)})
 
-    # --- end to end through host buffers (pinned), copies inside the timed
-    # region: each grid is copied in on one stream, swept on the compute
-    # stream and copied out on a third, largest grid first, so PCIe traffic in
-    # both directions overlaps the sweeps (and the next step's copies)
+    # --- end to end through the library's host-buffer call (ar_invoke_host):
+    # per N its own stream carrying the copy of u0 in, the selected variant's
+    # sweeps and the copy of the result out (one cudaMemcpyAsync each way);
+    # the six streams overlap one grid's copies with another's sweeps
     host_in = {n: bufs[n][0].cpu().pin_memory() for n in SIZES}
     host_out = {n: torch.empty_like(host_in[n]).pin_memory() for n in SIZES}
     e2e_steps = max(3, min(args.steps, 10))
-    s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    streams = {n: torch.cuda.Stream(device=dev) for n in SIZES}
     order = sorted(SIZES, reverse=True)
-    ev_in = {n: torch.cuda.Event() for n in SIZES}
-    ev_comp = {n: torch.cuda.Event() for n in SIZES}
-    ev_out = {n: torch.cuda.Event() for n in SIZES}
+    copies = {n: ([(host_in[n], bufs[n][0], 8 * n ** 3)], [(host_out[n], bufs[n][1], 8 * n ** 3)]) for n in SIZES}
     torch.cuda.synchronize()
     a0 = torch.cuda.Event(enable_timing=True)
     a1 = torch.cuda.Event(enable_timing=True)
-    a0.record(s_in)
-    stream.wait_event(a0)
-    s_out.wait_event(a0)
+    a0.record(stream)
+    for n in SIZES:
+        streams[n].wait_event(a0)
     for k in range(e2e_steps):
         for n in order:
-            with torch.cuda.stream(s_in):
-                if k > 0:
-                    s_in.wait_event(ev_comp[n])  # the previous sweep of this grid has read u0
-                bufs[n][0].copy_(host_in[n], non_blocking=True)
-                ev_in[n].record(s_in)
-            stream.wait_event(ev_in[n])
-            if k > 0:
-                stream.wait_event(ev_out[n])  # the previous result has left the device
-            region.invoke([n, SWEEPS], argblocks[n], stream=stream)
-            ev_comp[n].record(stream)
-            with torch.cuda.stream(s_out):
-                s_out.wait_event(ev_comp[n])
-                host_out[n].copy_(bufs[n][1], non_blocking=True)
-                ev_out[n].record(s_out)
-    s_out.wait_stream(stream)
-    s_out.wait_stream(s_in)
-    a1.record(s_out)
+            region.invoke_host([n, SWEEPS], argblocks[n], *copies[n], stream=streams[n])
+    for n in SIZES:
+        stream.wait_stream(streams[n])
+    a1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = a0.elapsed_time(a1) / e2e_steps
+    ref0 = bufs[big][1].cpu()
+    assert torch.equal(host_out[big], ref0), "host result differs from the device result"
     h2d = sum(8 * n ** 3 for n in SIZES)
     e2e = {"value": step_bytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": h2d, "ms_per_step": e2e_ms,
-           "note": "copies from/to pinned host memory on their own streams, overlapped with the sweeps"}
+           "note": "ar_invoke_host per N (pinned host u0 in, the region's selected variant, result out), "
+                   "one stream per N"}
+
+    configs = None
+    if rank == 0 and ws == 1 and kind == "jacobi7" and not args.no_configs:
+        del bufs, argblocks, flush, host_in, host_out
+        torch.cuda.empty_cache()
+        configs = other_configs(args)
 
     if rank != 0:
         return
@@ -457,14 +527,21 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64 data, f32-pair arithmetic", "data": "synthetic",
         "config": jacobi_config(ws, kind),
         "selection": {"exhaustive_best_gbs": step_bytes / t_best / 1e6, "default_gbs": step_bytes / t_def / 1e6,
                       "selected_table_gbs": step_bytes / t_sel / 1e6, "regret_pct": regret,
                       "default_variant": names[default], "per_N": per, "tree": tree,
                       "online": {"mean_regret_pct": statistics.mean(o["regret_pct"] for o in online),
                                  "per_N": online},
+                      "held_out": {"sweeps10_mean_regret_pct": statistics.mean(held_sweeps),
+                                   "sweeps10_per_N": held_sweeps,
+                                   "leave_one_N_out_mean_regret_pct": statistics.mean(held_n),
+                                   "leave_one_N_out_per_N": held_n,
+                                   "note": "regret_pct above is in-sample (the tree is trained on all 24 profiled "
+                                           "points); here sweeps = 10 is held out, or each N in turn"},
                       "profiling_s": t_prof, "profiled_points": len(table), "variants": V},
+        "native_f64": native64,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -472,6 +549,12 @@ def run_ours(args):
         "clocks": clk,
         "fp64_fma_per_s": fp64_fma,
     }
+    line["config"]["arithmetic"] = (
+        "float64 in and out; the df variants the tree selects compute in float pairs (two float32 values, "
+        "~2^-46 relative per split value, TwoSum chains, one float64 add per output); the best native float64 "
+        "variant is reported under native_f64")
+    if configs is not None:
+        line["configs"] = configs
     print(json.dumps(line), flush=True)
 
 
@@ -723,13 +806,18 @@ class Arena:
         return self.t.data_ptr() + o
 
 
-def run_mixed(args):
-    """Config 5: a stream of `calls` region invocations (loop ~ U{4}, sizes
+def mixed_record(n_calls, tau, reps_fb=2, regret_sample=96):
+    """Config 5: a stream of `n_calls` region invocations (loop ~ U{4}, sizes
     log-uniform over each loop's range, SpMV from a pool of 32 matrices) run by
     the persistent executor in batches of 256 replayed from one captured CUDA
-    graph; the per-loop MLPs, trained on the executor's own single-call times,
-    choose the variants on the device.  Calls whose confidence is below tau
-    are profiled exhaustively afterwards (the fallback) and counted."""
+    graph; per-loop MLPs choose the variants on the device.  Training set and
+    fallback both go through the library (ar_exec_fallback): the training
+    calls are profiled exhaustively into one region per loop, which is trained
+    and uploaded; after every batch the calls whose confidence is below tau
+    are profiled the same way (unless their features were profiled before),
+    their records join the regions, and the regions are retrained and their
+    device models refreshed before the next batch.  Regret is scored on a
+    random sample of the stream by exhaustive profiling (5 timed runs)."""
     import torch
 
     import paper_2303_08873_b300 as ar
@@ -738,7 +826,7 @@ def run_mixed(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(device=dev)
     B = ar.AR_EXEC_MAX_CALLS
-    loop_ids, sizes = synth.mixed_stream(5, args.calls)
+    loop_ids, sizes = synth.mixed_stream(5, n_calls)
     # pool of SpMV matrices (device-generated), shared inputs; y per call
     pool = []
     for k in range(32):
@@ -792,65 +880,55 @@ def run_mixed(args):
     h_out = [torch.zeros_like(t, device="cpu").pin_memory() for t in (o_var, o_conf, o_feat, o_t0, o_t1, o_st)]
     wsb = ar.ar_exec_workspace_bytes(B)
     ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
-    force_d = torch.zeros(B, dtype=torch.int32, device=dev)
+    fb_wsb = ar.ar_exec_fallback_workspace_bytes(1 << 24)
+    fb_ws = torch.empty(fb_wsb, dtype=torch.uint8, device=dev)
 
-    def run_batch(calls, force=None, models=None):
-        """Eager batch (profiling): returns per-call (variant, conf, features, ns, status)."""
+    def run_batch(calls, models=None):
+        """Eager batch: returns per-call (variant, conf, features, ns, status)."""
         n = len(calls)
         table_d[:96 * n].copy_(torch.frombuffer(bytearray(ar.exec_table_bytes(calls)), dtype=torch.uint8))
-        fv = None
-        if force is not None:
-            force_d[:n].copy_(torch.tensor(force, dtype=torch.int32))
-            fv = force_d
-        ar.ar_exec_batch(table_d, n, models, fv, o_var, o_conf, o_feat, o_t0, o_t1, o_st, ws, wsb, stream=stream)
+        ar.ar_exec_batch(table_d, n, models, None, o_var, o_conf, o_feat, o_t0, o_t1, o_st, ws, wsb, stream=stream)
         stream.synchronize()
         return (o_var[:n].cpu().numpy(), o_conf[:n].cpu().numpy(), o_feat[:n].cpu().numpy(),
                 (o_t1[:n] - o_t0[:n]).cpu().numpy(), o_st[:n].cpu().numpy())
 
-    def exhaustive(loop, size, reps):
-        """Executor time (ns, mean of reps) of every variant for one call."""
-        V = ar.loop_num_variants(loop)
-        times = []
-        feats = None
-        for v in range(V):
-            acc = []
-            for _ in range(reps + 1):
-                c, _, _ = make_call(loop, size, *arenas())
-                _, _, f, ns, st = run_batch([c], force=[v])
-                assert st[0] == 0
-                acc.append(float(ns[0]))
-                feats = f[0]
-            times.append(statistics.mean(acc[1:]))
-        return times, feats
+    def new_records_ms(regs, before):
+        """Executor ms of the records added since `before` (per-loop counts)."""
+        return sum(ms for L in range(4) if regs[L] is not None for _, _, ms in regs[L].records(before[L]))
 
-    # --- training: executor single-call profiles of sampled sizes per loop
+    def counts(regs):
+        return [regs[L].counts()[0] if regs[L] is not None else 0 for L in range(4)]
+
+    nfeat = {0: 1, 1: 3, 2: 5, 3: 1}  # the executor's features per loop (ar_loops.h)
+    # --- training: the library's exhaustive profiling of sampled calls per loop
     rng = np.random.Generator(np.random.PCG64(55))
     lo = {0: 2.0 ** 10, 1: 32.0, 3: 1024.0}
     hi = {0: 2.0 ** 24, 1: 512.0, 3: 262144.0}
     train_sizes = {L: [int(np.exp(rng.uniform(np.log(lo[L]), np.log(hi[L])))) for _ in range(24)] for L in (0, 1, 3)}
     train_sizes[2] = list(range(32))
-    regions, keep = {}, []
+    regions = [ar.Region(f"mixed-{LOOPS[L]}", nfeat[L], "mlp,64,epochs=400,seed=3", 10 ** 9) for L in range(4)]
+    for L in range(4):
+        regions[L].add_builtin(L)
     models = ar.ArExecModels()
     models.H = 64
-    nfeat = {0: 1, 1: 3, 2: 5, 3: 1}  # the executor's features per loop (ar_loops.h)
-    prof_ns = 0.0
+    keep = []
     t0w = time.perf_counter()
     for L in range(4):
-        r = ar.Region(f"mixed-{LOOPS[L]}", nfeat[L], "mlp,64,epochs=400,seed=3", 10 ** 9)
-        r.add_builtin(L)
-        for size in train_sizes[L]:
-            times, f = exhaustive(L, size, 2)
-            prof_ns += 3 * sum(times)
-            for v, t in enumerate(times):
-                r.add_record(list(f[:nfeat[L]]), v, t * 1e-6)
-        r.train()
-        m = r.mlp()
+        a64, a32, sc = arenas()
+        calls = [make_call(L, s_, a64, a32, sc)[0] for s_ in train_sizes[L]]
+        feats = run_batch(calls)[2]
+        only = [regions[q] if q == L else None for q in range(4)]
+        ar.ar_exec_fallback(calls, feats, np.zeros(len(calls), np.float32), 0.5, only, reps_fb, None, False,
+                            fb_ws, fb_wsb, stream=stream)
+        regions[L].train()
+        m = regions[L].mlp()
         th, mu, sd = (torch.from_numpy(m[k]).to(dev) for k in ("theta", "mu", "sd"))
         keep += [th, mu, sd]
         models.F[L], models.V[L] = m["F"], m["V"]
         models.theta[L], models.mu[L], models.sd[L] = th.data_ptr(), mu.data_ptr(), sd.data_ptr()
-        regions[L] = r
+    train_ms = sum(ms for r in regions for _, _, ms in r.records()) * (reps_fb + 1) / reps_fb
     train_wall = time.perf_counter() - t0w
+    train_counts = counts(regions)
 
     # --- capture one batch graph: table copy, executor, result copies
     g = torch.cuda.CUDAGraph()
@@ -860,11 +938,12 @@ def run_mixed(args):
         for h, d in zip(h_out, (o_var, o_conf, o_feat, o_t0, o_t1, o_st)):
             h.copy_(d, non_blocking=True)
 
-    batches = [range(s0, min(s0 + B, args.calls)) for s0 in range(0, args.calls, B)]
+    batches = [range(s0, min(s0 + B, n_calls)) for s0 in range(0, n_calls, B)]
     # full batches replay the graph; a final partial batch runs eagerly
     lat = {L: [] for L in range(4)}
     byts = flops = 0.0
-    low = []
+    low = fb_profiled = 0
+    fb_wall = 0.0
     chosen = []
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     batch_ms = []
@@ -892,41 +971,60 @@ def run_mixed(args):
         ev1.record(stream)
         stream.synchronize()
         batch_ms.append(ev0.elapsed_time(ev1))
-        var, conf, feat, t0n, t1n, st = (h.numpy()[:n] for h in h_out)
+        var, conf, feat, t0n, t1n, st = (h.numpy()[:n].copy() for h in h_out)
         assert np.all(st == 0), "executor status"
         for k, q in enumerate(idx):
             L = int(loop_ids[q])
             lat[L].append((int(t1n[k]) - int(t0n[k])) * 1e-3)
             chosen.append((L, int(sizes[q]), int(var[k])))
-            if conf[k] < args.tau:
-                low.append(q)
+        # the confidence fallback through the library: profile, record, retrain, refresh the device models
+        low += int(np.sum(conf < tau))
+        tf = time.perf_counter()
+        _, cnt = ar.ar_exec_fallback(calls, feat, conf, tau, regions, reps_fb, models, True, fb_ws, fb_wsb,
+                                     stream=stream)
+        fb_wall += time.perf_counter() - tf
+        fb_profiled += cnt
     stream_ms = sum(batch_ms)
-    mem_bytes = byts  # daxpy + Jacobi + SpMV algorithmic bytes
-    # --- regret on a sample of the stream (exhaustive executor times)
-    samp = rng.choice(len(chosen), size=min(96, len(chosen)), replace=False)
+    fb_ms = new_records_ms(regions, train_counts) * (reps_fb + 1) / reps_fb
+    # --- regret on a sample of the stream: exhaustive profiling (5 timed runs)
+    # of each sampled call through the library into fresh regions
+    samp = rng.choice(len(chosen), size=min(regret_sample, len(chosen)), replace=False)
+    judge = [ar.Region(f"judge-{LOOPS[L]}", nfeat[L], "exhaustive", 10 ** 9) for L in range(4)]
+    for L in range(4):
+        judge[L].add_builtin(L)
     regrets = {L: [] for L in range(4)}
+    exh_ms = []
     for q in samp:
         L, size, v = chosen[q]
-        times, _ = exhaustive(L, size, 5)  # 5 timed runs per variant: regret is not measurement noise
-        regrets[L].append(times[v] / min(times) - 1.0)
-    # --- fallback: exhaustive profiling of the low-confidence calls (counted, timed on a sample)
-    fb_sample = [low[q] for q in rng.choice(len(low), size=min(24, len(low)), replace=False)] if low else []
-    t_fb = time.perf_counter()
-    fb_ns = 0.0
-    for q in fb_sample:
-        times, _ = exhaustive(int(loop_ids[q]), int(sizes[q]), 2)
-        fb_ns += 3 * sum(times)
-    t_fb = time.perf_counter() - t_fb
+        c = make_call(L, size, *arenas())[0]
+        feats = run_batch([c])[2]
+        only = [judge[p] if p == L else None for p in range(4)]
+        ar.ar_exec_fallback([c], feats, np.zeros(1, np.float32), 0.5, only, 5, None, False, fb_ws, fb_wsb,
+                            stream=stream)
+        key = tuple(float(x) for x in np.asarray(feats[0][:nfeat[L]], dtype=np.float32))
+        per_v = {}
+        for f_, v_, ms_ in judge[L].records():
+            if f_ == key:
+                per_v.setdefault(v_, []).append(ms_)
+        means = [statistics.mean(per_v[w]) for w in range(ar.loop_num_variants(L))]
+        regrets[L].append(means[v] / min(means) - 1.0)
+        exh_ms.append((reps_fb + 1) * sum(means))  # exhaustive profile of this call at the fallback's reps
     all_reg = [x for L in range(4) for x in regrets[L]]
-    line = {
-        "metric": METRIC, "value": mem_bytes / (stream_ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1,
+    hbm_peak, peak_src = peaks()
+    _, fp32_fma = ar.ar_measure_fma_rates()
+    fp32_roof = fp32_fma / 12.0 * NBODY_FLOPS / 1e9
+    mem_gbs = byts / (stream_ms * 1e-3) / 1e9
+    nb_gflops = flops / (stream_ms * 1e-3) / 1e9
+    exhaustive_all_ms = statistics.mean(exh_ms) * n_calls
+    return {
+        "metric": METRIC, "value": mem_gbs, "unit": "GB/s", "n_gpus": 1,
         "dtype": "f64 (daxpy, Jacobi, SpMV) / f32 (n-body)", "data": "synthetic", "higher_is_better": True,
         "vs_baseline": None,
-        "config": {"workload": f"mixed stream of {args.calls} calls (loop ~ U{{4}}, sizes log-uniform), batches "
-                               f"of {B} replayed from one CUDA graph, device MLP selection, tau = {args.tau}",
+        "config": {"workload": f"mixed stream of {n_calls} calls (loop ~ U{{4}}, sizes log-uniform), batches "
+                               f"of {B} replayed from one CUDA graph, device MLP selection, confidence fallback "
+                               f"below tau = {tau} through ar_exec_fallback ({reps_fb} timed runs per variant)",
                    "batches": len(batches)},
-        "stream": {"ms": stream_ms, "memory_loops_gbs": mem_bytes / (stream_ms * 1e-3) / 1e9,
-                   "nbody_gflops": flops / (stream_ms * 1e-3) / 1e9,
+        "stream": {"ms": stream_ms, "memory_loops_gbs": mem_gbs, "nbody_gflops": nb_gflops,
                    "batch_ms_p50": float(np.percentile(batch_ms, 50)),
                    "latency_us": {LOOPS[L]: {"p50": float(np.percentile(lat[L], 50)),
                                              "p99": float(np.percentile(lat[L], 99)), "calls": len(lat[L])}
@@ -935,31 +1033,29 @@ def run_mixed(args):
         "selection": {"mean_regret_pct": 100 * statistics.mean(all_reg),
                       "per_loop_regret_pct": {LOOPS[L]: 100 * statistics.mean(regrets[L]) for L in range(4)
                                               if regrets[L]},
-                      "regret_sample_calls": len(samp), "low_confidence_calls": len(low),
-                      "low_confidence_pct": 100.0 * len(low) / args.calls},
-        "cost": {"training_profile_gpu_ms": prof_ns * 1e-6, "training_wall_s": train_wall,
-                 "fallback_profile_gpu_ms_per_call": (fb_ns * 1e-6 / len(fb_sample)) if fb_sample else 0.0,
-                 "profiling_cost_ratio": None},
+                      "regret_sample_calls": len(samp),
+                      "note": "regret of the variant the device MLP chose when the call ran (before any fallback)"},
+        "fallback": {"low_confidence_calls": low, "low_confidence_pct": 100.0 * low / n_calls,
+                     "profiled_calls": fb_profiled, "answered_from_records": low - fb_profiled,
+                     "gpu_ms": fb_ms, "wall_s": fb_wall,
+                     "stream_plus_fallback_gbs": byts / ((stream_ms + fb_ms) * 1e-3) / 1e9},
+        "cost": {"training_profile_gpu_ms": train_ms, "training_wall_s": train_wall,
+                 "fallback_profile_gpu_ms": fb_ms,
+                 "exhaustive_every_call_gpu_ms": exhaustive_all_ms,
+                 "profiling_cost_ratio": (train_ms + fb_ms) / exhaustive_all_ms,
+                 "note": "GPU time of every profiled execution (warm-up included) of the learned method "
+                         "(training set + fallbacks) over exhaustive profiling of every call of the stream "
+                         "(estimated from the regret sample at the same repetitions)"},
+        "roofline": {"bound": "hbm", "achieved": mem_gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": mem_gbs / hbm_peak, "peak_source": peak_src, "traffic": None,
+                     "kernel": "exec_run (all loops in one launch)",
+                     "nbody": {"achieved_gflops": nb_gflops, "peak_gflops": fp32_roof, "frac": nb_gflops / fp32_roof},
+                     "machine_frac": mem_gbs / hbm_peak + nb_gflops / fp32_roof},
     }
-    # profiling cost of the learned method (training set + fallbacks) over
-    # exhaustive profiling of every call, estimated from the sampled calls
-    exh_per_call_ms = statistics.mean(3 * sum(exhaustive(L, s_, 1)[0]) * 1e-6 for L, s_, _ in
-                                      (chosen[q] for q in samp[:24]))
-    learned = prof_ns * 1e-6 + len(low) * line["cost"]["fallback_profile_gpu_ms_per_call"]
-    line["cost"]["profiling_cost_ratio"] = learned / (exh_per_call_ms * args.calls)
-    # both rates are over the same wall time: the stream's share of the machine
-    # is the sum of the two roofline fractions
-    hbm_peak, peak_src = peaks()
-    _, fp32_fma = ar.ar_measure_fma_rates()
-    fp32_roof = fp32_fma / 12.0 * NBODY_FLOPS / 1e9
-    mem_frac = line["value"] / hbm_peak
-    nb_frac = line["stream"]["nbody_gflops"] / fp32_roof
-    line["roofline"] = {"bound": "hbm", "achieved": line["value"], "peak": hbm_peak, "unit": "GB/s", "frac": mem_frac,
-                        "peak_source": peak_src, "traffic": None, "kernel": "exec_run (all loops in one launch)",
-                        "nbody": {"achieved_gflops": line["stream"]["nbody_gflops"], "peak_gflops": fp32_roof,
-                                  "frac": nb_frac},
-                        "machine_frac": mem_frac + nb_frac}
-    print(json.dumps(line), flush=True)
+
+
+def run_mixed(args):
+    print(json.dumps(mixed_record(args.calls, args.tau)), flush=True)
 
 
 # ---------------------------------------------------------------- evaluation protocol, all loops
@@ -1066,7 +1162,7 @@ def run_protocol(args):
 
 
 # ---------------------------------------------------------------- daxpy (config 1)
-def run_daxpy(args):
+def daxpy_record(steps, warmup):
     """Config 1: daxpy n = 2^20, 15 variants, exhaustive profiling (5 reps after
     a warm-up, L2 flushed before each) picks the argmin -- the plain method, no
     learned model.  Timed: `steps` invocations through the region, each after
@@ -1091,9 +1187,9 @@ def run_daxpy(args):
     default = ar.loop_default_variant(ar.AR_LOOP_DAXPY)
     names = [ar.loop_variant_name(ar.AR_LOOP_DAXPY, v) for v in range(V)]
     bytes_ = 24.0 * n
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             r.invoke([n], args_blk, stream=stream)
         for e0, e1 in ev:
             flush.fill_(1)
@@ -1120,7 +1216,7 @@ def run_daxpy(args):
     stream.synchronize()
     warm_ms = w0.elapsed_time(w1) / 100
     line = {"metric": METRIC, "value": bytes_ / (t_med * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1, "dtype": "f64",
-            "data": "synthetic", "higher_is_better": True, "vs_baseline": None, "steps": args.steps,
+            "data": "synthetic", "higher_is_better": True, "vs_baseline": None, "steps": steps,
             "config": {"workload": "daxpy float64 n = 2^20, a = 1.5, 15 variants, exhaustive profiling (5 reps, "
                                    "L2 flushed) picks the argmin", "l2": "flushed (512 MB) before every timed call"},
             "selection": {"selected": names[v], "exhaustive_best": names[best], "default": names[default],
@@ -1133,11 +1229,15 @@ def run_daxpy(args):
                          "note": "25 MB per call: 3.9 us at the HBM roof, comparable to launch latency"},
             "warm_graph": {"us_per_call": warm_ms * 1e3, "gbs": bytes_ / (warm_ms * 1e-3) / 1e9,
                            "note": "x, y resident in L2; 100 calls in one CUDA graph"}}
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def run_daxpy(args):
+    print(json.dumps(daxpy_record(args.steps, args.warmup)), flush=True)
 
 
 # ---------------------------------------------------------------- n-body (config 4)
-def run_nbody(args):
+def nbody_record(steps, warmup):
     """Config 4: all-pairs n-body, N in {1k, 4k, 16k, 64k, 256k}, 9 variants;
     exhaustive profiling per N picks the variant; the timed step invokes the
     selected variant once per N.  Also the batched form (64 systems, sizes
@@ -1168,11 +1268,11 @@ def run_nbody(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             for N in Ns:
                 r.invoke([N], blks[N], stream=stream)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             for N in Ns:
                 if N == Ns[-1]:
                     k0.record(stream)
@@ -1181,7 +1281,7 @@ def run_nbody(args):
                     k1.record(stream)
         e1.record(stream)
     stream.synchronize()
-    ms_step = e0.elapsed_time(e1) / args.steps
+    ms_step = e0.elapsed_time(e1) / steps
     flops = sum(NBODY_FLOPS * N * N for N in Ns)
     big_ms = k0.elapsed_time(k1)
     inter_s = Ns[-1] ** 2 / (big_ms * 1e-3)
@@ -1205,7 +1305,7 @@ def run_nbody(args):
     bflops = NBODY_FLOPS * float(np.sum(sizes.astype(np.float64) ** 2))
     line = {"metric": METRIC, "value": flops / (ms_step * 1e-3) / 1e9, "unit": "GFLOP/s", "n_gpus": 1,
             "dtype": "f32", "data": "synthetic", "higher_is_better": True, "vs_baseline": None,
-            "steps": args.steps, "ms_per_step": ms_step,
+            "steps": steps, "ms_per_step": ms_step,
             "config": {"workload": "all-pairs n-body float32, eps 1e-2, N in {1k,4k,16k,64k,256k}, 9 variants, "
                                    "exhaustive profiling per N", "flops_per_interaction": NBODY_FLOPS},
             "selection": {"per_N": per},
@@ -1217,8 +1317,13 @@ def run_nbody(args):
                                     "peak_source": "packed float32 pair FMA lane rate (ar_measure_fp32x2_rate) / "
                                                    "12 FP32 lane operations per interaction"}},
             "batched": {"systems": int(offs.size - 1), "bodies": int(sizes.sum()), "ms": bms,
-                        "gflops": bflops / (bms * 1e-3) / 1e9}}
-    print(json.dumps(line), flush=True)
+                        "gflops": bflops / (bms * 1e-3) / 1e9,
+                        "roofline_frac": bflops / (bms * 1e-3) / (peak_inter * NBODY_FLOPS)}}
+    return line
+
+
+def run_nbody(args):
+    print(json.dumps(nbody_record(args.steps, args.warmup)), flush=True)
 
 
 def main():

@@ -14,11 +14,14 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libadaptive_region.so")
+# AR_CHECKED=1 selects the bounds-check flavour of the library (build.py --checked)
+CHECKED = os.environ.get("AR_CHECKED", "0") == "1"
+LIB_PATH = os.path.join(HERE, "libadaptive_region_checked.so" if CHECKED else "libadaptive_region.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(
-        f"{LIB_PATH} is missing: build it with `python paper_2303_08873_b300/build.py` "
+        f"{LIB_PATH} is missing: build it with `python paper_2303_08873_b300/build.py"
+        f"{' --checked' if CHECKED else ''}` "
         "(there is no non-CUDA fallback)")
 lib = ctypes.CDLL(LIB_PATH)
 
@@ -157,6 +160,7 @@ _SIGS = {
     "ar_mlp_train": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp, _i, _i, _f, _vp, _vp]),
     "ar_measure_fma_rates": (_i, [_pd, _pd]),
     "ar_measure_fp32x2_rate": (_i, [_pd]),
+    "ar_check_status": (_i, [_pi, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32), _i]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -356,6 +360,14 @@ def ar_measure_fma_rates():
     a, b = ctypes.c_double(), ctypes.c_double()
     check(lib.ar_measure_fma_rates(ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def ar_check_status(clear: bool = True):
+    """(enabled, first failing check as (source id << 16 | line), failures)
+    of the bounds-check build; (False, 0, 0) in the normal build."""
+    en, first, cnt = ctypes.c_int(), ctypes.c_uint32(), ctypes.c_uint32()
+    check(lib.ar_check_status(ctypes.byref(en), ctypes.byref(first), ctypes.byref(cnt), int(clear)))
+    return bool(en.value), first.value, cnt.value
 
 
 def ar_measure_fp32x2_rate():
@@ -565,7 +577,7 @@ class Region:
 
 
 __all__ = ["ArExecCall", "ArExecModels", "ar_exec_workspace_bytes", "ar_exec_batch", "exec_table_bytes",
-           "ar_exec_fallback", "ar_exec_fallback_workspace_bytes", "ArHostCopy",
+           "ar_exec_fallback", "ar_exec_fallback_workspace_bytes", "ArHostCopy", "ar_check_status", "CHECKED",
            "AR_EXEC_MAX_CALLS", "AR_EXEC_MAX_PHASES", "ArError", "Region", "ArDaxpyArgs", "ArJacobi7Args", "ArHeat7Args", "ArSpmvArgs", "ArNbodyArgs", "ar_spmv",
            "ar_spmv_workspace_bytes", "ar_spmv_merge_path_noalloc", "ar_spmv_gather_floor", "ar_csr_features", "ar_csr_features_workspace_bytes", "ar_nbody",
            "ar_nbody_batched", "ar_nbody_batched_workspace_bytes", "LAUNCH_FN", "FAKE_TIME_FN", "lib", "ptr",
