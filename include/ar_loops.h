@@ -224,6 +224,18 @@ typedef struct ar_nbody_args {
 } ar_nbody_args;
 int ar_nbody(int variant, int64_t N, const float *pos4, float *acc4, float eps, void *stream);
 
+/* Launch geometry of n-body variant `variant` at N >= 1 bodies on the
+ * current device, as ar_nbody would launch it: i-tiles (*grid), the
+ * thread-block cluster size over which each i-tile's j range is split (1 =
+ * not split), bodies per thread, resident blocks per SM of the kernel that
+ * runs (occupancy API) and the SM count.  grid x cluster / (resident x sms)
+ * is the number of waves the launch takes, the quantity that decides which
+ * variant is fastest near the split thresholds; it is a pure function of N
+ * and the device, so a selector can use it as a feature.  Host-only (no
+ * kernel runs); AR_ERR_ARG for a bad variant or N < 1. */
+int ar_nbody_geometry(int variant, int64_t N, int64_t *grid, int *cluster, int *bodies_per_thread,
+                      int *resident_per_sm, int *sms);
+
 /* `count` independent systems in one persistent launch: system b is bodies
  * [offs[b], offs[b+1]) of pos4/acc4 (offs: device int32 [count+1],
  * non-decreasing).  Work items (system, 256-body tile) run largest system
@@ -386,6 +398,20 @@ int ar_mlp_adam(float *theta, const float *grad, float *m, float *v, int64_t n, 
 int ar_mlp_train(float *theta, float *adam_m, float *adam_v, const float *mu, const float *sd, int F, int H,
                  int V, int n, const float *feats, const int *labels, const int *perm, int epochs, int batch,
                  float lr, float *loss, void *stream);
+
+/* ------------------------------------------------------------ bounds check ---
+ * The library also builds as a bounds-check flavour (compiled with
+ * AR_CHECKED; libadaptive_region_checked.so): every index check written into
+ * the kernels (tensor-copy coordinates, alignment and shared-memory ranges
+ * of the stencil rings, the edge fix-ups, global stores of the stencils,
+ * every shared and global index of the merge-path blocks, the executor's
+ * work-item lookup) is compiled in; a failing check records itself and its
+ * access is skipped, so a bad index shows up as a status, never as a fault.
+ * ar_check_status reports *enabled (1 in that flavour, 0 otherwise), the
+ * first failing check (source-file id << 16 | source line, 0 if none) and
+ * the number of failures since the last clear; clear != 0 resets them.
+ * Blocking (reads device memory). */
+int ar_check_status(int *enabled, uint32_t *first_failure, uint32_t *failures, int clear);
 
 /* ---------------------------------------------------------------- peaks ---
  * Issue-rate microbenchmarks (blocking, for roofline denominators): run a

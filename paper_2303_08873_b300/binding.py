@@ -145,6 +145,7 @@ _SIGS = {
     "ar_spmv_gather_floor": (_i, [_i64, _vp, _vp, _vp, _vp, _vp]),
     "ar_csr_features": (_i, [_i64, _vp, _vp, _vp, _sz, _vp]),
     "ar_nbody": (_i, [_i, _i64, _vp, _vp, _f, _vp]),
+    "ar_nbody_geometry": (_i, [_i, _i64, _pi64, _pi, _pi, _pi, _pi]),
     "ar_nbody_batched_workspace_bytes": (_i, [_i, ctypes.POINTER(_sz)]),
     "ar_nbody_batched": (_i, [_i, _vp, _vp, _vp, _f, _vp, _sz, _vp]),
     "ar_exec_workspace_bytes": (_i, [_i, ctypes.POINTER(_sz)]),
@@ -271,6 +272,15 @@ def ar_csr_features(rows, rowptr, out5, workspace, workspace_bytes, stream=None)
 
 def ar_nbody(variant, N, pos4, acc4, eps=1e-2, stream=None):
     return check(lib.ar_nbody(variant, N, ptr(pos4), ptr(acc4), eps, stream_handle(stream)))
+
+
+def ar_nbody_geometry(variant, N):
+    """dict(grid, cluster, bodies_per_thread, resident_per_sm, sms, waves)."""
+    g, c, b, r, m = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    check(lib.ar_nbody_geometry(variant, N, ctypes.byref(g), ctypes.byref(c), ctypes.byref(b), ctypes.byref(r),
+                                ctypes.byref(m)))
+    return {"grid": g.value, "cluster": c.value, "bodies_per_thread": b.value, "resident_per_sm": r.value,
+            "sms": m.value, "waves": g.value * c.value / (r.value * m.value)}
 
 
 def ar_nbody_batched_workspace_bytes(count):
@@ -580,7 +590,7 @@ __all__ = ["ArExecCall", "ArExecModels", "ar_exec_workspace_bytes", "ar_exec_bat
            "ar_exec_fallback", "ar_exec_fallback_workspace_bytes", "ArHostCopy", "ar_check_status", "CHECKED",
            "AR_EXEC_MAX_CALLS", "AR_EXEC_MAX_PHASES", "ArError", "Region", "ArDaxpyArgs", "ArJacobi7Args", "ArHeat7Args", "ArSpmvArgs", "ArNbodyArgs", "ar_spmv",
            "ar_spmv_workspace_bytes", "ar_spmv_merge_path_noalloc", "ar_spmv_gather_floor", "ar_csr_features", "ar_csr_features_workspace_bytes", "ar_nbody",
-           "ar_nbody_batched", "ar_nbody_batched_workspace_bytes", "LAUNCH_FN", "FAKE_TIME_FN", "lib", "ptr",
+           "ar_nbody_batched", "ar_nbody_batched_workspace_bytes", "ar_nbody_geometry", "LAUNCH_FN", "FAKE_TIME_FN", "lib", "ptr",
            "stream_handle", "check", "loop_num_variants", "loop_default_variant", "loop_variant_name", "ar_daxpy",
            "ar_jacobi7", "ar_heat7", "ar_mlp_num_params", "ar_mlp_forward", "ar_mlp_grad", "ar_mlp_adam", "ar_mlp_train",
            "ar_measure_fma_rates", "ar_measure_fp32x2_rate", "EXPORTED", "AR_LOOP_DAXPY", "AR_LOOP_JACOBI7", "AR_LOOP_SPMV",

@@ -4,9 +4,12 @@ Every ``csrc/*.cu`` and ``csrc/*.cpp`` is compiled by nvcc (host C++17, device
 code for ``-gencode arch=compute_103a,code=sm_103a``) and linked into one
 shared library next to this file.  The library exports the C ABI declared in
 ``include/ar.h`` and ``include/ar_loops.h``.  Rebuilds only when a source or
-header is newer than the library.
+header is newer than the library.  ``--checked`` builds the bounds-check
+flavour ``libadaptive_region_checked.so`` (-DAR_CHECKED: every AR_CHK index
+check in the kernels is compiled in; the binding loads it when the
+environment variable AR_CHECKED is 1).
 
-Usage: ``python paper_2303_08873_b300/build.py [--force] [--verbose]``.
+Usage: ``python paper_2303_08873_b300/build.py [--force] [--verbose] [--checked]``.
 """
 from __future__ import annotations
 
@@ -22,6 +25,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libadaptive_region.so")
+OBJDIR_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libadaptive_region_checked.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
@@ -38,8 +43,8 @@ def _newest_input() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
-def _compile(src: str, verbose: bool, extra) -> str:
-    obj = os.path.join(OBJDIR, os.path.basename(src) + ".o")
+def _compile(src: str, verbose: bool, extra, objdir: str = OBJDIR) -> str:
+    obj = os.path.join(objdir, os.path.basename(src) + ".o")
     lang = ["-x", "cu"] if src.endswith(".cu") else []
     cmd = [NVCC, *ARCH, *FLAGS, *extra, *lang, "-c", src, "-o", obj]
     if verbose:
@@ -52,26 +57,27 @@ def _compile(src: str, verbose: bool, extra) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False) -> str:
-    """Compile and link the library if needed; return its path."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
-        return LIB
-    os.makedirs(OBJDIR, exist_ok=True)
-    extra = ["-Xptxas", "-v"] if ptxas_verbose else []
+def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False, checked: bool = False) -> str:
+    """Compile and link the library (or its bounds-check flavour) if needed;
+    return its path."""
+    lib, objdir = (LIB_CHECKED, OBJDIR_CHECKED) if checked else (LIB, OBJDIR)
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _newest_input():
+        return lib
+    os.makedirs(objdir, exist_ok=True)
+    extra = (["-Xptxas", "-v"] if ptxas_verbose else []) + (["-DAR_CHECKED"] if checked else [])
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose or ptxas_verbose, extra), sources()))
-    tmp = LIB + ".tmp"
+        objs = list(ex.map(lambda s: _compile(s, verbose or ptxas_verbose, extra, objdir), sources()))
+    tmp = lib + ".tmp"
     cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs]
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="--verbose" in sys.argv,
-          ptxas_verbose="--ptxas" in sys.argv)
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv,
+                ptxas_verbose="--ptxas" in sys.argv, checked="--checked" in sys.argv))

@@ -7,6 +7,7 @@
 // elements with the EPT accesses of a thread spaced BS words apart, so every
 // warp access is fully coalesced; all loads of a thread are issued before
 // its first FMA to keep several 16-byte requests in flight.
+#define AR_TU 1
 #include <cstdio>
 
 #include "common.cuh"
@@ -112,3 +113,7 @@ extern "C" int ar_daxpy(int variant, int64_t n, double a, const double* x, doubl
     default: return dispatch_ept<4>(e, n, a, x, y, s);
   }
 }
+
+namespace ar {
+AR_CHECK_READER(chk_read_daxpy)
+}  // namespace ar

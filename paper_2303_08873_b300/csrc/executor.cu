@@ -9,6 +9,7 @@
 // blocks that are already running; the wait is bounded and reports
 // AR_ERR_TIMEOUT per call.  Data written inside this launch (Jacobi sweeps,
 // merge-path carries) are read with L1-bypassing loads (ld.global.cg).
+#define AR_TU 5
 #include <cudaTypedefs.h>
 
 #include <cstdio>
@@ -458,7 +459,9 @@ __device__ bool jacobi_tma_tile(const CUtensorMap* map, int N, int bx, int by, i
     const int slot = g % kXRing;
     const uint32_t bar = smem_addr(&bars[slot]);
     mbar_arrive_expect_tx(bar, G::BYTES);
-    tma_load_3d(smem_addr(buf + (size_t)slot * G::SLOT), map, i0 - 2, j0 - 1, kb - 1 + g * kXDZ, bar);
+    if (AR_CHK(((i0 - 2) & 1) == 0 && (smem_addr(buf + (size_t)slot * G::SLOT) & 127u) == 0 &&
+               in_smem(smraw, G::SMEM, buf + (size_t)slot * G::SLOT, G::BYTES)))
+      tma_load_3d(smem_addr(buf + (size_t)slot * G::SLOT), map, i0 - 2, j0 - 1, kb - 1 + g * kXDZ, bar);
   };
   if (tid == 0)
     for (int g = 0; g < min(ngroups, kXRing - 1); ++g) issue(g);
@@ -508,7 +511,7 @@ __device__ bool jacobi_tma_tile(const CUtensorMap* map, int N, int bx, int by, i
             s += pc[G::PX];
             s += dm;
             s += up;
-            if (inside) *od = s * kSixth;
+            if (inside && AR_CHK(od - dst >= 0 && od - dst < NN * N)) *od = s * kSixth;
             od += NN;
           }
           dm = d0;
@@ -518,7 +521,7 @@ __device__ bool jacobi_tma_tile(const CUtensorMap* map, int N, int bx, int by, i
           const float2 up = reinterpret_cast<const float2*>(box)[r * G::PLANE + c];
           if (live) {
             const float2 res = df_avg6(pc[-1], pc[1], pc[-G::PX], pc[G::PX], fm, up);
-            if (inside) {
+            if (inside && AR_CHK(od - dst >= 0 && od - dst < NN * N)) {
               if (dst_pairs) {
                 *op = res;
               } else {
@@ -627,7 +630,10 @@ __device__ bool jacobi_tma_odd_tile(const CUtensorMap* map, int N, int bx, int b
       for (int b = 0; b < 2; ++b) {
         const int yb = y0 + ((((k + y0) & 1) == b) ? 0 : 1);
         const long long R = (long long)k * N + yb;
-        tma_load_2d(smem_addr(sb + r * G::PLANE + b * G::HALF), map, b * N + i0 - 2 - b, (int)((R - b) >> 1), bar);
+        double* to = sb + r * G::PLANE + b * G::HALF;
+        if (AR_CHK(((b * N + i0 - 2 - b) & 1) == 0 && (smem_addr(to) & 127u) == 0 &&
+                   in_smem(smraw, G::SMEM, to, G::PX * G::HB * 8u)))
+          tma_load_2d(smem_addr(to), map, b * N + i0 - 2 - b, (int)((R - b) >> 1), bar);
       }
     }
   };
@@ -705,7 +711,7 @@ __device__ bool jacobi_tma_odd_tile(const CUtensorMap* map, int N, int bx, int b
             s += pp[pb + cn];
             s += dm;
             s += up;
-            if (inside) *od = s * kSixth;
+            if (inside && AR_CHK(od - dst >= 0 && od - dst < NN * N)) *od = s * kSixth;
             od += NN;
           }
           dm = d0;
@@ -715,7 +721,7 @@ __device__ bool jacobi_tma_odd_tile(const CUtensorMap* map, int N, int bx, int b
           const float2 up = reinterpret_cast<const float2*>(box)[r * G::PLANE + cu];
           if (live) {
             const float2 res = df_avg6(pp[pb + cc - 1], pp[pb + cc + 1], pp[pb + cs], pp[pb + cn], fm, up);
-            if (inside) {
+            if (inside && AR_CHK(od - dst >= 0 && od - dst < NN * N)) {
               if (dst_pairs) {
                 *op = res;
               } else {
@@ -1109,10 +1115,18 @@ __global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_cal
           else
             hi = mid - 1;
         }
+        // the item lies in entry lo's range, inside its (call, phase) tiles;
+        // otherwise (checked build) it is skipped under entry 0's indices
+        const bool valid = AR_CHK(lo >= 0 && lo < E && prefix[lo] <= it && it < prefix[lo + 1] &&
+                                  it - prefix[lo] < (long long)tiles[(lo % ncalls) * PM + lo / ncalls]);
+        if (!valid) {
+          lo = 0;
+          atomicExch(status, (int)AR_ERR_ARG);
+        }
         pos = lo;
         const int p = lo / ncalls, c = lo % ncalls;
-        int ok = 1;
-        if (p > 0) {
+        int ok = valid ? 1 : 0;
+        if (ok && p > 0) {
           if (!dep_wait(done + c * PM + p - 1, tiles[c * PM + p - 1], kDepSpin)) {
             ok = 0;
             atomicExch(status + c, (int)AR_ERR_TIMEOUT);
@@ -1122,7 +1136,7 @@ __global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_cal
         if (ok) atomicMin((unsigned long long*)t0 + c, (unsigned long long)gtimer());
         s_c = c;
         s_p = p;
-        s_t = it - prefix[lo];
+        s_t = valid ? it - prefix[lo] : 0;
         s_ok = ok;
       }
     }
@@ -1325,3 +1339,7 @@ extern "C" int ar_exec_batch(const ar_exec_call* calls, int ncalls, const ar_exe
                                           flags, maps, usetma);
   return launch_status();
 }
+
+namespace ar {
+AR_CHECK_READER(chk_read_executor)
+}  // namespace ar

@@ -22,6 +22,7 @@
 //            supplies the Dirichlet ghosts (also in z); two boxes in flight
 //   3 df     as tma, plus an in-place conversion of each landed box from
 //            float64 to float pairs; sums by TwoSum on the FP32 pipe
+#define AR_TU 2
 #include <cudaTypedefs.h>
 
 #include <cstdio>
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(BX* BY) jacobi_naive(int N, const double* __re
   s += (j < N - 1 ? in[c + N] : 0.0);
   s += (k > 0 ? in[c - NN] : 0.0);
   s += (k < N - 1 ? in[c + NN] : 0.0);
-  out[c] = stencil_f64<ST>(ST == kHeat ? in[c] : 0.0, s, cf);
+  if (AR_CHK(c < NN * N)) out[c] = stencil_f64<ST>(ST == kHeat ? in[c] : 0.0, s, cf);
 }
 
 // ------------------------------------------------------------------ 2.5D smem
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(BX* BY) jacobi_smem(int N, int KC, const doubl
       s += tile[b][ty + 2][tx + 1];
       s += below;
       s += above;
-      out[k * NN + col] = stencil_f64<ST>(cur, s, cf);
+      if (AR_CHK(k * NN + col < NN * N)) out[k * NN + col] = stencil_f64<ST>(cur, s, cf);
     }
     below = cur;
     cur = above;
@@ -165,7 +166,11 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
     const int slot = g % kRing;
     const uint32_t bar = smem_addr(&bars[slot]);
     mbar_arrive_expect_tx(bar, G::BYTES);
-    tma_load_3d(smem_addr(buf + (size_t)slot * G::SLOT), src_map, i0 - 2, j0 - 1, kb - 1 + g * kDZ, bar);
+    // float64 tensor copies: x even (16-byte start), a 128-byte aligned
+    // destination inside the dynamic shared array
+    if (AR_CHK(((i0 - 2) & 1) == 0 && (smem_addr(buf + (size_t)slot * G::SLOT) & 127u) == 0 &&
+               in_dyn_smem(smem_raw, buf + (size_t)slot * G::SLOT, G::BYTES)))
+      tma_load_3d(smem_addr(buf + (size_t)slot * G::SLOT), src_map, i0 - 2, j0 - 1, kb - 1 + g * kDZ, bar);
   };
   if (tid == 0)
     for (int g = 0; g < min(ngroups, kRing - 1); ++g) issue(g);
@@ -174,7 +179,8 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
   const bool inside = i < N && j < N;
   const int64_t NN = (int64_t)N * N;
   const int64_t col = (int64_t)j * N + i;
-  const int c = (ty + 1) * G::PX + tx + 2;
+  // the centre's neighbours +-1 and +-PX stay inside one staged plane
+  const int c = AR_CHK(tx + 3 < G::PX && ty + 2 < G::PY) ? (ty + 1) * G::PX + tx + 2 : G::PX + 2;
   double* outd = flagged ? out_alt : static_cast<double*>(outv);
   float2* outp = static_cast<float2*>(outv);
   // z queue: the values of planes p-1 and p at this thread's column
@@ -229,7 +235,7 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
             s += pc[G::PX];
             s += dm;
             s += up;
-            if (inside) *od = stencil_f64<ST>(pc[0], s, cf);
+            if (inside && AR_CHK(od - outd >= 0 && od - outd < NN * N)) *od = stencil_f64<ST>(pc[0], s, cf);
             od += NN;
           }
           dm = d0;
@@ -239,7 +245,7 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma(const __grid_constant__ CUt
           const float2 up = reinterpret_cast<const float2*>(box)[r * G::PLANE + c];
           if (live) {
             const float2 res = stencil_pair<ST>(pc[0], pc[-1], pc[1], pc[-G::PX], pc[G::PX], fm, up, cf);
-            if (inside) {
+            if (inside && AR_CHK(od - outd >= 0 && od - outd < NN * N && op - outp >= 0 && op - outp < NN * N)) {
               if constexpr (MODE == M_DP || MODE == M_PP) {  // pairs out (the native case is above)
                 // stored unnormalised: the next sweep sums the hi parts exactly and
                 // the lo parts in float, so |lo| of a few ulps of hi costs ~2^-46
@@ -366,7 +372,8 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma_odd(const __grid_constant__
   // splitting a landed group in place reads no garbage (which would mark it)
   constexpr int kPad = G::HALF - G::PX * G::HB;
   for (int e = tid; e < kRing * kDZ * 2 * kPad; e += BX * BY)
-    buf[(e / kPad) * G::HALF + G::PX * G::HB + e % kPad] = 0.0;
+    if (AR_CHK((e / kPad) * G::HALF + G::PX * G::HB + e % kPad < kRing * G::GROUP))
+      buf[(e / kPad) * G::HALF + G::PX * G::HB + e % kPad] = 0.0;
   fence_proxy_async_smem();
   __syncthreads();
 
@@ -383,7 +390,10 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma_odd(const __grid_constant__
         const int yb = y0 + ((((k + y0) & 1) == b) ? 0 : 1);  // first tile row of parity b
         const long long R = (long long)k * N + yb;
         const int yrow = (int)((R - b) >> 1);                  // R - b is even: exact, also below 0
-        tma_load_2d(smem_addr(sb + r * G::PLANE + b * G::HALF), src_map, b * N + i0 - 2 - b, yrow, bar);
+        double* dst = sb + r * G::PLANE + b * G::HALF;
+        if (AR_CHK(((b * N + i0 - 2 - b) & 1) == 0 && (smem_addr(dst) & 127u) == 0 &&
+                   in_dyn_smem(smem_raw, dst, G::PX * G::HB * 8u)))
+          tma_load_2d(smem_addr(dst), src_map, b * N + i0 - 2 - b, yrow, bar);
       }
     }
   };
@@ -428,6 +438,7 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma_odd(const __grid_constant__
         const int y = y0 + 2 * idx + ((((k + y0) & 1) == b) ? 0 : 1);
         const int xb = i0 - 2 - b;  // x of the row's first column
         double* d = box + r * G::PLANE + b * G::HALF + idx * G::PX;
+        if (!AR_CHK(d - box >= 0 && d - box + G::PX <= G::GROUP)) continue;
         if ((unsigned)y >= (unsigned)N || (unsigned)k >= (unsigned)N) {
           for (int c = 0; c < G::PX; ++c) d[c] = 0.0;
         } else {
@@ -436,7 +447,8 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma_odd(const __grid_constant__
           for (int c = c1; c < G::PX; ++c) d[c] = 0.0;
           if (k == N - 1 && y == N - 1) {
             const double* row = src + ((int64_t)k * N + y) * N + xb;
-            for (int c = c0; c < c1; ++c) d[c] = __ldcg(row + c);
+            for (int c = c0; c < c1; ++c)
+              d[c] = AR_CHK(row + c - src >= 0 && row + c - src < NN * N) ? __ldcg(row + c) : 0.0;
           }
         }
       }
@@ -474,7 +486,7 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma_odd(const __grid_constant__
             s += pp[pb + cn];
             s += dm;
             s += up;
-            if (inside) *od = stencil_f64<ST>(pp[pb + cc], s, cf);
+            if (inside && AR_CHK(od - outd >= 0 && od - outd < NN * N)) *od = stencil_f64<ST>(pp[pb + cc], s, cf);
             od += NN;
           }
           dm = d0;
@@ -485,7 +497,7 @@ __global__ void __launch_bounds__(BX* BY) jacobi_tma_odd(const __grid_constant__
           if (live) {
             const float2 res =
                 stencil_pair<ST>(pp[pb + cc], pp[pb + cc - 1], pp[pb + cc + 1], pp[pb + cs], pp[pb + cn], fm, up, cf);
-            if (inside) {
+            if (inside && AR_CHK(od - outd >= 0 && od - outd < NN * N && op - outp >= 0 && op - outp < NN * N)) {
               if constexpr (MODE == M_DP || MODE == M_PP) {
                 *op = res;
               } else {
@@ -892,3 +904,7 @@ extern "C" int ar_heat7(int variant, int N, int steps, double alpha, const doubl
   const ar::StencilCoef cf{alpha, ahi, (float)(alpha - (double)ahi), bhi, (float)(beta - (double)bhi)};
   return ar::stencil_run<ar::kHeat>(variant, N, steps, cf, u0, out, work, status, stream);
 }
+
+namespace ar {
+AR_CHECK_READER(chk_read_jacobi7)
+}  // namespace ar

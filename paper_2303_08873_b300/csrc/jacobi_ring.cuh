@@ -95,7 +95,11 @@ __device__ __forceinline__ void jacobi_ring_tile(int N, int BX, int BY, int bx, 
         if (m < nmine) {
           const bool o = odd && ((kp + cy[m]) & 1);
           const int bytes = kin ? (o ? cb1[m] : cb0[m]) : 0;
-          cp_async16(base + soff[m], bytes ? plane_src + cxy0[m] - (o ? 1 : 0) : src, bytes);
+          const double* from = bytes ? plane_src + cxy0[m] - (o ? 1 : 0) : src;
+          // destination inside the ring, source inside the grid for the bytes copied
+          if (AR_CHK(slot_of(kp) * PL + soff[m] + 2 <= kRingPlanes * PL && soff[m] >= 0 &&
+                     (from - src) >= 0 && (from - src) * 8 + bytes <= NN * N * 8))
+            cp_async16(base + soff[m], from, bytes);
         }
       }
     }
@@ -109,7 +113,7 @@ __device__ __forceinline__ void jacobi_ring_tile(int N, int BX, int BY, int bx, 
     double* base = ring + slot_of(kp) * PL;
 #pragma unroll
     for (int m = 0; m < kRingChunks; ++m) {
-      if (m < nmine) {
+      if (m < nmine && AR_CHK(slot_of(kp) * PL + soff[m] + 2 <= kRingPlanes * PL)) {
         double* e = base + soff[m];
         if (may_zero && kin && (((kp + cy[m]) & 1) ? z1[m] : z0[m])) e[0] = 0.0;
         if (split) {
@@ -142,7 +146,8 @@ __device__ __forceinline__ void jacobi_ring_tile(int N, int BX, int BY, int bx, 
     }
     __syncthreads();
     issue(kk + kRingPlanes - 2);  // into the slot of plane kk - 2, read last in the previous step
-    if (inside) {
+    // every staged read inside the ring, the store inside the grid
+    if (inside && AR_CHK(rc - PX - 1 >= 0 && rc + PX + 2 <= PL && outo >= 0 && outo < NN * N)) {
       // odd N: the neighbour rows (y +- 1 and planes k +- 1) have the other parity
       const int on = odd ? 1 - o : 0;
       const int c0 = sc * PL + rc + o;

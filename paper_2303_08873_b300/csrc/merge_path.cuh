@@ -70,7 +70,7 @@ __device__ __forceinline__ int64_t search(int64_t d, int64_t lo, int64_t hi, con
 // then its x gathers.  Returns false if an operand is outside the float-pair
 // split range (PAIRS only).
 template <bool PAIRS, int B = kBatch>
-__device__ __forceinline__ bool stage_products(int Z, int64_t j0, const int* __restrict__ col,
+__device__ __forceinline__ bool stage_products(int Z, int64_t j0, int64_t nnz, const int* __restrict__ col,
                                                const double* __restrict__ val, const double* __restrict__ x,
                                                double* sprod) {
   bool ok = true;
@@ -83,14 +83,15 @@ __device__ __forceinline__ bool stage_products(int Z, int64_t j0, const int* __r
     for (int u = 0; u < B; ++u) {
       const int z = t + (b0 + u) * kThreads;
       if (z < Z) {
-        cc[u] = ld_col(col + j0 + z);
-        vv[u] = ld_val(val + j0 + z);
+        const bool in = AR_CHK(j0 + z >= 0 && j0 + z < nnz);
+        cc[u] = in ? ld_col(col + j0 + z) : 0;
+        vv[u] = in ? ld_val(val + j0 + z) : 0.0;
       }
     }
 #pragma unroll
     for (int u = 0; u < B; ++u) {
       const int z = t + (b0 + u) * kThreads;
-      if (z < Z) {
+      if (z < Z && AR_CHK(cc[u] >= 0 && 8 * z + 8 <= kStageBytes)) {
         const double xv = __ldg(x + cc[u]);
         if constexpr (PAIRS) {
           float vh, vl, xh, xl;
@@ -135,12 +136,14 @@ __device__ void block(int64_t rows, int64_t nnz, const int* __restrict__ rowptr,
   int* send = reinterpret_cast<int*>(smem + 8 * (size_t)Z);
   // relative row ends rowptr[i0 + q + 1] - j0 >= 0; the sentinel stops the
   // walk at the last row of the matrix
-  for (int q = t; q <= NR; q += kThreads) send[q] = q < NR ? (int)(__ldg(rowptr + i0 + q + 1) - j0) : 0x7fffffff;
+  for (int q = t; q <= NR; q += kThreads)
+    if (AR_CHK(8 * Z + 4 * (q + 1) <= kStageBytes && (q == NR || i0 + q + 1 <= rows)))
+      send[q] = q < NR ? (int)(__ldg(rowptr + i0 + q + 1) - j0) : 0x7fffffff;
   bool native = !DF;
   if constexpr (!DF) {
     __syncthreads();  // the row ends are read by every thread's search below
   } else {
-    native = __syncthreads_or(!stage_products<true, B>(Z, j0, col, val, x, sprod));  // also publishes the row ends
+    native = __syncthreads_or(!stage_products<true, B>(Z, j0, nnz, col, val, x, sprod));  // also publishes the row ends
   }
   const int64_t d0 = min(db + (int64_t)t * kItems, de);
   const int n = (int)(min(d0 + kItems, de) - d0);
@@ -148,7 +151,7 @@ __device__ void block(int64_t rows, int64_t nnz, const int* __restrict__ rowptr,
   int64_t lo = max(i0, d0 - nnz), hi = min(i1, d0);
   while (lo < hi) {
     const int64_t mid = (lo + hi) >> 1;
-    if ((int64_t)send[mid - i0] + j0 <= d0 - mid - 1)
+    if ((AR_CHK(mid - i0 >= 0 && mid - i0 <= NR) ? (int64_t)send[mid - i0] : 0) + j0 <= d0 - mid - 1)
       lo = mid + 1;
     else
       hi = mid;
@@ -157,21 +160,23 @@ __device__ void block(int64_t rows, int64_t nnz, const int* __restrict__ rowptr,
   for (int pass = 0; pass < 2; ++pass) {
     if (native) {
       if (DF) __syncthreads();  // the float-pair products are read no more
-      stage_products<false, B>(Z, j0, col, val, x, sprod);
+      stage_products<false, B>(Z, j0, nnz, col, val, x, sprod);
     }
     __syncthreads();
     int ir = ir0, jr = jr0;
-    int re = send[ir];
+    int re = AR_CHK(ir >= 0 && ir <= NR) ? send[ir] : 0x7fffffff;
     bool finite = true;
     if (native) {
       double s = 0.0;
       for (int it = 0; it < n; ++it) {
         if (jr >= re) {  // consume the end of row i0 + ir
-          y[i0 + ir] = s;
+          if (AR_CHK(i0 + ir < rows)) y[i0 + ir] = s;
           s = 0.0;
-          re = send[++ir];
+          ++ir;
+          re = AR_CHK(ir <= NR) ? send[ir] : 0x7fffffff;
         } else {          // consume nonzero j0 + jr
-          s += sprod[jr++];
+          s += AR_CHK(jr >= 0 && jr < Z) ? sprod[jr] : 0.0;
+          ++jr;
         }
       }
       sval[t] = s;
@@ -180,11 +185,14 @@ __device__ void block(int64_t rows, int64_t nnz, const int* __restrict__ rowptr,
       for (int it = 0; it < n; ++it) {
         if (jr >= re) {  // the pair goes to y as is; converted below, by all threads at once
           finite &= pair_finite(S, C);
-          reinterpret_cast<float2*>(y)[i0 + ir] = make_float2(S, C);
+          if (AR_CHK(i0 + ir < rows)) reinterpret_cast<float2*>(y)[i0 + ir] = make_float2(S, C);
           S = C = 0.f;
-          re = send[++ir];
+          ++ir;
+          re = AR_CHK(ir <= NR) ? send[ir] : 0x7fffffff;
         } else {
-          const float2 pp = reinterpret_cast<const float2*>(sprod)[jr++];
+          const float2 pp =
+              AR_CHK(jr >= 0 && jr < Z) ? reinterpret_cast<const float2*>(sprod)[jr] : make_float2(0.f, 0.f);
+          ++jr;
           pair_add(S, C, pp.x, pp.y);
         }
       }
@@ -201,6 +209,7 @@ __device__ void block(int64_t rows, int64_t nnz, const int* __restrict__ rowptr,
     // every lane busy (a float64 add costs its whole warp on the float64 pipe)
     __syncthreads();
     for (int64_t i = i0 + t; i < i1; i += kThreads) {
+      if (!AR_CHK(i < rows)) continue;
       const float2 pp = reinterpret_cast<const float2*>(y)[i];
       y[i] = f2d_bits(pp.x) + f2d_bits(pp.y);
     }
@@ -223,7 +232,7 @@ __device__ void block(int64_t rows, int64_t nnz, const int* __restrict__ rowptr,
     // the next thread consumed the row's end and wrote y[r] in phase 2
     const bool closed_here = t + 1 < kThreads && min(db + (int64_t)(t + 1) * kItems, de) < de;
     if (closed_here) {
-      y[r] += v;
+      if (AR_CHK(r < rows)) y[r] += v;
     } else {
       *carry_row = r;
       *carry_val = v;

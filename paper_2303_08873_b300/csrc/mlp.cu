@@ -14,6 +14,7 @@
 // per-unit reductions (consecutive units) are both bank-conflict free.  Every
 // reduction over samples runs s = 0 .. B-1 in order: results are
 // deterministic.
+#define AR_TU 6
 #include <cmath>
 #include <cstdio>
 #include <string>
@@ -528,3 +529,7 @@ extern "C" int ar_mlp_train(float* theta, float* adam_m, float* adam_v, const fl
   }
   return launch_status();
 }
+
+namespace ar {
+AR_CHECK_READER(chk_read_mlp)
+}  // namespace ar

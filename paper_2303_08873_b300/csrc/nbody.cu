@@ -28,6 +28,7 @@
 // first (an i-tile costs the system's size) and pulled from an atomic counter
 // by resident blocks (as many as fit at the kernel's register count), so the
 // long items start first and the tail is short.
+#define AR_TU 4
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
@@ -234,35 +235,80 @@ bool split_fits(int cs) {
   return k == 1;
 }
 
-// Two bodies per thread when the grid still fills the GPU twice over,
-// otherwise one; and when even one body per thread leaves fewer than two
-// blocks per SM, the j range is split over a cluster of up to kMaxCluster
-// blocks per i-tile (nbody_tile_split).
+// Blocks per SM at the register count of nbody_tile_split<T, U> and of
+// nbody_tile<T, U, B> (asked once per kernel).
 template <int T, int U>
-int launch_r(int64_t N, const float4* p, float4* a, float eps2, cudaStream_t s) {
-  const int64_t want = 2LL * device_sms();
-  const bool two = ceil_div(N, 2 * T) >= want;
-  const int64_t grid = ceil_div(N, two ? 2 * T : T);
-  if (grid > 0x7fffffffLL) return AR_ERR_ARG;
-  if (two) {
-    nbody_tile<T, U, 2><<<(unsigned)grid, T, 0, s>>>(N, p, a, eps2);
-    return launch_status();
-  }
-  // the largest cluster whose blocks still fit in one wave of resident
-  // slots; when not even two do, enough clusters for two blocks per SM
-  static const int resident = [] {
-    int r = 0;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, nbody_tile_split<T, U>, T, 0) == cudaSuccess && r > 0
-               ? r
+int resident_split() {
+  static const int r = [] {
+    int n = 0;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, nbody_tile_split<T, U>, T, 0) == cudaSuccess && n > 0
+               ? n
                : 1;
   }();
-  const int64_t fit = (int64_t)resident * device_sms() / grid;
-  const int cs = fit >= 2 ? (int)std::min<int64_t>({(int64_t)kMaxCluster, fit, grid})
-                          : (int)std::min<int64_t>({(int64_t)kMaxCluster, ceil_div(want, grid), grid});
+  return r;
+}
+template <int T, int U, int B>
+int resident_tile() {
+  static const int r = [] {
+    int n = 0;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, nbody_tile<T, U, B>, T, 0) == cudaSuccess && n > 0 ? n
+                                                                                                             : 1;
+  }();
+  return r;
+}
+
+// Launch geometry of variant (T, U) at N bodies: two bodies per thread when
+// the grid still fills the GPU twice over, otherwise one; and when even one
+// body per thread leaves fewer than two blocks per SM, the j range is split
+// over a cluster of up to kMaxCluster blocks per i-tile (nbody_tile_split):
+// the largest cluster whose blocks still fit in one wave of resident slots,
+// and when not even two do, enough clusters for two blocks per SM.
+// `resident` (blocks per SM of the kernel that runs) is filled only when
+// asked for.
+struct Geom {
+  int64_t grid;  // i-tiles (blocks, or clusters when split)
+  int cs;        // cluster size; 1 when the j range is not split
+  int bpt;       // bodies per thread
+  int resident;
+};
+template <int T, int U>
+Geom geometry(int64_t N, bool need_resident) {
+  Geom g{};
+  const int64_t want = 2LL * device_sms();
+  const bool two = ceil_div(N, 2 * T) >= want;
+  g.bpt = two ? 2 : 1;
+  g.grid = ceil_div(N, two ? 2 * T : T);
+  g.cs = 1;
+  if (two) {
+    if (need_resident) g.resident = resident_tile<T, U, 2>();
+    return g;
+  }
+  const int resident = resident_split<T, U>();
+  const int64_t fit = (int64_t)resident * device_sms() / g.grid;
+  const int cs = fit >= 2 ? (int)std::min<int64_t>({(int64_t)kMaxCluster, fit, g.grid})
+                          : (int)std::min<int64_t>({(int64_t)kMaxCluster, ceil_div(want, g.grid), g.grid});
   if (cs >= 2 && split_fits<T, U>(cs)) {
+    g.cs = cs;
+    g.resident = resident;
+  } else if (need_resident) {
+    g.resident = resident_tile<T, U, 1>();
+  }
+  return g;
+}
+
+template <int T, int U>
+int launch_r(int64_t N, const float4* p, float4* a, float eps2, cudaStream_t s) {
+  const Geom g = geometry<T, U>(N, false);
+  if (g.grid > 0x7fffffffLL) return AR_ERR_ARG;
+  if (g.bpt == 2) {
+    nbody_tile<T, U, 2><<<(unsigned)g.grid, T, 0, s>>>(N, p, a, eps2);
+    return launch_status();
+  }
+  if (g.cs >= 2) {
+    const int cs = g.cs;
     const int64_t chunk = ceil_div(ceil_div(N, cs), T) * T;  // j bodies per block, whole tiles
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(grid * cs));
+    cfg.gridDim = dim3((unsigned)(g.grid * cs));
     cfg.blockDim = dim3(T);
     cfg.stream = s;
     cudaLaunchAttribute at;
@@ -275,8 +321,17 @@ int launch_r(int64_t N, const float4* p, float4* a, float eps2, cudaStream_t s) 
       return AR_ERR_CUDA;
     return launch_status();
   }
-  nbody_tile<T, U, 1><<<(unsigned)grid, T, 0, s>>>(N, p, a, eps2);
+  nbody_tile<T, U, 1><<<(unsigned)g.grid, T, 0, s>>>(N, p, a, eps2);
   return launch_status();
+}
+
+template <int T>
+Geom geometry_u(int u, int64_t N) {
+  switch (u) {
+    case 0: return geometry<T, 1>(N, true);
+    case 1: return geometry<T, 4>(N, true);
+    default: return geometry<T, 8>(N, true);
+  }
 }
 
 template <int T>
@@ -325,6 +380,24 @@ extern "C" int ar_nbody(int variant, int64_t N, const float* pos4, float* acc4, 
   }
 }
 
+extern "C" int ar_nbody_geometry(int variant, int64_t N, int64_t* grid, int* cluster, int* bodies_per_thread,
+                                 int* resident_per_sm, int* sms) {
+  if (variant < 0 || variant >= kNbodyVariants || N < 1) return AR_ERR_ARG;
+  Geom g;
+  switch (variant / 3) {
+    case 0: g = geometry_u<128>(variant % 3, N); break;
+    case 1: g = geometry_u<256>(variant % 3, N); break;
+    default: g = geometry_u<512>(variant % 3, N); break;
+  }
+  if (cudaGetLastError() != cudaSuccess) return AR_ERR_CUDA;
+  if (grid) *grid = g.grid;
+  if (cluster) *cluster = g.cs;
+  if (bodies_per_thread) *bodies_per_thread = g.bpt;
+  if (resident_per_sm) *resident_per_sm = g.resident;
+  if (sms) *sms = device_sms();
+  return AR_OK;
+}
+
 extern "C" int ar_nbody_batched_workspace_bytes(int count, size_t* bytes) {
   if (count < 0 || !bytes) return AR_ERR_ARG;
   *bytes = batch_ws(count);
@@ -355,3 +428,7 @@ extern "C" int ar_nbody_batched(int count, const int32_t* offs, const float* pos
                                             reinterpret_cast<float4*>(acc4), eps * eps, order, prefix, counter);
   return launch_status();
 }
+
+namespace ar {
+AR_CHECK_READER(chk_read_nbody)
+}  // namespace ar

@@ -4,6 +4,7 @@
 // so the float64 rate bounds the native float64 loop variants.  The packed
 // float32 form (FFMA2, two lanes' FMAs per instruction) is measured apart:
 // on B300 it reaches about 91 % of the scalar float32 lane rate.
+#define AR_TU 7
 #include <type_traits>
 
 #include "common.cuh"
@@ -89,3 +90,7 @@ extern "C" int ar_measure_fp32x2_rate(double* fp32_lane_fma_per_s) {
   if (!fp32_lane_fma_per_s) return AR_ERR_ARG;
   return ar::rate<float2>(8192, fp32_lane_fma_per_s);
 }
+
+namespace ar {
+AR_CHECK_READER(chk_read_peaks)
+}  // namespace ar

@@ -19,6 +19,7 @@
 // the row lengths; rows that straddle threads are summed by a segmented scan
 // inside the block, rows that straddle blocks by a second small kernel over
 // the per-block carries.
+#define AR_TU 3
 #include <cstdio>
 #include <mutex>
 
@@ -390,3 +391,7 @@ extern "C" int ar_spmv_merge_path_noalloc(int64_t rows, int64_t nnz, const int32
   return launch_pdl(spmv_mp_fixup, dim3((unsigned)ceil_div(nb, 256)), dim3(256), 0, s, (int)nb, carry_row, carry_val,
                     y);
 }
+
+namespace ar {
+AR_CHECK_READER(chk_read_spmv)
+}  // namespace ar

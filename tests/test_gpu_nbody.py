@@ -149,3 +149,21 @@ def test_roofline_denominators_are_plausible():
     packed = ar.ar_measure_fp32x2_rate()
     assert 0 < fp64 < 0.2 * fp32
     assert 0.5 * fp32 < packed < 1.1 * fp32
+
+
+@pytest.mark.parametrize("N", [1, 1000, 4097, 30000, 65536, 262144])
+def test_launch_geometry_follows_the_split_rule(N):
+    """ar_nbody_geometry against the rule it reports: two bodies per thread
+    once ceil(N / 2T) fills two blocks per SM, else one; the j range split
+    over a cluster only below two blocks per SM, never past 8 blocks."""
+    for v in range(9):
+        T = (128, 256, 512)[v // 3]
+        g = ar.ar_nbody_geometry(v, N)
+        sms = g["sms"]
+        two = -(-N // (2 * T)) >= 2 * sms
+        assert g["bodies_per_thread"] == (2 if two else 1)
+        assert g["grid"] == -(-N // (T * g["bodies_per_thread"]))
+        assert 1 <= g["cluster"] <= min(8, g["grid"]) or (g["cluster"] == 1 and g["grid"] == 1)
+        if two:
+            assert g["cluster"] == 1
+        assert g["resident_per_sm"] >= 1 and g["waves"] > 0

@@ -383,3 +383,10 @@ def test_invoke_host_rejects_bad_copy_lists_before_enqueuing():
         r.invoke_host([float("nan")], None, [], [])
     assert e.value.code == ar.AR_ERR_ARG
     assert r.counts() == (0, 0)
+
+
+def test_normal_build_reports_checks_disabled():
+    # the normal build's readers answer without touching the device
+    if ar.CHECKED:
+        pytest.skip("this process loaded the bounds-check build")
+    assert ar.ar_check_status(clear=False) == (False, 0, 0)
