@@ -83,11 +83,11 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--workload", default="jacobi7",
-                   choices=["jacobi7", "heat7", "spmv", "mixed", "daxpy", "nbody", "protocol"],
+                   choices=["jacobi7", "heat7", "spmv", "mixed", "daxpy", "nbody", "protocol", "cosched"],
                    help="jacobi7: the headline line; heat7: the same region and grids with the explicit "
                         "heat step; spmv: the learned-selector study; mixed: the persistent mixed-stream "
-                        "executor; protocol: K-fold and Online for daxpy, Jacobi and n-body (each prints one "
-                        "JSON line)")
+                        "executor; protocol: K-fold and Online for daxpy, Jacobi and n-body; cosched: GPU / "
+                        "host-core splits of loops on host data (each prints one JSON line)")
     p.add_argument("--calls", type=int, default=10000, help="mixed: calls in the stream")
     p.add_argument("--tau", type=float, default=0.5, help="mixed: confidence below which a call is profiled")
     p.add_argument("--train", type=int, default=2000, help="spmv: profiled training matrices")
@@ -274,8 +274,9 @@ def other_configs(args):
     default run stays within a few minutes, as compact records for the
     headline line: daxpy (exhaustive selection), SpMV selection (MLP vs tree
     vs default on 300 training and 100 held-out matrices), n-body per N with
-    the batched form, and a 2,560-call mixed stream with the confidence
-    fallback."""
+    the batched form, the paper's evaluation protocol (K-fold and Online) on
+    daxpy, Jacobi and n-body, co-scheduling and device selection on host
+    data, and a 2,560-call mixed stream with the confidence fallback."""
     import torch
 
     out = {}
@@ -302,6 +303,25 @@ def other_configs(args):
     out["nbody"] = {"value": nb["value"], "unit": "GFLOP/s", "config": nb["config"]["workload"],
                     "per_N": nb["selection"]["per_N"], "roofline": nb["roofline"], "batched": nb["batched"],
                     "wall_s": time.perf_counter() - t}
+    torch.cuda.empty_cache()
+    t = time.perf_counter()
+    pr = protocol_record(200)
+    out["protocol"] = {"value": pr["value"], "unit": "%", "metric": pr["metric"], "config": pr["config"],
+                       "loops": {name: {"adaptive_75": {m: r["kfold_mean_regret_pct"][m]["adaptive_75"]
+                                                        for m in r["kfold_mean_regret_pct"]},
+                                        "mlp": r["kfold_mean_regret_pct"]["mlp"],
+                                        **({"mlp_n_only": r["kfold_mean_regret_pct_n_only"]["mlp"]}
+                                           if "kfold_mean_regret_pct_n_only" in r else {}),
+                                        "online_mean_regret_pct": r["online"]["mean_regret_pct"]}
+                                 for name, r in pr["loops"].items()},
+                       "wall_s": time.perf_counter() - t}
+    torch.cuda.empty_cache()
+    t = time.perf_counter()
+    cs = cosched_record()
+    out["cosched"] = {"value": cs["value"], "unit": "GB/s", "config": cs["config"],
+                      "daxpy": {k: v for k, v in cs["daxpy"].items() if k != "per_n"},
+                      "daxpy_best_fraction_per_n": {str(p["n"]): p["best_fraction"] for p in cs["daxpy"]["per_n"]},
+                      "spmv": cs["spmv"], "wall_s": time.perf_counter() - t}
     torch.cuda.empty_cache()
     t = time.perf_counter()
     mx = mixed_record(2560, args.tau)
@@ -908,7 +928,7 @@ def mixed_record(n_calls, tau, reps_fb=2, regret_sample=96):
     train_sizes[2] = list(range(32))
     regions = [ar.Region(f"mixed-{LOOPS[L]}", nfeat[L], "mlp,64,epochs=400,seed=3", 10 ** 9) for L in range(4)]
     for L in range(4):
-        regions[L].add_builtin(L)
+        regions[L].add_exec_variants(L)
     models = ar.ArExecModels()
     models.H = 64
     keep = []
@@ -991,7 +1011,7 @@ def mixed_record(n_calls, tau, reps_fb=2, regret_sample=96):
     samp = rng.choice(len(chosen), size=min(regret_sample, len(chosen)), replace=False)
     judge = [ar.Region(f"judge-{LOOPS[L]}", nfeat[L], "exhaustive", 10 ** 9) for L in range(4)]
     for L in range(4):
-        judge[L].add_builtin(L)
+        judge[L].add_exec_variants(L)
     regrets = {L: [] for L in range(4)}
     exh_ms = []
     for q in samp:
@@ -1006,7 +1026,7 @@ def mixed_record(n_calls, tau, reps_fb=2, regret_sample=96):
         for f_, v_, ms_ in judge[L].records():
             if f_ == key:
                 per_v.setdefault(v_, []).append(ms_)
-        means = [statistics.mean(per_v[w]) for w in range(ar.loop_num_variants(L))]
+        means = [statistics.mean(per_v[w]) for w in range(ar.ar_exec_num_variants(L))]
         regrets[L].append(means[v] / min(means) - 1.0)
         exh_ms.append((reps_fb + 1) * sum(means))  # exhaustive profile of this call at the fallback's reps
     all_reg = [x for L in range(4) for x in regrets[L]]
@@ -1059,7 +1079,16 @@ def run_mixed(args):
 
 
 # ---------------------------------------------------------------- evaluation protocol, all loops
-def run_protocol(args):
+NBODY_GEOM_VARIANTS = (1, 2, 4, 5, 7, 8)  # t128/t256/t512 x unroll 4/8
+
+
+def nbody_features(ar, N):
+    """n-body selector features: N and the waves of the unroll-4 and unroll-8
+    variants' launches (grid x cluster / (resident blocks x SMs))."""
+    return [float(N)] + [float(np.float32(ar.ar_nbody_geometry(v, int(N))["waves"])) for v in NBODY_GEOM_VARIANTS]
+
+
+def protocol_record(epochs):
     """The paper's evaluation protocol (Section 4.1: K-fold Adaptive-25/50/75,
     Adaptive-100, Static,Best) and its Online mode (Section 4.2) for daxpy,
     Jacobi and n-body, on profile tables of seeded feature points (the SpMV
@@ -1105,7 +1134,10 @@ def run_protocol(args):
         "jacobi7": (ar.AR_LOOP_JACOBI7,
                     [[float(N), float(rng.choice([1, 5, 10, 20]))] for N in log_uniform_ints(32, Nmax, 48)],
                     jacobi_args),
-        "nbody": (ar.AR_LOOP_NBODY, [[float(n)] for n in log_uniform_ints(1 << 10, Bmax, 40)],
+        # n-body: N and the number of waves each unroll-4 / unroll-8 variant's
+        # launch takes (ar_nbody_geometry; a pure function of N and the
+        # device): the split rule makes the winner change where these cross 1
+        "nbody": (ar.AR_LOOP_NBODY, [nbody_features(ar, n) for n in log_uniform_ints(1 << 10, Bmax, 40)],
                   lambda f: ar.ArNbodyArgs(int(f[0]), pos.data_ptr(), acc.data_ptr(), synth.NBODY_EPS)),
     }
     result = {}
@@ -1122,8 +1154,11 @@ def run_protocol(args):
         t_prof = time.perf_counter() - t0
         assert int(status[0].item()) == 0
         t1 = time.perf_counter()
-        kf = kfold_protocol(table, V, F, args.epochs)
+        kf = kfold_protocol(table, V, F, epochs)
         t_kfold = time.perf_counter() - t1
+        kf_n_only = None
+        if name == "nbody":  # the same profiles with N as the only feature
+            kf_n_only = kfold_protocol([([f[0]], ms) for f, ms in table], V, 1, epochs)
         # Online mode
         ro = ar.Region(f"online-{name}", F, "dtree,2")
         ro.add_builtin(L)
@@ -1142,6 +1177,7 @@ def run_protocol(args):
         result[name] = {
             "points": len(points), "variants": V, "features": F,
             "kfold_mean_regret_pct": kf,
+            **({"kfold_mean_regret_pct_n_only": kf_n_only} if kf_n_only else {}),
             "online": {"explore_calls": calls, "mean_regret_pct": 100 * online_regret,
                        "explore_overhead_pct": 100 * (sum(t for _, _, t in explore) /
                                                       sum(best[tuple(float(x) for x in f)] for f, _, t in explore)
@@ -1156,9 +1192,117 @@ def run_protocol(args):
             "config": {"workload": "evaluation protocol: K = 4, f = 25/50/75 %, 10 shuffles, Adaptive-100, "
                                    "Static,Best, Online; daxpy n in [2^10, 2^26] (64 points), Jacobi N in [32, 512] "
                                    "x sweeps in {1,5,10,20} (48), n-body N in [1k, 256k] (40)",
-                       "value": "mean over the three loops of the MLP's Adaptive-75 regret"},
+                       "value": "mean over the three loops of the MLP's Adaptive-75 regret",
+                       "nbody_features": "N and the waves of the t128/t256/t512 x unroll 4/8 launches "
+                                         "(ar_nbody_geometry); kfold_mean_regret_pct_n_only: N alone"},
             "loops": result}
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def run_protocol(args):
+    print(json.dumps(protocol_record(args.epochs)), flush=True)
+
+
+# ---------------------------------------------------------------- host data: co-scheduling, device selection
+def cosched_record(reps=5):
+    """The paper's co-scheduling use case (Section 3.2, Listing 5; Section
+    5.4) and device selection (Listing 3; Section 5.2) on host-resident data:
+    daxpy at 12 sizes n log-uniform in [2^14, 2^27] and four SpMV matrices,
+    every GPU fraction of [0.0:1.0:0.1] profiled through a split region
+    (ar_region_add_split: the GPU part copied in, computed by a CUDA variant
+    and copied back while the host cores run the rest; `reps` timed runs
+    after a warm-up, wall time by CUDA events around the blocking call).  The
+    depth-2 tree on n is scored leave-one-size-out; device selection (host
+    cores or GPU, fractions 0 and 1) is trained and scored on the same
+    table's two columns."""
+    import torch
+
+    import paper_2303_08873_b300 as ar
+    import synth
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    nmax = 1 << 27
+    rng = np.random.Generator(np.random.PCG64(77))
+    sizes = sorted({int(np.float32(round(np.exp(rng.uniform(np.log(2 ** 14), np.log(nmax)))))) for _ in range(12)})
+    a, x, y = synth.daxpy_inputs(7, nmax)
+    hx, hy = torch.from_numpy(x).pin_memory(), torch.from_numpy(y).pin_memory()
+    del x, y
+    xd, yd = torch.empty(nmax, dtype=torch.float64, device=dev), torch.empty(nmax, dtype=torch.float64, device=dev)
+    args = ar.ArDaxpySplitArgs(0, a, hx.data_ptr(), hy.data_ptr(), xd.data_ptr(), yd.data_ptr(), 6)
+    co = ar.Region("cosched-daxpy", 1, f"dtree,2,reps={reps}", 10 ** 9)
+    V = co.add_split(ar.AR_LOOP_DAXPY)
+    fr = [co.variant(v)["value"] for v in range(V)]
+    t0 = time.perf_counter()
+    table = {}
+    for n in sizes:
+        args.n = n
+        ms, _ = co.profile([n], args, stream=stream)
+        table[n] = [float(m) for m in ms]
+    t_prof = time.perf_counter() - t0
+
+    def tree_choice(train, n, cols):
+        r = ar.Region("cosched-fit", 1, "dtree,2", 10 ** 9)
+        for v in range(len(cols)):
+            r.register(f"v{v}", float(v), lambda a_, v_, x_, s_, u_: 0)
+        for m in train:
+            for k, v in enumerate(cols):
+                r.add_record([m], k, table[m][v])
+        r.train()
+        return cols[r.select([n])[0]]
+
+    per = []
+    for n in sizes:
+        ms = table[n]
+        best = int(np.argmin(ms))
+        loo = tree_choice([m for m in sizes if m != n], n, list(range(V)))
+        dev_loo = tree_choice([m for m in sizes if m != n], n, [0, V - 1])
+        per.append({"n": n, "best_fraction": fr[best], "gpu_only_ms": ms[V - 1], "cpu_only_ms": ms[0],
+                    "best_ms": ms[best], "best_over_gpu_only": ms[V - 1] / ms[best],
+                    "tree_loo_fraction": fr[loo], "tree_loo_regret_pct": 100 * (ms[loo] / ms[best] - 1),
+                    "device_loo": "gpu" if dev_loo == V - 1 else "cpu",
+                    "device_loo_regret_pct": 100 * (ms[dev_loo] / min(ms[0], ms[V - 1]) - 1)})
+    tot = {k: sum(table[n][v] for n in sizes) for k, v in (("cpu", 0), ("gpu", V - 1))}
+    bytes_ = sum(24.0 * n for n in sizes)
+    sel_ms = sum(table[p["n"]][fr.index(p["tree_loo_fraction"])] for p in per)
+    best_ms = sum(p["best_ms"] for p in per)
+    # SpMV: four matrices, every fraction
+    sp = []
+    for seed, kind, rows, prm in ((61, "zipf", 200000, 1.5), (62, "zipf", 2000000, 1.8), (63, "band", 1000000, 65),
+                                  (64, "band", 4000000, 17)):
+        rp, c, v = synth.csr_zipf(seed, rows, prm) if kind == "zipf" else synth.csr_band(seed, rows, prm)
+        xs = synth.spmv_x(seed, rows)
+        h = [t.pin_memory() for t in (rp, c, v, xs)]
+        d = [torch.empty_like(t, device=dev) for t in h]
+        nnz = int(rp[-1])
+        hys = torch.empty(rows, dtype=torch.float64).pin_memory()
+        ysd = torch.empty(rows, dtype=torch.float64, device=dev)
+        sargs = ar.ArSpmvSplitArgs(rows=rows, nnz=nnz, cols=rows, rowptr=h[0].data_ptr(), col=h[1].data_ptr(),
+                                   val=h[2].data_ptr(), x=h[3].data_ptr(), y=hys.data_ptr(),
+                                   rowptr_dev=d[0].data_ptr(), col_dev=d[1].data_ptr(), val_dev=d[2].data_ptr(),
+                                   x_dev=d[3].data_ptr(), y_dev=ysd.data_ptr(), gpu_variant=4)
+        rs = ar.Region("cosched-spmv", 1, f"exhaustive,reps={reps}")
+        rs.add_split(ar.AR_LOOP_SPMV)
+        ms, best = rs.profile([rows], sargs, stream=stream)
+        sp.append({"kind": kind, "rows": rows, "nnz": nnz, "best_fraction": fr[best],
+                   "best_over_gpu_only": ms[V - 1] / ms[best], "cpu_only_over_gpu_only": ms[0] / ms[V - 1],
+                   "best_gbs": spmv_bytes(rows, nnz) / (ms[best] * 1e-3) / 1e9})
+    return {
+        "metric": METRIC, "value": bytes_ / (sel_ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1, "dtype": "f64",
+        "data": "synthetic, host-resident (pinned)", "higher_is_better": True, "vs_baseline": None,
+        "config": {"workload": "daxpy on host data, n log-uniform in [2^14, 2^27] (12 sizes), GPU fraction "
+                               "[0.0:1.0:0.1] (11 variants), depth-2 tree on n scored leave-one-size-out; device "
+                               "selection (fractions 0 / 1); SpMV on 4 matrices", "host_threads": ar.ar_split_threads(),
+                   "value": "daxpy algorithmic bytes (24 n) over the tree's leave-one-out choices' time"},
+        "daxpy": {"per_n": per, "best_gbs": bytes_ / (best_ms * 1e-3) / 1e9,
+                  "gpu_only_gbs": bytes_ / (tot["gpu"] * 1e-3) / 1e9, "cpu_only_gbs": bytes_ / (tot["cpu"] * 1e-3) / 1e9,
+                  "tree_loo_mean_regret_pct": statistics.mean(p["tree_loo_regret_pct"] for p in per),
+                  "device_loo_mean_regret_pct": statistics.mean(p["device_loo_regret_pct"] for p in per)},
+        "spmv": sp, "profiling_wall_s": t_prof}
+
+
+def run_cosched(args):
+    print(json.dumps(cosched_record()), flush=True)
 
 
 # ---------------------------------------------------------------- daxpy (config 1)
@@ -1340,6 +1484,8 @@ def main():
         run_nbody(args)
     elif args.workload == "protocol":
         run_protocol(args)
+    elif args.workload == "cosched":
+        run_cosched(args)
     else:  # the stencil workloads: jacobi7 (default) and heat7
         run_ours(args)
 

@@ -45,6 +45,11 @@ int ar_loop_variant_name(int loop, int variant, char *buf, int len);
  * launchers that read `args` as the loop's ar_*_args block below.  Variant
  * values are the variant indices. */
 int ar_region_add_builtin(ar_region *r, int loop, int *out_count);
+/* The same for the loop's first `count` variants only (1 .. the loop's
+ * count; AR_ERR_ARG otherwise), e.g. the variants the mixed-stream executor
+ * runs (ar_exec_num_variants), for a region that learns the executor's
+ * choices. */
+int ar_region_add_builtin_first(ar_region *r, int loop, int count, int *out_count);
 
 /* ---------------------------------------------------------------- daxpy ---
  * y[i] <- a*x[i] + y[i] for i in [0, n), float64, one fused multiply-add per
@@ -139,10 +144,15 @@ int ar_heat7(int variant, int N, int steps, double alpha, const double *u0, doub
  * (operands split into float pairs, products and row sums carried to
  * ~2^-46 relative of the sum of |val x|; the rows of a path block holding a
  * nonzero operand of magnitude outside [2^-62, 2^62), or a sum that
- * overflows a float, are redone in float64).
- * Default: thread-per-row.  Only merge-path (6, 7) uses the caller's
- * workspace (ar_spmv_workspace_bytes; device memory, contents need no
- * initialisation; AR_ERR_ARG if too small).  Results are deterministic. */
+ * overflows a float, are redone in float64), 8 length-binned (rows grouped
+ * by length class, 0-2, 3-4, 5-8, 9-16, 17-32, 33-64, 65-128, 129-256,
+ * 257-1024, 1025+, with 1, 1, 1, 2, 2, 4, 8, 8, 16, 32 lanes per row and up
+ * to 8 nonzeros per lane per pass: few float64 lane-slots per nonzero while
+ * no row takes more than 16 passes; four launches: count, scan, scatter of
+ * the rows into class order, one persistent pass, longest class first).
+ * Default: thread-per-row.  Merge-path (6, 7) and binned (8) use the
+ * caller's workspace (ar_spmv_workspace_bytes; device memory, contents need
+ * no initialisation; AR_ERR_ARG if too small).  Results are deterministic. */
 typedef struct ar_spmv_args {
   int64_t rows;
   int64_t nnz;
@@ -245,6 +255,63 @@ int ar_nbody_batched_workspace_bytes(int count, size_t *bytes);
 int ar_nbody_batched(int count, const int32_t *offs, const float *pos4, float *acc4, float eps, void *workspace,
                      size_t workspace_bytes, void *stream);
 
+/* ------------------------------------------------ host data: GPU / host split ---
+ * Loops whose data live in HOST memory, with the iteration space split
+ * between the GPU and the host cores: the paper's co-scheduling use case
+ * (Section 3.2, Listing 5: numeric variants [0.0:1.0:0.1] are the fraction
+ * of the loop run on the GPU, the GPU part runs asynchronously while the host
+ * cores run the rest, and the region waits for both) and, with fractions 0
+ * and 1 only, its device-selection use case (Section 3.2, Listing 3: variants
+ * cpu and gpu).  For fraction f the GPU takes the first m = round(f n)
+ * elements (daxpy) or rows (SpMV): their inputs are copied host -> device
+ * (one cudaMemcpyAsync per array), one of the loop's CUDA variants
+ * (gpu_variant) runs on them, and the result slice is copied back, all on
+ * `stream`; meanwhile an OpenMP loop of this library computes the rest on
+ * the host cores (daxpy: the same fused multiply-add as the device, so every
+ * split gives the same bits; SpMV: each row's products summed by fused
+ * multiply-add in nonzero order).  The call blocks until both parts are done
+ * (host memory pinned for the copies to overlap the host loop).  Device
+ * buffers: caller-owned, at least the GPU part's size (the whole arrays for
+ * f = 1); unused when m = 0.  AR_ERR_ARG for f outside [0, 1], bad sizes or
+ * pointers, a bad gpu_variant or workspace (SpMV: the variant's
+ * ar_spmv_workspace_bytes for the GPU's rows); AR_ERR_CUDA if a copy or
+ * launch fails (the stream is synchronised before returning). */
+typedef struct ar_daxpy_split_args {
+  int64_t n;
+  double a;
+  const double *x; /* host */
+  double *y;       /* host, updated in place */
+  double *x_dev, *y_dev;
+  int gpu_variant; /* ar_daxpy variant of the GPU part */
+} ar_daxpy_split_args;
+int ar_daxpy_split(double gpu_fraction, const ar_daxpy_split_args *args, void *stream);
+
+typedef struct ar_spmv_split_args {
+  int64_t rows, nnz, cols;   /* cols: length of x */
+  const int32_t *rowptr;     /* host CSR, as for ar_spmv */
+  const int32_t *col;
+  const double *val, *x;     /* host */
+  double *y;                 /* host, written */
+  int32_t *rowptr_dev, *col_dev;
+  double *val_dev, *x_dev, *y_dev;
+  void *workspace;           /* device, for the GPU variant */
+  size_t workspace_bytes;
+  int gpu_variant;           /* ar_spmv variant of the GPU part */
+} ar_spmv_split_args;
+int ar_spmv_split(double gpu_fraction, const ar_spmv_split_args *args, void *stream);
+
+/* Register the GPU fractions [begin:end:step] (inclusive, 0 <= begin,
+ * end <= 1) as variants of a region whose executions run ar_daxpy_split
+ * (loop AR_LOOP_DAXPY) or ar_spmv_split (AR_LOOP_SPMV) on an args block of
+ * the matching type; each variant's value is its fraction.  [0.0:1.0:0.1]
+ * is the co-scheduling region, [0:1:1] the device-selection region (variant
+ * 0 = host cores, 1 = GPU).  The region's timing (CUDA events around the
+ * blocking call) covers both parts and the copies. */
+int ar_region_add_split(ar_region *r, int loop, double begin, double end, double step, int *out_count);
+
+/* Host threads the split loops' OpenMP part uses. */
+int ar_split_threads(void);
+
 /* ------------------------------------------------------------ mixed stream ---
  * Persistent execution of a batch of region invocations of the four loops
  * (up to AR_EXEC_MAX_CALLS per batch) in three launches on `stream`:
@@ -255,13 +322,15 @@ int ar_nbody_batched(int count, const int32_t *offs, const float *pos4, float *a
  *   2. plan (one block): per call, the variant -- force_variant[c] if given,
  *      else the argmax of the loop's MLP (models->theta[loop]; the loop's
  *      default variant if that is NULL) with its confidence -- and the
- *      phase-major table of work items (one phase per Jacobi sweep; two for
- *      merge-path SpMV, main pass and carry fix-up; one otherwise);
+ *      table of work items (one phase per Jacobi sweep; two for merge-path
+ *      SpMV, main pass and carry fix-up; one otherwise), ordered by groups
+ *      of 64 consecutive calls and phase-major inside a group;
  *   3. run: a persistent kernel whose blocks pull work items from an atomic
  *      counter and run the chosen variant's tile of that call.  An item of
  *      phase p waits (bounded) until every item of phase p-1 of its call is
- *      done; items are handed out phase-major, so every awaited item was
- *      handed out earlier.
+ *      done; every awaited item was handed out earlier, and all of a
+ *      group's items are handed out before the next group's, so a call's
+ *      latency is about its group's rather than the whole batch's.
  * The tiles compute exactly what the stand-alone variants compute (same
  * data, same tolerances).  Jacobi tiles of the tma and df families with
  * shapes 32x4 and 32x8 stage their planes by tensor copies when N is even,
@@ -306,6 +375,9 @@ typedef struct ar_exec_models {
   const float *theta[4], *mu[4], *sd[4];
 } ar_exec_models;
 int ar_exec_workspace_bytes(int max_calls, size_t *bytes);
+/* Variants the executor runs for a loop (AR_ERR_ARG for another loop): all
+ * of daxpy, Jacobi and n-body, and SpMV variants 0-7 (not spmv_binned). */
+int ar_exec_num_variants(int loop);
 
 /* Self-test of the bounded device waits that every kernel here uses (the
  * executor's dependency wait and the tensor-copy mbarrier wait): kind 0
@@ -348,7 +420,8 @@ int ar_exec_batch(const ar_exec_call *calls, int ncalls, const ar_exec_models *m
  *    HOST copies of the batch's table and outputs; the calls' device buffers
  *    must still be valid.
  *  regions[4]: one region per loop (NULL skips that loop's calls) with the
- *    loop's variant count and the executor's feature count (1, 3, 5, 1);
+ *    executor's variant count (ar_exec_num_variants) and feature count
+ *    (1, 3, 5, 1);
  *    AR_ERR_STATE otherwise.  reps: 1 .. 16.
  *  workspace: device memory of ar_exec_fallback_workspace_bytes(n), n the
  *    largest daxpy n that may fall back (AR_ERR_ARG for a larger one).

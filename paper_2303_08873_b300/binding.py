@@ -80,6 +80,17 @@ class ArNbodyArgs(ctypes.Structure):
     _fields_ = [("N", _i64), ("pos4", _vp), ("acc4", _vp), ("eps", _f)]
 
 
+class ArDaxpySplitArgs(ctypes.Structure):
+    _fields_ = [("n", _i64), ("a", _d), ("x", _vp), ("y", _vp), ("x_dev", _vp), ("y_dev", _vp),
+                ("gpu_variant", _i)]
+
+
+class ArSpmvSplitArgs(ctypes.Structure):
+    _fields_ = [("rows", _i64), ("nnz", _i64), ("cols", _i64), ("rowptr", _vp), ("col", _vp), ("val", _vp),
+                ("x", _vp), ("y", _vp), ("rowptr_dev", _vp), ("col_dev", _vp), ("val_dev", _vp), ("x_dev", _vp),
+                ("y_dev", _vp), ("workspace", _vp), ("workspace_bytes", _sz), ("gpu_variant", _i)]
+
+
 class ArExecCall(ctypes.Structure):
     _fields_ = [("loop", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("n", _i64), ("nnz", _i64), ("a", _d),
                 ("eps", _f), ("reserved", ctypes.c_int32), ("in0", _vp), ("in1", _vp), ("in2", _vp), ("in3", _vp),
@@ -135,6 +146,7 @@ _SIGS = {
     "ar_loop_default_variant": (_i, [_i]),
     "ar_loop_variant_name": (_i, [_i, _i, _cs, _i]),
     "ar_region_add_builtin": (_i, [_vp, _i, _pi]),
+    "ar_region_add_builtin_first": (_i, [_vp, _i, _i, _pi]),
     "ar_daxpy": (_i, [_i, _i64, _d, _vp, _vp, _vp]),
     "ar_jacobi7": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp, _vp]),
     "ar_heat7": (_i, [_i, _i, _i, _d, _vp, _vp, _vp, _vp, _vp]),
@@ -148,7 +160,12 @@ _SIGS = {
     "ar_nbody_geometry": (_i, [_i, _i64, _pi64, _pi, _pi, _pi, _pi]),
     "ar_nbody_batched_workspace_bytes": (_i, [_i, ctypes.POINTER(_sz)]),
     "ar_nbody_batched": (_i, [_i, _vp, _vp, _vp, _f, _vp, _sz, _vp]),
+    "ar_daxpy_split": (_i, [_d, ctypes.POINTER(ArDaxpySplitArgs), _vp]),
+    "ar_spmv_split": (_i, [_d, ctypes.POINTER(ArSpmvSplitArgs), _vp]),
+    "ar_region_add_split": (_i, [_vp, _i, _d, _d, _d, _pi]),
+    "ar_split_threads": (_i, []),
     "ar_exec_workspace_bytes": (_i, [_i, ctypes.POINTER(_sz)]),
+    "ar_exec_num_variants": (_i, [_i]),
     "ar_wait_selftest": (_i, [_i, ctypes.c_uint, _vp, _vp]),
     "ar_exec_batch": (_i, [_vp, _i, ctypes.POINTER(ArExecModels), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "ar_exec_fallback_workspace_bytes": (_i, [_i64, ctypes.POINTER(_sz)]),
@@ -294,6 +311,22 @@ def ar_nbody_batched(count, offs, pos4, acc4, eps, workspace, workspace_bytes, s
                                       stream_handle(stream)))
 
 
+def ar_daxpy_split(gpu_fraction, args, stream=None):
+    return check(lib.ar_daxpy_split(gpu_fraction, ctypes.byref(args), stream_handle(stream)))
+
+
+def ar_spmv_split(gpu_fraction, args, stream=None):
+    return check(lib.ar_spmv_split(gpu_fraction, ctypes.byref(args), stream_handle(stream)))
+
+
+def ar_split_threads():
+    return check(lib.ar_split_threads())
+
+
+def ar_exec_num_variants(loop):
+    return check(lib.ar_exec_num_variants(loop))
+
+
 def ar_exec_workspace_bytes(max_calls):
     b = ctypes.c_size_t()
     check(lib.ar_exec_workspace_bytes(max_calls, ctypes.byref(b)))
@@ -414,6 +447,21 @@ class Region:
         n = ctypes.c_int()
         self._ck(lib.ar_region_add_builtin(self.h, loop, ctypes.byref(n)))
         return n.value
+
+    def add_builtin_first(self, loop: int, count: int) -> int:
+        n = ctypes.c_int()
+        self._ck(lib.ar_region_add_builtin_first(self.h, loop, count, ctypes.byref(n)))
+        return n.value
+
+    def add_split(self, loop: int, begin: float = 0.0, end: float = 1.0, step: float = 0.1) -> int:
+        """GPU fractions [begin:end:step] of a host-data split loop (ar_region_add_split)."""
+        n = ctypes.c_int()
+        self._ck(lib.ar_region_add_split(self.h, loop, begin, end, step, ctypes.byref(n)))
+        return n.value
+
+    def add_exec_variants(self, loop: int) -> int:
+        """The variants the mixed-stream executor runs for `loop`."""
+        return self.add_builtin_first(loop, ar_exec_num_variants(loop))
 
     def register(self, name: str, value: float, launcher) -> int:
         cb = launcher if isinstance(launcher, LAUNCH_FN) else LAUNCH_FN(launcher)
@@ -587,7 +635,8 @@ class Region:
 
 
 __all__ = ["ArExecCall", "ArExecModels", "ar_exec_workspace_bytes", "ar_exec_batch", "exec_table_bytes",
-           "ar_exec_fallback", "ar_exec_fallback_workspace_bytes", "ArHostCopy", "ar_check_status", "CHECKED",
+           "ar_exec_fallback", "ar_exec_fallback_workspace_bytes", "ar_exec_num_variants",
+           "ArDaxpySplitArgs", "ArSpmvSplitArgs", "ar_daxpy_split", "ar_spmv_split", "ar_split_threads", "ArHostCopy", "ar_check_status", "CHECKED",
            "AR_EXEC_MAX_CALLS", "AR_EXEC_MAX_PHASES", "ArError", "Region", "ArDaxpyArgs", "ArJacobi7Args", "ArHeat7Args", "ArSpmvArgs", "ArNbodyArgs", "ar_spmv",
            "ar_spmv_workspace_bytes", "ar_spmv_merge_path_noalloc", "ar_spmv_gather_floor", "ar_csr_features", "ar_csr_features_workspace_bytes", "ar_nbody",
            "ar_nbody_batched", "ar_nbody_batched_workspace_bytes", "ar_nbody_geometry", "LAUNCH_FN", "FAKE_TIME_FN", "lib", "ptr",

@@ -64,7 +64,13 @@ extern "C" int ar_loop_variant_name(int loop, int variant, char* buf, int len) {
 extern "C" int ar_region_add_builtin(ar_region* r, int loop, int* out_count) {
   const LoopEntry* e = entry(loop);
   if (!r || !e) return AR_ERR_ARG;
-  const int n = e->count();
+  return ar_region_add_builtin_first(r, loop, e->count(), out_count);
+}
+
+extern "C" int ar_region_add_builtin_first(ar_region* r, int loop, int count, int* out_count) {
+  const LoopEntry* e = entry(loop);
+  if (!r || !e || count < 1 || count > e->count()) return AR_ERR_ARG;
+  const int n = count;
   for (int v = 0; v < n; ++v) {
     char nm[64];
     e->name(v, nm, sizeof nm);

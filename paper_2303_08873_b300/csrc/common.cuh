@@ -112,7 +112,9 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 int device_sms();
 
 // Variants per loop (the executor's device tables are sized by these).
-constexpr int kDaxpyVariants = 15, kJacobiVariants = 16, kSpmvVariants = 8, kNbodyVariants = 9;
+constexpr int kDaxpyVariants = 15, kJacobiVariants = 16, kSpmvVariants = 9, kNbodyVariants = 9;
+// The mixed-stream executor runs the first 8 SpMV variants (not the binned one).
+constexpr int kExecSpmvVariants = 8;
 
 // Per-loop launch hooks used by the builtin launcher table.
 int daxpy_launch(void* args, int variant, double value, void* stream, void* user);

@@ -3,11 +3,11 @@
 // persistent launch that pulls (phase, call, tile) work items from an atomic
 // counter and dispatches each to the chosen variant's tile function.
 //
-// Ordering and waits: items are numbered phase-major (all calls' phase 0,
-// then phase 1, ...), so an item of phase p, which waits for the phase p-1
-// items of its own call, only ever waits for items handed out before it to
-// blocks that are already running; the wait is bounded and reports
-// AR_ERR_TIMEOUT per call.  Data written inside this launch (Jacobi sweeps,
+// Ordering and waits: items are numbered by groups of 64 calls, phase-major
+// inside a group (the group's calls' phase 0, then phase 1, ...), so an item
+// of phase p, which waits for the phase p-1 items of its own call, only ever
+// waits for items handed out before it to blocks that are already running;
+// the wait is bounded and reports AR_ERR_TIMEOUT per call.  Data written inside this launch (Jacobi sweeps,
 // merge-path carries) are read with L1-bypassing loads (ld.global.cg).
 #define AR_TU 5
 #include <cudaTypedefs.h>
@@ -40,7 +40,7 @@ constexpr int kMpBatchExec = 4;  // merge-path loads in flight per thread inside
 constexpr int kRunBlocksPerSm = 5;  // resident blocks of the persistent kernel per SM (registers spill; measured best)
 static_assert(mp::kThreads == T, "merge-path tiles use the executor's block size");
 
-__constant__ int c_nvar[4] = {kDaxpyVariants, kJacobiVariants, kSpmvVariants, kNbodyVariants};
+__constant__ int c_nvar[4] = {kDaxpyVariants, kJacobiVariants, kExecSpmvVariants, kNbodyVariants};
 __constant__ int c_default[4] = {6, 1, 0, 3};
 __constant__ int c_dx_ept[3] = {1, 2, 4};
 __constant__ int c_j_bx[4] = {32, 32, 64, 128};
@@ -52,6 +52,21 @@ struct ModelsDev {
   int F[4], V[4], H;
   const float *theta[4], *mu[4], *sd[4];
 };
+
+// Work-item order: entries (phase p, call c) are handed out group by group
+// (kGroup consecutive calls), phase-major inside a group, so all of a group's
+// items are handed out before the next group's (a call's latency is about its
+// group's, not the batch's) while every wait still targets items handed out
+// earlier (phase p - 1 of the same call, earlier in the same group).
+constexpr int kGroup = 64;
+__device__ __forceinline__ void entry_pc(int e, int ncalls, int& p, int& c) {
+  const int g = e / (kGroup * PM);           // every group but the last is full
+  const int c0 = g * kGroup;
+  const int gn = min(kGroup, ncalls - c0);   // calls in this group
+  const int r = e - c0 * PM;
+  p = r / gn;
+  c = c0 + r % gn;
+}
 
 __device__ __forceinline__ uint64_t gtimer() {
   uint64_t t;
@@ -342,12 +357,17 @@ __global__ void __launch_bounds__(T) exec_plan(const ar_exec_call* __restrict__ 
     conf[c] = cf;
   }
   __syncthreads();
-  // phase-major exclusive prefix over (p, c): thread t owns a run of entries
+  // exclusive prefix over the entries in hand-out order (entry_pc): thread t
+  // owns a run of entries
   const int total = PM * ncalls;
   const int per = (total + T - 1) / T;
   const int lo = threadIdx.x * per, hi = min(total, lo + per);
   long long s = 0;
-  for (int e = lo; e < hi; ++e) s += tiles[(e % ncalls) * PM + e / ncalls];
+  for (int e = lo; e < hi; ++e) {
+    int ep, ec;
+    entry_pc(e, ncalls, ep, ec);
+    s += tiles[ec * PM + ep];
+  }
   scan[threadIdx.x] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -364,7 +384,9 @@ __global__ void __launch_bounds__(T) exec_plan(const ar_exec_call* __restrict__ 
   long long acc = scan[threadIdx.x];
   for (int e = lo; e < hi; ++e) {
     prefix[e] = acc;
-    acc += tiles[(e % ncalls) * PM + e / ncalls];
+    int ep, ec;
+    entry_pc(e, ncalls, ep, ec);
+    acc += tiles[ec * PM + ep];
   }
 }
 
@@ -1117,14 +1139,16 @@ __global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_cal
         }
         // the item lies in entry lo's range, inside its (call, phase) tiles;
         // otherwise (checked build) it is skipped under entry 0's indices
+        int p = 0, c = 0;
+        if (lo >= 0 && lo < E) entry_pc(lo, ncalls, p, c);
         const bool valid = AR_CHK(lo >= 0 && lo < E && prefix[lo] <= it && it < prefix[lo + 1] &&
-                                  it - prefix[lo] < (long long)tiles[(lo % ncalls) * PM + lo / ncalls]);
+                                  it - prefix[lo] < (long long)tiles[c * PM + p]);
         if (!valid) {
           lo = 0;
+          p = c = 0;
           atomicExch(status, (int)AR_ERR_ARG);
         }
         pos = lo;
-        const int p = lo / ncalls, c = lo % ncalls;
         int ok = valid ? 1 : 0;
         if (ok && p > 0) {
           if (!dep_wait(done + c * PM + p - 1, tiles[c * PM + p - 1], kDepSpin)) {
@@ -1283,6 +1307,11 @@ extern "C" int ar_wait_selftest(int kind, unsigned int limit, int32_t* status, v
   return launch_status();
 }
 
+extern "C" int ar_exec_num_variants(int loop) {
+  const int nvar[4] = {kDaxpyVariants, kJacobiVariants, kExecSpmvVariants, kNbodyVariants};
+  return loop >= 0 && loop < 4 ? nvar[loop] : AR_ERR_ARG;
+}
+
 extern "C" int ar_exec_workspace_bytes(int max_calls, size_t* bytes) {
   if (max_calls < 1 || max_calls > AR_EXEC_MAX_CALLS || !bytes) return AR_ERR_ARG;
   *bytes = layout(max_calls).total;
@@ -1303,7 +1332,7 @@ extern "C" int ar_exec_batch(const ar_exec_call* calls, int ncalls, const ar_exe
   if (models) {
     if (models->H != 32 && models->H != 64) return AR_ERR_ARG;
     const int nfeat[4] = {1, 3, 5, 1};
-    const int nvar[4] = {kDaxpyVariants, kJacobiVariants, kSpmvVariants, kNbodyVariants};
+    const int nvar[4] = {kDaxpyVariants, kJacobiVariants, kExecSpmvVariants, kNbodyVariants};
     for (int L = 0; L < 4; ++L) {
       m.F[L] = models->F[L];
       m.V[L] = models->V[L];

@@ -108,7 +108,7 @@ extern "C" int ar_exec_fallback(const ar_exec_call* calls, int ncalls, const flo
     if (!regions[L]) continue;
     int V = 0, nf = 0;
     if (ar_region_info(regions[L], &V, &nf, nullptr, nullptr, nullptr) != AR_OK) return AR_ERR_ARG;
-    if (V != ar_loop_num_variants(L) || V > kMaxVar || nf != kExecNf[L]) return AR_ERR_STATE;
+    if (V != ar_exec_num_variants(L) || V > kMaxVar || nf != kExecNf[L]) return AR_ERR_STATE;
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int32_t force_h[kMaxVar];
@@ -127,7 +127,7 @@ extern "C" int ar_exec_fallback(const ar_exec_call* calls, int ncalls, const flo
     const ar_exec_call& k = calls[c];
     if (k.loop < 0 || k.loop > 3 || !(conf[c] < tau) || !regions[k.loop]) continue;
     ar_region* r = regions[k.loop];
-    const int L = k.loop, V = ar_loop_num_variants(L), nf = kExecNf[L];
+    const int L = k.loop, V = ar_exec_num_variants(L), nf = kExecNf[L];
     const float* f = features + 8 * c;
     // features recorded for every variant before: take the recorded best
     if (ar::region_key_means(r, f, nf, &mean) == V) {

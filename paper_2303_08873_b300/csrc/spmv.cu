@@ -112,6 +112,299 @@ size_t mp_workspace(int64_t rows, int64_t nnz) {
   return (size_t)(nb + 1) * 8 + (size_t)nb * 8 + (size_t)nb * 8 + 256;
 }
 
+// ------------------------------------------------------------ length-binned
+// Rows are grouped by length class and each class runs the decomposition that
+// spends the fewest float64 lane-slots: a float64 instruction costs its whole
+// warp whatever lanes are active, and on B300 the float64 pipe, not HBM,
+// bounds CSR SpMV.  A row of length n on K lanes costs K (ceil(n / K) +
+// log2 K) lane-slots (the FMAs plus the shuffle-reduction adds), which favours
+// few lanes, but a row's latency grows with its passes, and the longest row
+// bounds the kernel; so K grows with the length class (1 lane up to length 8,
+// 2 up to 32, 4 up to 64, 8 up to 256, 16 up to 1024, 32 beyond), which keeps
+// every row within 16 passes and spends ~1.1 lane-slots per nonzero on
+// power-law rows against 1.6-2.6 for vector-k.  Each lane sums up to 8
+// nonzeros per pass with all its column, value and x loads issued before the
+// FMAs, over as many passes as the row needs (the last one trimmed to the
+// row); rows of one class have similar lengths, so a warp's lanes finish
+// together.
+//
+// Four launches: count (rows per class per block of kBinRows rows), scan
+// (class offsets; units = warps of work per class), scatter (each row's id,
+// first and end nonzero into the class's slots, in increasing row order) and
+// a persistent kernel of one wave whose warps take units round-robin from
+// the longest class down, loading the next unit's rows while they sum the
+// current one.  Every row's sum has a fixed order (per lane in nonzero order,
+// then a fixed lane tree), so results do not depend on the schedule.
+constexpr int kBins = 10;
+constexpr int kBinRows = 4096;  // rows per counting / scatter block
+constexpr int kBinThreads = 256;
+static_assert(2 * kBins + 2 <= kBinThreads, "the persistent kernel loads meta with one thread per entry");
+// classes: lengths 0-2, 3-4, 5-8, 9-16, 17-32, 33-64, 65-128, 129-256,
+// 257-1024, 1025+ (lanes per row; nonzeros per lane and pass)
+__constant__ int kBinLanes[kBins] = {1, 1, 1, 2, 2, 4, 8, 8, 16, 32};
+__constant__ int kBinU[kBins] = {2, 4, 8, 8, 8, 8, 8, 8, 8, 8};
+
+__device__ __forceinline__ int bin_of(int len) {
+  return len <= 2     ? 0
+         : len <= 4    ? 1
+         : len <= 8    ? 2
+         : len <= 16   ? 3
+         : len <= 32   ? 4
+         : len <= 64   ? 5
+         : len <= 128  ? 6
+         : len <= 256  ? 7
+         : len <= 1024 ? 8
+                       : 9;
+}
+
+// Workspace: counts int32[nblk * kBins] (per block; exclusive offsets after
+// the scan), meta int64[2 * kBins + 2] (class starts in the slot arrays;
+// unit prefix, longest class first), and per slot the row id, first and end
+// nonzero (int32[rows] each).
+struct BinWs {
+  int* counts;
+  long long* meta;
+  int *row, *beg, *end;
+};
+size_t bin_workspace(int64_t rows) {
+  const int64_t nblk = ceil_div(rows, kBinRows);
+  return (size_t)nblk * kBins * 4 + 256 + (size_t)(2 * kBins + 2) * 8 + 256 + 3 * ((size_t)rows * 4 + 256) + 256;
+}
+BinWs bin_ws(void* w, int64_t rows) {
+  auto up = [](uintptr_t p) { return (p + 255) & ~uintptr_t(255); };
+  const int64_t nblk = ceil_div(rows, kBinRows);
+  BinWs b;
+  uintptr_t p = up(reinterpret_cast<uintptr_t>(w));
+  b.counts = reinterpret_cast<int*>(p);
+  p = up(p + (size_t)nblk * kBins * 4);
+  b.meta = reinterpret_cast<long long*>(p);
+  p = up(p + (size_t)(2 * kBins + 2) * 8);
+  b.row = reinterpret_cast<int*>(p);
+  p = up(p + (size_t)rows * 4);
+  b.beg = reinterpret_cast<int*>(p);
+  p = up(p + (size_t)rows * 4);
+  b.end = reinterpret_cast<int*>(p);
+  return b;
+}
+
+// Block b counts the classes of rows [b kBinRows, (b+1) kBinRows).
+__global__ void __launch_bounds__(kBinThreads) spmv_bin_count(int64_t rows, const int* __restrict__ rowptr,
+                                                               int* __restrict__ counts) {
+  pdl_begin();
+  __shared__ int cnt[kBins];
+  if (threadIdx.x < kBins) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t r0 = (int64_t)blockIdx.x * kBinRows, r1 = min(rows, r0 + kBinRows);
+  int mine[kBins] = {};
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += kBinThreads) ++mine[bin_of(__ldg(rowptr + r + 1) - __ldg(rowptr + r))];
+#pragma unroll
+  for (int c = 0; c < kBins; ++c) {
+    int v = mine[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&cnt[c], v);  // integer sums: order-free
+  }
+  __syncthreads();
+  if (threadIdx.x < kBins) counts[(int64_t)blockIdx.x * kBins + threadIdx.x] = cnt[threadIdx.x];
+}
+
+// One block: per class, exclusive offsets over the blocks (in place), the
+// class starts, and the unit prefix (a unit = one warp: 32 / lanes rows of
+// the class), longest class first.
+__global__ void __launch_bounds__(kBinThreads) spmv_bin_scan(int nblk, int* __restrict__ counts,
+                                                              long long* __restrict__ meta) {
+  pdl_begin();
+  __shared__ long long tot[kBins];
+  const int w = threadIdx.x / 32, lane = threadIdx.x & 31;
+  for (int c = w; c < kBins; c += kBinThreads / 32) {  // warp w scans classes w, w + 8, ...
+    long long run = 0;
+    for (int b0 = 0; b0 < nblk; b0 += 32) {
+      const int b = b0 + lane;
+      const int v = b < nblk ? counts[(int64_t)b * kBins + c] : 0;
+      int incl = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      if (b < nblk) counts[(int64_t)b * kBins + c] = (int)(run + incl - v);
+      run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) tot[c] = run;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long s = 0;
+    for (int c = 0; c < kBins; ++c) {
+      meta[c] = s;
+      s += tot[c];
+    }
+    meta[kBins] = s;
+    long long u = 0;
+    for (int q = 0; q < kBins; ++q) {
+      const int c = kBins - 1 - q;
+      meta[kBins + 1 + q] = u;
+      const int rpw = 32 / kBinLanes[c];  // rows per warp
+      u += (tot[c] + rpw - 1) / rpw;
+    }
+    meta[2 * kBins + 1] = u;
+  }
+}
+
+// Block b writes its rows into their class's slots, in row order (ranks from
+// warp ballots, warps in order).
+__global__ void __launch_bounds__(kBinThreads) spmv_bin_scatter(int64_t rows, const int* __restrict__ rowptr,
+                                                                 const int* __restrict__ counts,
+                                                                 const long long* __restrict__ meta,
+                                                                 int* __restrict__ srow, int* __restrict__ sbeg,
+                                                                 int* __restrict__ send) {
+  pdl_begin();
+  __shared__ int base[kBins];
+  __shared__ int wcnt[kBinThreads / 32][kBins];
+  const int w = threadIdx.x / 32, lane = threadIdx.x & 31;
+  if (threadIdx.x < kBins) base[threadIdx.x] = counts[(int64_t)blockIdx.x * kBins + threadIdx.x];
+  const int64_t r0 = (int64_t)blockIdx.x * kBinRows, r1 = min(rows, r0 + kBinRows);
+  for (int64_t c0 = r0; c0 < r1; c0 += kBinThreads) {
+    const int64_t r = c0 + threadIdx.x;
+    const int b = r < r1 ? __ldg(rowptr + r) : 0, e = r < r1 ? __ldg(rowptr + r + 1) : 0;
+    const int c = r < r1 ? bin_of(e - b) : -1;
+    const unsigned lt = (1u << lane) - 1u;
+    int rank = 0;
+#pragma unroll
+    for (int q = 0; q < kBins; ++q) {
+      const unsigned m = __ballot_sync(0xffffffffu, c == q);
+      if (c == q) rank = __popc(m & lt);
+      if (lane == 0) wcnt[w][q] = __popc(m);
+    }
+    __syncthreads();
+    if (c >= 0) {
+      int off = base[c] + rank;
+      for (int v = 0; v < w; ++v) off += wcnt[v][c];
+      const long long dst = meta[c] + off;
+      if (AR_CHK(dst >= 0 && dst < rows)) {
+        srow[dst] = (int)r;
+        sbeg[dst] = b;
+        send[dst] = e;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < kBins) {
+      int add = 0;
+      for (int v = 0; v < kBinThreads / 32; ++v) add += wcnt[v][threadIdx.x];
+      base[threadIdx.x] += add;
+    }
+    __syncthreads();
+  }
+}
+
+// This lane's row of unit u: class, row id, nonzero range (r = -1: none).
+struct BinRow {
+  int c, r, b, e;
+};
+__device__ __forceinline__ BinRow bin_row(long long u, const long long* sm, const int* __restrict__ srow,
+                                          const int* __restrict__ sbeg, const int* __restrict__ send) {
+  int q = 0;  // position of the unit's class in the longest-first order
+  while (q + 1 < kBins && sm[kBins + 2 + q] <= u) ++q;
+  BinRow d;
+  d.c = kBins - 1 - q;
+  const int K = kBinLanes[d.c];
+  const long long slot = (u - sm[kBins + 1 + q]) * (32 / K) + (threadIdx.x & 31) / K;
+  if (slot < sm[d.c + 1] - sm[d.c]) {
+    const long long s = sm[d.c] + slot;
+    d.r = __ldg(srow + s);
+    d.b = __ldg(sbeg + s);
+    d.e = __ldg(send + s);
+  } else {
+    d.r = -1;
+    d.b = d.e = 0;
+  }
+  return d;
+}
+
+// One row per group of K lanes, U nonzeros per lane per pass.
+template <int K, int U>
+__device__ __forceinline__ void binned_row(const BinRow& d, const int* __restrict__ col,
+                                           const double* __restrict__ val, const double* __restrict__ x,
+                                           double* __restrict__ y) {
+  const int l = (threadIdx.x & 31) % K;
+  double s = 0.0;
+  for (int j0 = d.b; j0 < d.e; j0 += K * U) {
+    const int nu = min(U, (d.e - j0 + K - 1) / K);  // passes this row still needs, uniform in the group
+    int cc[U];
+    double vv[U], xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = j0 + l + u * K;
+      const bool in = u < nu && j < d.e;
+      cc[u] = in ? (K == 1 ? __ldg(col + j) : mp::ld_col(col + j)) : -1;
+      vv[u] = in ? (K == 1 ? __ldg(val + j) : mp::ld_val(val + j)) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = cc[u] >= 0 ? __ldg(x + cc[u]) : 0.0;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (u < nu && cc[u] >= 0) s = fma(vv[u], xv[u], s);
+  }
+  if constexpr (K > 1) {
+#pragma unroll
+    for (int o = K / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, K);
+  }
+  if (d.r >= 0 && l == 0) y[d.r] = s;
+}
+
+__global__ void __launch_bounds__(kBinThreads) spmv_binned(const int* __restrict__ col, const double* __restrict__ val,
+                                                           const double* __restrict__ x, double* __restrict__ y,
+                                                           const int* __restrict__ srow, const int* __restrict__ sbeg,
+                                                           const int* __restrict__ send,
+                                                           const long long* __restrict__ meta) {
+  pdl_begin();
+  __shared__ long long sm[2 * kBins + 2];
+  if (threadIdx.x < 2 * kBins + 2) sm[threadIdx.x] = meta[threadIdx.x];
+  __syncthreads();
+  const long long units = sm[2 * kBins + 1];
+  const long long nwarps = (long long)gridDim.x * (kBinThreads / 32);
+  long long u = (long long)blockIdx.x * (kBinThreads / 32) + threadIdx.x / 32;
+  BinRow d = u < units ? bin_row(u, sm, srow, sbeg, send) : BinRow{0, -1, 0, 0};
+  for (; u < units; u += nwarps) {
+    // the next unit's rows load while this one is summed
+    const BinRow dn = u + nwarps < units ? bin_row(u + nwarps, sm, srow, sbeg, send) : BinRow{0, -1, 0, 0};
+    switch (kBinLanes[d.c] * 16 + kBinU[d.c]) {  // (lanes, nonzeros per lane and pass)
+      case 16 + 2: binned_row<1, 2>(d, col, val, x, y); break;
+      case 16 + 4: binned_row<1, 4>(d, col, val, x, y); break;
+      case 16 + 8: binned_row<1, 8>(d, col, val, x, y); break;
+      case 32 + 8: binned_row<2, 8>(d, col, val, x, y); break;
+      case 64 + 8: binned_row<4, 8>(d, col, val, x, y); break;
+      case 128 + 8: binned_row<8, 8>(d, col, val, x, y); break;
+      case 256 + 8: binned_row<16, 8>(d, col, val, x, y); break;
+      default: binned_row<32, 8>(d, col, val, x, y); break;
+    }
+    d = dn;
+  }
+}
+
+int launch_binned(int64_t rows, const int* rp, const int* c, const double* v, const double* x, double* y,
+                  void* workspace, size_t workspace_bytes, cudaStream_t s) {
+  if (!workspace || workspace_bytes < bin_workspace(rows)) return AR_ERR_ARG;
+  if (rows > 0x7fffffffLL) return AR_ERR_ARG;
+  static const int resident = [] {  // one wave of the persistent kernel
+    int r = 0;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, spmv_binned, kBinThreads, 0) == cudaSuccess && r > 0
+               ? r
+               : 1;
+  }();
+  const int64_t nblk = ceil_div(rows, kBinRows);
+  const BinWs w = bin_ws(workspace, rows);
+  spmv_bin_count<<<(unsigned)nblk, kBinThreads, 0, s>>>(rows, rp, w.counts);
+  if (launch_status() != AR_OK) return AR_ERR_CUDA;
+  int rc = launch_pdl(spmv_bin_scan, dim3(1), dim3(kBinThreads), 0, s, (int)nblk, w.counts, w.meta);
+  if (rc == AR_OK)
+    rc = launch_pdl(spmv_bin_scatter, dim3((unsigned)nblk), dim3(kBinThreads), 0, s, rows, rp,
+                    (const int*)w.counts, (const long long*)w.meta, w.row, w.beg, w.end);
+  if (rc != AR_OK) return rc;
+  return launch_pdl(spmv_binned, dim3((unsigned)(device_sms() * resident)), dim3(kBinThreads), 0, s, c, v, x, y,
+                    (const int*)w.row, (const int*)w.beg, (const int*)w.end, (const long long*)w.meta);
+}
+
 // ------------------------------------------------------------ features
 constexpr int kFeatBlocks = 592;  // 4 per SM on B300
 
@@ -190,8 +483,9 @@ __global__ void csr_stats_final(int64_t rows, int nparts, const long long* __res
 }
 
 constexpr int kNumVariants = kSpmvVariants;
-const char* const kNames[kNumVariants] = {"spmv_thread_row", "spmv_warp_row", "spmv_vec2",       "spmv_vec4",
-                                          "spmv_vec8",       "spmv_vec16",    "spmv_merge_path", "spmv_df_merge_path"};
+const char* const kNames[kNumVariants] = {"spmv_thread_row", "spmv_warp_row", "spmv_vec2",
+                                          "spmv_vec4",       "spmv_vec8",     "spmv_vec16",
+                                          "spmv_merge_path", "spmv_df_merge_path", "spmv_binned"};
 
 template <int K>
 int launch_vector(int64_t rows, const int* rp, const int* c, const double* v, const double* x, double* y,
@@ -225,7 +519,7 @@ using namespace ar;
 
 extern "C" int ar_spmv_workspace_bytes(int variant, int64_t rows, int64_t nnz, size_t* bytes) {
   if (variant < 0 || variant >= kNumVariants || rows < 0 || nnz < 0 || !bytes) return AR_ERR_ARG;
-  *bytes = variant >= 6 ? mp_workspace(rows, nnz) : 0;
+  *bytes = variant == 8 ? bin_workspace(rows) : variant >= 6 ? mp_workspace(rows, nnz) : 0;
   return AR_OK;
 }
 
@@ -248,6 +542,7 @@ extern "C" int ar_spmv(int variant, int64_t rows, int64_t nnz, const int32_t* ro
     case 3: return launch_vector<4>(rows, rp, c, val, x, y, s);
     case 4: return launch_vector<8>(rows, rp, c, val, x, y, s);
     case 5: return launch_vector<16>(rows, rp, c, val, x, y, s);
+    case 8: return launch_binned(rows, rp, c, val, x, y, workspace, workspace_bytes, s);
     default: {
       if (!workspace || workspace_bytes < mp_workspace(rows, nnz)) return AR_ERR_ARG;
       const int64_t nb = ceil_div(rows + nnz, kMpPerBlock);

@@ -52,7 +52,7 @@ def main():
         xs = synth.spmv_x(6, rows).numpy()
         sref, absum = loops.spmv_rows(rp, c, vv, xs, np.arange(rows))
         d = [dev(rp), dev(c), dev(vv), dev(xs)]
-        for v in range(8):
+        for v in range(ar.loop_num_variants(2)):
             yd = torch.full((rows,), np.nan, dtype=torch.float64, device="cuda")
             wsb = ar.ar_spmv_workspace_bytes(v, rows, nnz)
             ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device="cuda")

@@ -230,7 +230,7 @@ def test_bad_variant_and_loop_are_reported_per_call():
 def _trained_models():
     """One MLP per loop, trained on the device from a deterministic cost model
     of the features (no timing involved)."""
-    nv = [ar.loop_num_variants(L) for L in range(4)]
+    nv = [ar.ar_exec_num_variants(L) for L in range(4)]
     specs = [(1, nv[0], lambda f: int(np.log2(f[0])) % 15),
              (3, nv[1], lambda f: ((int(f[0]) // 40) % 8) * 2 + int(f[2])),
              (5, nv[2], lambda f: 7 if f[2] > 40 else (6 if f[2] > 20 else (1 if f[4] > 1000 else 3))),
@@ -371,7 +371,7 @@ def _fallback_regions(spec):
     regions = []
     for L, nf in enumerate((1, 3, 5, 1)):
         r = ar.Region(f"fb{L}", nf, spec, 10 ** 9)
-        r.add_builtin(L)
+        r.add_exec_variants(L)
         regions.append(r)
     return regions
 
@@ -403,7 +403,7 @@ def test_fallback_profiles_low_confidence_calls_into_records():
     best, cnt = ar.ar_exec_fallback(b.calls, r["features"], conf, 0.5, regions, reps, None, False, ws, wsb)
     assert cnt == 3 and best[1] == -1
     for k, L in ((0, 0), (2, 2), (3, 3)):
-        V = ar.loop_num_variants(L)
+        V = ar.ar_exec_num_variants(L)
         recs = regions[L].records()
         assert len(recs) == V * reps
         nf = regions[L].nf
@@ -430,7 +430,7 @@ def test_fallback_retrains_and_refreshes_device_models():
     models.H = 64
     keep = []
     for L, F in enumerate((1, 3, 5, 1)):
-        V = ar.loop_num_variants(L)
+        V = ar.ar_exec_num_variants(L)
         th = torch.zeros(ar.ar_mlp_num_params(F, 64, V), dtype=torch.float32, device="cuda")
         mu = torch.zeros(F, dtype=torch.float32, device="cuda")
         sd = torch.ones(F, dtype=torch.float32, device="cuda")

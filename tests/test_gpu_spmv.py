@@ -149,7 +149,7 @@ def test_full_size_sampled_rows(params):
     xh = x.cpu().numpy()
     ref, absum = loops.spmv_rows(srp.astype(np.int32), sc, sv, xh, np.arange(which.size))
     y = torch.empty(rows, dtype=torch.float64, device="cuda")
-    wsb = ar.ar_spmv_workspace_bytes(6, rows, nnz)
+    wsb = max(ar.ar_spmv_workspace_bytes(var, rows, nnz) for var in range(V))
     ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
     wt = torch.from_numpy(which).cuda()
     for v in range(V):
