@@ -926,7 +926,12 @@ def mixed_record(n_calls, tau, reps_fb=2, regret_sample=96):
     hi = {0: 2.0 ** 24, 1: 512.0, 3: 262144.0}
     train_sizes = {L: [int(np.exp(rng.uniform(np.log(lo[L]), np.log(hi[L])))) for _ in range(24)] for L in (0, 1, 3)}
     train_sizes[2] = list(range(32))
-    regions = [ar.Region(f"mixed-{LOOPS[L]}", nfeat[L], "mlp,64,epochs=400,seed=3", 10 ** 9) for L in range(4)]
+    # daxpy tie=0.03: inside the persistent executor daxpy variants that differ
+    # only in block size run alike, and timing noise would otherwise pick
+    # among them at random, leaving the MLP unsure; the other loops keep the
+    # 0.5 % tie of the paper reading
+    regions = [ar.Region(f"mixed-{LOOPS[L]}", nfeat[L], "mlp,64,epochs=400,seed=3" + (",tie=0.03" if L == 0 else ""), 10 ** 9)
+               for L in range(4)]
     for L in range(4):
         regions[L].add_exec_variants(L)
     models = ar.ArExecModels()
@@ -963,6 +968,7 @@ def mixed_record(n_calls, tau, reps_fb=2, regret_sample=96):
     lat = {L: [] for L in range(4)}
     byts = flops = 0.0
     low = fb_profiled = 0
+    low_by = [0, 0, 0, 0]
     fb_wall = 0.0
     chosen = []
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -999,6 +1005,8 @@ def mixed_record(n_calls, tau, reps_fb=2, regret_sample=96):
             chosen.append((L, int(sizes[q]), int(var[k])))
         # the confidence fallback through the library: profile, record, retrain, refresh the device models
         low += int(np.sum(conf < tau))
+        for k, q in enumerate(idx):
+            low_by[int(loop_ids[q])] += int(conf[k] < tau)
         tf = time.perf_counter()
         _, cnt = ar.ar_exec_fallback(calls, feat, conf, tau, regions, reps_fb, models, True, fb_ws, fb_wsb,
                                      stream=stream)
@@ -1056,6 +1064,8 @@ def mixed_record(n_calls, tau, reps_fb=2, regret_sample=96):
                       "regret_sample_calls": len(samp),
                       "note": "regret of the variant the device MLP chose when the call ran (before any fallback)"},
         "fallback": {"low_confidence_calls": low, "low_confidence_pct": 100.0 * low / n_calls,
+                     "low_confidence_by_loop": {LOOPS[L]: low_by[L] for L in range(4)},
+                     "region_tie": {"daxpy": 0.03, "others": 0.005},
                      "profiled_calls": fb_profiled, "answered_from_records": low - fb_profiled,
                      "gpu_ms": fb_ms, "wall_s": fb_wall,
                      "stream_plus_fallback_gbs": byts / ((stream_ms + fb_ms) * 1e-3) / 1e9},

@@ -79,7 +79,12 @@ typedef double (*ar_fake_time_fn)(const float *features, int nf, int variant, vo
  *                   options: "explore=roundrobin" (default), "reps=<n>"
  *                   (ar_profile repetitions, default 5), "conf=<tau>" (MLP
  *                   confidence threshold, default 0.5), "epochs=<n>"
- *                   (MLP training epochs, default 200), "seed=<n>".
+ *                   (MLP training epochs, default 200), "seed=<n>",
+ *                   "tie=<f>" (0 <= f < 1: variants whose mean time is
+ *                   within a fraction f of the fastest tie, the lowest
+ *                   index wins, in labels and exhaustive argmins; default
+ *                   0.005 - a larger f keeps labels steady among variants
+ *                   that run alike).
  *   min_train_data  unique (features, variant) points needed before the
  *                   automatic training; <= 0 means "number of variants"
  *                   (Section 3.1 default), fixed when the first execution
@@ -189,14 +194,15 @@ int ar_select(ar_region *r, const float *features, int nf, int *out_variant, flo
  * variant bodies must be repeatable on them.  Appends every timed execution
  * as a record.  out_ms (num_variants floats, may be NULL) receives each
  * variant's mean (+inf for unusable ones); out_best the fastest, means
- * within 0.5 % tying to the lowest index. */
+ * within the region's tie fraction (0.5 % by default) tying to the lowest
+ * index. */
 int ar_profile(ar_region *r, const float *features, int nf, void *args, void *stream, int reps,
                float *out_ms, int *out_best);
 
 /* Train the region's model on all records so far (__apollo_region_train).
  * Resolves pending events first (blocking).  Labels: for each distinct
- * feature vector, the variant with the lowest mean time (ties within 0.5 %
- * to the lowest index).  AR_ERR_STATE with no records; AR_ERR_CUDA if MLP
+ * feature vector, the variant with the lowest mean time (ties within the
+ * region's tie fraction, 0.5 % by default, to the lowest index).  AR_ERR_STATE with no records; AR_ERR_CUDA if MLP
  * training on the device fails. */
 int ar_train(ar_region *r);
 

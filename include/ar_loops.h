@@ -399,7 +399,8 @@ int ar_exec_batch(const ar_exec_call *calls, int ncalls, const ar_exec_models *m
  * loop's region.  For each call c in [0, ncalls) with conf[c] < tau:
  *  - if the loop's region already holds records of every variant for the
  *    call's exact feature vector, nothing runs: best[c] is the fastest mean
- *    of those records (ties within 0.5 % to the lowest index);
+ *    of those records (ties within the region's tie fraction, 0.5 % by
+ *    default, to the lowest index);
  *  - otherwise every variant runs as a one-call ar_exec_batch forced to it,
  *    once untimed and `reps` times timed by the executor's own per-call time
  *    (t_end - t_start), each timed run preceded by the region's L2 flush

@@ -131,7 +131,7 @@ extern "C" int ar_exec_fallback(const ar_exec_call* calls, int ncalls, const flo
     const float* f = features + 8 * c;
     // features recorded for every variant before: take the recorded best
     if (ar::region_key_means(r, f, nf, &mean) == V) {
-      best[c] = ar::best_of_means(mean);
+      best[c] = ar::best_of_means(mean, ar::region_tie(r));
       continue;
     }
     if (L == AR_LOOP_DAXPY && k.n > save_cap) {
@@ -188,7 +188,7 @@ extern "C" int ar_exec_fallback(const ar_exec_call* calls, int ncalls, const flo
         m[v] += ms / reps;
       }
     if (result != AR_OK) break;
-    best[c] = ar::best_of_means(m);
+    best[c] = ar::best_of_means(m, ar::region_tie(r));
     fed[L] = true;
     ++profiled;
     // leave the call's outputs as its best variant computes them: daxpy's y

@@ -30,17 +30,18 @@ std::array<float, AR_MAX_FEATURES> key_values(const FKey& k) {
   return v;
 }
 
-int best_of_means(const std::vector<double>& mean) {
+int best_of_means(const std::vector<double>& mean, double tie) {
   double m = INFINITY;
   for (double t : mean)
     if (std::isfinite(t) && t < m) m = t;
   if (!std::isfinite(m)) return -1;
   for (size_t v = 0; v < mean.size(); ++v)
-    if (std::isfinite(mean[v]) && mean[v] <= m * 1.005) return (int)v;
+    if (std::isfinite(mean[v]) && mean[v] <= m * (1.0 + tie)) return (int)v;
   return -1;
 }
 
-void label_records(const std::vector<Record>& recs, int V, std::vector<FKey>* keys, std::vector<int>* labels) {
+void label_records(const std::vector<Record>& recs, int V, std::vector<FKey>* keys, std::vector<int>* labels,
+                   double tie) {
   std::map<FKey, std::vector<std::pair<double, int>>> acc;
   for (const auto& r : recs) {
     auto& slot = acc[record_key(r)];
@@ -56,7 +57,7 @@ void label_records(const std::vector<Record>& recs, int V, std::vector<FKey>* ke
     std::vector<double> mean((size_t)V, INFINITY);
     for (int v = 0; v < V; ++v)
       if (kv.second[v].second > 0) mean[v] = kv.second[v].first / kv.second[v].second;
-    const int b = best_of_means(mean);
+    const int b = best_of_means(mean, tie);
     if (b < 0) continue;
     keys->push_back(kv.first);
     labels->push_back(b);

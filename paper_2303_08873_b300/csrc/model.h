@@ -27,13 +27,15 @@ FKey record_key(const Record& r);
 std::array<float, AR_MAX_FEATURES> key_values(const FKey& k);
 
 // Index of the fastest mean (non-finite means skipped): the lowest index whose
-// mean is within 0.5 % of the minimum; -1 if none is finite.
-int best_of_means(const std::vector<double>& mean);
+// mean is within a fraction `tie` (default 0.5 %) of the minimum; -1 if none
+// is finite.
+constexpr double kTieRel = 0.005;
+int best_of_means(const std::vector<double>& mean, double tie = kTieRel);
 
 // Training set from records: one sample per distinct feature vector (sorted
 // by bit pattern), labelled with best_of_means of its per-variant means.
 void label_records(const std::vector<Record>& recs, int num_variants, std::vector<FKey>* keys,
-                   std::vector<int>* labels);
+                   std::vector<int>* labels, double tie = kTieRel);
 
 // CART decision tree (Gini; thresholds at midpoints of consecutive distinct
 // values; x <= thr goes left; ties to the lowest feature, then the lowest
@@ -94,6 +96,8 @@ uint64_t fnv1a(const uint8_t* p, size_t n);
 int region_key_means(const ar_region* r, const float* f, int nf, std::vector<double>* mean);
 // The region's L2 flush buffer (ar_set_l2_flush), or nullptr / 0.
 void region_flush_buffer(const ar_region* r, void** buf, size_t* bytes);
+// The region's tie fraction for labels and exhaustive argmins (spec "tie=").
+double region_tie(const ar_region* r);
 
 struct Blob {
   std::vector<uint8_t> data;

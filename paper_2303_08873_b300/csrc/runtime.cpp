@@ -57,6 +57,7 @@ struct ar_region {
   int fixed = 0;
   int reps = 5;
   float tau = 0.5f;
+  double tie = ar::kTieRel;  // means within this fraction of the fastest tie (lowest index wins)
   int epochs = 200;
   uint64_t seed = 0x5eed;
   int min_train_req = 0;  // as passed; <= 0: number of variants
@@ -197,6 +198,11 @@ int parse_spec(ar_region* r, const char* spec) {
       double d = strtod(val.c_str(), &end);
       if (*end || !(d >= 0.0 && d <= 1.0)) return fail(r, AR_ERR_ARG, "bad conf");
       r->tau = (float)d;
+    } else if (key == "tie") {
+      char* end = nullptr;
+      double d = strtod(val.c_str(), &end);
+      if (*end || !(d >= 0.0 && d < 1.0)) return fail(r, AR_ERR_ARG, "bad tie");
+      r->tie = d;
     } else if (key == "epochs") {
       if (!parse_int(val, &v) || v < 1 || v > 100000) return fail(r, AR_ERR_ARG, "bad epochs");
       r->epochs = (int)v;
@@ -654,7 +660,7 @@ int ar_profile(ar_region* r, const float* features, int nf, void* args, void* st
   }
   for (auto x : ev) give_event(r, x);
   if (result != AR_OK) return result;
-  const int best = ar::best_of_means(mean);
+  const int best = ar::best_of_means(mean, r->tie);
   if (best < 0) return fail(r, AR_ERR_STATE, "no variant could be profiled");
   if (r->kind == K_EXHAUSTIVE) {
     r->table[key] = best;
@@ -682,7 +688,7 @@ int ar_train(ar_region* r) {
   if (r->records.empty()) return fail(r, AR_ERR_STATE, "no records to train on");
   std::vector<FKey> keys;
   std::vector<int> labels;
-  ar::label_records(r->records, (int)r->variants.size(), &keys, &labels);
+  ar::label_records(r->records, (int)r->variants.size(), &keys, &labels, r->tie);
   switch (r->kind) {
     case K_DTREE: {
       std::vector<std::array<float, AR_MAX_FEATURES>> X(keys.size());
@@ -1020,6 +1026,8 @@ int region_key_means(const ar_region* r, const float* f, int nf, std::vector<dou
     }
   return have;
 }
+
+double region_tie(const ar_region* r) { return r->tie; }
 
 void region_flush_buffer(const ar_region* r, void** buf, size_t* bytes) {
   *buf = r->flush_buf;

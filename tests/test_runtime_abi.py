@@ -390,3 +390,24 @@ def test_normal_build_reports_checks_disabled():
     if ar.CHECKED:
         pytest.skip("this process loaded the bounds-check build")
     assert ar.ar_check_status(clear=False) == (False, 0, 0)
+
+
+def test_tie_option_widens_the_label_ties_to_the_lowest_index():
+    times = {0: 1.02, 1: 1.0, 2: 1.01}  # variant 0 within 2 % of the fastest
+
+    def make(spec):
+        r = ar.Region("tie", 1, spec, 10 ** 9)
+        for v in range(3):
+            r.register(f"v{v}", float(v), _noop)
+        r.set_fake_timer(lambda f, v: times[v])
+        return r
+
+    default, wide = make("exhaustive"), make("exhaustive,tie=0.03")
+    assert default.profile([1.0], reps=1)[1] == 1  # the paper reading: 0.5 %
+    assert wide.profile([1.0], reps=1)[1] == 0
+    for r, want in ((default, 1), (wide, 0)):
+        r.train()
+        assert r.select([1.0])[0] == want
+    for bad in ("dtree,tie=1", "dtree,tie=-0.1", "dtree,tie=x"):
+        with pytest.raises(ar.ArError):
+            ar.Region("bad", 1, bad, 1)
