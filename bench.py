@@ -669,7 +669,6 @@ def spmv_study(n_train, n_test, rows_max, epochs, kfold=False):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    ws = torch.empty(16 << 20, dtype=torch.uint8, device=dev)
     fwsb = ar.ar_csr_features_workspace_bytes(0)
     fws = torch.empty(fwsb, dtype=torch.uint8, device=dev)
     f5 = torch.zeros(5, dtype=torch.float32, device=dev)
@@ -679,7 +678,7 @@ def spmv_study(n_train, n_test, rows_max, epochs, kfold=False):
     def floor_ms(keep, nnz):
         """Mean time of the gather-floor kernel on one matrix (3 runs after a
         warm-up, L2 flushed before each, like the variants' profiles)."""
-        _, c, v, x, _ = keep
+        _, c, v, x, _, _ = keep
         t = []
         with torch.cuda.stream(stream):
             ar.ar_spmv_gather_floor(nnz, c, v, x, sink, stream=stream)
@@ -699,12 +698,17 @@ def spmv_study(n_train, n_test, rows_max, epochs, kfold=False):
         nnz = int(rp[-1].item())
         x = synth.spmv_x(seed, rows, device="cuda")
         y = torch.empty(rows, dtype=torch.float64, device=dev)
+        # the largest workspace any variant needs on this matrix (merge path:
+        # 24 B per 4096 path items; binned: 12 B per row): a variant whose
+        # launch is refused is marked unusable for the rest of the study
+        wsb = max(ar.ar_spmv_workspace_bytes(var, rows, nnz) for var in range(ar.loop_num_variants(ar.AR_LOOP_SPMV)))
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
         ar.ar_csr_features(rows, rp, f5, fws, fwsb, stream=stream)
         stream.synchronize()
         feats = f5.cpu().tolist()
         a = ar.ArSpmvArgs(rows, nnz, rp.data_ptr(), c.data_ptr(), v.data_ptr(), x.data_ptr(), y.data_ptr(),
-                          ws.data_ptr(), ws.numel())
-        return feats, a, (rp, c, v, x, y), rows, nnz, prm["kind"]
+                          ws.data_ptr(), wsb)
+        return feats, a, (rp, c, v, x, y, ws), rows, nnz, prm["kind"]
 
     mlp = ar.Region("spmv-mlp", 5, f"mlp,64,epochs={epochs},seed=7", 10 ** 9)
     tree = ar.Region("spmv-dtree", 5, "dtree,2", 10 ** 9)
@@ -767,7 +771,12 @@ def spmv_study(n_train, n_test, rows_max, epochs, kfold=False):
                       "mlp_low_confidence_calls": low_conf,
                       "best_variant_histogram": {names[v]: sum(1 for p in per if p["best"] == v) for v in range(V)}},
         "cost": {"profiling_wall_s": t_prof, "profiling_gpu_ms": prof_ms, "train_mlp_s": t_mlp,
-                 "train_records": len(mlp.records())},
+                 "train_records": len(mlp.records()),
+                 # exhaustive profiling of one call (warm-up + 5 timed runs of every
+                 # variant), and after how many calls the learned selector's one-off
+                 # training profiles cost less than profiling every call
+                 "exhaustive_per_call_gpu_ms": statistics.mean(6 * sum(p["ms"]) for p in per),
+                 "break_even_calls": prof_ms / statistics.mean(6 * sum(p["ms"]) for p in per)},
     }
     hbm_peak, peak_src = peaks()
     # the variant most often fastest on the test set, and its DRAM bytes per

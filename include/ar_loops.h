@@ -275,7 +275,8 @@ int ar_nbody_batched(int count, const int32_t *offs, const float *pos4, float *a
  * f = 1); unused when m = 0.  AR_ERR_ARG for f outside [0, 1], bad sizes or
  * pointers, a bad gpu_variant or workspace (SpMV: the variant's
  * ar_spmv_workspace_bytes for the GPU's rows); AR_ERR_CUDA if a copy or
- * launch fails (the stream is synchronised before returning). */
+ * launch fails (the stream is synchronised before returning, the host part
+ * is not run, and the output's contents are undefined). */
 typedef struct ar_daxpy_split_args {
   int64_t n;
   double a;
@@ -429,7 +430,9 @@ int ar_exec_batch(const ar_exec_call *calls, int ncalls, const ar_exec_models *m
  *  best: HOST int32[ncalls]; *num_profiled (may be NULL): calls profiled.
  * Blocking: synchronises `stream` once per profiled call and before return.
  * Returns AR_OK, AR_ERR_ARG, AR_ERR_STATE, AR_ERR_CUDA, or the first failing
- * execution's status (e.g. AR_ERR_TIMEOUT). */
+ * execution's status (e.g. AR_ERR_TIMEOUT); after an error the outputs of
+ * the call being profiled are undefined (earlier calls keep theirs) and the
+ * records appended so far stay in the regions. */
 int ar_exec_fallback_workspace_bytes(int64_t max_daxpy_n, size_t *bytes);
 int ar_exec_fallback(const ar_exec_call *calls, int ncalls, const float *features, const float *conf, float tau,
                      ar_region *const *regions, int reps, const ar_exec_models *models, int retrain, void *workspace,
