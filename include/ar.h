@@ -24,6 +24,11 @@
  *    resolved lazily.  Only ar_profile, ar_train, ar_flush_records,
  *    ar_region_save and ar_region_load block the host.
  *  - Threads: a region object must not be used by two threads at once.
+ *  - Logging: the environment variable AR_LOG (read once per process) sets a
+ *    log level for stderr lines "[ar] <region id>: ...": 0 or unset quiet,
+ *    1 training, automatic-training triggers, variants marked unusable and
+ *    confidence-fallback summaries, 2 also every exhaustive profile, model
+ *    selection and execution policy.
  */
 #ifndef AR_H
 #define AR_H

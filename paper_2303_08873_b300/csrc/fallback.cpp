@@ -223,5 +223,11 @@ extern "C" int ar_exec_fallback(const ar_exec_call* calls, int ncalls, const flo
       if (result == AR_OK && models && kind == 1) result = upload_mlp(regions[L], models, L, s);
     }
   if (num_profiled) *num_profiled = profiled;
+  if (ar::log_level() >= 1) {
+    int low = 0;
+    for (int c = 0; c < ncalls; ++c) low += conf[c] < tau;
+    ar::log_line("exec-fallback", "%d of %d calls below confidence %.3f: %d profiled, %d from records%s; status %d",
+                 low, ncalls, (double)tau, profiled, low - profiled, retrain ? ", regions retrained" : "", result);
+  }
   return result;
 }

@@ -89,6 +89,13 @@ struct SplitMix64 {
 
 uint64_t fnv1a(const uint8_t* p, size_t n);
 
+// Log level from the environment variable AR_LOG (read once): 0 quiet
+// (default), 1 training, automatic-training triggers, variants marked
+// unusable and fallback summaries, 2 also every exhaustive profile and every
+// model selection.  Lines go to stderr, prefixed "[ar] <region id>".
+int log_level();
+void log_line(const char* region_id, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+
 // Region internals used by other parts of the library (runtime.cpp).
 // Per-variant mean ms over the region's resolved records of one exact feature
 // vector (+inf where a variant has none); returns the number of variants that
@@ -98,6 +105,8 @@ int region_key_means(const ar_region* r, const float* f, int nf, std::vector<dou
 void region_flush_buffer(const ar_region* r, void** buf, size_t* bytes);
 // The region's tie fraction for labels and exhaustive argmins (spec "tie=").
 double region_tie(const ar_region* r);
+// The region's id.
+const char* region_id(const ar_region* r);
 
 struct Blob {
   std::vector<uint8_t> data;

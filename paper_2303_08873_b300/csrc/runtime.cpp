@@ -315,9 +315,14 @@ int choose(ar_region* r, const float* f) {
   if (r->kind == K_FIXED) return next_usable(r, std::min(r->fixed, (int)r->variants.size() - 1));
   if (r->trained) {
     int v = predict(r, f, nullptr);
-    if (v >= 0) return next_usable(r, v);
+    if (v >= 0) {
+      if (ar::log_level() >= 2) ar::log_line(r->id.c_str(), "policy %d from the model", next_usable(r, v));
+      return next_usable(r, v);
+    }
   }
-  return explore_policy(r);
+  const int e = explore_policy(r);
+  if (ar::log_level() >= 2) ar::log_line(r->id.c_str(), "policy %d from exploration", e);
+  return e;
 }
 
 void freeze(ar_region* r) {
@@ -500,6 +505,9 @@ int ar_end(ar_region* r, void* stream) {
   r->unique.insert({key, v});
   if (!r->auto_trained && !r->trained && r->kind != K_FIXED && (int)r->unique.size() >= r->min_train) {
     r->auto_trained = true;
+    if (ar::log_level() >= 1)
+      ar::log_line(r->id.c_str(), "%zu unique points reached min_train_data %d: training", r->unique.size(),
+                   r->min_train);
     return ar_train(r);
   }
   return AR_OK;
@@ -524,6 +532,7 @@ int ar_invoke(ar_region* r, const float* features, int nf, void* args, void* str
   const int lrc = var.fn(args, v, var.value, stream, var.user);
   if (lrc != 0) {
     var.usable = false;
+    if (ar::log_level() >= 1) ar::log_line(r->id.c_str(), "variant %d (%s) failed to launch: unusable", v, var.name.c_str());
     close_ctx(r);
     return fail(r, AR_ERR_CUDA, "variant %d (%s) launcher failed with %d", v, var.name.c_str(), lrc);
   }
@@ -576,6 +585,7 @@ int ar_select(ar_region* r, const float* features, int nf, int* out_variant, flo
   float c = 1.f;
   int v = predict(r, f, &c);
   if (v < 0) return fail(r, AR_ERR_NOMODEL, "model has no entry for these features");
+  if (ar::log_level() >= 2) ar::log_line(r->id.c_str(), "selected %d (%s), confidence %.3f", v, r->variants[v].name.c_str(), c);
   *out_variant = v;
   if (out_conf) *out_conf = c;
   return AR_OK;
@@ -662,6 +672,9 @@ int ar_profile(ar_region* r, const float* features, int nf, void* args, void* st
   if (result != AR_OK) return result;
   const int best = ar::best_of_means(mean, r->tie);
   if (best < 0) return fail(r, AR_ERR_STATE, "no variant could be profiled");
+  if (ar::log_level() >= 2)
+    ar::log_line(r->id.c_str(), "profiled %d variants x %d reps: best %d (%s) %.4g ms", V, reps, best,
+                 r->variants[best].name.c_str(), mean[best]);
   if (r->kind == K_EXHAUSTIVE) {
     r->table[key] = best;
     r->trained = true;
@@ -718,6 +731,10 @@ int ar_train(ar_region* r) {
       break;
   }
   r->trained = true;
+  if (ar::log_level() >= 1)
+    ar::log_line(r->id.c_str(), "trained %s on %zu labelled feature vectors from %zu records",
+                 r->kind == K_DTREE ? "dtree" : r->kind == K_RFC ? "rfc" : r->kind == K_MLP ? "mlp" : "exhaustive",
+                 keys.size(), r->records.size());
   return AR_OK;
 }
 
@@ -1028,6 +1045,25 @@ int region_key_means(const ar_region* r, const float* f, int nf, std::vector<dou
 }
 
 double region_tie(const ar_region* r) { return r->tie; }
+
+const char* region_id(const ar_region* r) { return r->id.c_str(); }
+
+int log_level() {
+  static const int level = [] {
+    const char* e = getenv("AR_LOG");
+    return e ? atoi(e) : 0;
+  }();
+  return level;
+}
+
+void log_line(const char* region_id, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  fprintf(stderr, "[ar] %s: %s\n", region_id ? region_id : "-", buf);
+}
 
 void region_flush_buffer(const ar_region* r, void** buf, size_t* bytes) {
   *buf = r->flush_buf;

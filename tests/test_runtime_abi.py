@@ -411,3 +411,32 @@ def test_tie_option_widens_the_label_ties_to_the_lowest_index():
     for bad in ("dtree,tie=1", "dtree,tie=-0.1", "dtree,tie=x"):
         with pytest.raises(ar.ArError):
             ar.Region("bad", 1, bad, 1)
+
+
+def test_ar_log_levels_write_region_events_to_stderr():
+    import subprocess
+    import sys
+    import textwrap
+
+    code = textwrap.dedent("""
+        import paper_2303_08873_b300 as ar
+        r = ar.Region("logged", 1, "dtree", 4)
+        for v in range(2):
+            r.register(f"v{v}", float(v), lambda a, v, x, s, u: 0)
+        r.set_fake_timer(lambda f, v: 1.0 + v)
+        r.profile([1.0], reps=1)
+        r.profile([2.0], reps=1)
+        r.train()
+        r.select([1.0])
+    """)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = {}
+    for level in ("0", "1", "2"):
+        env = dict(os.environ, AR_LOG=level)
+        p = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True,
+                           timeout=120)
+        assert p.returncode == 0, p.stderr
+        out[level] = [ln for ln in p.stderr.splitlines() if ln.startswith("[ar] logged:")]
+    assert out["0"] == []
+    assert any("trained dtree" in ln for ln in out["1"]) and not any("profiled" in ln for ln in out["1"])
+    assert any("profiled 2 variants" in ln for ln in out["2"]) and any("selected 0" in ln for ln in out["2"])
