@@ -516,9 +516,13 @@ __device__ bool jacobi_tma_tile(const CUtensorMap* map, int N, int bx, int by, i
       }
       marker_any |= __syncthreads_or(marker);
     }
-    auto planes = [&](auto native_c, auto guard_c) {
+    // the sweep mode is a compile-time constant of each instantiation (as in
+    // the stand-alone kernels): no mode tests in the unrolled plane loop
+    auto planes = [&](auto native_c, auto guard_c, auto src_pairs_c, auto dst_pairs_c) {
       constexpr bool NAT = decltype(native_c)::value;
       constexpr bool GUARD = decltype(guard_c)::value;
+      constexpr bool SP = decltype(src_pairs_c)::value;
+      constexpr bool DP = decltype(dst_pairs_c)::value;
 #pragma unroll
       for (int r = 0; r < kXDZ; ++r) {
         const int p = g * kXDZ - 1 + r;
@@ -544,11 +548,11 @@ __device__ bool jacobi_tma_tile(const CUtensorMap* map, int N, int bx, int by, i
           if (live) {
             const float2 res = df_avg6(pc[-1], pc[1], pc[-G::PX], pc[G::PX], fm, up);
             if (inside && AR_CHK(od - dst >= 0 && od - dst < NN * N)) {
-              if (dst_pairs) {
+              if constexpr (DP) {
                 *op = res;
               } else {
-                double v = src_pairs ? finite_pair_to_double(res) : pair_to_double(res);
-                if (!src_pairs && (__double_as_longlong(v) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) {
+                double v = SP ? finite_pair_to_double(res) : pair_to_double(res);
+                if (!SP && (__double_as_longlong(v) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) {
                   // an input outside the float-pair range: redo in float64
                   const int k = kb + p - 1;
                   double sd = atcg(src, N, i - 1, j, k) + atcg(src, N, i + 1, j, k);
@@ -572,16 +576,29 @@ __device__ bool jacobi_tma_tile(const CUtensorMap* map, int N, int bx, int by, i
     using T_ = std::true_type;
     using F_ = std::false_type;
     const bool guard = g == 0 || g * kXDZ + kXDZ - 2 > kc;
+    auto pair_planes = [&](auto guard_c) {
+      if (src_pairs) {
+        if (dst_pairs)
+          planes(F_{}, guard_c, T_{}, T_{});
+        else
+          planes(F_{}, guard_c, T_{}, F_{});
+      } else {
+        if (dst_pairs)
+          planes(F_{}, guard_c, F_{}, T_{});
+        else
+          planes(F_{}, guard_c, F_{}, F_{});
+      }
+    };
     if (!pair_math) {
       if (guard)
-        planes(T_{}, T_{});
+        planes(T_{}, T_{}, F_{}, F_{});
       else
-        planes(T_{}, F_{});
+        planes(T_{}, F_{}, F_{}, F_{});
     } else {
       if (guard)
-        planes(F_{}, T_{});
+        pair_planes(T_{});
       else
-        planes(F_{}, F_{});
+        pair_planes(F_{});
     }
     // every reader of box g-1 is past this barrier: its slot takes box g+2
     fence_proxy_async_smem();
@@ -715,9 +732,13 @@ __device__ bool jacobi_tma_odd_tile(const CUtensorMap* map, int N, int bx, int b
       }
       marker_any |= __syncthreads_or(marker);
     }
-    auto planes = [&](auto native_c, auto guard_c) {
+    // the sweep mode is a compile-time constant of each instantiation (as in
+    // the stand-alone kernels): no mode tests in the unrolled plane loop
+    auto planes = [&](auto native_c, auto guard_c, auto src_pairs_c, auto dst_pairs_c) {
       constexpr bool NAT = decltype(native_c)::value;
       constexpr bool GUARD = decltype(guard_c)::value;
+      constexpr bool SP = decltype(src_pairs_c)::value;
+      constexpr bool DP = decltype(dst_pairs_c)::value;
 #pragma unroll
       for (int r = 0; r < kXDZ; ++r) {
         const int p = g * kXDZ - 1 + r;
@@ -744,11 +765,11 @@ __device__ bool jacobi_tma_odd_tile(const CUtensorMap* map, int N, int bx, int b
           if (live) {
             const float2 res = df_avg6(pp[pb + cc - 1], pp[pb + cc + 1], pp[pb + cs], pp[pb + cn], fm, up);
             if (inside && AR_CHK(od - dst >= 0 && od - dst < NN * N)) {
-              if (dst_pairs) {
+              if constexpr (DP) {
                 *op = res;
               } else {
-                double v = src_pairs ? finite_pair_to_double(res) : pair_to_double(res);
-                if (!src_pairs && (__double_as_longlong(v) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) {
+                double v = SP ? finite_pair_to_double(res) : pair_to_double(res);
+                if (!SP && (__double_as_longlong(v) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) {
                   const int k = kb + p - 1;
                   double sd = atcg(src, N, i - 1, j, k) + atcg(src, N, i + 1, j, k);
                   sd += atcg(src, N, i, j - 1, k);
@@ -771,16 +792,29 @@ __device__ bool jacobi_tma_odd_tile(const CUtensorMap* map, int N, int bx, int b
     using T_ = std::true_type;
     using F_ = std::false_type;
     const bool guard = g == 0 || g * kXDZ + kXDZ - 2 > kc;
+    auto pair_planes = [&](auto guard_c) {
+      if (src_pairs) {
+        if (dst_pairs)
+          planes(F_{}, guard_c, T_{}, T_{});
+        else
+          planes(F_{}, guard_c, T_{}, F_{});
+      } else {
+        if (dst_pairs)
+          planes(F_{}, guard_c, F_{}, T_{});
+        else
+          planes(F_{}, guard_c, F_{}, F_{});
+      }
+    };
     if (!pair_math) {
       if (guard)
-        planes(T_{}, T_{});
+        planes(T_{}, T_{}, F_{}, F_{});
       else
-        planes(T_{}, F_{});
+        planes(T_{}, F_{}, F_{}, F_{});
     } else {
       if (guard)
-        planes(F_{}, T_{});
+        pair_planes(T_{});
       else
-        planes(F_{}, F_{});
+        pair_planes(F_{});
     }
     fence_proxy_async_smem();
     __syncthreads();
