@@ -981,8 +981,8 @@ __device__ bool jacobi_sweep_tile(const ar_exec_call& k, int v, int64_t t, const
 // from float64 data and the catch-up computes sweep S-1.  maps: the call's
 // tensor maps of (u0, out, work), or nullptr.  Returns false if a bounded
 // wait gave up.
-__device__ bool jacobi_tile(const ar_exec_call& k, int v, int p, int64_t t, int* flag, unsigned char* smraw,
-                            const CUtensorMap* maps, uint64_t* bars) {
+__device__ bool jacobi_tile(const ar_exec_call& k, int v, int p, int64_t t, bool flagged, int* flag,
+                            unsigned char* smraw, const CUtensorMap* maps, uint64_t* bars) {
   const int S = k.sweeps, N = (int)k.n;
   const double* u0 = static_cast<const double*>(k.in0);
   double* out = static_cast<double*>(k.out0);
@@ -996,8 +996,6 @@ __device__ bool jacobi_tile(const ar_exec_call& k, int v, int p, int64_t t, int*
   if (!jacobi_pair_chain(k, v))
     return jacobi_sweep_tile(k, v, t, src_of(p), dst_of(p), fam == 3, false, false, nullptr, smraw,
                              map_of(src_of(p)), bars);
-  // block-uniform: the tile bodies below hold barriers
-  const bool flagged = __syncthreads_or(p >= 1 && __ldcg(flag) != 0);
   if (p == S) {  // catch-up: float64 sweep S-1 over a contiguous chunk of unknowns
     if (!flagged) return true;
     const double* src = src_of(S - 1);
@@ -1146,30 +1144,42 @@ __global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_cal
                                                  const int* __restrict__ usetma) {
   __shared__ __align__(128) unsigned char smraw[kSmemBytes];  // tensor-copy destinations
   __shared__ __align__(8) uint64_t s_bars[kXRing];
-  __shared__ long long s_item, s_t;
-  __shared__ int s_c, s_p, s_ok;
+  __shared__ __align__(16) ar_exec_call s_k;  // the current item's call, copied when the call changes
+  __shared__ long long s_item, s_t, s_next, s_end;
+  __shared__ int s_c, s_p, s_ok, s_v, s_tma, s_flagged, s_pos, s_ready, s_cur;
   const int E = PM * ncalls;
   const long long total = prefix[E];
-  int pos = 0;  // thread 0: entry of this block's previous item
+  if (threadIdx.x == 0) {
+    s_next = (long long)atomicAdd(counter, 1ull);
+    s_pos = 0;       // entry of this block's previous item
+    s_end = -1;      // prefix[s_pos + 1] once looked up
+    s_ready = -1;    // entry whose dependency this block has seen met
+    s_cur = -1;      // call held in s_k
+  }
   for (;;) {
     if (threadIdx.x == 0) {
-      const long long it = (long long)atomicAdd(counter, 1ull);
+      const long long it = s_next;
       s_item = it;
       if (it < total) {
-        // last entry whose range starts at or before it: this block's items
-        // only grow, so gallop forward from its previous entry, then bisect
-        int lo = pos, step = 1;
-        while (lo + step < E && prefix[lo + step] <= it) {
-          lo += step;
-          step <<= 1;
-        }
-        int hi = min(lo + step, E - 1);
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (prefix[mid] <= it)
-            lo = mid;
-          else
-            hi = mid - 1;
+        // last entry whose range starts at or before it.  A block's items
+        // only grow: most lie in its previous item's entry; otherwise gallop
+        // forward from that entry, then bisect
+        int lo = s_pos;
+        if (!(it < s_end)) {
+          int step = 1;
+          while (lo + step < E && prefix[lo + step] <= it) {
+            lo += step;
+            step <<= 1;
+          }
+          int hi = min(lo + step, E - 1);
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= it)
+              lo = mid;
+            else
+              hi = mid - 1;
+          }
+          s_end = (lo >= 0 && lo < E) ? prefix[lo + 1] : -1;
         }
         // the item lies in entry lo's range, inside its (call, phase) tiles;
         // otherwise (checked build) it is skipped under entry 0's indices
@@ -1180,18 +1190,33 @@ __global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_cal
         if (!valid) {
           lo = 0;
           p = c = 0;
+          s_end = -1;
           atomicExch(status, (int)AR_ERR_ARG);
         }
-        pos = lo;
+        s_pos = lo;
         int ok = valid ? 1 : 0;
-        if (ok && p > 0) {
-          if (!dep_wait(done + c * PM + p - 1, tiles[c * PM + p - 1], kDepSpin)) {
-            ok = 0;
-            atomicExch(status + c, (int)AR_ERR_TIMEOUT);
-          }
-          __threadfence();
+        if (c != s_cur) {
+          s_k = calls[c];
+          s_v = vint[c];
+          s_tma = usetma[c];
+          s_cur = c;
+          if (ok) atomicMin((unsigned long long*)t0 + c, (unsigned long long)gtimer());
         }
-        if (ok) atomicMin((unsigned long long*)t0 + c, (unsigned long long)gtimer());
+        // phase p > 0 waits once per entry for all of phase p - 1 (counters
+        // only grow within a batch); the acquire fence then covers every
+        // later item of the entry.  A float-pair chain's flag is final by
+        // then: only its first sweep raises it
+        if (ok && lo != s_ready) {
+          if (p > 0) {
+            if (!dep_wait(done + c * PM + p - 1, tiles[c * PM + p - 1], kDepSpin)) {
+              ok = 0;
+              atomicExch(status + c, (int)AR_ERR_TIMEOUT);
+            }
+            __threadfence();
+          }
+          s_flagged = p > 0 && __ldcg(flags + c) != 0;
+          if (ok) s_ready = lo;
+        }
         s_c = c;
         s_p = p;
         s_t = valid ? it - prefix[lo] : 0;
@@ -1202,15 +1227,15 @@ __global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_cal
     if (s_item >= total) break;
     const int c = s_c, p = s_p;
     const long long t = s_t;
-    const ar_exec_call k = calls[c];
-    const int v = vint[c];
+    const ar_exec_call k = s_k;
+    const int v = s_v;
     // the plan validated (loop, variant); re-checked so that a call table
     // changed under a running batch cannot index outside the variant tables
     if (s_ok && k.loop >= 0 && k.loop < 4 && v >= 0 && v < c_nvar[k.loop]) {
       switch (k.loop) {
         case AR_LOOP_DAXPY: daxpy_tile(k, v, t); break;
         case AR_LOOP_JACOBI7:
-          if (!jacobi_tile(k, v, p, t, flags + c, smraw, usetma[c] ? maps + 3 * c : nullptr, s_bars) &&
+          if (!jacobi_tile(k, v, p, t, s_flagged != 0, flags + c, smraw, s_tma ? maps + 3 * c : nullptr, s_bars) &&
               threadIdx.x == 0)
             atomicExch(status + c, (int)AR_ERR_TIMEOUT);
           break;
@@ -1220,9 +1245,13 @@ __global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_cal
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+      // the next claim goes out before the release fence so the two round
+      // trips overlap
+      const long long nx = (long long)atomicAdd(counter, 1ull);
       __threadfence();
       atomicAdd(done + c * PM + p, 1);
       atomicMax((unsigned long long*)t1 + c, (unsigned long long)gtimer());
+      s_next = nx;
     }
   }
 }
