@@ -29,7 +29,9 @@ namespace {
 
 constexpr int T = 256;                   // threads per executor block
 constexpr int PM = AR_EXEC_MAX_PHASES;   // phases per call
-constexpr int kJKC = 32;                 // Jacobi planes per tile
+constexpr int kJKCMax = 62;              // Jacobi planes per tile at most (64 loaded: 16 four-plane boxes)
+constexpr int kJBox = 4;                 // planes per tensor-copy box of the Jacobi tiles
+constexpr int kJTilesPerBlock = 1;       // a Jacobi call's tiles per persistent block, at least (if N allows)
 constexpr int kJB = 4;                   // Jacobi planes whose loads are issued together
 constexpr int kDxTile = 16384;           // daxpy elements per tile
 constexpr int kSpPasses = 16;            // SpMV row groups per tile (thread-row, vector-k)
@@ -102,13 +104,26 @@ __device__ __forceinline__ int phases_of(const ar_exec_call& c, int v) {
 // n-body i-bodies per tile: one per thread, two for 512-body tiles.
 __device__ __forceinline__ int nb_bodies(int v) { return c_nb_tile[v / 3] > T ? c_nb_tile[v / 3] : T; }
 
-__device__ int64_t tiles_of(const ar_exec_call& c, int v, int p) {
+// Planes per Jacobi tile of an N^3 call run by variant v: as many as keep
+// the call's tiles at least `target` (kJTilesPerBlock per block of the
+// persistent kernel), at most kJKCMax, with the depth plus the two halo
+// planes a whole number of the tensor copies' 4-plane boxes.  The chunks
+// are not balanced over N: the ragged last chunk's tiles are handed out last
+// in their phase, and short tiles there even out the phase's tail.
+__device__ int jacobi_kc(int N, int v, long long target) {
+  const long long cb = cdiv(N, c_j_bx[v % 4]) * cdiv(N, c_j_by[v % 4]);
+  long long kc = cdiv((long long)N * cb, target);
+  kc = max(2LL, min((long long)kJKCMax, kc));
+  return (int)(cdiv(kc + 2, kJBox) * kJBox - 2);
+}
+
+__device__ int64_t tiles_of(const ar_exec_call& c, int v, int p, long long jtarget) {
   switch (c.loop) {
     case AR_LOOP_DAXPY: return cdiv(c.n, kDxTile);
     case AR_LOOP_JACOBI7: {
       const int64_t N = c.n;
       if (jacobi_pair_chain(c, v) && p == c.sweeps) return kCatchTiles;
-      return cdiv(N, c_j_bx[v % 4]) * cdiv(N, c_j_by[v % 4]) * cdiv(N, kJKC);
+      return cdiv(N, c_j_bx[v % 4]) * cdiv(N, c_j_by[v % 4]) * cdiv(N, jacobi_kc((int)N, v, jtarget));
     }
     case AR_LOOP_SPMV: {
       if (v == 0) return cdiv(c.n, (int64_t)T * kSpPasses);
@@ -277,7 +292,8 @@ __global__ void __launch_bounds__(T) exec_plan(const ar_exec_call* __restrict__ 
                                                const __grid_constant__ CUtensorMap tm8,
                                                const __grid_constant__ CUtensorMap to4,
                                                const __grid_constant__ CUtensorMap to8, bool tma_ok, bool tma_odd_ok,
-                                               CUtensorMap* __restrict__ maps, int* __restrict__ usetma) {
+                                               CUtensorMap* __restrict__ maps, int* __restrict__ usetma,
+                                               long long jtarget) {
   __shared__ long long scan[T];
   const int c = threadIdx.x;
   if (c < ncalls) {
@@ -323,7 +339,7 @@ __global__ void __launch_bounds__(T) exec_plan(const ar_exec_call* __restrict__ 
       v -= v % 3;  // double2 variants need 16-byte alignment: one element per thread
     const int ph = st == AR_OK ? phases_of(k, v) : 0;
     for (int p = 0; p < PM; ++p) {
-      tiles[c * PM + p] = p < ph ? (int)tiles_of(k, v, p) : 0;
+      tiles[c * PM + p] = p < ph ? (int)tiles_of(k, v, p, jtarget) : 0;
       done[c * PM + p] = 0;
     }
     // tensor maps of u0, out and work for the tensor-copy Jacobi tiles (tma
@@ -438,7 +454,7 @@ __device__ __forceinline__ double atcg(const double* __restrict__ u, int N, int 
 // Box geometry of the tensor-copy tiles (shapes 32x4 and 32x8): boxes of
 // (BX+4) x (BY+2) x kXDZ float64 in a kXRing-slot ring at a 128-byte aligned
 // base inside the block's shared memory, one mbarrier per slot.
-constexpr int kXDZ = 4, kXRing = 3;
+constexpr int kXDZ = kJBox, kXRing = 3;
 template <int BX, int BY>
 struct XGeom {
   static constexpr int PX = BX + 4, PY = BY + 2, PLANE = PX * PY, GROUP = PLANE * kXDZ;
@@ -841,14 +857,14 @@ __device__ bool jacobi_tma_odd_tile(const CUtensorMap* map, int N, int bx, int b
 // `map`: a tensor map of src (tma and df families, shapes 32x4 and 32x8,
 // when the plan made one), else nullptr.  Returns false if a bounded wait
 // gave up.
-__device__ bool jacobi_sweep_tile(const ar_exec_call& k, int v, int64_t t, const double* src, double* dst,
+__device__ bool jacobi_sweep_tile(const ar_exec_call& k, int v, int64_t t, int kc, const double* src, double* dst,
                                   bool pair_math, bool src_pairs, bool dst_pairs, int* flag, unsigned char* smraw,
                                   const CUtensorMap* map, uint64_t* bars) {
   const int N = (int)k.n;
   const int fam = v / 4, BX = c_j_bx[v % 4], BY = c_j_by[v % 4];
   const int64_t gx = (N + BX - 1) / BX, gy = (N + BY - 1) / BY;
   const int bx = (int)(t % gx), by = (int)((t / gx) % gy), bz = (int)(t / (gx * gy));
-  const int kb = bz * kJKC, ke = min(N, kb + kJKC);
+  const int kb = bz * kc, ke = min(N, kb + kc);
   if (map && fam >= 2 && v % 4 <= 1) {
     if (N & 1)
       return v % 4 == 0 ? jacobi_tma_odd_tile<32, 4>(map, N, bx, by, kb, ke, src, dst, pair_math, src_pairs,
@@ -981,7 +997,7 @@ __device__ bool jacobi_sweep_tile(const ar_exec_call& k, int v, int64_t t, const
 // from float64 data and the catch-up computes sweep S-1.  maps: the call's
 // tensor maps of (u0, out, work), or nullptr.  Returns false if a bounded
 // wait gave up.
-__device__ bool jacobi_tile(const ar_exec_call& k, int v, int p, int64_t t, bool flagged, int* flag,
+__device__ bool jacobi_tile(const ar_exec_call& k, int v, int p, int64_t t, int kc, bool flagged, int* flag,
                             unsigned char* smraw, const CUtensorMap* maps, uint64_t* bars) {
   const int S = k.sweeps, N = (int)k.n;
   const double* u0 = static_cast<const double*>(k.in0);
@@ -994,7 +1010,7 @@ __device__ bool jacobi_tile(const ar_exec_call& k, int v, int p, int64_t t, bool
   };
   const int fam = v / 4;
   if (!jacobi_pair_chain(k, v))
-    return jacobi_sweep_tile(k, v, t, src_of(p), dst_of(p), fam == 3, false, false, nullptr, smraw,
+    return jacobi_sweep_tile(k, v, t, kc, src_of(p), dst_of(p), fam == 3, false, false, nullptr, smraw,
                              map_of(src_of(p)), bars);
   if (p == S) {  // catch-up: float64 sweep S-1 over a contiguous chunk of unknowns
     if (!flagged) return true;
@@ -1014,10 +1030,10 @@ __device__ bool jacobi_tile(const ar_exec_call& k, int v, int p, int64_t t, bool
     return true;
   }
   if (flagged)  // one sweep late, in float64
-    return jacobi_sweep_tile(k, v, t, src_of(p - 1), dst_of(p - 1), false, false, false, nullptr, smraw,
+    return jacobi_sweep_tile(k, v, t, kc, src_of(p - 1), dst_of(p - 1), false, false, false, nullptr, smraw,
                              map_of(src_of(p - 1)), bars);
-  return jacobi_sweep_tile(k, v, t, src_of(p), dst_of(p), true, p > 0, p < S - 1, flag, smraw, map_of(src_of(p)),
-                           bars);
+  return jacobi_sweep_tile(k, v, t, kc, src_of(p), dst_of(p), true, p > 0, p < S - 1, flag, smraw,
+                           map_of(src_of(p)), bars);
 }
 
 __device__ void spmv_tile(const ar_exec_call& k, int v, int p, int64_t t, unsigned char* smraw) {
@@ -1146,7 +1162,7 @@ __global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_cal
   __shared__ __align__(8) uint64_t s_bars[kXRing];
   __shared__ __align__(16) ar_exec_call s_k;  // the current item's call, copied when the call changes
   __shared__ long long s_item, s_t, s_next, s_end;
-  __shared__ int s_c, s_p, s_ok, s_v, s_tma, s_flagged, s_pos, s_ready, s_cur;
+  __shared__ int s_c, s_p, s_ok, s_v, s_tma, s_flagged, s_pos, s_ready, s_cur, s_kc;
   const int E = PM * ncalls;
   const long long total = prefix[E];
   if (threadIdx.x == 0) {
@@ -1200,6 +1216,11 @@ __global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_cal
           s_v = vint[c];
           s_tma = usetma[c];
           s_cur = c;
+          // a Jacobi call's planes per tile (the plan counted its tiles by
+          // the same rule and the same block count)
+          s_kc = s_k.loop == AR_LOOP_JACOBI7 && s_v >= 0 && s_v < c_nvar[AR_LOOP_JACOBI7]
+                     ? jacobi_kc((int)s_k.n, s_v, (long long)kJTilesPerBlock * gridDim.x)
+                     : 0;
           if (ok) atomicMin((unsigned long long*)t0 + c, (unsigned long long)gtimer());
         }
         // phase p > 0 waits once per entry for all of phase p - 1 (counters
@@ -1235,7 +1256,8 @@ __global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_cal
       switch (k.loop) {
         case AR_LOOP_DAXPY: daxpy_tile(k, v, t); break;
         case AR_LOOP_JACOBI7:
-          if (!jacobi_tile(k, v, p, t, s_flagged != 0, flags + c, smraw, s_tma ? maps + 3 * c : nullptr, s_bars) &&
+          if (!jacobi_tile(k, v, p, t, s_kc, s_flagged != 0, flags + c, smraw, s_tma ? maps + 3 * c : nullptr,
+                           s_bars) &&
               threadIdx.x == 0)
             atomicExch(status + c, (int)AR_ERR_TIMEOUT);
           break;
@@ -1423,11 +1445,13 @@ extern "C" int ar_exec_batch(const ar_exec_call* calls, int ncalls, const ar_exe
   const bool tma_ok = tma_templates_ready(reinterpret_cast<unsigned char*>(maps), s, &tmt);
   if (cudaMemsetAsync(part, 0, (size_t)ncalls * 3 * 8, s) != cudaSuccess) return AR_ERR_CUDA;
   if (cudaMemsetAsync(flags, 0, (size_t)ncalls * 4, s) != cudaSuccess) return AR_ERR_CUDA;
+  const int run_blocks = device_sms() * kRunBlocksPerSm;  // the persistent kernel's grid
   exec_features<<<dim3(64, (unsigned)ncalls), T, 0, s>>>(calls, features, part);
   exec_plan<<<1, T, 0, s>>>(calls, ncalls, m, have, force_variant, variant, conf, features, part, tiles, prefix,
                             done, counter, t_start, t_end, status, vint, tmt.tm4, tmt.tm8, tmt.to4, tmt.to8,
-                            tma_ok && tmt.even_ok, tma_ok && tmt.odd_ok, maps, usetma);
-  exec_run<<<device_sms() * kRunBlocksPerSm, T, 0, s>>>(calls, ncalls, vint, tiles, prefix, done, counter, t_start, t_end, status,
+                            tma_ok && tmt.even_ok, tma_ok && tmt.odd_ok, maps, usetma,
+                            (long long)kJTilesPerBlock * run_blocks);
+  exec_run<<<run_blocks, T, 0, s>>>(calls, ncalls, vint, tiles, prefix, done, counter, t_start, t_end, status,
                                           flags, maps, usetma);
   return launch_status();
 }

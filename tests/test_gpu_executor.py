@@ -134,7 +134,7 @@ def test_every_variant_of_every_loop_in_one_batch():
 
 def test_edge_sizes_of_every_loop_in_one_batch():
     """Sizes at and just past the executor's tile edges (daxpy 16384-element
-    tiles, Jacobi 32-plane tiles and the even-N plane ring, SpMV row groups and
+    tiles, Jacobi plane chunks and the even-N plane ring, SpMV row groups and
     4096-item merge-path blocks, n-body 256/512-body tiles), and the degenerate
     ones (one element, one unknown, one row, one body), every loop and family."""
     b = Batch()
@@ -204,6 +204,25 @@ def test_jacobi_tensor_copy_tiles():
     assert np.all(r["status"] == 0)
     for k, ok in enumerate(b.check):
         assert ok(), (k, b.calls[k].loop, force[k])
+
+
+def test_jacobi_deep_tiles():
+    """From N ~ 200 up a Jacobi tile spans the deepest chunk, 62 planes, and
+    the last chunk takes what is left (N = 310: five full chunks; N = 311: a
+    last chunk of one plane; N = 257 / 258 / 300: 9 / 10 / 52): the
+    tensor-copy tiles on even and odd N, the plane ring (df 128x2), the
+    shared-memory family and a call whose input lies outside the pair range."""
+    b = Batch()
+    force = []
+    for k, (N, sweeps, v, plant) in enumerate([(310, 2, 13, None), (311, 3, 13, None), (300, 2, 12, None),
+                                               (258, 2, 15, None), (257, 2, 9, None), (300, 1, 5, None),
+                                               (310, 3, 13, 1e40)]):
+        b.jacobi(N, sweeps, 800 + k, plant)
+        force.append(v)
+    r = b.run(force=force)
+    assert np.all(r["status"] == 0)
+    for k, ok in enumerate(b.check):
+        assert ok(), (k, force[k])
 
 
 def test_bad_variant_and_loop_are_reported_per_call():
