@@ -59,15 +59,17 @@ struct ModelsDev {
 // (kGroup consecutive calls), phase-major inside a group, so all of a group's
 // items are handed out before the next group's (a call's latency is about its
 // group's, not the batch's) while every wait still targets items handed out
-// earlier (phase p - 1 of the same call, earlier in the same group).
+// earlier (phase p - 1 of the same call, earlier in the same group).  Inside
+// a phase the group's calls go in `perm` order: longest estimated item first,
+// so the short items fill the batch's tail.
 constexpr int kGroup = 64;
-__device__ __forceinline__ void entry_pc(int e, int ncalls, int& p, int& c) {
+__device__ __forceinline__ void entry_pc(int e, int ncalls, const int* perm, int& p, int& c) {
   const int g = e / (kGroup * PM);           // every group but the last is full
   const int c0 = g * kGroup;
   const int gn = min(kGroup, ncalls - c0);   // calls in this group
   const int r = e - c0 * PM;
   p = r / gn;
-  c = c0 + r % gn;
+  c = perm[c0 + r % gn];
 }
 
 __device__ __forceinline__ uint64_t gtimer() {
@@ -132,6 +134,25 @@ __device__ int64_t tiles_of(const ar_exec_call& c, int v, int p, long long jtarg
       return p == 0 ? nb : cdiv(nb, T);
     }
     default: return cdiv(c.n, nb_bodies(v));
+  }
+}
+
+// Rough duration of one item of call k under variant v (ns, one block of a
+// full persistent launch: about 8.8 GB/s of DRAM traffic or 81 GFLOP/s of
+// FP32 work per block); only the order of these estimates is used.
+__device__ float item_ns(const ar_exec_call& k, int v, long long jtarget) {
+  switch (k.loop) {
+    case AR_LOOP_DAXPY: return kDxTile * 24.f / 8.8f;
+    case AR_LOOP_JACOBI7:
+      return (float)c_j_bx[v % 4] * c_j_by[v % 4] * jacobi_kc((int)k.n, v, jtarget) * 16.f / 8.8f;
+    case AR_LOOP_SPMV: {
+      const float per_row = k.n > 0 ? (float)k.nnz / (float)k.n : 0.f;
+      const float items = v == 0 ? (float)T * kSpPasses * (1.f + per_row)
+                          : v < 6 ? (float)(T / c_sp_k[v - 1]) * kSpPasses * (1.f + per_row)
+                                  : (float)kMpPerTile;
+      return items * 12.f / 8.8f;
+    }
+    default: return (float)nb_bodies(v) * (float)k.n * 20.f / 81.f;
   }
 }
 
@@ -293,8 +314,10 @@ __global__ void __launch_bounds__(T) exec_plan(const ar_exec_call* __restrict__ 
                                                const __grid_constant__ CUtensorMap to4,
                                                const __grid_constant__ CUtensorMap to8, bool tma_ok, bool tma_odd_ok,
                                                CUtensorMap* __restrict__ maps, int* __restrict__ usetma,
-                                               long long jtarget) {
+                                               long long jtarget, int* __restrict__ perm) {
   __shared__ long long scan[T];
+  __shared__ float s_cost[T];
+  __shared__ int s_perm[T];
   const int c = threadIdx.x;
   if (c < ncalls) {
     const ar_exec_call k = calls[c];
@@ -365,12 +388,22 @@ __global__ void __launch_bounds__(T) exec_plan(const ar_exec_call* __restrict__ 
       }
     }
     usetma[c] = use;
+    s_cost[c] = st == AR_OK ? item_ns(k, v, jtarget) : 0.f;
     t0[c] = ~0ull;
     t1[c] = 0ull;
     status[c] = st;
     variant[c] = st == AR_OK ? v : -1;
     vint[c] = v;
     conf[c] = cf;
+  }
+  __syncthreads();
+  // each group's calls, longest estimated item first (ties by call index)
+  if (c < ncalls) {
+    const int c0 = c / kGroup * kGroup, gn = min(kGroup, ncalls - c0);
+    int rank = 0;
+    for (int q = c0; q < c0 + gn; ++q) rank += s_cost[q] > s_cost[c] || (s_cost[q] == s_cost[c] && q < c);
+    s_perm[c0 + rank] = c;
+    perm[c0 + rank] = c;
   }
   __syncthreads();
   // exclusive prefix over the entries in hand-out order (entry_pc): thread t
@@ -381,7 +414,7 @@ __global__ void __launch_bounds__(T) exec_plan(const ar_exec_call* __restrict__ 
   long long s = 0;
   for (int e = lo; e < hi; ++e) {
     int ep, ec;
-    entry_pc(e, ncalls, ep, ec);
+    entry_pc(e, ncalls, s_perm, ep, ec);
     s += tiles[ec * PM + ep];
   }
   scan[threadIdx.x] = s;
@@ -401,7 +434,7 @@ __global__ void __launch_bounds__(T) exec_plan(const ar_exec_call* __restrict__ 
   for (int e = lo; e < hi; ++e) {
     prefix[e] = acc;
     int ep, ec;
-    entry_pc(e, ncalls, ep, ec);
+    entry_pc(e, ncalls, s_perm, ep, ec);
     acc += tiles[ec * PM + ep];
   }
 }
@@ -1096,27 +1129,23 @@ __device__ void spmv_tile(const ar_exec_call& k, int v, int p, int64_t t, unsign
     mp::block<true, kMpBatchExec>(rows, nnz, rp, col, val, x, y, db, i0, i1, carry_row + t, carry_val + t, smraw);
 }
 
-// nb_bodies(v) i-bodies (one or two per thread) against all N bodies, in
-// Tt-body j tiles held in the pair layout of nbody_math.cuh.
-__device__ void nbody_tile(const ar_exec_call& k, int v, int64_t t, unsigned char* smraw) {
-  const int Tt = c_nb_tile[v / 3], uidx = v % 3;
-  const float4* pos = static_cast<const float4*>(k.in0);
-  float4* acc = static_cast<float4*>(k.out0);
-  const int64_t N = k.n;
-  const float eps2 = k.eps * k.eps;
+// R i-bodies per thread (bodies i0 + r T) against all N bodies, j tiles of
+// Tt bodies staged in shared memory in the pair layout of nbody_math.cuh;
+// one pass over each tile serves all R.
+template <int R>
+__device__ __forceinline__ void nbody_rows(const float4* __restrict__ pos, float4* __restrict__ acc, int64_t N,
+                                           int64_t i0, int Tt, int uidx, float eps2, float4* tile) {
   const float2 eps2v = make_float2(eps2, eps2);
-  float4* tile = reinterpret_cast<float4*>(smraw);
-  const int nown = nb_bodies(v) / T;  // i-bodies per thread
-  float2 npx[2][1], npy[2][1], npz[2][1];
-  int64_t ii[2];
-  float ax[2][1] = {{0.f}, {0.f}}, ay[2][1] = {{0.f}, {0.f}}, az[2][1] = {{0.f}, {0.f}};
-  for (int o = 0; o < nown; ++o) {
-    ii[o] = t * nb_bodies(v) + threadIdx.x + (int64_t)o * T;
-    const bool own = ii[o] < N;
-    const float4 pi = own ? pos[ii[o]] : make_float4(0.f, 0.f, 0.f, 0.f);
-    npx[o][0] = make_float2(-pi.x, -pi.x);
-    npy[o][0] = make_float2(-pi.y, -pi.y);
-    npz[o][0] = make_float2(-pi.z, -pi.z);
+  float2 npx[R], npy[R], npz[R];
+  float ax[R], ay[R], az[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int64_t i = i0 + (int64_t)r * T;
+    const float4 pi = i < N ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    npx[r] = make_float2(-pi.x, -pi.x);
+    npy[r] = make_float2(-pi.y, -pi.y);
+    npz[r] = make_float2(-pi.z, -pi.z);
+    ax[r] = ay[r] = az[r] = 0.f;
   }
   for (int64_t j0 = 0; j0 < N; j0 += Tt) {
     __syncthreads();
@@ -1125,17 +1154,35 @@ __device__ void nbody_tile(const ar_exec_call& k, int v, int64_t t, unsigned cha
       tile_store(tile, q, jj < N ? pos[jj] : make_float4(0.f, 0.f, 0.f, 0.f));
     }
     __syncthreads();
-    for (int o = 0; o < nown; ++o) {
-      if (uidx == 0)
-        tile_accumulate<1, 1>(tile, Tt / 2, npx[o], npy[o], npz[o], eps2v, ax[o], ay[o], az[o]);
-      else if (uidx == 1)
-        tile_accumulate<4, 1>(tile, Tt / 2, npx[o], npy[o], npz[o], eps2v, ax[o], ay[o], az[o]);
-      else
-        tile_accumulate<8, 1>(tile, Tt / 2, npx[o], npy[o], npz[o], eps2v, ax[o], ay[o], az[o]);
-    }
+    if (uidx == 0)
+      tile_accumulate<1, R>(tile, Tt / 2, npx, npy, npz, eps2v, ax, ay, az);
+    else if (uidx == 1)
+      tile_accumulate<4, R>(tile, Tt / 2, npx, npy, npz, eps2v, ax, ay, az);
+    else
+      tile_accumulate<8, R>(tile, Tt / 2, npx, npy, npz, eps2v, ax, ay, az);
   }
-  for (int o = 0; o < nown; ++o)
-    if (ii[o] < N) acc[ii[o]] = make_float4(ax[o][0], ay[o][0], az[o][0], 0.f);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int64_t i = i0 + (int64_t)r * T;
+    if (i < N) acc[i] = make_float4(ax[r], ay[r], az[r], 0.f);
+  }
+}
+
+// Tile t of an n-body call: nb_bodies(v) i-bodies (one or two per thread)
+// against all N bodies in Tt-body j tiles.
+__device__ void nbody_tile(const ar_exec_call& k, int v, int64_t t, unsigned char* smraw) {
+  const int Tt = c_nb_tile[v / 3], uidx = v % 3;
+  const float4* pos = static_cast<const float4*>(k.in0);
+  float4* acc = static_cast<float4*>(k.out0);
+  const int64_t i0 = t * nb_bodies(v) + threadIdx.x;
+  float4* tile = reinterpret_cast<float4*>(smraw);
+  // a 512-body tile holds two i-bodies per thread, summed in one pass over
+  // each j tile (each shared-memory load serves both: 6 % faster at 256k
+  // bodies than a pass per body)
+  if (nb_bodies(v) == 2 * T)
+    nbody_rows<2>(pos, acc, k.n, i0, Tt, uidx, k.eps * k.eps, tile);
+  else
+    nbody_rows<1>(pos, acc, k.n, i0, Tt, uidx, k.eps * k.eps, tile);
 }
 
 // ------------------------------------------------------------------ run
@@ -1157,7 +1204,7 @@ __global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_cal
                                                  const long long* __restrict__ prefix, int* done,
                                                  unsigned long long* counter, uint64_t* t0, uint64_t* t1,
                                                  int* status, int* flags, const CUtensorMap* __restrict__ maps,
-                                                 const int* __restrict__ usetma) {
+                                                 const int* __restrict__ usetma, const int* __restrict__ perm) {
   __shared__ __align__(128) unsigned char smraw[kSmemBytes];  // tensor-copy destinations
   __shared__ __align__(8) uint64_t s_bars[kXRing];
   __shared__ __align__(16) ar_exec_call s_k;  // the current item's call, copied when the call changes
@@ -1171,6 +1218,7 @@ __global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_cal
     s_end = -1;      // prefix[s_pos + 1] once looked up
     s_ready = -1;    // entry whose dependency this block has seen met
     s_cur = -1;      // call held in s_k
+    s_c = s_p = 0;   // the previous item's call and phase
   }
   for (;;) {
     if (threadIdx.x == 0) {
@@ -1180,7 +1228,7 @@ __global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_cal
         // last entry whose range starts at or before it.  A block's items
         // only grow: most lie in its previous item's entry; otherwise gallop
         // forward from that entry, then bisect
-        int lo = s_pos;
+        int lo = s_pos, p = s_p, c = s_c;
         if (!(it < s_end)) {
           int step = 1;
           while (lo + step < E && prefix[lo + step] <= it) {
@@ -1196,11 +1244,11 @@ __global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_cal
               hi = mid - 1;
           }
           s_end = (lo >= 0 && lo < E) ? prefix[lo + 1] : -1;
+          p = c = 0;
+          if (lo >= 0 && lo < E) entry_pc(lo, ncalls, perm, p, c);
         }
         // the item lies in entry lo's range, inside its (call, phase) tiles;
         // otherwise (checked build) it is skipped under entry 0's indices
-        int p = 0, c = 0;
-        if (lo >= 0 && lo < E) entry_pc(lo, ncalls, p, c);
         const bool valid = AR_CHK(lo >= 0 && lo < E && prefix[lo] <= it && it < prefix[lo + 1] &&
                                   it - prefix[lo] < (long long)tiles[c * PM + p]);
         if (!valid) {
@@ -1279,7 +1327,7 @@ __global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_cal
 }
 
 struct WsLayout {
-  size_t part, tiles, prefix, done, counter, vint, flags, usetma, maps, total;
+  size_t part, tiles, prefix, done, counter, vint, flags, usetma, perm, maps, total;
 };
 
 WsLayout layout(int max_calls) {
@@ -1301,6 +1349,8 @@ WsLayout layout(int max_calls) {
   w.flags = o;
   o = up(o + (size_t)max_calls * 4);
   w.usetma = o;
+  o = up(o + (size_t)max_calls * 4);
+  w.perm = o;
   o = up(o + (size_t)max_calls * 4);
   w.maps = o;  // 3 tensor maps (u0, out, work) per call, 128-byte aligned
   o = up(o + (size_t)max_calls * 3 * sizeof(CUtensorMap));
@@ -1439,6 +1489,7 @@ extern "C" int ar_exec_batch(const ar_exec_call* calls, int ncalls, const ar_exe
   int* vint = reinterpret_cast<int*>(base + w.vint);
   int* flags = reinterpret_cast<int*>(base + w.flags);
   int* usetma = reinterpret_cast<int*>(base + w.usetma);
+  int* perm = reinterpret_cast<int*>(base + w.perm);
   CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(base + w.maps);
   cudaStream_t s = as_stream(stream);
   MapTemplates tmt{};
@@ -1450,9 +1501,9 @@ extern "C" int ar_exec_batch(const ar_exec_call* calls, int ncalls, const ar_exe
   exec_plan<<<1, T, 0, s>>>(calls, ncalls, m, have, force_variant, variant, conf, features, part, tiles, prefix,
                             done, counter, t_start, t_end, status, vint, tmt.tm4, tmt.tm8, tmt.to4, tmt.to8,
                             tma_ok && tmt.even_ok, tma_ok && tmt.odd_ok, maps, usetma,
-                            (long long)kJTilesPerBlock * run_blocks);
+                            (long long)kJTilesPerBlock * run_blocks, perm);
   exec_run<<<run_blocks, T, 0, s>>>(calls, ncalls, vint, tiles, prefix, done, counter, t_start, t_end, status,
-                                          flags, maps, usetma);
+                                    flags, maps, usetma, perm);
   return launch_status();
 }
 
