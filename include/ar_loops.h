@@ -325,7 +325,9 @@ int ar_split_threads(void);
  *      default variant if that is NULL) with its confidence -- and the
  *      table of work items (one phase per Jacobi sweep; two for merge-path
  *      SpMV, main pass and carry fix-up; one otherwise), ordered by groups
- *      of 64 consecutive calls and phase-major inside a group;
+ *      of 64 consecutive calls and phase-major inside a group, a group's
+ *      calls inside a phase longest estimated item first (an n-body item
+ *      of a large N before the short memory-bound items);
  *   3. run: a persistent kernel whose blocks pull work items from an atomic
  *      counter and run the chosen variant's tile of that call.  An item of
  *      phase p waits (bounded) until every item of phase p-1 of its call is
