@@ -504,40 +504,55 @@ def run_ours(args):
                        "explore_overhead_pct": 100 * (explore_ms / (calls * ms_n[best]) - 1)})
 
     # --- end to end through the library's host-buffer call (ar_invoke_host):
-    # per N its own stream carrying the copy of u0 in, the selected variant's
-    # sweeps and the copy of the result out (one cudaMemcpyAsync each way);
-    # the six streams overlap one grid's copies with another's sweeps
+    # per N and lane its own stream carrying the copy of u0 in, the selected
+    # variant's sweeps and the copy of the result out (one cudaMemcpyAsync
+    # each way).  Steps alternate between two lanes (own device grids, status
+    # arrays and host result buffers), so one step's copies out overlap the
+    # next step's copies in on the duplex link, and the streams of different
+    # N overlap one grid's copies with another's sweeps
+    lanes = 2
     host_in = {n: bufs[n][0].cpu().pin_memory() for n in SIZES}
-    host_out = {n: torch.empty_like(host_in[n]).pin_memory() for n in SIZES}
-    e2e_steps = max(3, min(args.steps, 10))
-    streams = {n: torch.cuda.Stream(device=dev) for n in SIZES}
+    lane_bufs = {n: [bufs[n]] + [[torch.empty_like(b) for b in bufs[n]] for _ in range(lanes - 1)] for n in SIZES}
+    lane_status = {n: [torch.zeros(2, dtype=torch.int32, device=dev) for _ in range(lanes)] for n in SIZES}
+    lane_args = {n: [stencil_args(ar, kind, n, SWEEPS, [b.data_ptr() for b in lane_bufs[n][q]],
+                                  lane_status[n][q].data_ptr()) for q in range(lanes)] for n in SIZES}
+    host_out = {n: [torch.empty_like(host_in[n]).pin_memory() for _ in range(lanes)] for n in SIZES}
+    e2e_steps = max(4, min(args.steps, 10))
+    streams = {n: [torch.cuda.Stream(device=dev) for _ in range(lanes)] for n in SIZES}
     order = sorted(SIZES, reverse=True)
-    copies = {n: ([(host_in[n], bufs[n][0], 8 * n ** 3)], [(host_out[n], bufs[n][1], 8 * n ** 3)]) for n in SIZES}
+    copies = {n: [([(host_in[n], lane_bufs[n][q][0], 8 * n ** 3)], [(host_out[n][q], lane_bufs[n][q][1], 8 * n ** 3)])
+                  for q in range(lanes)] for n in SIZES}
     torch.cuda.synchronize()
     a0 = torch.cuda.Event(enable_timing=True)
     a1 = torch.cuda.Event(enable_timing=True)
     a0.record(stream)
     for n in SIZES:
-        streams[n].wait_event(a0)
+        for q in range(lanes):
+            streams[n][q].wait_event(a0)
     for k in range(e2e_steps):
+        q = k % lanes
         for n in order:
-            region.invoke_host([n, SWEEPS], argblocks[n], *copies[n], stream=streams[n])
+            region.invoke_host([n, SWEEPS], lane_args[n][q], *copies[n][q], stream=streams[n][q])
     for n in SIZES:
-        stream.wait_stream(streams[n])
+        for q in range(lanes):
+            stream.wait_stream(streams[n][q])
     a1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = a0.elapsed_time(a1) / e2e_steps
     ref0 = bufs[big][1].cpu()
-    assert torch.equal(host_out[big], ref0), "host result differs from the device result"
+    for q in range(lanes):
+        assert torch.equal(host_out[big][q], ref0), "host result differs from the device result"
+    assert all(int(t[0]) == 0 for n in SIZES for t in lane_status[n]), "a status array reports an error"
     h2d = sum(8 * n ** 3 for n in SIZES)
     e2e = {"value": step_bytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": h2d, "ms_per_step": e2e_ms,
            "note": "ar_invoke_host per N (pinned host u0 in, the region's selected variant, result out), "
-                   "one stream per N"}
+                   "steps alternating between two lanes of device grids, one stream per N and lane"}
+    del lane_bufs, lane_args, lane_status, host_out, host_in, copies, streams
 
     configs = None
     if rank == 0 and ws == 1 and kind == "jacobi7" and not args.no_configs:
-        del bufs, argblocks, flush, host_in, host_out
+        del bufs, argblocks, flush
         torch.cuda.empty_cache()
         configs = other_configs(args)
 

@@ -83,8 +83,10 @@ int ar_daxpy(int variant, int64_t n, double a, const double *x, double *y, void 
  * kernel.  Default: naive 32x8 (variant 1).
  * `status` (device int[2], may be NULL): status[0] receives AR_ERR_TIMEOUT if
  * a bounded wait inside a tma/df kernel gave up (the caller zeroes it);
- * status[1] is scratch for the df family, which with a status array and 2+
- * sweeps keeps float pairs (8 bytes per unknown) in out/work between sweeps
+ * status[1] is scratch for the df family (calls that may run at the same
+ * time on different streams need their own status arrays), which with a
+ * status array and 2+ sweeps keeps float pairs (8 bytes per unknown) in
+ * out/work between sweeps
  * and, when an input lies outside the float-pair range, recomputes the whole
  * call in float64 (one extra launch at the end, which otherwise exits at
  * once).  Without a status array every df sweep converts from and to
