@@ -907,6 +907,7 @@ def mixed_record(n_calls, tau, reps_fb=2, regret_sample=96):
         N = int(size)
         c.n, c.eps = N, synth.NBODY_EPS
         c.in0, c.out0 = a32.take(16 * N), sc.take(16 * N)
+        c.out1, c.out1_bytes = sc.take(16 * N * 8), 16 * N * 8  # partial sums of up to 8 j chunks
         return c, 0.0, NBODY_FLOPS * N * N
 
     def arenas():

@@ -337,7 +337,14 @@ int ar_split_threads(void);
  *      group's items are handed out before the next group's, so a call's
  *      latency is about its group's rather than the whole batch's.
  * The tiles compute exactly what the stand-alone variants compute (same
- * data, same tolerances).  Jacobi tiles of the tma and df families with
+ * data, same tolerances).  An n-body call whose tiles of i-bodies are
+ * fewer than the persistent kernel's blocks may hand its j range out in
+ * chunks: when out1 is 16-byte aligned, distinct from in0 and out0, and
+ * holds S >= 2 arrays of N float4 (out1_bytes >= 32 N), each tile sums one
+ * (i tile, j chunk) into array s and a second phase adds each body's S
+ * partials in chunk order into out0 (S at most what out1_bytes holds, one
+ * j tile per chunk at least; deterministic, the sum order differs from the
+ * unsplit call's).  Without such an out1 the call runs unsplit.  Jacobi tiles of the tma and df families with
  * shapes 32x4 and 32x8 stage their planes by tensor copies when N is even,
  * N >= 36 and u0/out/work are 16-byte aligned (through tensor maps the plan
  * kernel makes on the device from host-encoded templates; the first batch
@@ -372,8 +379,10 @@ typedef struct ar_exec_call {
   float eps;      /* n-body softening */
   int32_t reserved;
   const void *in0, *in1, *in2, *in3; /* daxpy x | Jacobi u0 | SpMV rowptr, col, val, x | n-body pos4 */
-  void *out0, *out1;                 /* daxpy y | Jacobi out, work | SpMV y, merge-path workspace | n-body acc4 */
-  uint64_t out1_bytes;               /* SpMV: merge-path workspace bytes (16 per 4096 rows+nnz) */
+  void *out0, *out1;                 /* daxpy y | Jacobi out, work | SpMV y, merge-path workspace |
+                                        n-body acc4, optional partial-sum workspace (see below) */
+  uint64_t out1_bytes;               /* SpMV: merge-path workspace bytes (16 per 4096 rows+nnz);
+                                        n-body: partial-sum workspace bytes */
 } ar_exec_call;
 typedef struct ar_exec_models {
   int32_t F[4], V[4], H; /* per loop: features (1, 3, 5, 1), variants (must match the loop); hidden 32/64 */

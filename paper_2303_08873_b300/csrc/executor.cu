@@ -97,14 +97,40 @@ __device__ __forceinline__ bool jacobi_pair_chain(const ar_exec_call& c, int v) 
   return c.loop == AR_LOOP_JACOBI7 && v / 4 == 3 && c.sweeps >= 2 && c.sweeps + 1 <= PM;
 }
 
-__device__ __forceinline__ int phases_of(const ar_exec_call& c, int v) {
-  if (c.loop == AR_LOOP_JACOBI7) return c.sweeps + (jacobi_pair_chain(c, v) ? 1 : 0);
-  if (c.loop == AR_LOOP_SPMV && v >= 6) return 2;  // merge path: blocks, then the carry fix-up
-  return 1;
-}
-
 // n-body i-bodies per tile: one per thread, two for 512-body tiles.
 __device__ __forceinline__ int nb_bodies(int v) { return c_nb_tile[v / 3] > T ? c_nb_tile[v / 3] : T; }
+
+// Chunks an n-body call's j range is split over, S, and the j bodies per
+// chunk (whole Tt-body j tiles).  S > 1 only when the call's i tiles number
+// fewer than `target` and its out1 holds S partial-sum arrays (16 N bytes
+// each, 16-byte aligned, apart from the positions and accelerations): then
+// the tiles of phase 0 each sum one (i tile, j chunk) into out1 and phase 1
+// adds the S partials per body in chunk order.
+struct NbSplit {
+  int S;
+  int64_t chunk;
+};
+__device__ NbSplit nbody_split(const ar_exec_call& k, int v, long long target) {
+  const int64_t N = k.n, Tt = c_nb_tile[v / 3];
+  const int64_t ti = cdiv(N, nb_bodies(v));
+  NbSplit r{1, N};
+  if (N <= 0 || ti >= target || !k.out1 || ((uintptr_t)k.out1 & 15u) != 0 || k.out1 == k.in0 ||
+      k.out1 == k.out0)
+    return r;
+  int64_t S = min(cdiv(target, ti), cdiv(N, Tt));
+  S = min(S, (int64_t)(k.out1_bytes / (16ull * (uint64_t)N)));
+  if (S <= 1) return r;
+  r.chunk = cdiv(cdiv(N, S), Tt) * Tt;
+  r.S = (int)cdiv(N, r.chunk);  // no empty chunk
+  return r;
+}
+
+__device__ __forceinline__ int phases_of(const ar_exec_call& c, int v, long long target) {
+  if (c.loop == AR_LOOP_JACOBI7) return c.sweeps + (jacobi_pair_chain(c, v) ? 1 : 0);
+  if (c.loop == AR_LOOP_SPMV && v >= 6) return 2;  // merge path: blocks, then the carry fix-up
+  if (c.loop == AR_LOOP_NBODY && nbody_split(c, v, target).S > 1) return 2;  // chunk partials, then their sum
+  return 1;
+}
 
 // Planes per Jacobi tile of an N^3 call run by variant v: as many as keep
 // the call's tiles at least `target` (kJTilesPerBlock per block of the
@@ -133,7 +159,10 @@ __device__ int64_t tiles_of(const ar_exec_call& c, int v, int p, long long jtarg
       const int64_t nb = cdiv(c.n + c.nnz, kMpPerTile);
       return p == 0 ? nb : cdiv(nb, T);
     }
-    default: return cdiv(c.n, nb_bodies(v));
+    default: {
+      const NbSplit sp = nbody_split(c, v, jtarget);
+      return p == 0 ? cdiv(c.n, nb_bodies(v)) * sp.S : cdiv(c.n, T);
+    }
   }
 }
 
@@ -152,7 +181,7 @@ __device__ float item_ns(const ar_exec_call& k, int v, long long jtarget) {
                                   : (float)kMpPerTile;
       return items * 12.f / 8.8f;
     }
-    default: return (float)nb_bodies(v) * (float)k.n * 20.f / 81.f;
+    default: return (float)nb_bodies(v) * (float)nbody_split(k, v, jtarget).chunk * 20.f / 81.f;
   }
 }
 
@@ -360,7 +389,7 @@ __global__ void __launch_bounds__(T) exec_plan(const ar_exec_call* __restrict__ 
     if (st == AR_OK && k.loop == AR_LOOP_DAXPY && v % 3 != 0 &&
         (((uintptr_t)k.in0 | (uintptr_t)k.out0) & 15u) != 0)
       v -= v % 3;  // double2 variants need 16-byte alignment: one element per thread
-    const int ph = st == AR_OK ? phases_of(k, v) : 0;
+    const int ph = st == AR_OK ? phases_of(k, v, jtarget) : 0;
     for (int p = 0; p < PM; ++p) {
       tiles[c * PM + p] = p < ph ? (int)tiles_of(k, v, p, jtarget) : 0;
       done[c * PM + p] = 0;
@@ -1129,29 +1158,32 @@ __device__ void spmv_tile(const ar_exec_call& k, int v, int p, int64_t t, unsign
     mp::block<true, kMpBatchExec>(rows, nnz, rp, col, val, x, y, db, i0, i1, carry_row + t, carry_val + t, smraw);
 }
 
-// R i-bodies per thread (bodies i0 + r T) against all N bodies, j tiles of
-// Tt bodies staged in shared memory in the pair layout of nbody_math.cuh;
-// one pass over each tile serves all R.
+// R i-bodies per thread (bodies i0 + r T) against the bodies [jb, je), j
+// tiles of Tt bodies staged in shared memory in the pair layout of
+// nbody_math.cuh; one pass over each tile serves all R.  The sums go to
+// out[i].
 template <int R>
-__device__ __forceinline__ void nbody_rows(const float4* __restrict__ pos, float4* __restrict__ acc, int64_t N,
-                                           int64_t i0, int Tt, int uidx, float eps2, float4* tile) {
+__device__ __forceinline__ void nbody_rows(const float4* __restrict__ pos, float4* __restrict__ out, int64_t N,
+                                           int64_t i0, int64_t jb, int64_t je, int Tt, int uidx, float eps2,
+                                           float4* tile) {
   const float2 eps2v = make_float2(eps2, eps2);
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
   float2 npx[R], npy[R], npz[R];
   float ax[R], ay[R], az[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int64_t i = i0 + (int64_t)r * T;
-    const float4 pi = i < N ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 pi = i < N ? pos[i] : zero;
     npx[r] = make_float2(-pi.x, -pi.x);
     npy[r] = make_float2(-pi.y, -pi.y);
     npz[r] = make_float2(-pi.z, -pi.z);
     ax[r] = ay[r] = az[r] = 0.f;
   }
-  for (int64_t j0 = 0; j0 < N; j0 += Tt) {
+  for (int64_t j0 = jb; j0 < je; j0 += Tt) {
     __syncthreads();
     for (int q = threadIdx.x; q < Tt; q += T) {
       const int64_t jj = j0 + q;
-      tile_store(tile, q, jj < N ? pos[jj] : make_float4(0.f, 0.f, 0.f, 0.f));
+      tile_store(tile, q, jj < je ? pos[jj] : zero);  // zero mass past the range adds exactly 0
     }
     __syncthreads();
     if (uidx == 0)
@@ -1164,25 +1196,49 @@ __device__ __forceinline__ void nbody_rows(const float4* __restrict__ pos, float
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int64_t i = i0 + (int64_t)r * T;
-    if (i < N) acc[i] = make_float4(ax[r], ay[r], az[r], 0.f);
+    if (i < N) out[i] = make_float4(ax[r], ay[r], az[r], 0.f);
   }
 }
 
-// Tile t of an n-body call: nb_bodies(v) i-bodies (one or two per thread)
-// against all N bodies in Tt-body j tiles.
-__device__ void nbody_tile(const ar_exec_call& k, int v, int64_t t, unsigned char* smraw) {
+// Tile t of phase p of an n-body call whose j range is split into S chunks
+// of `chunk` bodies (nbody_split; S = 1: not split).  Phase 0: nb_bodies(v)
+// i-bodies (one or two per thread) against one chunk (all N bodies when not
+// split), into acc or, split, into partial-sum array s of out1; tile t is
+// (chunk t / i-tiles, i-tile t mod i-tiles).  Phase 1: T bodies per tile,
+// each body's S partials added in chunk order.
+__device__ void nbody_tile(const ar_exec_call& k, int v, int p, int64_t t, int S, int64_t chunk,
+                           unsigned char* smraw) {
+  const int64_t N = k.n;
+  float4* acc = static_cast<float4*>(k.out0);
+  float4* part = static_cast<float4*>(k.out1);
+  if (p == 1) {  // written in this launch by other blocks: L1-bypassing loads
+    const int64_t i = t * T + threadIdx.x;
+    if (i >= N) return;
+    float4 a = __ldcg(part + i);
+    for (int s = 1; s < S; ++s) {
+      const float4 q = __ldcg(part + (int64_t)s * N + i);
+      a.x += q.x;
+      a.y += q.y;
+      a.z += q.z;
+    }
+    acc[i] = make_float4(a.x, a.y, a.z, 0.f);
+    return;
+  }
   const int Tt = c_nb_tile[v / 3], uidx = v % 3;
   const float4* pos = static_cast<const float4*>(k.in0);
-  float4* acc = static_cast<float4*>(k.out0);
-  const int64_t i0 = t * nb_bodies(v) + threadIdx.x;
+  const int64_t ti = cdiv(N, nb_bodies(v));
+  const int64_t s = S > 1 ? t / ti : 0, it = S > 1 ? t % ti : t;
+  const int64_t i0 = it * nb_bodies(v) + threadIdx.x;
+  const int64_t jb = s * chunk, je = S > 1 ? min(N, jb + chunk) : N;
+  float4* out = S > 1 ? part + s * N : acc;
   float4* tile = reinterpret_cast<float4*>(smraw);
   // a 512-body tile holds two i-bodies per thread, summed in one pass over
   // each j tile (each shared-memory load serves both: 6 % faster at 256k
   // bodies than a pass per body)
   if (nb_bodies(v) == 2 * T)
-    nbody_rows<2>(pos, acc, k.n, i0, Tt, uidx, k.eps * k.eps, tile);
+    nbody_rows<2>(pos, out, N, i0, jb, je, Tt, uidx, k.eps * k.eps, tile);
   else
-    nbody_rows<1>(pos, acc, k.n, i0, Tt, uidx, k.eps * k.eps, tile);
+    nbody_rows<1>(pos, out, N, i0, jb, je, Tt, uidx, k.eps * k.eps, tile);
 }
 
 // ------------------------------------------------------------------ run
@@ -1209,7 +1265,8 @@ __global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_cal
   __shared__ __align__(8) uint64_t s_bars[kXRing];
   __shared__ __align__(16) ar_exec_call s_k;  // the current item's call, copied when the call changes
   __shared__ long long s_item, s_t, s_next, s_end;
-  __shared__ int s_c, s_p, s_ok, s_v, s_tma, s_flagged, s_pos, s_ready, s_cur, s_kc;
+  __shared__ int s_c, s_p, s_ok, s_v, s_tma, s_flagged, s_pos, s_ready, s_cur, s_geo;
+  __shared__ long long s_chunk;
   const int E = PM * ncalls;
   const long long total = prefix[E];
   if (threadIdx.x == 0) {
@@ -1264,11 +1321,21 @@ __global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_cal
           s_v = vint[c];
           s_tma = usetma[c];
           s_cur = c;
-          // a Jacobi call's planes per tile (the plan counted its tiles by
-          // the same rule and the same block count)
-          s_kc = s_k.loop == AR_LOOP_JACOBI7 && s_v >= 0 && s_v < c_nvar[AR_LOOP_JACOBI7]
-                     ? jacobi_kc((int)s_k.n, s_v, (long long)kJTilesPerBlock * gridDim.x)
-                     : 0;
+          // the call's tile geometry, by the rules and the block count the
+          // plan counted its tiles with: a Jacobi call's planes per tile, an
+          // n-body call's j chunks and their length
+          s_geo = 0;
+          s_chunk = 0;
+          const long long target = (long long)kJTilesPerBlock * gridDim.x;
+          if (s_k.loop >= 0 && s_k.loop < 4 && s_v >= 0 && s_v < c_nvar[s_k.loop]) {
+            if (s_k.loop == AR_LOOP_JACOBI7) {
+              s_geo = jacobi_kc((int)s_k.n, s_v, target);
+            } else if (s_k.loop == AR_LOOP_NBODY) {
+              const NbSplit sp = nbody_split(s_k, s_v, target);
+              s_geo = sp.S;
+              s_chunk = sp.chunk;
+            }
+          }
           if (ok) atomicMin((unsigned long long*)t0 + c, (unsigned long long)gtimer());
         }
         // phase p > 0 waits once per entry for all of phase p - 1 (counters
@@ -1304,13 +1371,13 @@ __global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_cal
       switch (k.loop) {
         case AR_LOOP_DAXPY: daxpy_tile(k, v, t); break;
         case AR_LOOP_JACOBI7:
-          if (!jacobi_tile(k, v, p, t, s_kc, s_flagged != 0, flags + c, smraw, s_tma ? maps + 3 * c : nullptr,
+          if (!jacobi_tile(k, v, p, t, s_geo, s_flagged != 0, flags + c, smraw, s_tma ? maps + 3 * c : nullptr,
                            s_bars) &&
               threadIdx.x == 0)
             atomicExch(status + c, (int)AR_ERR_TIMEOUT);
           break;
         case AR_LOOP_SPMV: spmv_tile(k, v, p, t, smraw); break;
-        default: nbody_tile(k, v, t, smraw); break;
+        default: nbody_tile(k, v, p, t, s_geo, s_chunk, smraw); break;
       }
     }
     __syncthreads();

@@ -12,7 +12,8 @@ rate.
   python -m paper_2303_08873_b300.run_variant daxpy 8 --size 33554432
 
 With ``--exec`` the same call also runs as a one-call batch of the persistent
-mixed-stream executor (``ar_exec_batch``, variant forced) and both rates are
+mixed-stream executor (``ar_exec_batch``, variant forced; an n-body call
+carries a partial-sum workspace for up to 64 j chunks) and both rates are
 printed.  With ``--floor`` (spmv) the gather-floor measurement kernel
 (``ar_spmv_gather_floor``) is timed on the same matrix.  Variant ``all`` runs
 every variant of the loop in turn (one line each), e.g. for a per-variant ncu
@@ -92,7 +93,9 @@ def main():
         pos = torch.from_numpy(synth.nbody_inputs(4, a.size)).to(dev)
         acc = torch.empty_like(pos)
         make_run = lambda var: lambda: ar.ar_nbody(var, a.size, pos, acc, synth.NBODY_EPS)  # noqa: E731
-        call = ar.ArExecCall(loop=3, n=a.size, eps=synth.NBODY_EPS, in0=pos.data_ptr(), out0=acc.data_ptr())
+        part = torch.empty(a.size * 4 * 64, dtype=torch.float32, device=dev)  # partial sums of up to 64 j chunks
+        call = ar.ArExecCall(loop=3, n=a.size, eps=synth.NBODY_EPS, in0=pos.data_ptr(), out0=acc.data_ptr(),
+                             out1=part.data_ptr(), out1_bytes=part.numel() * 4)
         work, unit = 20.0 * a.size ** 2, "GFLOP/s"
 
     def timed(fn):

@@ -64,14 +64,22 @@ class Batch:
         self.check.append(lambda y=y, ref=ref, absum=absum: np.all(np.abs(host(y) - ref) <= 1e-10 * absum))
         return loops.csr_row_stats(rph)
 
-    def nbody(self, N, seed, negate=None):
+    def nbody(self, N, seed, negate=None, ws_bytes=0, ws_offset=0):
+        """ws_bytes > 0: a partial-sum workspace in out1 (filled with NaN),
+        starting ws_offset bytes into its allocation; returned."""
         p = synth.nbody_inputs(seed, N)
         if negate is not None:
             p[negate, 3] *= -1.0
         pd = dev(p)
         acc = torch.full((N, 4), np.nan, dtype=torch.float32, device="cuda")
         self.keep += [pd, acc]
-        self.calls.append(ar.ArExecCall(loop=3, n=N, eps=EPS, in0=pd.data_ptr(), out0=acc.data_ptr()))
+        call = ar.ArExecCall(loop=3, n=N, eps=EPS, in0=pd.data_ptr(), out0=acc.data_ptr())
+        ws = None
+        if ws_bytes > 0:
+            ws = torch.full(((ws_bytes + ws_offset + 3) // 4,), np.nan, dtype=torch.float32, device="cuda")
+            self.keep.append(ws)
+            call.out1, call.out1_bytes = ws.data_ptr() + ws_offset, ws_bytes
+        self.calls.append(call)
         ref = loops.nbody(p, EPS)
         scale = np.max(np.linalg.norm(ref, axis=1))
 
@@ -79,6 +87,7 @@ class Batch:
             a = host(acc)
             return np.max(np.linalg.norm(a[:, :3] - ref, axis=1)) <= 1e-4 * scale and np.all(a[:, 3] == 0)
         self.check.append(ok)
+        return ws
 
     def run(self, force=None, models=None, stream=None):
         n = len(self.calls)
@@ -223,6 +232,39 @@ def test_jacobi_deep_tiles():
     assert np.all(r["status"] == 0)
     for k, ok in enumerate(b.check):
         assert ok(), (k, force[k])
+
+
+def test_nbody_j_chunks_with_a_partials_workspace():
+    """An n-body call with fewer i tiles than the persistent kernel has blocks
+    splits its j range over chunks when out1 holds the partial sums (16 N
+    bytes per chunk, 16-byte aligned); a second phase adds each body's
+    partials in chunk order.  Chunk edges one body past a j tile (N = 129),
+    a last chunk shorter than a tile, every variant, a workspace for exactly
+    two chunks, a misaligned one and a call that fits in one j tile (neither
+    splits: the workspace stays untouched), and calls without a workspace,
+    in one batch."""
+    b = Batch()
+    force, cases = [], []
+    big = 64 << 20
+    for k, (N, v, wsb, off, splits) in enumerate([
+            (129, 1, big, 0, True), (700, 7, big, 0, True), (4099, 2, big, 0, True), (20000, 5, big, 0, True),
+            (65536, 7, big, 0, True), (5000, 3, 2 * 16 * 5000, 0, True), (5000, 6, big, 4, False),
+            (100, 4, big, 0, False), (3000, 8, 0, 0, False), (1, 0, big, 0, False)]):
+        ws = b.nbody(N, 900 + k, ws_bytes=min(wsb, 16 * N * 1024), ws_offset=off)
+        force.append(v)
+        cases.append((N, ws, off, splits))
+    r = b.run(force=force)
+    assert np.all(r["status"] == 0)
+    for k, ok in enumerate(b.check):
+        assert ok(), (k, force[k])
+    for N, ws, off, splits in cases:
+        if ws is None:
+            continue
+        first = ws.cpu().numpy()[off // 4: off // 4 + 4 * N]  # partial-sum array of chunk 0
+        if splits:
+            assert np.all(np.isfinite(first)), N
+        else:
+            assert np.all(np.isnan(ws.cpu().numpy())), N
 
 
 def test_bad_variant_and_loop_are_reported_per_call():
