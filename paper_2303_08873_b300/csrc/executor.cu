@@ -1105,26 +1105,33 @@ __device__ void spmv_tile(const ar_exec_call& k, int v, int p, int64_t t, unsign
   const double* x = static_cast<const double*>(k.in3);
   double* y = static_cast<double*>(k.out0);
   const int64_t rows = k.n, nnz = k.nnz;
-  if (v == 0) {  // kSpPasses groups of T rows, one row per thread
-    for (int g = 0; g < kSpPasses; ++g) {
-      const int64_t r = (t * kSpPasses + g) * T + threadIdx.x;
-      if (r < rows) {
-        double s = 0.0;
-        for (int e = __ldg(rp + r); e < __ldg(rp + r + 1); ++e) s = fma(__ldg(val + e), __ldg(x + __ldg(col + e)), s);
-        y[r] = s;
-      }
-    }
-    return;
-  }
-  if (v < 6) {  // kSpPasses groups of T/K rows, K lanes per row
-    const int K = c_sp_k[v - 1];
+  if (v < 6) {  // kSpPasses groups of T/K rows, K lanes per row (thread-row: K = 1)
+    const int K = v == 0 ? 1 : c_sp_k[v - 1];
     const int lane = threadIdx.x % K;
     for (int g = 0; g < kSpPasses; ++g) {
       const int64_t r = (t * kSpPasses + g) * (T / K) + threadIdx.x / K;
       double s = 0.0;
-      if (r < rows)
-        for (int e = __ldg(rp + r) + lane; e < __ldg(rp + r + 1); e += K)
-          s = fma(__ldg(val + e), __ldg(x + __ldg(col + e)), s);
+      if (r < rows) {
+        // the lane's nonzeros e = b + lane + K m in order, four per step
+        // while four remain (their col and val loads, then their x
+        // gathers, then the FMAs), the rest one at a time
+        const int e1 = __ldg(rp + r + 1);
+        int j0 = __ldg(rp + r) + lane;
+        for (; j0 + 3 * K < e1; j0 += 4 * K) {
+          int cc[4];
+          double vv[4], xv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            cc[u] = __ldg(col + j0 + u * K);
+            vv[u] = __ldg(val + j0 + u * K);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) xv[u] = __ldg(x + cc[u]);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) s = fma(vv[u], xv[u], s);
+        }
+        for (; j0 < e1; j0 += K) s = fma(__ldg(val + j0), __ldg(x + __ldg(col + j0)), s);
+      }
       for (int o = K / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, K);
       if (r < rows && lane == 0) y[r] = s;
     }
