@@ -701,6 +701,10 @@ __device__ bool jacobi_tma_tile(const CUtensorMap* map, int N, int bx, int by, i
 // element x sits at column x - i0 + 2 + b; rows and columns outside the grid
 // are zeroed on edge tiles and the grid's last row (past the view) is loaded
 // by the threads -- the staging of the stand-alone jacobi_tma_odd kernel.
+// The readers take a plane's row-parity offsets from its index r inside the
+// box (r & 1), which is the plane's parity relative to the box's first
+// plane only while every box starts on a plane of the same parity.
+static_assert(kXDZ % 2 == 0, "odd-N tiles need an even box depth");
 template <int BX, int BY>
 struct XOddGeom {
   static constexpr int PX = BX + 4, HB = (BY + 2) / 2;
