@@ -38,6 +38,10 @@ namespace ar {
 namespace {
 
 constexpr int kDZ = 4;     // planes per TMA box
+// jacobi_tma_odd takes a plane's row-parity bundle from its index r inside
+// the box (r & 1), which needs every box to start on a plane of the same
+// parity: an even box depth.
+static_assert(kDZ % 2 == 0, "odd-N tiles need an even box depth");
 constexpr int kRing = 3;   // boxes resident per block
 constexpr int kShapeX[4] = {32, 32, 64, 128};
 constexpr int kShapeY[4] = {4, 8, 4, 2};
