@@ -1102,35 +1102,6 @@ __device__ bool jacobi_tile(const ar_exec_call& k, int v, int p, int64_t t, int 
                            map_of(src_of(p)), bars);
 }
 
-// mp::search by one warp (every lane returns the result): the rows consumed
-// at path diagonal d, the smallest i in [max(0, d - nnz), min(rows, d)] with
-// rowptr[i + 1] + i + 1 > d (the upper end if none).  Each step probes 32
-// evenly spaced points of the range and keeps the part between the last
-// probe below d and the first above, so a range of n rows takes about
-// log_33 n dependent loads instead of log_2 n.
-__device__ int64_t warp_search(int64_t d, int64_t rows, const int* __restrict__ rowptr, int64_t nnz) {
-  const int lane = threadIdx.x & 31;
-  int64_t lo = max((int64_t)0, d - nnz), hi = min(rows, d);
-  while (hi - lo > 32) {
-    const int64_t n = hi - lo;
-    const int64_t q = lo + (int64_t)(lane + 1) * n / 33;  // lo < q < hi
-    const bool above = (int64_t)__ldg(rowptr + q + 1) > d - q - 1;
-    const unsigned m = __ballot_sync(0xffffffffu, above);
-    const int k = m ? __ffs(m) - 1 : 32;
-    const int64_t qk = __shfl_sync(0xffffffffu, q, k & 31), qp = __shfl_sync(0xffffffffu, q, (k + 31) & 31);
-    if (k == 32) {
-      lo = qp + 1;  // every probe below: the answer lies past the last one
-    } else {
-      hi = qk;
-      if (k > 0) lo = qp + 1;
-    }
-  }
-  const int64_t q = lo + lane;
-  const bool above = q < hi && (int64_t)__ldg(rowptr + q + 1) > d - q - 1;
-  const unsigned m = __ballot_sync(0xffffffffu, above);
-  return m ? lo + __ffs(m) - 1 : hi;
-}
-
 __device__ void spmv_tile(const ar_exec_call& k, int v, int p, int64_t t, unsigned char* smraw) {
   const int* rp = static_cast<const int*>(k.in0);
   const int* col = static_cast<const int*>(k.in1);
@@ -1187,7 +1158,7 @@ __device__ void spmv_tile(const ar_exec_call& k, int v, int p, int64_t t, unsign
   int64_t* sbounds = reinterpret_cast<int64_t*>(smraw + mp::kSmemBytes);
   const int64_t db = t * kMpPerTile, de = min(db + kMpPerTile, rows + nnz);
   if (threadIdx.x < 64) {  // warp 0 finds the block's first row, warp 1 its end
-    const int64_t r = warp_search(threadIdx.x < 32 ? db : de, rows, rp, nnz);
+    const int64_t r = mp::search_warp(threadIdx.x < 32 ? db : de, rows, rp, nnz);
     if ((threadIdx.x & 31) == 0) sbounds[threadIdx.x >> 5] = r;
   }
   __syncthreads();
