@@ -38,7 +38,7 @@ constexpr int kSpPasses = 16;            // SpMV row groups per tile (thread-row
 constexpr int kCatchTiles = 512;         // tiles of a df call's catch-up phase
 constexpr uint32_t kDepSpin = 1u << 24;  // dependency polls (with backoff) before giving up
 constexpr int kMpPerTile = mp::kPerBlock;
-constexpr int kMpBatchExec = 4;  // merge-path loads in flight per thread inside the persistent kernel
+constexpr int kMpBatchExec = 8;  // merge-path loads in flight per thread inside the persistent kernel
 constexpr int kRunBlocksPerSm = 5;  // resident blocks of the persistent kernel per SM (registers spill; measured best)
 static_assert(mp::kThreads == T, "merge-path tiles use the executor's block size");
 
