@@ -4,11 +4,20 @@
 // counter and dispatches each to the chosen variant's tile function.
 //
 // Ordering and waits: items are numbered by groups of 64 calls, phase-major
-// inside a group (the group's calls' phase 0, then phase 1, ...), so an item
-// of phase p, which waits for the phase p-1 items of its own call, only ever
-// waits for items handed out before it to blocks that are already running;
-// the wait is bounded and reports AR_ERR_TIMEOUT per call.  Data written inside this launch (Jacobi sweeps,
-// merge-path carries) are read with L1-bypassing loads (ld.global.cg).
+// inside a group (the group's calls' phase 0, then phase 1, ...; inside a
+// phase the longest estimated item first), so an item of phase p, which
+// waits for the phase p-1 items of its own call, only ever waits for items
+// handed out before it to blocks that are already running; the wait is
+// bounded and reports AR_ERR_TIMEOUT per call.  Data written inside this
+// launch (Jacobi sweeps, merge-path carries, n-body chunk partials) are read
+// with L1-bypassing loads (ld.global.cg) or tensor copies.
+//
+// Per item, thread 0 takes the next item index (issued before the previous
+// item's release fence), finds its (call, phase) entry (usually the previous
+// item's, kept in shared memory with the entry's end), and waits for the
+// entry's dependency once per block and entry; the call descriptor and its
+// tile geometry (Jacobi planes per tile, n-body j chunks) are copied to
+// shared memory when the call changes.
 #define AR_TU 5
 #include <cudaTypedefs.h>
 
