@@ -267,6 +267,25 @@ def test_nbody_j_chunks_with_a_partials_workspace():
             assert np.all(np.isnan(ws.cpu().numpy())), N
 
 
+def test_merge_path_calls_of_many_blocks():
+    """Merge-path calls with thousands of path blocks (more than the
+    persistent kernel's blocks, so blocks take several items and the carry
+    fix-up spans many): a 500k-row power-law matrix (~6k path blocks), a
+    400k-row band-33 matrix (~3.3k) and a small one, float64 and float-pair
+    forms, in one batch."""
+    b = Batch()
+    force = []
+    mats = [synth.csr_zipf(41, 500000, 1.5), synth.csr_band(42, 400000, 33), synth.csr_zipf(43, 30000, 1.5)]
+    for k, m in enumerate(mats):
+        for v in (6, 7):
+            b.spmv(m, 1000 + 10 * k + v)
+            force.append(v)
+    r = b.run(force=force)
+    assert np.all(r["status"] == 0)
+    for k, ok in enumerate(b.check):
+        assert ok(), (k, force[k])
+
+
 def test_bad_variant_and_loop_are_reported_per_call():
     b = Batch()
     b.daxpy(1000, 1)
