@@ -86,9 +86,8 @@ int ar_daxpy(int variant, int64_t n, double a, const double *x, double *y, void 
  * status[1] is scratch for the df family (calls that may run at the same
  * time on different streams need their own status arrays), which with a
  * status array and 2+ sweeps keeps float pairs (8 bytes per unknown) in
- * out/work between sweeps
- * and, when an input lies outside the float-pair range, recomputes the whole
- * call in float64 (one extra launch at the end, which otherwise exits at
+ * out/work between sweeps and, when an input lies outside the float-pair
+ * range, recomputes the whole call in float64 (one extra launch at the end, which otherwise exits at
  * once).  Without a status array every df sweep converts from and to
  * float64 and redoes out-of-range points in float64.  The sweeps of one call
  * are chained by programmatic dependent launch (each waits for the previous
@@ -333,7 +332,8 @@ int ar_split_threads(void);
  *   3. run: a persistent kernel whose blocks pull work items from an atomic
  *      counter and run the chosen variant's tile of that call.  An item of
  *      phase p waits (bounded) until every item of phase p-1 of its call is
- *      done; every awaited item was handed out earlier, and all of a
+ *      done (a wait that gives up sets the call's status to AR_ERR_TIMEOUT,
+ *      and the call's later items are then skipped without waiting); every awaited item was handed out earlier, and all of a
  *      group's items are handed out before the next group's, so a call's
  *      latency is about its group's rather than the whole batch's.
  * The tiles compute exactly what the stand-alone variants compute (same

@@ -1364,7 +1364,10 @@ __global__ void __launch_bounds__(T, kRunBlocksPerSm) exec_run(const ar_exec_cal
         // then: only its first sweep raises it
         if (ok && lo != s_ready) {
           if (p > 0) {
-            if (!dep_wait(done + c * PM + p - 1, tiles[c * PM + p - 1], kDepSpin)) {
+            // a call whose wait already gave up skips its later items at
+            // once, so one lost dependency costs one bounded wait per block
+            if (reinterpret_cast<volatile int*>(status)[c] == (int)AR_ERR_TIMEOUT ||
+                !dep_wait(done + c * PM + p - 1, tiles[c * PM + p - 1], kDepSpin)) {
               ok = 0;
               atomicExch(status + c, (int)AR_ERR_TIMEOUT);
             }
