@@ -38,7 +38,7 @@ namespace {
 
 constexpr int T = 256;                   // threads per executor block
 constexpr int PM = AR_EXEC_MAX_PHASES;   // phases per call
-constexpr int kJKCMax = 62;              // Jacobi planes per tile at most (64 loaded: 16 four-plane boxes)
+constexpr int kJKCMax = 94;              // Jacobi planes per tile at most (96 loaded: 24 four-plane boxes)
 constexpr int kJBox = 4;                 // planes per tensor-copy box of the Jacobi tiles
 constexpr int kJTilesPerBlock = 1;       // a Jacobi call's tiles per persistent block, at least (if N allows)
 constexpr int kJB = 4;                   // Jacobi planes whose loads are issued together

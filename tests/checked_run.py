@@ -1,5 +1,5 @@
 """Every variant of every loop, the batched n-body and one executor batch at
-small sizes (plus three Jacobi calls near N = 300 that take the executor's
+small sizes (plus three Jacobi calls of N 258-377 that take the executor's
 deepest plane chunks), run in the bounds-check build of the library; prints a JSON
 line with the check status and the parity of each result against the
 oracle.  Run as a child process with AR_CHECKED=1 (tests/test_gpu_checked.py)."""
@@ -81,7 +81,7 @@ def main():
     for v in range(16):
         b.jacobi(37 if v % 2 else 40, 3, 60 + v)
         force.append(v)
-    for N, v in ((310, 13), (311, 12), (258, 15)):  # 62-plane tiles; last chunks of 62, 1 and 10 planes
+    for N, v in ((376, 13), (377, 12), (258, 15)):  # 94-plane tiles; last chunks of 94, 1 and 70 planes
         b.jacobi(N, 2, 120 + N)
         force.append(v)
     zipf = synth.csr_zipf(7, 12000, 1.6)

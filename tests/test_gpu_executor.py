@@ -216,14 +216,14 @@ def test_jacobi_tensor_copy_tiles():
 
 
 def test_jacobi_deep_tiles():
-    """From N ~ 200 up a Jacobi tile spans the deepest chunk, 62 planes, and
-    the last chunk takes what is left (N = 310: five full chunks; N = 311: a
-    last chunk of one plane; N = 257 / 258 / 300: 9 / 10 / 52): the
-    tensor-copy tiles on even and odd N, the plane ring (df 128x2), the
+    """From N ~ 250 up a Jacobi tile spans the deepest chunk, 94 planes, and
+    the last chunk takes what is left (N = 376: four full chunks; N = 377: a
+    last chunk of one plane; N = 311 / 258 / 257 / 300: 29 / 70 / 69 / 18):
+    the tensor-copy tiles on even and odd N, the plane ring (df 128x2), the
     shared-memory family and a call whose input lies outside the pair range."""
     b = Batch()
     force = []
-    for k, (N, sweeps, v, plant) in enumerate([(310, 2, 13, None), (311, 3, 13, None), (300, 2, 12, None),
+    for k, (N, sweeps, v, plant) in enumerate([(376, 2, 13, None), (377, 3, 12, None), (311, 3, 13, None),
                                                (258, 2, 15, None), (257, 2, 9, None), (300, 1, 5, None),
                                                (310, 3, 13, 1e40)]):
         b.jacobi(N, sweeps, 800 + k, plant)
