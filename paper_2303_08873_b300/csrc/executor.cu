@@ -426,7 +426,8 @@ __global__ void __launch_bounds__(T) exec_plan(const ar_exec_call* __restrict__ 
       }
     }
     usetma[c] = use;
-    s_cost[c] = st == AR_OK ? item_ns(k, v, jtarget) : 0.f;
+    // never NaN: the ranks below must be a permutation of the group
+    s_cost[c] = st == AR_OK ? fmaxf(item_ns(k, v, jtarget), 0.f) : 0.f;
     t0[c] = ~0ull;
     t1[c] = 0ull;
     status[c] = st;
